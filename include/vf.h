@@ -1,0 +1,238 @@
+/*
+ * vf.h -- C ABI of libvf: hierarchically compressed radiosity view-factor
+ * matrices on one GB300 (sm_103a).
+ *
+ * The library computes, for a triangle mesh, the view-factor matrix F of the
+ * discrete radiosity system B = E + diag(rho) F B (Section 1, Eq.
+ * radiosity-system), stores it compressed over a quadtree or octree of the
+ * facets (Sections 3.1, 4), and applies it to many right-hand sides inside
+ * the Jacobi solve (Sections 3, 5.1).  Every step runs in the library's own
+ * CUDA kernels; host code only marshals arguments, builds the index trees
+ * and schedules launches.
+ *
+ * Conventions
+ *  - Ownership: handles are created and freed by the library.  Caller buffers
+ *    (vertices, faces, X, Y, E, B, rho) are read or written during the call
+ *    and never kept or freed by it.
+ *  - Pointers: "host" arguments are ordinary CPU memory; "device" arguments
+ *    are CUDA device pointers on the handle's device (for example the data
+ *    pointer of a torch CUDA tensor).
+ *  - Layout: right-hand sides are column-major N x R with an explicit leading
+ *    dimension ld >= N, rows in the mesh's face order.
+ *  - Streams: device work is ordered on the caller's stream (NULL = the
+ *    legacy default stream).  Calls that return host data synchronise it.
+ *  - Errors: every call returns a vf_status; vf_last_error() gives the
+ *    calling thread's last message.  VF_E_NOCONV still writes the best
+ *    iterate.  Device-side waits are bounded and report VF_E_TIMEOUT.
+ *  - Threads: handles are immutable after creation and may be shared by
+ *    concurrent calls on different streams.
+ */
+#ifndef VF_H
+#define VF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vf_mesh vf_mesh;
+typedef struct vf_tree vf_tree;
+typedef struct vf_hmat vf_hmat;
+typedef struct vf_rank_predictor vf_rank_predictor;
+typedef struct CUstream_st* vf_stream; /* a cudaStream_t */
+
+typedef enum {
+    VF_OK = 0,
+    VF_E_INVAL = 1,   /* bad argument (size, pointer, option) */
+    VF_E_NOMEM = 2,   /* device or host allocation failed */
+    VF_E_CUDA = 3,    /* a CUDA runtime call failed */
+    VF_E_NOCONV = 4,  /* solve hit max_iter; outputs hold the last iterate */
+    VF_E_TIMEOUT = 5, /* a bounded device-side wait gave up */
+    VF_E_OOB = 6,     /* a device-side bounds check fired */
+    VF_E_IO = 7,      /* file could not be opened, read or written */
+    VF_E_CORRUPT = 8  /* file failed its magic/version/CRC checks */
+} vf_status;
+
+typedef enum { VF_PREC_FP32 = 0, VF_PREC_BF16 = 1, VF_PREC_FP8 = 2 } vf_precision;
+typedef enum { VF_TREE_QUAD = 0, VF_TREE_OCT = 1 } vf_tree_kind;
+typedef enum { VF_BLK_ZERO = 0, VF_BLK_DENSE = 1, VF_BLK_CSR = 2, VF_BLK_SVD = 3, VF_BLK_HIER = 4 } vf_block_kind;
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* vf_last_error(void);
+const char* vf_version(void);
+
+/* ------------------------------------------------------------------ mesh
+ * Section 3: A_i, x_i, n_i of each triangle (midpoint collocation).
+ * vf_mesh_create copies the host vertices (nv x 3, FP64) and faces (nf x 3,
+ * int32, counter-clockwise = outward normal by the right-hand rule) to the
+ * device and snaps the vertices to an integer grid: unit = 2^e with
+ * extent / 2^e <= 2^18 (extent = largest bounding-box side), so every
+ * visibility decision is made exactly in integers.  Geometry is computed on
+ * the device in FP64 from the snapped coordinates.
+ * Errors: VF_E_INVAL for nv < 3, nf < 1, a face index out of range or a
+ * zero-extent vertex set; VF_E_NOMEM, VF_E_CUDA. */
+typedef struct {
+    int32_t device; /* CUDA device ordinal */
+} vf_mesh_opts;
+
+vf_status vf_mesh_create(const double* verts, int64_t nv, const int32_t* faces, int64_t nf,
+                         const vf_mesh_opts* opts, vf_mesh** out);
+void vf_mesh_destroy(vf_mesh* m);
+int64_t vf_mesh_nfacets(const vf_mesh* m);
+/* grid unit and the integer grid origin (base * unit = world coordinates of grid 0) */
+vf_status vf_mesh_grid(const vf_mesh* m, double* unit, int64_t base[3]);
+/* Host outputs in face order: area[nf], centroid[nf*3] (relative to the grid
+ * origin), unit normal[nf*3]; any pointer may be NULL. */
+vf_status vf_mesh_geometry(const vf_mesh* m, double* area, double* centroid, double* normal);
+
+/* Section 3.2: V_ij = 1 iff n_i.d_ij > 0, n_j.d_ji > 0 (exact, integer) and
+ * the open segment (x_i, x_j) meets no other closed triangle (edge and
+ * vertex touches block; a coplanar segment is not blocked).  Rows `rows`
+ * (host, nrows facet indices; NULL = all facets) are written to V (host,
+ * nrows x nf bytes, row-major).  Computed by the library's BVH kernels. */
+vf_status vf_mesh_visibility(const vf_mesh* m, const int64_t* rows, int64_t nrows, uint8_t* V);
+
+/* Section 2, Eq. insolation-for-point-sun with the sun at 1 AU:
+ * E[i + r*lde] = solar_flux * max(0, n_i . s_r) * V_sun(i, s_r), where
+ * V_sun is 1 iff n_i . s_q > 0 and the ray from x_i along
+ * s_q = round(2^20 s_r) meets no other triangle.  sun_dirs: host, R x 3
+ * unit vectors.  E: device FP32, column-major, lde >= nf, face order. */
+vf_status vf_mesh_insolation(const vf_mesh* m, const double* sun_dirs, int32_t R, double solar_flux,
+                             float* E, int64_t lde, vf_stream stream);
+
+/* ------------------------------------------------------------- partition
+ * Algorithm 2 (quadtree on centroids, Section 4.1) and its octree analogue.
+ * Each node splits at the midpoint of its own centroids' bounding box
+ * (exact integer compare 2c >= lo + hi, ties go to the upper child); child
+ * index 2[x>=]+[y>=] (octree 4[x>=]+2[y>=]+[z>=]); empty children dropped;
+ * members keep their parent's order; nodes numbered in depth-first preorder.
+ * Stops at count <= leaf_size, depth == max_depth or a zero-extent box. */
+typedef struct {
+    int32_t kind;      /* vf_tree_kind */
+    int32_t leaf_size; /* default 64 */
+    int32_t max_depth; /* default 32 */
+} vf_partition_opts;
+
+vf_status vf_partition(const vf_mesh* m, const vf_partition_opts* opts, vf_tree** out);
+void vf_tree_destroy(vf_tree* t);
+int64_t vf_tree_nnodes(const vf_tree* t);
+/* perm[k] = face index at tree position k (host, nf entries). */
+vf_status vf_tree_perm(const vf_tree* t, int32_t* perm);
+/* Per node (host arrays of vf_tree_nnodes entries; any may be NULL). */
+vf_status vf_tree_nodes(const vf_tree* t, int32_t* first, int32_t* count, int32_t* depth,
+                        int32_t* parent);
+
+/* -------------------------------------------------------------- assembly
+ * Algorithms 1, 3 and 4 (Sections 3.3, 4.2, 4.3).  Visibility of every pair
+ * is computed once on the device as a bit matrix; entries
+ * F_ij = [n_i.(x_j-x_i)][n_j.(x_i-x_j)] V_ij A_j / (pi |x_i-x_j|^4) (Eq.
+ * FF-def) are evaluated on the fly.  Starting at the pairs of the root's
+ * children, each block pair is stored as the cheapest of: zero (no visible
+ * pair), dense (4mn bytes), CSR (8 nnz + 4(m+1)), the q-truncated SVD
+ * U'V'^T with q the smallest rank such that sigma_{q+1} < tol sigma_1 and
+ * U' = U_q Sigma_q, V' = V_q compacted to the block's nonzero rows m' and
+ * columns n' (4q(m'+n') + 4(m'+n')), or the hierarchical block over its
+ * child pairs; a leaf block (two tree leaves, or m n < leaf_threshold) is
+ * dense or CSR.  Ties: zero < dense < CSR < SVD < hierarchical.  A
+ * hierarchical block whose nonzero children are all CSR (all dense) is
+ * coalesced into one CSR (dense) block.  The SVD probe starts at rank k0
+ * and doubles up to k_max; a block needing more fails the probe.  Factors
+ * are verified by an FP64-accumulated check of ||F_IJ - U'V'^T||_2.
+ * Errors: VF_E_INVAL, VF_E_NOMEM, VF_E_CUDA. */
+typedef struct {
+    double tol;             /* compression tolerance, e.g. 1e-3 */
+    int64_t leaf_threshold; /* default 4096 */
+    int32_t k0;             /* initial probe rank, default 8 */
+    int32_t k_max;          /* largest probe rank, default 128 */
+    int32_t power_iters;    /* subspace iterations of the probe, default 2 */
+    int32_t verify;         /* 1: FP64 truncation check on accepted SVD blocks */
+    uint32_t precisions;    /* bit (1 << vf_precision): copies to build; FP32 always */
+    const vf_rank_predictor* predictor; /* NULL: plain probe path */
+    uint64_t seed;
+} vf_assemble_opts;
+
+typedef struct {
+    int64_t nblocks[5];     /* stored blocks per vf_block_kind (HIER counts inner nodes) */
+    int64_t bytes[5];       /* FP32 payload bytes per kind */
+    int64_t nnz_visible;    /* visible ordered pairs (nonzeros of F) */
+    int64_t probes;         /* SVD probes run (each k counts once) */
+    int64_t probes_failed;  /* probes that found no acceptable rank */
+    int64_t probes_skipped; /* blocks where the byte bound ruled the SVD out */
+    int64_t probes_predicted_skip; /* probes the predictor skipped */
+    int64_t verify_failed;  /* SVD blocks whose check failed (rank raised) */
+    int32_t max_rank;
+    double t_visibility, t_stats, t_probe, t_pack, t_total; /* seconds */
+} vf_assemble_stats;
+
+vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_assemble_opts* opts,
+                      vf_hmat** out, vf_assemble_stats* stats);
+void vf_hmat_destroy(vf_hmat* h);
+int64_t vf_hmat_nfacets(const vf_hmat* h);
+/* Stored blocks (host, nblocks rows of 7 int32: row node, col node, kind, q,
+ * m', n', reserved); call with desc = NULL to get the count. */
+vf_status vf_hmat_blocks(const vf_hmat* h, int64_t* nblocks, int32_t* desc);
+/* Total device payload bytes for one precision. */
+int64_t vf_hmat_bytes(const vf_hmat* h, vf_precision p);
+
+/* ---------------------------------------------------------------- apply
+ * Algorithm 5 (Section 4.4): Y = F_hat X for R columns.  X, Y: device FP32,
+ * column-major, face order (the tree permutation is applied inside).
+ * p selects the factor copy (FP32 master, BF16, or FP8 E4M3 with a scale
+ * per block); accumulation is FP32.  Errors: VF_E_INVAL (R < 1, ld < N,
+ * precision not built), VF_E_CUDA. */
+vf_status vf_apply(const vf_hmat* h, vf_precision p, const float* X, int64_t ldx, int32_t R, float* Y,
+                   int64_t ldy, vf_stream stream);
+
+/* ---------------------------------------------------------------- solve
+ * B = (I - diag(rho) F)^{-1} E by Jacobi (Sections 3, 5.1): B_0 = E,
+ * B_{k+1} = E + rho .* (F B_k); a column is done when
+ * ||B_{k+1} - B_k||_2 <= rtol ||E||_2; a zero column returns 0.  The sweep
+ * loop runs on the device inside one CUDA graph (conditional while node,
+ * bounded by max_iter).  With precision BF16/FP8 and refine = 1 the inner
+ * sweeps use the low-precision factors and an outer loop corrects with the
+ * residual r = E - B + rho .* F B computed from the FP32 factors with FP64
+ * accumulation.  clamp = 1 sets negative outputs to 0 (Section 4.2).
+ * rho: device FP32 [nf] in face order, or NULL for opts.rho.  E, B: device
+ * FP32 column-major, face order.  VF_E_NOCONV: B holds the last iterate. */
+typedef struct {
+    double rtol;        /* default 1e-6 */
+    int32_t max_iter;   /* per Jacobi loop, default 100 */
+    int32_t precision;  /* vf_precision of the sweeps */
+    int32_t refine;     /* 1: mixed-precision iterative refinement */
+    int32_t max_refine; /* default 8 */
+    double inner_rtol;  /* inner loop tolerance with refinement, default 1e-3 */
+    int32_t clamp;      /* 1: B = max(B, 0) at the end */
+    float rho;          /* uniform rho when the rho pointer is NULL */
+} vf_solve_opts;
+
+typedef struct {
+    int32_t sweeps;           /* low-precision (or FP32) sweeps */
+    int32_t refinements;      /* outer refinement steps */
+    int32_t converged;        /* 1 if every column met rtol */
+    double max_rel_residual;  /* max over columns of ||r||_2 / ||E||_2 */
+} vf_solve_stats;
+
+vf_status vf_solve(const vf_hmat* h, const float* rho, const float* E, int64_t lde, float* B, int64_t ldb,
+                   int32_t R, const vf_solve_opts* opts, vf_solve_stats* stats, vf_stream stream);
+
+/* Many meshes in one persistent launch per sweep (the batching workload):
+ * nmeshes problems, each with its own F, rho (device or NULL), E, B
+ * (device, column-major) and R; one shared work list over all meshes' row
+ * tiles.  stats: host array of nmeshes entries or NULL. */
+vf_status vf_solve_batched(const vf_hmat* const* F, int32_t nmeshes, const float* const* rho,
+                           const float* const* E, const int64_t* lde, float* const* B, const int64_t* ldb,
+                           const int32_t* R, const vf_solve_opts* opts, vf_solve_stats* stats,
+                           vf_stream stream);
+
+/* ------------------------------------------------------------ save/load
+ * Versioned binary file: header, block table and payload sections, each with
+ * a CRC32.  Load rejects a bad magic, version or CRC with VF_E_CORRUPT. */
+vf_status vf_hmat_save(const vf_hmat* h, const char* path);
+vf_status vf_hmat_load(const char* path, int32_t device, vf_hmat** out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VF_H */

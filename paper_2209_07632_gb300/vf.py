@@ -1,0 +1,379 @@
+"""Thin Python binding of libvf's C ABI (include/vf.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+Device buffers are torch CUDA tensors (float32, contiguous); an N x R
+column-major block with leading dimension N is a torch tensor of shape
+(R, N).  Importing this module loads the shared library and raises
+VFError if it has not been built -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libvf.so")
+
+VF_OK, VF_E_INVAL, VF_E_NOMEM, VF_E_CUDA, VF_E_NOCONV, VF_E_TIMEOUT, VF_E_OOB, VF_E_IO, VF_E_CORRUPT = range(9)
+PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
+KIND_NAMES = {0: "zero", 1: "dense", 2: "csr", 3: "svd", 4: "hier"}
+
+
+class VFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libvf status {status}: {msg}")
+        self.status = status
+
+
+# ------------------------------------------------------------------ structs
+class MeshOpts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32)]
+
+
+class PartitionOpts(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("leaf_size", ctypes.c_int32), ("max_depth", ctypes.c_int32)]
+
+
+class AssembleOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("leaf_threshold", ctypes.c_int64), ("k0", ctypes.c_int32),
+                ("k_max", ctypes.c_int32), ("power_iters", ctypes.c_int32), ("verify", ctypes.c_int32),
+                ("precisions", ctypes.c_uint32), ("predictor", ctypes.c_void_p), ("seed", ctypes.c_uint64)]
+
+
+class AssembleStats(ctypes.Structure):
+    _fields_ = [("nblocks", ctypes.c_int64 * 5), ("bytes", ctypes.c_int64 * 5), ("nnz_visible", ctypes.c_int64),
+                ("probes", ctypes.c_int64), ("probes_failed", ctypes.c_int64), ("probes_skipped", ctypes.c_int64),
+                ("probes_predicted_skip", ctypes.c_int64), ("verify_failed", ctypes.c_int64),
+                ("max_rank", ctypes.c_int32), ("t_visibility", ctypes.c_double), ("t_stats", ctypes.c_double),
+                ("t_probe", ctypes.c_double), ("t_pack", ctypes.c_double), ("t_total", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["nblocks"] = {KIND_NAMES[k]: int(self.nblocks[k]) for k in range(5)}
+        d["bytes"] = {KIND_NAMES[k]: int(self.bytes[k]) for k in range(5)}
+        return d
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("refine", ctypes.c_int32), ("max_refine", ctypes.c_int32), ("inner_rtol", ctypes.c_double),
+                ("clamp", ctypes.c_int32), ("rho", ctypes.c_float)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int32), ("refinements", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("max_rel_residual", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+# ------------------------------------------------------------------ loading
+_lib = None
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_SIGS = {
+    "vf_last_error": ([], ctypes.c_char_p),
+    "vf_version": ([], ctypes.c_char_p),
+    "vf_mesh_create": ([_P, _I64, _P, _I64, _P, _P], ctypes.c_int),
+    "vf_mesh_destroy": ([_P], None),
+    "vf_mesh_nfacets": ([_P], _I64),
+    "vf_mesh_grid": ([_P, _P, _P], ctypes.c_int),
+    "vf_mesh_geometry": ([_P, _P, _P, _P], ctypes.c_int),
+    "vf_mesh_visibility": ([_P, _P, _I64, _P], ctypes.c_int),
+    "vf_mesh_insolation": ([_P, _P, _I32, ctypes.c_double, _P, _I64, _P], ctypes.c_int),
+    "vf_partition": ([_P, _P, _P], ctypes.c_int),
+    "vf_tree_destroy": ([_P], None),
+    "vf_tree_nnodes": ([_P], _I64),
+    "vf_tree_perm": ([_P, _P], ctypes.c_int),
+    "vf_tree_nodes": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "vf_assemble": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "vf_hmat_destroy": ([_P], None),
+    "vf_hmat_nfacets": ([_P], _I64),
+    "vf_hmat_blocks": ([_P, _P, _P], ctypes.c_int),
+    "vf_hmat_bytes": ([_P, ctypes.c_int], _I64),
+    "vf_apply": ([_P, ctypes.c_int, _P, _I64, _I32, _P, _I64, _P], ctypes.c_int),
+    "vf_solve": ([_P, _P, _P, _I64, _P, _I64, _I32, _P, _P, _P], ctypes.c_int),
+    "vf_solve_batched": ([_P, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "vf_hmat_save": ([_P, ctypes.c_char_p], ctypes.c_int),
+    "vf_hmat_load": ([ctypes.c_char_p, _I32, _P], ctypes.c_int),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libvf; raise VFError (never fall back) if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise VFError(-1, f"libvf is not built ({path} missing); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def declared_symbols() -> list[str]:
+    return list(_SIGS)
+
+
+def _check(status: int, allow=()):
+    if status != VF_OK and status not in allow:
+        raise VFError(status, load().vf_last_error().decode(errors="replace"))
+    return status
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dev_ptr(t, name: str, n_rows: int | None = None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise VFError(VF_E_INVAL, f"{name}: need a contiguous float32 CUDA tensor")
+    if n_rows is not None and t.shape[-1] != n_rows:
+        raise VFError(VF_E_INVAL, f"{name}: last dimension {t.shape[-1]} != N = {n_rows}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------ handles
+class _Handle:
+    _destroy = ""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def close(self):
+        if self.ptr:
+            getattr(load(), self._destroy)(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh(_Handle):
+    _destroy = "vf_mesh_destroy"
+
+    @property
+    def n(self) -> int:
+        return int(load().vf_mesh_nfacets(self.ptr))
+
+
+class Tree(_Handle):
+    _destroy = "vf_tree_destroy"
+
+
+class HMat(_Handle):
+    _destroy = "vf_hmat_destroy"
+
+    @property
+    def n(self) -> int:
+        return int(load().vf_hmat_nfacets(self.ptr))
+
+
+# ------------------------------------------------------------------ API
+def vf_version() -> str:
+    return load().vf_version().decode()
+
+
+def vf_mesh_create(verts, faces, device: int = 0) -> Mesh:
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    f = np.ascontiguousarray(faces, dtype=np.int32)
+    out = ctypes.c_void_p()
+    opts = MeshOpts(device)
+    _check(load().vf_mesh_create(_np_ptr(v), v.shape[0], _np_ptr(f), f.shape[0], ctypes.byref(opts),
+                                 ctypes.byref(out)))
+    return Mesh(out)
+
+
+def vf_mesh_grid(m: Mesh):
+    unit = ctypes.c_double()
+    base = np.zeros(3, dtype=np.int64)
+    _check(load().vf_mesh_grid(m.ptr, ctypes.byref(unit), _np_ptr(base)))
+    return unit.value, base
+
+
+def vf_mesh_geometry(m: Mesh):
+    n = m.n
+    area = np.empty(n)
+    cent = np.empty((n, 3))
+    nrm = np.empty((n, 3))
+    _check(load().vf_mesh_geometry(m.ptr, _np_ptr(area), _np_ptr(cent), _np_ptr(nrm)))
+    return area, cent, nrm
+
+
+def vf_mesh_visibility(m: Mesh, rows=None) -> np.ndarray:
+    n = m.n
+    if rows is None:
+        V = np.empty((n, n), dtype=np.uint8)
+        _check(load().vf_mesh_visibility(m.ptr, None, n, _np_ptr(V)))
+        return V
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    V = np.empty((r.size, n), dtype=np.uint8)
+    _check(load().vf_mesh_visibility(m.ptr, _np_ptr(r), r.size, _np_ptr(V)))
+    return V
+
+
+def vf_mesh_insolation(m: Mesh, sun_dirs, solar_flux: float, E, stream=None):
+    d = np.ascontiguousarray(np.atleast_2d(sun_dirs), dtype=np.float64)
+    R = d.shape[0]
+    n = m.n
+    if E.shape != (R, n):
+        raise VFError(VF_E_INVAL, f"E must have shape (R, N) = {(R, n)}")
+    _check(load().vf_mesh_insolation(m.ptr, _np_ptr(d), R, float(solar_flux), _dev_ptr(E, "E", n), n,
+                                     _stream(stream)))
+    return E
+
+
+def vf_partition(m: Mesh, kind: str = "quad", leaf_size: int = 64, max_depth: int = 32) -> Tree:
+    opts = PartitionOpts(0 if kind == "quad" else 1, leaf_size, max_depth)
+    out = ctypes.c_void_p()
+    _check(load().vf_partition(m.ptr, ctypes.byref(opts), ctypes.byref(out)))
+    t = Tree(out)
+    t.n = m.n
+    return t
+
+
+def vf_tree_perm(t: Tree) -> np.ndarray:
+    perm = np.empty(t.n, dtype=np.int32)
+    _check(load().vf_tree_perm(t.ptr, _np_ptr(perm)))
+    return perm
+
+
+def vf_tree_nodes(t: Tree) -> dict:
+    k = int(load().vf_tree_nnodes(t.ptr))
+    arrs = {name: np.empty(k, dtype=np.int32) for name in ("first", "count", "depth", "parent")}
+    _check(load().vf_tree_nodes(t.ptr, *(_np_ptr(arrs[n]) for n in ("first", "count", "depth", "parent"))))
+    return arrs
+
+
+def vf_assemble(m: Mesh, t: Tree, tol: float = 1e-3, leaf_threshold: int = 4096, k0: int = 8, k_max: int = 128,
+                power_iters: int = 2, verify: bool = False, precisions=("fp32", "bf16"), predictor=None,
+                seed: int = 12345):
+    bits = 0
+    for p in precisions:
+        bits |= 1 << PREC[p]
+    opts = AssembleOpts(tol, leaf_threshold, k0, k_max, power_iters, int(verify), bits,
+                        predictor.ptr if predictor is not None else None, seed)
+    st = AssembleStats()
+    out = ctypes.c_void_p()
+    _check(load().vf_assemble(m.ptr, t.ptr, ctypes.byref(opts), ctypes.byref(out), ctypes.byref(st)))
+    return HMat(out), st.as_dict()
+
+
+def vf_hmat_blocks(h: HMat) -> np.ndarray:
+    """Stored blocks: rows of (row node, col node, kind, q, m', n', 0)."""
+    nb = ctypes.c_int64()
+    _check(load().vf_hmat_blocks(h.ptr, ctypes.byref(nb), None))
+    desc = np.empty((nb.value, 7), dtype=np.int32)
+    _check(load().vf_hmat_blocks(h.ptr, ctypes.byref(nb), _np_ptr(desc)))
+    return desc
+
+
+def vf_hmat_bytes(h: HMat, precision: str = "fp32") -> int:
+    return int(load().vf_hmat_bytes(h.ptr, PREC[precision]))
+
+
+def vf_apply(h: HMat, X, Y, precision: str = "fp32", stream=None):
+    n = h.n
+    R = 1 if X.dim() == 1 else X.shape[0]
+    if Y.shape != X.shape:
+        raise VFError(VF_E_INVAL, "X and Y shapes differ")
+    _check(load().vf_apply(h.ptr, PREC[precision], _dev_ptr(X, "X", n), n, R, _dev_ptr(Y, "Y", n), n,
+                           _stream(stream)))
+    return Y
+
+
+def _solve_opts(rtol, max_iter, precision, refine, max_refine, inner_rtol, clamp, rho_uniform):
+    return SolveOpts(rtol, max_iter, PREC[precision], int(refine), max_refine, inner_rtol, int(clamp),
+                     float(rho_uniform))
+
+
+def vf_solve(h: HMat, E, B, rho=0.12, rtol: float = 1e-6, max_iter: int = 100, precision: str = "fp32",
+             refine: bool = False, max_refine: int = 8, inner_rtol: float = 1e-3, clamp: bool = False,
+             stream=None) -> dict:
+    """B = (I - diag(rho) F)^{-1} E.  rho: a float (uniform) or a CUDA
+    tensor of N values.  Returns the solve statistics; raises on errors
+    other than non-convergence (reported as stats['converged'] == 0)."""
+    n = h.n
+    R = 1 if E.dim() == 1 else E.shape[0]
+    rho_ptr = None
+    rho_u = 0.0
+    if isinstance(rho, (int, float)):
+        rho_u = float(rho)
+    else:
+        rho_ptr = _dev_ptr(rho, "rho", n)
+    opts = _solve_opts(rtol, max_iter, precision, refine, max_refine, inner_rtol, clamp, rho_u)
+    st = SolveStats()
+    _check(load().vf_solve(h.ptr, rho_ptr, _dev_ptr(E, "E", n), n, _dev_ptr(B, "B", n), n, R, ctypes.byref(opts),
+                           ctypes.byref(st), _stream(stream)), allow=(VF_E_NOCONV,))
+    return st.as_dict()
+
+
+def vf_solve_batched(hs, Es, Bs, rho=0.12, rtol: float = 1e-6, max_iter: int = 100, precision: str = "fp32",
+                     refine: bool = False, max_refine: int = 8, inner_rtol: float = 1e-3, clamp: bool = False,
+                     stream=None) -> list:
+    k = len(hs)
+    P = ctypes.c_void_p * k
+    F = P(*[h.ptr for h in hs])
+    E = P(*[_dev_ptr(e, "E", h.n).value for e, h in zip(Es, hs)])
+    B = P(*[_dev_ptr(b, "B", h.n).value for b, h in zip(Bs, hs)])
+    lde = (ctypes.c_int64 * k)(*[h.n for h in hs])
+    R = (ctypes.c_int32 * k)(*[1 if e.dim() == 1 else e.shape[0] for e in Es])
+    opts = _solve_opts(rtol, max_iter, precision, refine, max_refine, inner_rtol, clamp,
+                       rho if isinstance(rho, (int, float)) else 0.0)
+    rho_arr = None
+    if not isinstance(rho, (int, float)):
+        rho_arr = P(*[_dev_ptr(r, "rho", h.n).value for r, h in zip(rho, hs)])
+    st = (SolveStats * k)()
+    _check(load().vf_solve_batched(F, k, rho_arr, E, lde, B, lde, R, ctypes.byref(opts), st, _stream(stream)),
+           allow=(VF_E_NOCONV,))
+    return [s.as_dict() for s in st]
+
+
+def vf_hmat_save(h: HMat, path: str):
+    _check(load().vf_hmat_save(h.ptr, path.encode()))
+
+
+def vf_hmat_load(path: str, device: int = 0) -> HMat:
+    out = ctypes.c_void_p()
+    _check(load().vf_hmat_load(path.encode(), device, ctypes.byref(out)))
+    return HMat(out)
+
+
+@dataclass
+class Problem:
+    """A mesh with its tree and compressed matrix, kept alive together."""
+    mesh: Mesh
+    tree: Tree
+    hmat: HMat
+    stats: dict
+
+
+def build_problem(verts, faces, kind: str = "quad", leaf_size: int = 64, tol: float = 1e-3, device: int = 0,
+                  **assemble_kw) -> Problem:
+    m = vf_mesh_create(verts, faces, device)
+    t = vf_partition(m, kind, leaf_size)
+    h, st = vf_assemble(m, t, tol=tol, **assemble_kw)
+    return Problem(m, t, h, st)
