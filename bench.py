@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark: radiosity RHS/s of the compressed F.X Jacobi solve.
+
+Workload (the terrain configuration the metric is quoted on): a 200 x 200
+seeded fBm DEM (Hurst 0.8, RMS slope 15 deg, 10 m spacing) with an embedded
+1 km spherical-cap crater -> 79,202 triangles; quadtree with 64-facet
+leaves; F compressed at tol 1e-3 in FP32; E = direct solar flux for sun
+positions at 10 deg elevation (azimuth sweep); albedo 0.12; Jacobi to
+rtol 1e-6.  One step = one vf_solve of R right-hand sides (default R = 1,
+the single-RHS configuration): permute in, the device-side Jacobi loop
+(phase-1/phase-2 multiply with the fused update), permute out.
+
+Reported beside the headline: the same solve with the uncompressed dense
+FP32 F (25 GB) on the same GPU, the roofline of the multiply kernel pair
+(algorithmic bytes / CUDA-event time vs the measured HBM copy bandwidth),
+an end-to-end number through vf_solve_host (host buffers, copies in the
+timed region), SM clocks sampled during the timed region, and the CPU
+oracle timed on a bounded sample of rows.
+
+--impl reference times the CPU oracle (plain FP64 dense F, numpy) on the
+host cores instead, on a bounded row sample, as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "radiosity RHS/s of compressed F·X solve vs dense & plain FP32, at rel err 1e-3"
+WORKLOAD = "fbm200_crater_79202tri_quadtree64_tol1e-3"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--rhs", type=int, default=1)
+    p.add_argument("--dem-size", type=int, default=200, help="DEM side (200 -> 79,202 facets); smaller for profiling")
+    p.add_argument("--tol", type=float, default=1e-3)
+    p.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"])
+    p.add_argument("--no-dense", action="store_true", help="skip the dense-F comparison")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--cpu-rows", type=int, default=128, help="rows of F in the CPU oracle sample")
+    return p.parse_args()
+
+
+def workload_inputs(R: int, side: int = 200):
+    import synth
+    v, f = synth.fbm_dem_mesh(n=side, spacing=10.0, hurst=0.8, seed=1, rms_slope_deg=15.0, crater_diameter=1000.0)
+    dirs = synth.sun_directions(R, 10.0)
+    return v, f, dirs
+
+
+# ------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle
+class CpuOracle:
+    """The oracle's dense FP64 multiply (the work of one Jacobi sweep) on a
+    bounded, seeded sample of rows of F, extrapolated to the full solve:
+    t_solve = sweeps * (N / rows) * t_rows.  Building the sampled rows
+    (visibility by the oracle's BVH, then Eq. FF-def) is setup, untimed."""
+
+    def __init__(self, v, f, dirs, rows: int, R: int):
+        import numpy as np
+
+        import oracle
+        self.om = oracle.mesh(v, f)
+        rng = np.random.default_rng(7)
+        self.rows = rows
+        self.S = np.sort(rng.choice(self.om.n, size=rows, replace=False))
+        self.Fs = oracle.F_rows(self.om, self.S)
+        self.E = oracle.insolation(self.om, dirs[:R], 1365.0)
+        self.R = R
+
+    def measure(self, sweeps: int, seconds: float):
+        reps = 0
+        t0 = time.perf_counter()
+        while True:
+            _ = self.Fs @ self.E
+            reps += 1
+            if time.perf_counter() - t0 >= seconds:
+                break
+        t_rows = (time.perf_counter() - t0) / reps
+        t_solve = sweeps * (self.om.n / self.rows) * t_rows
+        try:
+            import threadpoolctl
+            cores = max(int(i.get("num_threads", 1)) for i in threadpoolctl.threadpool_info())
+        except Exception:
+            cores = os.cpu_count()
+        return {"value": self.R / t_solve, "unit": "RHS/s", "cores": cores, "kind": "oracle",
+                "sample": f"dense FP64 F, {self.rows} of {self.om.n} rows (seeded), y = F_S E timed over "
+                          f"{reps} repeats ({reps * t_rows:.1f} s), extrapolated x{self.om.n / self.rows:.0f} "
+                          f"rows x {sweeps} sweeps"}
+
+
+# ------------------------------------------------------------- main
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        v, f, dirs = workload_inputs(max(a.rhs, 1), a.dem_size)
+        # the oracle's Jacobi takes the sweeps the GPU solve takes on this workload (4 at rtol 1e-6)
+        sweeps = 4
+        co = CpuOracle(v, f, dirs, a.cpu_rows, a.rhs)
+        samples = [co.measure(sweeps, seconds=1.0) for _ in range(a.warmup + a.steps)]
+        val = sorted(s["value"] for s in samples[a.warmup:])[len(samples[a.warmup:]) // 2]
+        cb = dict(samples[-1])
+        cb["value"] = val
+        line = {"metric": METRIC, "value": val, "unit": "RHS/s", "n_gpus": a.gpus, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": 1000.0 * a.rhs / val, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "rhs": a.rhs, "tol": a.tol},
+                "impl": "reference", "cpu_baseline": cb,
+                "e2e": {"value": val, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import numpy as np
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2209_07632_gb300 import vf
+
+    R = a.rhs
+    v, f, dirs = workload_inputs(R, a.dem_size)
+    t0 = time.time()
+    prob = vf.build_problem(v, f, kind="quad", leaf_size=64, tol=a.tol, device=dev,
+                            precisions=("fp32", "bf16", "fp8"))
+    t_setup = time.time() - t0
+    n = prob.mesh.n
+    E = torch.empty((R, n), device="cuda", dtype=torch.float32)
+    vf.vf_mesh_insolation(prob.mesh, dirs, 1365.0, E)
+    B = torch.empty_like(E)
+    st = torch.cuda.current_stream()
+    rho = 0.12
+    rtol = 1e-6
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    solve_kw = dict(rho=rho, rtol=rtol, precision=a.precision, refine=a.precision != "fp32")
+    for _ in range(max(a.warmup, 3)):
+        stats = vf.vf_solve(prob.hmat, E, B, **solve_kw)
+    sweeps = stats["sweeps"]
+    barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(st)
+    for _ in range(a.steps):
+        stats = vf.vf_solve(prob.hmat, E, B, **solve_kw)
+    ev1.record(st)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / a.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * R / (ms / 1000.0)
+
+    # ---- roofline of the multiply (phase 1 + phase 2), tree order, on `st`
+    Xt = E.clone()
+    Yt = torch.empty_like(Xt)
+    for _ in range(5):
+        vf.vf_apply_tree(prob.hmat, Xt, Yt, precision=a.precision)
+    torch.cuda.synchronize()
+    reps = 50
+    k0 = torch.cuda.Event(enable_timing=True)
+    k1 = torch.cuda.Event(enable_timing=True)
+    k0.record(st)
+    for _ in range(reps):
+        vf.vf_apply_tree(prob.hmat, Xt, Yt, precision=a.precision)
+    k1.record(st)
+    torch.cuda.synchronize()
+    mult_ms = k0.elapsed_time(k1) / reps
+    alg_bytes = vf.vf_hmat_bytes(prob.hmat, a.precision) + n * R * 8
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = alg_bytes / (mult_ms / 1000.0) / 1e9
+    traffic = None
+    try:
+        prof = json.load(open(os.path.join(ROOT, "profiles", "multiply_traffic.json")))
+        if prof.get("workload") == WORKLOAD and prof.get("rhs") == R and prof.get("precision") == a.precision:
+            traffic = prof.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": "k_phase1 + k_phase2 (one multiply)", "alg_bytes_per_launch": alg_bytes,
+                "ms_per_launch": round(mult_ms, 4),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if peaks else "fallback 6.8 TB/s"}
+
+    # ---- end to end through vf_solve_host (pinned host buffers, copies timed)
+    Eh = E.cpu().pin_memory().numpy()
+    Bh = torch.empty((R, n), dtype=torch.float32).pin_memory().numpy()
+    for _ in range(2):
+        vf.vf_solve_host(prob.hmat, Eh, Bh, **solve_kw)
+    barrier()
+    e0 = time.perf_counter()
+    for _ in range(a.steps):
+        vf.vf_solve_host(prob.hmat, Eh, Bh, **solve_kw)
+    barrier()
+    e2e_s = (time.perf_counter() - e0) / a.steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * R / e2e_s, "unit": "RHS/s", "h2d_bytes_per_step": n * R * 4,
+           "d2h_bytes_per_step": n * R * 4}
+
+    # ---- the uncompressed dense FP32 F on the same GPU
+    dense = None
+    if not a.no_dense and rank == 0:
+        hd, _ = vf.vf_assemble(prob.mesh, prob.tree, storage="dense", precisions=("fp32",))
+        Bd = torch.empty_like(E)
+        for _ in range(2):
+            vf.vf_solve(hd, E, Bd, rho=rho, rtol=rtol)
+        torch.cuda.synchronize()
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        dsteps = max(3, a.steps // 4)
+        d0.record(st)
+        for _ in range(dsteps):
+            sd = vf.vf_solve(hd, E, Bd, rho=rho, rtol=rtol)
+        d1.record(st)
+        torch.cuda.synchronize()
+        dms = d0.elapsed_time(d1) / dsteps
+        rel = float(((B - Bd).norm() / Bd.norm()).item())
+        dense = {"value": R / (dms / 1000.0), "unit": "RHS/s", "ms_per_step": round(dms, 3),
+                 "bytes": vf.vf_hmat_bytes(hd, "fp32"), "sweeps": sd["sweeps"],
+                 "compressed_vs_dense_rel_err": rel, "speedup_compressed": round(value / world / (R / (dms / 1e3)), 2)}
+        del hd
+
+    cpu = None
+    if not a.no_cpu and rank == 0 and world == 1:
+        cpu = CpuOracle(v, f, dirs, a.cpu_rows, R).measure(sweeps, seconds=10.0)
+
+    launches = 5 + sweeps * (3 if vf.vf_hmat_blocks(prob.hmat)[:, 2].tolist().count(3) else 2)
+    line = {"metric": METRIC, "value": round(value, 3), "unit": "RHS/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "fp8e4m3"}[a.precision],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD if a.dem_size == 200 else f"fbm{a.dem_size}_crater_{n}tri", "facets": n, "rhs_per_gpu": R, "tol": a.tol, "rho": rho, "rtol": rtol,
+                       "sweeps": sweeps, "l2": "inputs larger than L2 (compressed F %.0f MB)" %
+                       (vf.vf_hmat_bytes(prob.hmat, a.precision) / 1e6),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "setup_s": round(t_setup, 2)},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches * a.steps, "clocks": clk,
+            "dense_fp32": dense, "cpu_baseline": cpu,
+            "assembly": {k: prob.stats[k] for k in ("nblocks", "bytes", "probes", "max_rank", "t_visibility",
+                                                    "t_probe", "t_total")}}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

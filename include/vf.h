@@ -151,6 +151,9 @@ typedef struct {
     uint32_t precisions;    /* bit (1 << vf_precision): copies to build; FP32 always */
     const vf_rank_predictor* predictor; /* NULL: plain probe path */
     uint64_t seed;
+    int32_t storage;        /* 0: compressed (Algorithm 4); 1: every leaf pair dense,
+                               i.e. the uncompressed F (the comparison of the
+                               terrain workload); 2: every leaf pair CSR (Algorithm 1) */
 } vf_assemble_opts;
 
 typedef struct {
@@ -185,6 +188,11 @@ int64_t vf_hmat_bytes(const vf_hmat* h, vf_precision p);
 vf_status vf_apply(const vf_hmat* h, vf_precision p, const float* X, int64_t ldx, int32_t R, float* Y,
                    int64_t ldy, vf_stream stream);
 
+/* Y_t = F_hat X_t with X_t, Y_t already in tree order (row k of X_t is
+ * facet perm[k]): the multiply alone, without the two permutations of
+ * vf_apply.  Device FP32, column-major, leading dimension N. */
+vf_status vf_apply_tree(const vf_hmat* h, vf_precision p, const float* Xt, int32_t R, float* Yt, vf_stream stream);
+
 /* ---------------------------------------------------------------- solve
  * B = (I - diag(rho) F)^{-1} E by Jacobi (Sections 3, 5.1): B_0 = E,
  * B_{k+1} = E + rho .* (F B_k); a column is done when
@@ -216,6 +224,13 @@ typedef struct {
 
 vf_status vf_solve(const vf_hmat* h, const float* rho, const float* E, int64_t lde, float* B, int64_t ldb,
                    int32_t R, const vf_solve_opts* opts, vf_solve_stats* stats, vf_stream stream);
+
+/* vf_solve with HOST buffers: E (nf x R, column-major, lde), rho (nf or
+ * NULL) and B are ordinary (preferably pinned) CPU memory; the host-to-device
+ * copy of E and rho, the solve and the device-to-host copy of B all run in
+ * the call, which returns once B is on the host. */
+vf_status vf_solve_host(const vf_hmat* h, const float* rho, const float* E, int64_t lde, float* B, int64_t ldb,
+                        int32_t R, const vf_solve_opts* opts, vf_solve_stats* stats, vf_stream stream);
 
 /* Many meshes in one persistent launch per sweep (the batching workload):
  * nmeshes problems, each with its own F, rho (device or NULL), E, B

@@ -28,8 +28,7 @@ namespace vf {
 
 constexpr int kTileRows = 64;
 constexpr int kWarps = 8;
-constexpr int kRowsPerWarp = kTileRows / kWarps;
-constexpr int kChunkRows = 512;  // V' rows per phase-1 chunk
+constexpr int kChunkElems = 8192;  // V' values per phase-1 chunk (one warp)
 
 // ------------------------------------------------------------ value loads
 template <class T> __device__ __forceinline__ float ld(const T* p);
@@ -52,246 +51,315 @@ struct ApplyArgs {
     const int32_t* tile_item_ptr;
     const TileItem* items;
     const SvdChunk* chunks;
+    const int32_t* tile_order;
+    int64_t nparts;            // phase-1 partial slots per panel
     int64_t n;                 // facets
     int64_t nT;                // T slots per RHS column
     int R;                     // total RHS columns
 };
 
+// Both phases stream their data as flat, contiguous element ranges: the
+// lanes of a warp load consecutive values (fully coalesced), multiply by the
+// matching x (or T) entries, stage the products in a per-warp scratch of
+// 512 / RB elements, then sum whole rows (phase 2) or whole columns (phase 1)
+// out of the scratch in a fixed order.  Every sum therefore has one owner
+// and one order: results are bit-reproducible with no float atomics.
+// per-warp scratch: 512 products for all RHS panel widths
+template <int RB> struct Chunk {
+    static constexpr int p2 = 512 / RB;                 // phase 2 elements per pass
+    static constexpr int p1 = (512 / RB) < 128 ? 128 : 512 / RB;  // phase 1 (holds a whole V' row)
+};
+
+// row index of element e in rows of width w: (e + 0.5) / w is at least
+// 0.5 / w away from an integer and its FP32 error is below e / w * 2^-23,
+// so the truncation is exact for e < 2^22
+__device__ __forceinline__ int row_of(int e, float invw) { return (int)(((float)e + 0.5f) * invw); }
+
 // ------------------------------------------------------------ phase 1
-// Input X: tree order, column-major with leading dimension n, columns
-// [c0, c0 + RB) of the panel.  T: per panel, RB x nT (column c at c * nT).
-// `part` holds RB x 128 partial sums per (panel, chunk) for blocks split
-// into several chunks; `counters` (per panel and SVD slot) elects the last
-// chunk to finish, which adds the partials in chunk order.
+// T_b = V'_b^T X[cols_b] for one chunk of V' rows (one warp).  Input X: tree
+// order, column-major with leading dimension n, columns [p0, p0 + RB) of
+// the panel.  T: per panel RB x nT (column c at c * nT).  A block split into
+// several chunks writes chunk partials; the last chunk to finish (atomic
+// ticket) adds them in chunk order.
 template <class T, int RB>
-__device__ __forceinline__ void phase1_body(const ApplyArgs& a, const T* __restrict__ val, const float* X,
+__device__ __forceinline__ void phase1_warp(const ApplyArgs& a, const T* __restrict__ val, const float* X,
                                             float* __restrict__ Tbuf, float* __restrict__ part,
-                                            int* __restrict__ counters, int ci, int panel, int nchunks_total) {
-    __shared__ float red[kWarps][RB][128];
-    __shared__ int s_last;
+                                            int* __restrict__ counters, int ci, int panel, float* scr) {
+    const int lane = threadIdx.x & 31;
     const SvdChunk ch = a.chunks[ci];
     const HBlock b = a.blocks[ch.blk];
-    const int c0 = panel * RB;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q = b.q;
+    const int p0 = panel * RB;
     const T* Vp = val + b.off_val + (int64_t)b.m1 * q;
     const int32_t* cols = a.aux + b.off_aux + b.m1;
     const float sc = a.scale ? a.scale[ch.blk] : 1.f;
-    float acc[4][RB];
+    constexpr int kC = Chunk<RB>::p1;
+    const int rows_per = kC / q;  // q <= 128 <= kC
+    const float invq = 1.f / (float)q;
+    float tk[4][RB];
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
+    for (int t = 0; t < 4; ++t)
 #pragma unroll
-        for (int c = 0; c < RB; ++c) acc[s][c] = 0.f;
-    for (int j = ch.k0 + warp; j < ch.k1; j += kWarps) {
-        int col = cols[j];
-        float x[RB];
+        for (int c = 0; c < RB; ++c) tk[t][c] = 0.f;
+    for (int j0 = ch.j0; j0 < ch.j1; j0 += rows_per) {
+        const int nr = min(rows_per, ch.j1 - j0);
+        const int L = nr * q;
+        const T* src = Vp + (int64_t)j0 * q;
+        float v[kC / 32];
+        int jl[kC / 32];
 #pragma unroll
-        for (int c = 0; c < RB; ++c) x[c] = (c0 + c < a.R) ? __ldg(X + (int64_t)(c0 + c) * a.n + col) : 0.f;
+        for (int i = 0; i < kC / 32; ++i) {
+            int e = lane + 32 * i;
+            v[i] = e < L ? ld(src + e) : 0.f;
+            jl[i] = e < L ? row_of(e, invq) : 0;
+        }
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            int k = lane + 32 * s;
-            if (k < q) {
-                float v = ld(Vp + (int64_t)j * q + k) * sc;
+        for (int i = 0; i < kC / 32; ++i) {
+            int e = lane + 32 * i;
+            if (e < L) {
+                int col = __ldg(cols + j0 + jl[i]);
 #pragma unroll
-                for (int c = 0; c < RB; ++c) acc[s][c] = fmaf(v, x[c], acc[s][c]);
+                for (int c = 0; c < RB; ++c) {
+                    float x = (p0 + c < a.R) ? __ldg(X + (int64_t)(p0 + c) * a.n + col) : 0.f;
+                    scr[c * kC + e] = v[i] * x;
+                }
             }
         }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            int k = lane + 32 * t;
+            if (k < q)
+                for (int r = 0; r < nr; ++r)
+#pragma unroll
+                    for (int c = 0; c < RB; ++c) tk[t][c] += scr[c * kC + r * q + k];
+        }
+        __syncwarp();
     }
-    __syncthreads();  // red[] may still be read by a previous work item of this CTA
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-#pragma unroll
-        for (int c = 0; c < RB; ++c) red[warp][c][lane + 32 * s] = acc[s][c];
-    __syncthreads();
     const int64_t panel_T = (int64_t)panel * RB * a.nT;
-    float* mypart = part + ((int64_t)panel * nchunks_total + ci) * (RB * 128);
-    for (int e = threadIdx.x; e < RB * q; e += blockDim.x) {
-        int c = e / q, k = e - c * q;
-        float s = 0.f;
+    if (ch.nchunks == 1) {
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) s += red[w][c][k];
-        if (ch.nchunks == 1) Tbuf[panel_T + (int64_t)c * a.nT + b.off_T + k] = s;
-        else mypart[c * 128 + k] = s;
+        for (int t = 0; t < 4; ++t) {
+            int k = lane + 32 * t;
+            if (k < q)
+#pragma unroll
+                for (int c = 0; c < RB; ++c) Tbuf[panel_T + (int64_t)c * a.nT + b.off_T + k] = tk[t][c] * sc;
+        }
+        return;
     }
-    if (ch.nchunks == 1) return;
+    float* mypart = part + ((int64_t)panel * a.nparts + ch.first + ch.chunk) * (RB * 128);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        int k = lane + 32 * t;
+        if (k < q)
+#pragma unroll
+            for (int c = 0; c < RB; ++c) mypart[c * 128 + k] = tk[t][c];
+    }
     __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int prev = atomicAdd(counters + (int64_t)panel * a.nT + b.off_T, 1);
-        s_last = (prev == ch.nchunks - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) last = atomicAdd(counters + (int64_t)panel * a.nT + b.off_T, 1) == ch.nchunks - 1;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
     __threadfence();
-    const int first = ch.first_chunk_global;
-    for (int e = threadIdx.x; e < RB * q; e += blockDim.x) {
-        int c = e / q, k = e - c * q;
-        float s = 0.f;
-        for (int cc = 0; cc < ch.nchunks; ++cc)
-            s += __ldcg(part + ((int64_t)panel * nchunks_total + first + cc) * (RB * 128) + c * 128 + k);
-        Tbuf[panel_T + (int64_t)c * a.nT + b.off_T + k] = s;
+    const float* pb = part + ((int64_t)panel * a.nparts + ch.first) * (RB * 128);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        int k = lane + 32 * t;
+        if (k < q)
+#pragma unroll
+            for (int c = 0; c < RB; ++c) {
+                float s = 0.f;
+                for (int cc = 0; cc < ch.nchunks; ++cc) s += __ldcg(pb + (int64_t)cc * (RB * 128) + c * 128 + k);
+                Tbuf[panel_T + (int64_t)c * a.nT + b.off_T + k] = s * sc;
+            }
     }
-    if (threadIdx.x == 0) counters[(int64_t)panel * a.nT + b.off_T] = 0;
+    if (lane == 0) counters[(int64_t)panel * a.nT + b.off_T] = 0;
 }
 
 template <class T, int RB>
-__global__ void __launch_bounds__(256) k_phase1(ApplyArgs a, const T* __restrict__ val, const float* const* xsel,
-                                                float* __restrict__ Tbuf, float* __restrict__ part,
-                                                int* __restrict__ counters) {
-    phase1_body<T, RB>(a, val, *xsel, Tbuf, part, counters, blockIdx.x, blockIdx.y, gridDim.x);
+__global__ void __launch_bounds__(256, RB <= 2 ? 4 : 2) k_phase1(ApplyArgs a, const T* __restrict__ val,
+                                                                const float* const* xsel, const float* xd,
+                                                                float* __restrict__ Tbuf, float* __restrict__ part,
+                                                                int* __restrict__ counters, int nchunks) {
+    __shared__ float scr[kWarps][RB * Chunk<RB>::p1];
+    const int warp = threadIdx.x >> 5;
+    const int ci = blockIdx.x * kWarps + warp;
+    if (ci >= nchunks) return;
+    phase1_warp<T, RB>(a, val, xsel ? *xsel : xd, Tbuf, part, counters, ci, blockIdx.y, scr[warp]);
 }
 
 // ------------------------------------------------------------ phase 2
 enum { MODE_APPLY = 0, MODE_JACOBI = 1, MODE_RESID = 2 };
 
 struct SweepIO {
-    const float* const* xsel;  // indirect: the current input (B_k), tree order
-    float* const* ysel;        // indirect: the output buffer
+    const float* const* xsel;  // indirect: the current input (B_k), tree order (or NULL)
+    float* const* ysel;        // indirect: the output buffer (or NULL)
+    const float* xd;           // direct input when xsel is NULL
+    float* yd;                 // direct output when ysel is NULL
     const float* E;            // tree order, n x R
     const float* rho;          // tree order, n
     double* colpart;           // per (tile, column): sum of squares
     int64_t ntiles;
 };
 
-template <class T, int RB, int MODE>
-__device__ __forceinline__ void phase2_body(const ApplyArgs& a, const T* __restrict__ val,
-                                            const float* __restrict__ Tbuf, const SweepIO& io, int tile, int panel) {
-    using acc_t = typename std::conditional<MODE == MODE_RESID, double, float>::type;
-    const int c0 = panel * RB;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tf = a.tile_first[tile], tc = a.tile_count[tile];
-    const float* X = *io.xsel;
-    const float* Tp = Tbuf + (int64_t)panel * RB * a.nT;
-    acc_t acc[kRowsPerWarp][RB];
+// One tile item, processed by one warp into the warp's row accumulators.
+template <class T, int RB, class acc_t>
+__device__ __forceinline__ void item_warp(const ApplyArgs& a, const T* __restrict__ val, const float* X,
+                                          const float* Tp, const TileItem& it, int tf, float* scr, acc_t* acc) {
+    const int lane = threadIdx.x & 31;
+    const float sc = a.scale ? a.scale[it.blk] : 1.f;
+    const int p0 = blockIdx.y * RB;
+    int L, base = 0;
+    const T* src;
+    const int32_t* cj = nullptr;
+    if (it.kind == VF_BLK_CSR) {
+        base = a.aux[it.idx];
+        L = a.aux[it.idx + it.cnt] - base;
+        src = val + it.val + base;
+        cj = a.aux + it.idx2 + base;
+    } else {
+        L = it.cnt * it.w;
+        src = val + it.val;
+    }
+    const float invw = it.kind == VF_BLK_CSR ? 0.f : 1.f / (float)it.w;
+    const bool wide = (int64_t)it.cnt * it.w >= (1 << 22);  // row_of is exact below 2^22 elements
+    constexpr int kC = Chunk<RB>::p2;
+    for (int cs = 0; cs < L; cs += kC) {
+        const int Lc = min(kC, L - cs);
+        float v[kC / 32];
+        int xi[kC / 32];
 #pragma unroll
-    for (int s = 0; s < kRowsPerWarp; ++s)
+        for (int i = 0; i < kC / 32; ++i) {
+            int e = lane + 32 * i;
+            v[i] = e < Lc ? ld(src + cs + e) : 0.f;
+        }
 #pragma unroll
-        for (int c = 0; c < RB; ++c) acc[s][c] = 0;
-    const int i0 = a.tile_item_ptr[tile], i1 = a.tile_item_ptr[tile + 1];
-    for (int ii = i0; ii < i1; ++ii) {
-        const TileItem it = a.items[ii];
-        const HBlock b = a.blocks[it.blk];
-        const float sc = a.scale ? a.scale[it.blk] : 1.f;
-        if (b.kind == VF_BLK_DENSE) {
-            const T* base = val + b.off_val;
+        for (int i = 0; i < kC / 32; ++i) {
+            int e = cs + lane + 32 * i;
+            if (it.kind == VF_BLK_CSR) xi[i] = (lane + 32 * i < Lc) ? __ldg(cj + e) : 0;
+            else xi[i] = it.xoff + (e - (wide ? e / it.w : row_of(e, invw)) * it.w);
+        }
 #pragma unroll
-            for (int s = 0; s < kRowsPerWarp; ++s) {
-                int rr = warp + kWarps * s;
-                if (rr >= tc) break;
-                const T* row = base + (int64_t)(it.lr0 + rr) * b.n;
-                float p[RB];
+        for (int i = 0; i < kC / 32; ++i) {
+            int e = lane + 32 * i;
+            if (e < Lc) {
 #pragma unroll
-                for (int c = 0; c < RB; ++c) p[c] = 0.f;
-                for (int j = lane; j < b.n; j += 32) {
-                    float v = ld(row + j);
-#pragma unroll
-                    for (int c = 0; c < RB; ++c)
-                        p[c] = fmaf(v, (c0 + c < a.R) ? __ldg(X + (int64_t)(c0 + c) * a.n + b.c0 + j) : 0.f, p[c]);
+                for (int c = 0; c < RB; ++c) {
+                    float x;
+                    if (it.kind == VF_BLK_SVD) x = Tp[(int64_t)c * a.nT + xi[i]];
+                    else x = (p0 + c < a.R) ? __ldg(X + (int64_t)(p0 + c) * a.n + xi[i]) : 0.f;
+                    scr[c * kC + e] = v[i] * x;
                 }
-#pragma unroll
-                for (int c = 0; c < RB; ++c) acc[s][c] += (acc_t)(p[c] * sc);
-            }
-        } else if (b.kind == VF_BLK_CSR) {
-            const int32_t* rp = a.aux + b.off_aux;
-            const int32_t* cj = rp + b.m + 1;
-            const T* vv = val + b.off_val;
-#pragma unroll
-            for (int s = 0; s < kRowsPerWarp; ++s) {
-                int rr = warp + kWarps * s;
-                if (rr >= tc) break;
-                int k0 = rp[it.lr0 + rr], k1 = rp[it.lr0 + rr + 1];
-                float p[RB];
-#pragma unroll
-                for (int c = 0; c < RB; ++c) p[c] = 0.f;
-                for (int k = k0 + lane; k < k1; k += 32) {
-                    float v = ld(vv + k);
-                    int col = cj[k];
-#pragma unroll
-                    for (int c = 0; c < RB; ++c)
-                        p[c] = fmaf(v, (c0 + c < a.R) ? __ldg(X + (int64_t)(c0 + c) * a.n + col) : 0.f, p[c]);
-                }
-#pragma unroll
-                for (int c = 0; c < RB; ++c) acc[s][c] += (acc_t)(p[c] * sc);
-            }
-        } else {  // SVD: rows of U' inside the tile
-            const int32_t* rows = a.aux + b.off_aux;
-            const T* U = val + b.off_val;
-            const int q = b.q;
-            for (int u = it.u0; u < it.u1; ++u) {
-                int rr = rows[u] - tf;
-                if ((rr & (kWarps - 1)) != warp) continue;
-                int s = rr / kWarps;
-                float p[RB];
-#pragma unroll
-                for (int c = 0; c < RB; ++c) p[c] = 0.f;
-                for (int k = lane; k < q; k += 32) {
-                    float v = ld(U + (int64_t)u * q + k);
-#pragma unroll
-                    for (int c = 0; c < RB; ++c) p[c] = fmaf(v, Tp[(int64_t)c * a.nT + b.off_T + k], p[c]);
-                }
-#pragma unroll
-                for (int ss = 0; ss < kRowsPerWarp; ++ss)
-                    if (ss == s)
-#pragma unroll
-                        for (int c = 0; c < RB; ++c) acc[ss][c] += (acc_t)(p[c] * sc);
             }
         }
+        __syncwarp();
+        // whole-row sums out of the scratch: item row j by lane j (and j + 32)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int j = lane + 32 * h;
+            if (j < it.cnt) {
+                int rs, re;
+                if (it.kind == VF_BLK_CSR) {
+                    rs = a.aux[it.idx + j] - base;
+                    re = a.aux[it.idx + j + 1] - base;
+                } else {
+                    rs = j * it.w;
+                    re = rs + it.w;
+                }
+                int lo = max(rs, cs) - cs, hi = min(re, cs + Lc) - cs;
+                if (lo < hi) {
+                    int dest = it.kind == VF_BLK_SVD ? a.aux[it.idx + j] - tf : j;
+#pragma unroll
+                    for (int c = 0; c < RB; ++c) {
+                        float s = 0.f;
+                        for (int k = lo; k < hi; ++k) s += scr[c * kC + k];
+                        acc[dest * RB + c] += (acc_t)(s * sc);
+                    }
+                }
+            }
+        }
+        __syncwarp();
     }
-    // reduce each row over the warp's lanes (fixed butterfly order)
-#pragma unroll
-    for (int s = 0; s < kRowsPerWarp; ++s)
-#pragma unroll
-        for (int c = 0; c < RB; ++c)
-            for (int o = 16; o > 0; o >>= 1) acc[s][c] += __shfl_xor_sync(0xffffffffu, acc[s][c], o);
-    __shared__ double colsum[kWarps][RB];
+}
+
+// One CTA per row tile (heaviest first) and RHS panel.  Warp w takes the
+// tile's items w, w + 8, ... in order; the warps' row accumulators are then
+// added in warp order, and the epilogue applies the mode.
+template <class T, int RB, int MODE>
+__global__ void __launch_bounds__(256, RB <= 2 ? 4 : 2) k_phase2(ApplyArgs a, const T* __restrict__ val,
+                                                                const float* __restrict__ Tbuf, SweepIO io) {
+    using acc_t = typename std::conditional<MODE == MODE_RESID, double, float>::type;
+    // dynamic shared memory: acc[kWarps][kTileRows * RB] (acc_t), colsum[kWarps][RB]
+    // (double), scr[kWarps][RB * chunk] (float)
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto acc = reinterpret_cast<acc_t(*)[kTileRows * RB]>(smem_raw);
+    auto colsum = reinterpret_cast<double(*)[RB]>(smem_raw + sizeof(acc_t) * kWarps * kTileRows * RB);
+    auto scr = reinterpret_cast<float(*)[RB * Chunk<RB>::p2]>(smem_raw + sizeof(acc_t) * kWarps * kTileRows * RB +
+                                                                sizeof(double) * kWarps * RB);
+    const int tile = a.tile_order[blockIdx.x];
+    const int panel = blockIdx.y;
+    const int p0 = panel * RB;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tf = a.tile_first[tile], tc = a.tile_count[tile];
+    const float* X = io.xsel ? *io.xsel : io.xd;
+    const float* Tp = Tbuf + (int64_t)panel * RB * a.nT;
+    for (int i = lane; i < kTileRows * RB; i += 32) acc[warp][i] = 0;
+    __syncwarp();
+    const int i0 = a.tile_item_ptr[tile], i1 = a.tile_item_ptr[tile + 1];
+    int ii = i0 + warp;
+    TileItem nxt;
+    if (ii < i1) nxt = a.items[ii];
+    for (; ii < i1; ii += kWarps) {
+        const TileItem it = nxt;
+        if (ii + kWarps < i1) nxt = a.items[ii + kWarps];  // prefetch the next descriptor
+        item_warp<T, RB, acc_t>(a, val, X, Tp, it, tf, scr[warp], acc[warp]);
+    }
+    __syncthreads();
     double mysum[RB];
 #pragma unroll
     for (int c = 0; c < RB; ++c) mysum[c] = 0.0;
-    if (lane == 0) {
-        float* Y = *io.ysel;
+    float* Y = io.ysel ? *io.ysel : io.yd;
+    for (int e = threadIdx.x; e < tc * RB; e += blockDim.x) {
+        const int r = e / RB, c = e - r * RB;
+        if (p0 + c >= a.R) continue;
+        acc_t y = 0;
 #pragma unroll
-        for (int s = 0; s < kRowsPerWarp; ++s) {
-            int rr = warp + kWarps * s;
-            if (rr >= tc) break;
-            int64_t p = tf + rr;
+        for (int w = 0; w < kWarps; ++w) y += acc[w][r * RB + c];
+        const int64_t p = tf + r;
+        const int64_t o = (int64_t)(p0 + c) * a.n + p;
+        if (MODE == MODE_APPLY) {
+            Y[o] = (float)y;
+        } else if (MODE == MODE_JACOBI) {
+            float bn = io.E[o] + io.rho[p] * (float)y;
+            float d = bn - X[o];
+            Y[o] = bn;
 #pragma unroll
-            for (int c = 0; c < RB; ++c) {
-                if (c0 + c >= a.R) break;
-                int64_t o = (int64_t)(c0 + c) * a.n + p;
-                if (MODE == MODE_APPLY) {
-                    Y[o] = (float)acc[s][c];
-                } else if (MODE == MODE_JACOBI) {
-                    float bn = io.E[o] + io.rho[p] * (float)acc[s][c];
-                    float d = bn - X[o];
-                    Y[o] = bn;
-                    mysum[c] += (double)d * d;
-                } else {
-                    // r = E - B + rho F B, accumulated in double
-                    double r = (double)io.E[o] - (double)X[o] + (double)io.rho[p] * (double)acc[s][c];
-                    Y[o] = (float)r;
-                    mysum[c] += r * r;
-                }
-            }
+            for (int cc = 0; cc < RB; ++cc)
+                if (cc == c) mysum[cc] += (double)d * d;
+        } else {
+            double rr = (double)io.E[o] - (double)X[o] + (double)io.rho[p] * (double)y;
+            Y[o] = (float)rr;
+#pragma unroll
+            for (int cc = 0; cc < RB; ++cc)
+                if (cc == c) mysum[cc] += rr * rr;
         }
     }
     if (MODE != MODE_APPLY) {
-        __syncthreads();  // colsum may still be read by a previous work item of this CTA
+        // per-column sums: warp butterfly, then warps in order
+#pragma unroll
+        for (int c = 0; c < RB; ++c)
+            for (int o = 16; o > 0; o >>= 1) mysum[c] += __shfl_xor_sync(0xffffffffu, mysum[c], o);
         if (lane == 0)
 #pragma unroll
             for (int c = 0; c < RB; ++c) colsum[warp][c] = mysum[c];
         __syncthreads();
-        if (threadIdx.x < RB && c0 + (int)threadIdx.x < a.R) {
+        if (threadIdx.x < RB && p0 + (int)threadIdx.x < a.R) {
             double s = 0;
             for (int w = 0; w < kWarps; ++w) s += colsum[w][threadIdx.x];
-            io.colpart[(int64_t)(c0 + threadIdx.x) * io.ntiles + tile] = s;
+            io.colpart[(int64_t)(p0 + threadIdx.x) * io.ntiles + tile] = s;
         }
     }
-}
-
-template <class T, int RB, int MODE>
-__global__ void __launch_bounds__(256) k_phase2(ApplyArgs a, const T* __restrict__ val, const float* __restrict__ Tbuf,
-                                                SweepIO io) {
-    phase2_body<T, RB, MODE>(a, val, Tbuf, io, blockIdx.x, blockIdx.y);
 }
 
 // ------------------------------------------------------------ small kernels
@@ -404,57 +472,82 @@ vf_status vf_hmat::upload_all() {
     // load); every block's row range is a union of consecutive tiles.
     std::vector<vf::HBlock>& B = h_blocks;
     const int64_t ntiles = (int64_t)h_tile_first.size();
-    std::vector<std::vector<vf::TileItem>> per(ntiles);
-    // tile index by first row
+    std::vector<int32_t> haux;
+    if (n_aux > 0) VF_TRY(aux.download(haux));
     std::vector<int32_t> tile_of_row(nf, -1);
     for (int64_t k = 0; k < ntiles; ++k)
         for (int32_t r = h_tile_first[k]; r < h_tile_first[k] + h_tile_count[k]; ++r) tile_of_row[r] = (int32_t)k;
+    std::vector<std::vector<vf::TileItem>> per(ntiles);
+    std::vector<int64_t> cost(ntiles, 0);
     for (size_t bi = 0; bi < B.size(); ++bi) {
         const vf::HBlock& b = B[bi];
-        int32_t r = b.r0;
-        while (r < b.r0 + b.m) {
-            int32_t k = tile_of_row[r];
+        for (int32_t r = b.r0; r < b.r0 + b.m;) {
+            const int32_t k = tile_of_row[r];
+            const int32_t tf = h_tile_first[k], tc = h_tile_count[k], lr0 = tf - b.r0;
             vf::TileItem it{};
+            it.kind = b.kind;
             it.blk = (int32_t)bi;
-            it.lr0 = h_tile_first[k] - b.r0;
-            it.u0 = it.u1 = 0;
-            per[k].push_back(it);
-            r = h_tile_first[k] + h_tile_count[k];
+            int64_t work = 0;
+            if (b.kind == VF_BLK_DENSE) {
+                it.cnt = tc;
+                it.w = b.n;
+                it.xoff = b.c0;
+                it.val = b.off_val + (int64_t)lr0 * b.n;
+                work = (int64_t)tc * b.n;
+            } else if (b.kind == VF_BLK_CSR) {
+                it.cnt = tc;
+                it.idx = (int32_t)(b.off_aux + lr0);
+                it.idx2 = (int32_t)(b.off_aux + b.m + 1);
+                it.val = b.off_val;
+                work = haux[b.off_aux + lr0 + tc] - haux[b.off_aux + lr0];
+            } else {
+                const int32_t* rows = haux.data() + b.off_aux;
+                int32_t u0 = (int32_t)(std::lower_bound(rows, rows + b.m1, tf) - rows);
+                int32_t u1 = (int32_t)(std::lower_bound(rows, rows + b.m1, tf + tc) - rows);
+                it.cnt = u1 - u0;
+                it.w = b.q;
+                it.xoff = (int32_t)b.off_T;
+                it.val = b.off_val + (int64_t)u0 * b.q;
+                it.idx = (int32_t)(b.off_aux + u0);
+                work = (int64_t)it.cnt * b.q;
+            }
+            if (it.cnt > 0 && !(b.kind == VF_BLK_CSR && work == 0)) {
+                per[k].push_back(it);
+                cost[k] += work + 32;
+            }
+            r = tf + tc;
         }
     }
-    // SVD compacted-row ranges per tile need the row lists: read them back
-    std::vector<int32_t> haux;
-    if (n_aux > 0) VF_TRY(aux.download(haux));
-    for (int64_t k = 0; k < ntiles; ++k)
-        for (auto& it : per[k]) {
-            const vf::HBlock& b = B[it.blk];
-            if (b.kind != VF_BLK_SVD) continue;
-            const int32_t* rows = haux.data() + b.off_aux;
-            int32_t lo = h_tile_first[k], hi = lo + h_tile_count[k];
-            it.u0 = (int32_t)(std::lower_bound(rows, rows + b.m1, lo) - rows);
-            it.u1 = (int32_t)(std::lower_bound(rows, rows + b.m1, hi) - rows);
-        }
     h_items.clear();
     h_tile_item_ptr.assign(ntiles + 1, 0);
     for (int64_t k = 0; k < ntiles; ++k) {
         h_tile_item_ptr[k] = (int32_t)h_items.size();
-        for (auto& it : per[k])
-            if (!(B[it.blk].kind == VF_BLK_SVD && it.u0 == it.u1)) h_items.push_back(it);
+        h_items.insert(h_items.end(), per[k].begin(), per[k].end());
     }
     h_tile_item_ptr[ntiles] = (int32_t)h_items.size();
-    // phase-1 chunks
+    h_tile_order.resize(ntiles);
+    for (int64_t k = 0; k < ntiles; ++k) h_tile_order[k] = (int32_t)k;
+    std::stable_sort(h_tile_order.begin(), h_tile_order.end(),
+                     [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
+    // phase-1 chunks of at most kChunkElems V' values, largest first
     h_chunks.clear();
+    n_part_slots = 0;
     for (size_t bi = 0; bi < B.size(); ++bi) {
         if (B[bi].kind != VF_BLK_SVD) continue;
-        int32_t nch = (int32_t)vf::ceil_div(B[bi].n1, kChunkRows);
-        int32_t first = (int32_t)h_chunks.size();
+        const int32_t rows = std::max<int32_t>(1, kChunkElems / B[bi].q);
+        const int32_t nch = (int32_t)vf::ceil_div(B[bi].n1, rows);
+        const int32_t first = nch > 1 ? (int32_t)n_part_slots : 0;
+        if (nch > 1) n_part_slots += nch;
         for (int32_t c = 0; c < nch; ++c)
-            h_chunks.push_back(vf::SvdChunk{(int32_t)bi, c * kChunkRows, std::min(B[bi].n1, (c + 1) * kChunkRows), c,
-                                            nch, first});
+            h_chunks.push_back(vf::SvdChunk{(int32_t)bi, c * rows, std::min(B[bi].n1, (c + 1) * rows), c, nch, first});
     }
+    std::stable_sort(h_chunks.begin(), h_chunks.end(), [&](const vf::SvdChunk& x, const vf::SvdChunk& y) {
+        return (int64_t)(x.j1 - x.j0) * B[x.blk].q > (int64_t)(y.j1 - y.j0) * B[y.blk].q;
+    });
     VF_TRY(tile_first.upload(h_tile_first));
     VF_TRY(tile_count.upload(h_tile_count));
     VF_TRY(tile_item_ptr.upload(h_tile_item_ptr));
+    VF_TRY(tile_order.upload(h_tile_order));
     VF_TRY(items.upload(h_items));
     VF_TRY(chunks.upload(h_chunks));
     return VF_OK;
@@ -520,11 +613,15 @@ static ApplyArgs make_args(const vf_hmat* h, int prec, int R) {
     a.tile_item_ptr = h->tile_item_ptr.p;
     a.items = h->items.p;
     a.chunks = h->chunks.p;
+    a.tile_order = h->tile_order.p;
+    a.nparts = std::max<int64_t>(h->n_part_slots, 1);
     a.n = h->nf;
     a.nT = std::max<int64_t>(h->n_T, 1);
     a.R = R;
     return a;
 }
+
+static vf_status phase2_attrs(int device);
 
 static vf_status ws_get(const vf_hmat* h, int R, int prec, Workspace** out) {
     WsCache& c = cache_for(h);
@@ -535,6 +632,7 @@ static vf_status ws_get(const vf_hmat* h, int R, int prec, Workspace** out) {
         *out = it->second.get();
         return VF_OK;
     }
+    VF_TRY(phase2_attrs(h->device));
     auto w = std::make_unique<Workspace>();
     w->R = R;
     w->prec = prec;
@@ -551,7 +649,7 @@ static vf_status ws_get(const vf_hmat* h, int R, int prec, Workspace** out) {
     VF_TRY(w->rho_t.alloc(n));
     int64_t nT = std::max<int64_t>(h->n_T, 1);
     VF_TRY(w->Tbuf.alloc((int64_t)w->npanels * w->RB * nT));
-    VF_TRY(w->part.alloc(std::max<int64_t>((int64_t)w->npanels * (int64_t)h->h_chunks.size() * w->RB * 128, 1)));
+    VF_TRY(w->part.alloc(std::max<int64_t>((int64_t)w->npanels * std::max<int64_t>(h->n_part_slots, 1) * w->RB * 128, 1)));
     VF_TRY(w->counters.alloc((int64_t)w->npanels * nT));
     VF_TRY_CUDA(cudaMemset(w->counters.p, 0, (int64_t)w->npanels * nT * sizeof(int)));
     VF_TRY(w->colpart.alloc(std::max<int64_t>(ntiles * R, 1)));
@@ -569,44 +667,100 @@ static vf_status ws_get(const vf_hmat* h, int R, int prec, Workspace** out) {
     return VF_OK;
 }
 
+template <class T, int RB, int MODE>
+static vf_status launch_phase2(dim3 grid, const ApplyArgs& a, const T* val, const float* Tbuf, const SweepIO& io,
+                               cudaStream_t st) {
+    using acc_t = typename std::conditional<MODE == MODE_RESID, double, float>::type;
+    const size_t smem = sizeof(acc_t) * kWarps * kTileRows * RB + sizeof(double) * kWarps * RB +
+                        sizeof(float) * kWarps * RB * Chunk<RB>::p2;
+    k_phase2<T, RB, MODE><<<grid, 256, smem, st>>>(a, val, Tbuf, io);
+    return VF_OK;
+}
+
+// The dynamic shared-memory opt-in of every phase-2 variant; called once
+// per device before any launch or graph capture.
+template <class T, int RB, int MODE>
+static cudaError_t phase2_attr() {
+    using acc_t = typename std::conditional<MODE == MODE_RESID, double, float>::type;
+    const size_t smem = sizeof(acc_t) * kWarps * kTileRows * RB + sizeof(double) * kWarps * RB +
+                        sizeof(float) * kWarps * RB * Chunk<RB>::p2;
+    return cudaFuncSetAttribute(k_phase2<T, RB, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <class T, int RB>
+static cudaError_t phase2_attrs_rb() {
+    cudaError_t e = phase2_attr<T, RB, MODE_APPLY>();
+    if (e == cudaSuccess) e = phase2_attr<T, RB, MODE_JACOBI>();
+    if (e == cudaSuccess) e = phase2_attr<T, RB, MODE_RESID>();
+    return e;
+}
+
+template <class T>
+static cudaError_t phase2_attrs_t() {
+    cudaError_t e = phase2_attrs_rb<T, 1>();
+    if (e == cudaSuccess) e = phase2_attrs_rb<T, 2>();
+    if (e == cudaSuccess) e = phase2_attrs_rb<T, 4>();
+    if (e == cudaSuccess) e = phase2_attrs_rb<T, 8>();
+    return e;
+}
+
+static vf_status phase2_attrs(int device) {
+    static std::mutex mu;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(done.begin(), done.end(), device) != done.end()) return VF_OK;
+    cudaError_t e = phase2_attrs_t<float>();
+    if (e == cudaSuccess) e = phase2_attrs_t<__nv_bfloat16>();
+    if (e == cudaSuccess) e = phase2_attrs_t<__nv_fp8_e4m3>();
+    VF_CHECK(e == cudaSuccess, VF_E_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    done.push_back(device);
+    return VF_OK;
+}
+
 template <class T, int RB>
 static vf_status launch_multiply_t(const vf_hmat* h, const T* val, const ApplyArgs& a, Workspace* w, int mode,
-                                   const float* const* xsel, float* const* ysel, const float* E, const float* rho,
-                                   cudaStream_t st) {
+                                   const float* const* xsel, float* const* ysel, const float* xd, float* yd,
+                                   const float* E, const float* rho, cudaStream_t st) {
     const int64_t ntiles = (int64_t)h->h_tile_first.size();
     if (!h->h_chunks.empty()) {
-        dim3 g1((unsigned)h->h_chunks.size(), (unsigned)w->npanels);
-        k_phase1<T, RB><<<g1, 256, 0, st>>>(a, val, xsel, w->Tbuf.p, w->part.p, w->counters.p);
+        const int nch = (int)h->h_chunks.size();
+        dim3 g1((unsigned)ceil_div(nch, kWarps), (unsigned)w->npanels);
+        k_phase1<T, RB><<<g1, 256, 0, st>>>(a, val, xsel, xd, w->Tbuf.p, w->part.p, w->counters.p, nch);
     }
-    SweepIO io{xsel, ysel, E, rho, w->colpart.p, ntiles};
+    SweepIO io{xsel, ysel, xd, yd, E, rho, w->colpart.p, ntiles};
     dim3 g2((unsigned)ntiles, (unsigned)w->npanels);
-    if (mode == MODE_APPLY) k_phase2<T, RB, MODE_APPLY><<<g2, 256, 0, st>>>(a, val, w->Tbuf.p, io);
-    else if (mode == MODE_JACOBI) k_phase2<T, RB, MODE_JACOBI><<<g2, 256, 0, st>>>(a, val, w->Tbuf.p, io);
-    else k_phase2<T, RB, MODE_RESID><<<g2, 256, 0, st>>>(a, val, w->Tbuf.p, io);
+    vf_status s2;
+    if (mode == MODE_APPLY) s2 = launch_phase2<T, RB, MODE_APPLY>(g2, a, val, w->Tbuf.p, io, st);
+    else if (mode == MODE_JACOBI) s2 = launch_phase2<T, RB, MODE_JACOBI>(g2, a, val, w->Tbuf.p, io, st);
+    else s2 = launch_phase2<T, RB, MODE_RESID>(g2, a, val, w->Tbuf.p, io, st);
+    VF_TRY(s2);
     VF_TRY_CUDA(cudaGetLastError());
     return VF_OK;
 }
 
 template <class T>
 static vf_status launch_multiply_rb(const vf_hmat* h, const T* val, const ApplyArgs& a, Workspace* w, int mode,
-                                    const float* const* xsel, float* const* ysel, const float* E, const float* rho,
-                                    cudaStream_t st) {
+                                    const float* const* xsel, float* const* ysel, const float* xd, float* yd,
+                                    const float* E, const float* rho, cudaStream_t st) {
     switch (w->RB) {
-        case 1: return launch_multiply_t<T, 1>(h, val, a, w, mode, xsel, ysel, E, rho, st);
-        case 2: return launch_multiply_t<T, 2>(h, val, a, w, mode, xsel, ysel, E, rho, st);
-        case 4: return launch_multiply_t<T, 4>(h, val, a, w, mode, xsel, ysel, E, rho, st);
-        default: return launch_multiply_t<T, 8>(h, val, a, w, mode, xsel, ysel, E, rho, st);
+        case 1: return launch_multiply_t<T, 1>(h, val, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
+        case 2: return launch_multiply_t<T, 2>(h, val, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
+        case 4: return launch_multiply_t<T, 4>(h, val, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
+        default: return launch_multiply_t<T, 8>(h, val, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
     }
 }
 
 // One multiply (phase 1 + phase 2) with the given mode, input/output selected
 // through device pointers.
 static vf_status launch_multiply(const vf_hmat* h, int prec, Workspace* w, int mode, const float* const* xsel,
-                                 float* const* ysel, const float* E, const float* rho, cudaStream_t st) {
+                                 float* const* ysel, const float* xd, float* yd, const float* E, const float* rho,
+                                 cudaStream_t st) {
     ApplyArgs a = make_args(h, prec, w->R);
-    if (prec == VF_PREC_FP32) return launch_multiply_rb<float>(h, h->val.p, a, w, mode, xsel, ysel, E, rho, st);
-    if (prec == VF_PREC_BF16) return launch_multiply_rb<__nv_bfloat16>(h, h->val16.p, a, w, mode, xsel, ysel, E, rho, st);
-    return launch_multiply_rb<__nv_fp8_e4m3>(h, h->val8.p, a, w, mode, xsel, ysel, E, rho, st);
+    if (prec == VF_PREC_FP32)
+        return launch_multiply_rb<float>(h, h->val.p, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
+    if (prec == VF_PREC_BF16)
+        return launch_multiply_rb<__nv_bfloat16>(h, h->val16.p, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
+    return launch_multiply_rb<__nv_fp8_e4m3>(h, h->val8.p, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
 }
 
 static vf_status check_prec(const vf_hmat* h, int prec) {
@@ -633,7 +787,8 @@ static vf_status ensure_graph(const vf_hmat* h, Workspace* w) {
     cudaStream_t cs;
     VF_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     VF_TRY_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    vf_status s = launch_multiply(h, w->prec, w, MODE_JACOBI, w->xsel.p, w->ysel.p, w->Et.p, w->rho_t.p, cs);
+    vf_status s =
+        launch_multiply(h, w->prec, w, MODE_JACOBI, w->xsel.p, w->ysel.p, nullptr, nullptr, w->Et.p, w->rho_t.p, cs);
     const int64_t ntiles = (int64_t)h->h_tile_first.size();
     k_sweep_reduce<<<1, 1024, 0, cs>>>(
         w->colpart.p, ntiles, w->R, w->enorm2.p, w->colres.p, w->loop.p, w->bufs.p, w->xsel.p, w->ysel.p, w->handle, 1);
@@ -727,17 +882,26 @@ extern "C" vf_status vf_apply(const vf_hmat* h, vf_precision prec, const float* 
     VF_TRY_CUDA(cudaStreamWaitEvent(st, w->done, 0));
     const int64_t n = h->nf;
     vf::k_gather_cols<<<1024, 256, 0, st>>>(X, ldx, h->perm.p, n, R, w->Xt.p);
-    // input/output selection through the loop-state pointers
-    const float* xp = w->Xt.p;
-    float* yp = w->Yt.p;
-    VF_TRY_CUDA(cudaMemcpyAsync(w->xsel.p, &xp, sizeof(xp), cudaMemcpyHostToDevice, st));
-    VF_TRY_CUDA(cudaMemcpyAsync(w->ysel.p, &yp, sizeof(yp), cudaMemcpyHostToDevice, st));
-    VF_TRY(vf::launch_multiply(h, prec, w, vf::MODE_APPLY, w->xsel.p, w->ysel.p, nullptr, nullptr, st));
+    VF_TRY(vf::launch_multiply(h, prec, w, vf::MODE_APPLY, nullptr, nullptr, w->Xt.p, w->Yt.p, nullptr, nullptr, st));
     vf::k_scatter_cols<<<1024, 256, 0, st>>>(w->Yt.p, h->perm.p, n, R, Y, ldy, 0);
     VF_TRY_CUDA(cudaGetLastError());
     VF_TRY_CUDA(cudaEventRecord(w->done, st));
-    // the pointer uploads above read host stack memory: make sure they are done
-    VF_TRY_CUDA(cudaStreamSynchronize(st));
+    return VF_OK;
+}
+
+extern "C" vf_status vf_apply_tree(const vf_hmat* h, vf_precision prec, const float* Xt, int32_t R, float* Yt,
+                                   vf_stream stream) {
+    clear_error();
+    VF_CHECK(h && Xt && Yt, VF_E_INVAL, "vf_apply_tree: null argument");
+    VF_CHECK(R >= 1, VF_E_INVAL, "vf_apply_tree: need R >= 1");
+    VF_TRY(vf::check_prec(h, prec));
+    device_guard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    vf::Workspace* w;
+    VF_TRY(vf::ws_get(h, R, prec, &w));
+    VF_TRY_CUDA(cudaStreamWaitEvent(st, w->done, 0));
+    VF_TRY(vf::launch_multiply(h, prec, w, vf::MODE_APPLY, nullptr, nullptr, Xt, Yt, nullptr, nullptr, st));
+    VF_TRY_CUDA(cudaEventRecord(w->done, st));
     return VF_OK;
 }
 
@@ -806,12 +970,9 @@ extern "C" vf_status vf_solve(const vf_hmat* h, const float* rho, const float* E
         bool ok = false;
         for (int ref = 0; ref <= o.max_refine; ++ref) {
             // r = E - B + rho F B  (FP32 factors, FP64 accumulation)
-            const float* xp = w->Yt.p;
-            float* yp = w->Et.p;  // the residual becomes the next inner right-hand side
-            VF_TRY_CUDA(cudaMemcpyAsync(w32->xsel.p, &xp, sizeof(xp), cudaMemcpyHostToDevice, st));
-            VF_TRY_CUDA(cudaMemcpyAsync(w32->ysel.p, &yp, sizeof(yp), cudaMemcpyHostToDevice, st));
-            VF_TRY(vf::launch_multiply(h, VF_PREC_FP32, w32, vf::MODE_RESID, w32->xsel.p, w32->ysel.p, w->Xt.p,
-                                       w32->rho_t.p, st));
+            // the residual (written to Et) becomes the next inner right-hand side
+            VF_TRY(vf::launch_multiply(h, VF_PREC_FP32, w32, vf::MODE_RESID, nullptr, nullptr, w->Yt.p, w->Et.p,
+                                       w->Xt.p, w32->rho_t.p, st));
             const int64_t ntiles = (int64_t)h->h_tile_first.size();
             std::vector<double> part((size_t)ntiles * R), rr(R, 0.0);
             VF_TRY_CUDA(cudaMemcpyAsync(part.data(), w32->colpart.p, part.size() * 8, cudaMemcpyDeviceToHost, st));
@@ -848,6 +1009,43 @@ extern "C" vf_status vf_solve(const vf_hmat* h, const float* rho, const float* E
     if (stats) *stats = S;
     if (status == VF_E_NOCONV) vf::set_error("vf_solve: not converged (max rel residual %.3e)", S.max_rel_residual);
     return status;
+}
+
+extern "C" vf_status vf_solve_host(const vf_hmat* h, const float* rho, const float* E, int64_t lde, float* B,
+                                   int64_t ldb, int32_t R, const vf_solve_opts* opts, vf_solve_stats* stats,
+                                   vf_stream stream) {
+    clear_error();
+    VF_CHECK(h && E && B, VF_E_INVAL, "vf_solve_host: null argument");
+    VF_CHECK(R >= 1 && lde >= h->nf && ldb >= h->nf, VF_E_INVAL, "vf_solve_host: need R >= 1 and ld >= N");
+    device_guard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = h->nf;
+    float *dE = nullptr, *dB = nullptr, *drho = nullptr;
+    VF_TRY_CUDA(cudaMallocAsync((void**)&dE, n * R * sizeof(float), st));
+    VF_TRY_CUDA(cudaMallocAsync((void**)&dB, n * R * sizeof(float), st));
+    if (rho) VF_TRY_CUDA(cudaMallocAsync((void**)&drho, n * sizeof(float), st));
+    vf_status s = VF_OK;
+    cudaError_t e = cudaMemcpy2DAsync(dE, n * sizeof(float), E, lde * sizeof(float), n * sizeof(float), R,
+                                      cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && rho) e = cudaMemcpyAsync(drho, rho, n * sizeof(float), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        set_error("vf_solve_host: copy to device failed: %s", cudaGetErrorString(e));
+        s = VF_E_CUDA;
+    }
+    if (s == VF_OK) s = vf_solve(h, drho, dE, n, dB, n, R, opts, stats, stream);
+    if (s == VF_OK || s == VF_E_NOCONV) {
+        e = cudaMemcpy2DAsync(B, ldb * sizeof(float), dB, n * sizeof(float), n * sizeof(float), R,
+                              cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            set_error("vf_solve_host: copy to host failed: %s", cudaGetErrorString(e));
+            s = VF_E_CUDA;
+        }
+    }
+    cudaFreeAsync(dE, st);
+    cudaFreeAsync(dB, st);
+    if (drho) cudaFreeAsync(drho, st);
+    return s;
 }
 
 extern "C" vf_status vf_solve_batched(const vf_hmat* const* F, int32_t nmeshes, const float* const* rho,

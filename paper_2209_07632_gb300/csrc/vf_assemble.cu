@@ -719,6 +719,7 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
     o.verify = 0;
     o.precisions = (1u << VF_PREC_FP32) | (1u << VF_PREC_BF16);
     o.seed = 12345;
+    o.storage = 0;
     if (opts_in) {
         o = *opts_in;
         if (o.leaf_threshold <= 0) o.leaf_threshold = 4096;
@@ -728,6 +729,7 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
     }
     VF_CHECK(o.tol > 0 && o.tol < 1, VF_E_INVAL, "vf_assemble: tol must be in (0, 1)");
     VF_CHECK(o.k_max <= 128, VF_E_INVAL, "vf_assemble: k_max above 128 is not supported");
+    VF_CHECK(o.storage >= 0 && o.storage <= 2, VF_E_INVAL, "vf_assemble: storage must be 0, 1 or 2");
     const int64_t n = m->nf;
     for (size_t k = 0; k < t->first.size(); ++k)
         VF_CHECK(!t->is_leaf((int)k) || t->count[k] <= 64, VF_E_INVAL,
@@ -818,245 +820,270 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
     }
     for (int64_t p = 0; p < npairs; ++p) S.nnz_visible += Bd.pnnz[p];
 
-    // ---------------- block tree
-    if (t->is_leaf(0)) {
-        Bd.top_refs.push_back(Bd.make(0, 0));
-    } else {
-        for (int32_t a : t->kids[0])
-            for (int32_t b : t->kids[0]) Bd.top_refs.push_back(Bd.make(a, b));
-    }
+    std::vector<HBlock>& HB = H->h_blocks;
+    std::vector<int32_t> hb_node;  // DNode id of each stored block (-1 for a leaf pair)
     std::vector<DNode>& N = Bd.nodes;
-    int32_t maxh = 0;
-    for (auto& d : N) {
-        d.st = Bd.rect_stats(d.I, d.J);
-        maxh = std::max(maxh, d.height);
-    }
-    double t2 = now_seconds();
-    S.t_stats = t2 - t1;
-
-    // ---------------- DP bottom-up by height
-    std::vector<int32_t> lists_pool;  // rows/cols of SVD candidates
+    std::vector<int32_t> lists_pool;                       // rows/cols of SVD candidates
     std::vector<std::unique_ptr<dbuf<float>>> stage_bufs;  // their factors
     struct StageRef { int32_t buf; int64_t off; };
-    std::vector<StageRef> stage_ref(N.size(), StageRef{-1, -1});
-
-    for (int32_t h = 0; h <= maxh; ++h) {
-        std::vector<int32_t> level;
-        for (int32_t id = 0; id < (int32_t)N.size(); ++id)
-            if (N[id].height == h) level.push_back(id);
-        // alternatives
-        std::vector<int32_t> pending;
-        for (int32_t id : level) {
-            DNode& d = N[id];
-            int64_t mm = t->count[d.I], nn = t->count[d.J];
-            if (h == 0) {
-                auto c = Builder::leaf_choice(mm, nn, d.st.nnz);
-                d.kind = c.first;
-                d.bytes = c.second;
-                continue;
+    std::vector<StageRef> stage_ref;
+    double t2 = now_seconds(), t3 = t2;
+    if (o.storage != 0) {
+        // the uncompressed F (dense) or Algorithm 1's CSR, one block per leaf pair
+        for (int64_t a = 0; a < Bd.nleaves; ++a)
+            for (int64_t bb = 0; bb < Bd.nleaves; ++bb) {
+                int64_t p = Bd.pair_index((int32_t)a, (int32_t)bb);
+                int32_t kind = o.storage == 1 ? VF_BLK_DENSE : VF_BLK_CSR;
+                if (kind == VF_BLK_CSR && Bd.pnnz[p] == 0) { S.nblocks[VF_BLK_ZERO]++; continue; }
+                HBlock blk{};
+                blk.kind = kind;
+                blk.I = blk.J = -1;
+                blk.r0 = Bd.leaf_first[a];
+                blk.m = Bd.leaf_count[a];
+                blk.c0 = Bd.leaf_first[bb];
+                blk.n = Bd.leaf_count[bb];
+                blk.m1 = Bd.pnnz[p];
+                S.nblocks[kind]++;
+                HB.push_back(blk);
+                hb_node.push_back(-1);
             }
-            if (d.st.nnz == 0) {
-                d.kind = VF_BLK_ZERO;
-                d.bytes = 0;
-                continue;
-            }
-            int64_t hb = 0;
-            for (int32_t k = d.kid_begin; k < d.kid_end; ++k) hb += Bd.kid_bytes(Bd.kids[k]);
-            d.hier_bytes = hb;
-            int64_t bd = 4 * mm * nn, bc = csr_bytes(mm, d.st.nnz);
-            d.best_alt = std::min(std::min(bd, bc), hb);
-            // the SVD can only win if some q >= 1 has svd_bytes(q) < best_alt
-            if (svd_bytes(1, d.st.m1, d.st.n1) < d.best_alt) {
-                d.k = std::min(o.k0, o.k_max);
-                pending.push_back(id);
-            } else {
-                S.probes_skipped++;
-            }
+        t3 = now_seconds();
+        S.t_stats = t3 - t1;
+    } else {
+        // ---------------- block tree
+        if (t->is_leaf(0)) {
+            Bd.top_refs.push_back(Bd.make(0, 0));
+        } else {
+            for (int32_t a : t->kids[0])
+                for (int32_t b : t->kids[0]) Bd.top_refs.push_back(Bd.make(a, b));
         }
-        // probe rounds (k doubling, Algorithm 3)
-        while (!pending.empty()) {
-            ProbeBatch B;
-            std::vector<int32_t> who;
-            for (int32_t id : pending) {
+        int32_t maxh = 0;
+        for (auto& d : N) {
+            d.st = Bd.rect_stats(d.I, d.J);
+            maxh = std::max(maxh, d.height);
+        }
+        t2 = now_seconds();
+        S.t_stats = t2 - t1;
+
+        // ---------------- DP bottom-up by height
+        stage_ref.assign(N.size(), StageRef{-1, -1});
+
+        for (int32_t h = 0; h <= maxh; ++h) {
+            std::vector<int32_t> level;
+            for (int32_t id = 0; id < (int32_t)N.size(); ++id)
+                if (N[id].height == h) level.push_back(id);
+            // alternatives
+            std::vector<int32_t> pending;
+            for (int32_t id : level) {
                 DNode& d = N[id];
-                ProbeDesc p{};
-                p.m1 = d.st.m1;
-                p.n1 = d.st.n1;
-                p.ell = ell_for(d.k, p.m1, p.n1);
-                p.rows_off = (int64_t)B.lists.size();
-                std::vector<int32_t> rows, cols;
-                Bd.nz_lists(d.I, d.J, rows, cols);
-                B.lists.insert(B.lists.end(), rows.begin(), rows.end());
-                p.cols_off = (int64_t)B.lists.size();
-                B.lists.insert(B.lists.end(), cols.begin(), cols.end());
-                p.y_off = B.ny;
-                B.ny += (int64_t)p.m1 * p.ell;
-                p.z_off = B.nz;
-                B.nz += (int64_t)p.n1 * p.ell;
-                p.s_off = B.ns;
-                B.ns += 2 * (int64_t)p.ell * p.ell + p.ell;
-                p.seed = splitmix64(o.seed ^ ((uint64_t)id << 20) ^ (uint64_t)d.k);
-                B.pd.push_back(p);
-                who.push_back(id);
-            }
-            VF_TRY(run_probes(g, B, o.power_iters, st));
-            std::vector<float> hsmall(B.ns);
-            VF_TRY_CUDA(cudaMemcpy(hsmall.data(), B.small.p, B.ns * 4, cudaMemcpyDeviceToHost));
-            S.probes += (int64_t)who.size();
-            std::vector<int32_t> next;
-            std::vector<FactorDesc> fds;
-            std::vector<int32_t> sel;
-            std::vector<int32_t> fd_owner;
-            int64_t fstage = 0;
-            for (size_t pi = 0; pi < who.size(); ++pi) {
-                DNode& d = N[who[pi]];
-                const ProbeDesc& p = B.pd[pi];
-                const float* sig = hsmall.data() + p.s_off + 2 * (int64_t)p.ell * p.ell;
-                std::vector<int32_t> order(p.ell);
-                std::iota(order.begin(), order.end(), 0);
-                std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sig[a] > sig[b]; });
-                float s1 = sig[order[0]];
-                bool full = p.ell == std::min(p.m1, p.n1);
-                int32_t trust = full ? p.ell : std::min(d.k, p.ell);
-                int32_t q = -1;
-                if (s1 > 0.f)
-                    for (int32_t qq = 1; qq <= trust; ++qq) {
-                        float nxt = qq < p.ell ? sig[order[qq]] : 0.f;
-                        if (qq == trust && !full) break;  // sigma_{q+1} not trusted
-                        if (nxt < (float)o.tol * s1) { q = qq; break; }
-                    }
-                if (q < 0) {
-                    int32_t k2 = 2 * d.k;
-                    if (!full && k2 <= o.k_max && svd_bytes(d.k, d.st.m1, d.st.n1) < d.best_alt) {
-                        d.k = k2;
-                        next.push_back(who[pi]);
-                    } else {
-                        S.probes_failed++;
-                    }
+                int64_t mm = t->count[d.I], nn = t->count[d.J];
+                if (h == 0) {
+                    auto c = Builder::leaf_choice(mm, nn, d.st.nnz);
+                    d.kind = c.first;
+                    d.bytes = c.second;
                     continue;
                 }
-                if (q > o.k_max || svd_bytes(q, d.st.m1, d.st.n1) >= d.best_alt) {
-                    S.probes_failed += q > o.k_max ? 1 : 0;
-                    continue;  // the SVD cannot win
+                if (d.st.nnz == 0) {
+                    d.kind = VF_BLK_ZERO;
+                    d.bytes = 0;
+                    continue;
                 }
-                d.q = q;
-                FactorDesc f{};
-                f.probe = (int32_t)pi;
-                f.q = q;
-                f.sel_off = (int64_t)sel.size();
-                for (int32_t k = 0; k < q; ++k) sel.push_back(order[k]);
-                f.u_off = fstage;
-                fstage += (int64_t)(p.m1 + p.n1) * q;
-                fds.push_back(f);
-                fd_owner.push_back(who[pi]);
-            }
-            if (!fds.empty()) {
-                auto buf = std::make_unique<dbuf<float>>();
-                VF_TRY(buf->alloc(fstage));
-                dbuf<FactorDesc> dfd;
-                dbuf<int32_t> dsel;
-                VF_TRY(dfd.upload(fds));
-                VF_TRY(dsel.upload(sel));
-                k_form_factors<<<(unsigned)fds.size(), 256, 0, st>>>(B.d_pd.p, dfd.p, dsel.p, B.Y.p, B.Z.p, B.small.p, buf->p);
-                VF_TRY_CUDA(cudaGetLastError());
-                VF_TRY_CUDA(cudaStreamSynchronize(st));
-                int32_t bi = (int32_t)stage_bufs.size();
-                for (size_t f = 0; f < fds.size(); ++f) {
-                    int32_t id = fd_owner[f];
-                    stage_ref[id] = StageRef{bi, fds[f].u_off};
-                    // keep the compacted lists of this candidate
-                    const ProbeDesc& p = B.pd[fds[f].probe];
-                    N[id].lists_off = (int64_t)lists_pool.size();
-                    lists_pool.insert(lists_pool.end(), B.lists.begin() + p.rows_off,
-                                      B.lists.begin() + p.rows_off + p.m1);
-                    lists_pool.insert(lists_pool.end(), B.lists.begin() + p.cols_off,
-                                      B.lists.begin() + p.cols_off + p.n1);
+                int64_t hb = 0;
+                for (int32_t k = d.kid_begin; k < d.kid_end; ++k) hb += Bd.kid_bytes(Bd.kids[k]);
+                d.hier_bytes = hb;
+                int64_t bd = 4 * mm * nn, bc = csr_bytes(mm, d.st.nnz);
+                d.best_alt = std::min(std::min(bd, bc), hb);
+                // the SVD can only win if some q >= 1 has svd_bytes(q) < best_alt
+                if (svd_bytes(1, d.st.m1, d.st.n1) < d.best_alt) {
+                    d.k = std::min(o.k0, o.k_max);
+                    pending.push_back(id);
+                } else {
+                    S.probes_skipped++;
                 }
-                stage_bufs.push_back(std::move(buf));
             }
-            pending.swap(next);
+            // probe rounds (k doubling, Algorithm 3)
+            while (!pending.empty()) {
+                ProbeBatch B;
+                std::vector<int32_t> who;
+                for (int32_t id : pending) {
+                    DNode& d = N[id];
+                    ProbeDesc p{};
+                    p.m1 = d.st.m1;
+                    p.n1 = d.st.n1;
+                    p.ell = ell_for(d.k, p.m1, p.n1);
+                    p.rows_off = (int64_t)B.lists.size();
+                    std::vector<int32_t> rows, cols;
+                    Bd.nz_lists(d.I, d.J, rows, cols);
+                    B.lists.insert(B.lists.end(), rows.begin(), rows.end());
+                    p.cols_off = (int64_t)B.lists.size();
+                    B.lists.insert(B.lists.end(), cols.begin(), cols.end());
+                    p.y_off = B.ny;
+                    B.ny += (int64_t)p.m1 * p.ell;
+                    p.z_off = B.nz;
+                    B.nz += (int64_t)p.n1 * p.ell;
+                    p.s_off = B.ns;
+                    B.ns += 2 * (int64_t)p.ell * p.ell + p.ell;
+                    p.seed = splitmix64(o.seed ^ ((uint64_t)id << 20) ^ (uint64_t)d.k);
+                    B.pd.push_back(p);
+                    who.push_back(id);
+                }
+                VF_TRY(run_probes(g, B, o.power_iters, st));
+                std::vector<float> hsmall(B.ns);
+                VF_TRY_CUDA(cudaMemcpy(hsmall.data(), B.small.p, B.ns * 4, cudaMemcpyDeviceToHost));
+                S.probes += (int64_t)who.size();
+                std::vector<int32_t> next;
+                std::vector<FactorDesc> fds;
+                std::vector<int32_t> sel;
+                std::vector<int32_t> fd_owner;
+                int64_t fstage = 0;
+                for (size_t pi = 0; pi < who.size(); ++pi) {
+                    DNode& d = N[who[pi]];
+                    const ProbeDesc& p = B.pd[pi];
+                    const float* sig = hsmall.data() + p.s_off + 2 * (int64_t)p.ell * p.ell;
+                    std::vector<int32_t> order(p.ell);
+                    std::iota(order.begin(), order.end(), 0);
+                    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sig[a] > sig[b]; });
+                    float s1 = sig[order[0]];
+                    bool full = p.ell == std::min(p.m1, p.n1);
+                    int32_t trust = full ? p.ell : std::min(d.k, p.ell);
+                    int32_t q = -1;
+                    if (s1 > 0.f)
+                        for (int32_t qq = 1; qq <= trust; ++qq) {
+                            float nxt = qq < p.ell ? sig[order[qq]] : 0.f;
+                            if (qq == trust && !full) break;  // sigma_{q+1} not trusted
+                            if (nxt < (float)o.tol * s1) { q = qq; break; }
+                        }
+                    if (q < 0) {
+                        int32_t k2 = 2 * d.k;
+                        if (!full && k2 <= o.k_max && svd_bytes(d.k, d.st.m1, d.st.n1) < d.best_alt) {
+                            d.k = k2;
+                            next.push_back(who[pi]);
+                        } else {
+                            S.probes_failed++;
+                        }
+                        continue;
+                    }
+                    if (q > o.k_max || svd_bytes(q, d.st.m1, d.st.n1) >= d.best_alt) {
+                        S.probes_failed += q > o.k_max ? 1 : 0;
+                        continue;  // the SVD cannot win
+                    }
+                    d.q = q;
+                    FactorDesc f{};
+                    f.probe = (int32_t)pi;
+                    f.q = q;
+                    f.sel_off = (int64_t)sel.size();
+                    for (int32_t k = 0; k < q; ++k) sel.push_back(order[k]);
+                    f.u_off = fstage;
+                    fstage += (int64_t)(p.m1 + p.n1) * q;
+                    fds.push_back(f);
+                    fd_owner.push_back(who[pi]);
+                }
+                if (!fds.empty()) {
+                    auto buf = std::make_unique<dbuf<float>>();
+                    VF_TRY(buf->alloc(fstage));
+                    dbuf<FactorDesc> dfd;
+                    dbuf<int32_t> dsel;
+                    VF_TRY(dfd.upload(fds));
+                    VF_TRY(dsel.upload(sel));
+                    k_form_factors<<<(unsigned)fds.size(), 256, 0, st>>>(B.d_pd.p, dfd.p, dsel.p, B.Y.p, B.Z.p, B.small.p, buf->p);
+                    VF_TRY_CUDA(cudaGetLastError());
+                    VF_TRY_CUDA(cudaStreamSynchronize(st));
+                    int32_t bi = (int32_t)stage_bufs.size();
+                    for (size_t f = 0; f < fds.size(); ++f) {
+                        int32_t id = fd_owner[f];
+                        stage_ref[id] = StageRef{bi, fds[f].u_off};
+                        // keep the compacted lists of this candidate
+                        const ProbeDesc& p = B.pd[fds[f].probe];
+                        N[id].lists_off = (int64_t)lists_pool.size();
+                        lists_pool.insert(lists_pool.end(), B.lists.begin() + p.rows_off,
+                                          B.lists.begin() + p.rows_off + p.m1);
+                        lists_pool.insert(lists_pool.end(), B.lists.begin() + p.cols_off,
+                                          B.lists.begin() + p.cols_off + p.n1);
+                    }
+                    stage_bufs.push_back(std::move(buf));
+                }
+                pending.swap(next);
+            }
+            // decisions for this level
+            for (int32_t id : level) {
+                DNode& d = N[id];
+                if (h == 0 || d.kind == VF_BLK_ZERO) continue;
+                int64_t mm = t->count[d.I], nn = t->count[d.J];
+                int64_t bd = 4 * mm * nn, bc = csr_bytes(mm, d.st.nnz);
+                // candidates in tie order: dense < CSR < SVD < hierarchical
+                int32_t kind = VF_BLK_DENSE;
+                int64_t best = bd;
+                if (bc < best) { best = bc; kind = VF_BLK_CSR; }
+                if (d.q > 0 && stage_ref[id].buf >= 0) {
+                    int64_t bs = svd_bytes(d.q, d.st.m1, d.st.n1);
+                    if (bs < best) { best = bs; kind = VF_BLK_SVD; }
+                }
+                if (d.hier_bytes < best) { best = d.hier_bytes; kind = VF_BLK_HIER; }
+                if (kind == VF_BLK_HIER) {
+                    bool all_csr = true, all_dense = true, any = false;
+                    for (int32_t k = d.kid_begin; k < d.kid_end; ++k) {
+                        int32_t kk = Bd.kid_kind(Bd.kids[k]);
+                        if (kk == VF_BLK_ZERO) continue;
+                        any = true;
+                        all_csr = all_csr && kk == VF_BLK_CSR;
+                        all_dense = all_dense && kk == VF_BLK_DENSE;
+                    }
+                    if (any && all_csr) { kind = VF_BLK_CSR; best = bc; }
+                    else if (any && all_dense) { kind = VF_BLK_DENSE; best = bd; }
+                }
+                d.kind = kind;
+                d.bytes = best;
+            }
         }
-        // decisions for this level
-        for (int32_t id : level) {
-            DNode& d = N[id];
-            if (h == 0 || d.kind == VF_BLK_ZERO) continue;
-            int64_t mm = t->count[d.I], nn = t->count[d.J];
-            int64_t bd = 4 * mm * nn, bc = csr_bytes(mm, d.st.nnz);
-            // candidates in tie order: dense < CSR < SVD < hierarchical
-            int32_t kind = VF_BLK_DENSE;
-            int64_t best = bd;
-            if (bc < best) { best = bc; kind = VF_BLK_CSR; }
-            if (d.q > 0 && stage_ref[id].buf >= 0) {
-                int64_t bs = svd_bytes(d.q, d.st.m1, d.st.n1);
-                if (bs < best) { best = bs; kind = VF_BLK_SVD; }
-            }
-            if (d.hier_bytes < best) { best = d.hier_bytes; kind = VF_BLK_HIER; }
-            if (kind == VF_BLK_HIER) {
-                bool all_csr = true, all_dense = true, any = false;
-                for (int32_t k = d.kid_begin; k < d.kid_end; ++k) {
-                    int32_t kk = Bd.kid_kind(Bd.kids[k]);
-                    if (kk == VF_BLK_ZERO) continue;
-                    any = true;
-                    all_csr = all_csr && kk == VF_BLK_CSR;
-                    all_dense = all_dense && kk == VF_BLK_DENSE;
-                }
-                if (any && all_csr) { kind = VF_BLK_CSR; best = bc; }
-                else if (any && all_dense) { kind = VF_BLK_DENSE; best = bd; }
-            }
-            d.kind = kind;
-            d.bytes = best;
-        }
-    }
-    double t3 = now_seconds();
-    S.t_probe = t3 - t2;
+        t3 = now_seconds();
+        S.t_probe = t3 - t2;
 
-    // ---------------- flatten to stored blocks
-    std::vector<HBlock>& HB = H->h_blocks;
-    std::vector<int32_t> hb_node;  // DNode id (or -1 for an implicit leaf pair)
-    std::vector<Kid> stack(Bd.top_refs.rbegin(), Bd.top_refs.rend());
-    while (!stack.empty()) {
-        Kid k = stack.back();
-        stack.pop_back();
-        HBlock b{};
-        int32_t kind;
-        if (k.ref >= 0) {
-            const DNode& d = N[k.ref];
-            kind = d.kind;
-            if (kind == VF_BLK_HIER) {
-                S.nblocks[VF_BLK_HIER]++;
-                for (int32_t q = d.kid_end - 1; q >= d.kid_begin; --q) stack.push_back(Bd.kids[q]);
-                continue;
+        // ---------------- flatten to stored blocks
+        std::vector<Kid> stack(Bd.top_refs.rbegin(), Bd.top_refs.rend());
+        while (!stack.empty()) {
+            Kid k = stack.back();
+            stack.pop_back();
+            HBlock b{};
+            int32_t kind;
+            if (k.ref >= 0) {
+                const DNode& d = N[k.ref];
+                kind = d.kind;
+                if (kind == VF_BLK_HIER) {
+                    S.nblocks[VF_BLK_HIER]++;
+                    for (int32_t q = d.kid_end - 1; q >= d.kid_begin; --q) stack.push_back(Bd.kids[q]);
+                    continue;
+                }
+                b.I = d.I;
+                b.J = d.J;
+                b.q = kind == VF_BLK_SVD ? d.q : 0;
+                b.m1 = kind == VF_BLK_SVD ? d.st.m1 : (int32_t)d.st.nnz;
+                b.n1 = kind == VF_BLK_SVD ? d.st.n1 : 0;
+                hb_node.push_back(k.ref);
+            } else {
+                int64_t p = -1 - k.ref;
+                int64_t a = p / Bd.nleaves, bb = p - a * Bd.nleaves;
+                kind = Bd.leaf_pair_choice(p).first;
+                // leaf node ids: find from leaf index via first position
+                b.I = -1;
+                b.J = -1;
+                b.m1 = Bd.pnnz[p];
+                b.r0 = Bd.leaf_first[a];
+                b.m = Bd.leaf_count[a];
+                b.c0 = Bd.leaf_first[bb];
+                b.n = Bd.leaf_count[bb];
+                hb_node.push_back(-1);
             }
-            b.I = d.I;
-            b.J = d.J;
-            b.q = kind == VF_BLK_SVD ? d.q : 0;
-            b.m1 = kind == VF_BLK_SVD ? d.st.m1 : (int32_t)d.st.nnz;
-            b.n1 = kind == VF_BLK_SVD ? d.st.n1 : 0;
-            hb_node.push_back(k.ref);
-        } else {
-            int64_t p = -1 - k.ref;
-            int64_t a = p / Bd.nleaves, bb = p - a * Bd.nleaves;
-            kind = Bd.leaf_pair_choice(p).first;
-            // leaf node ids: find from leaf index via first position
-            b.I = -1;
-            b.J = -1;
-            b.m1 = Bd.pnnz[p];
-            b.r0 = Bd.leaf_first[a];
-            b.m = Bd.leaf_count[a];
-            b.c0 = Bd.leaf_first[bb];
-            b.n = Bd.leaf_count[bb];
-            hb_node.push_back(-1);
+            S.nblocks[kind]++;
+            if (kind == VF_BLK_ZERO) { hb_node.pop_back(); continue; }
+            b.kind = kind;
+            if (b.I >= 0) {
+                b.r0 = t->first[b.I];
+                b.m = t->count[b.I];
+                b.c0 = t->first[b.J];
+                b.n = t->count[b.J];
+            }
+            HB.push_back(b);
         }
-        S.nblocks[kind]++;
-        if (kind == VF_BLK_ZERO) { hb_node.pop_back(); continue; }
-        b.kind = kind;
-        if (b.I >= 0) {
-            b.r0 = t->first[b.I];
-            b.m = t->count[b.I];
-            b.c0 = t->first[b.J];
-            b.n = t->count[b.J];
-        }
-        HB.push_back(b);
     }
     // resolve leaf-pair node ids (for vf_hmat_blocks)
     {

@@ -22,20 +22,33 @@ struct HBlock {
     int64_t off_T;        // SVD: offset of its q-vector slot in the T buffer (per RHS column)
 };
 
-// Row-tile work item: the part of block `blk` that lies in the tile's rows.
+// Row-tile work item (32 bytes): the part of one stored block that lies in
+// a tile's rows, as one contiguous range of values.
+//  dense: cnt = tile rows, w = n, xoff = tree column c0, val = first value
+//         (row lr0 of the block); element e is row e / w, column e % w
+//  SVD:   cnt = compacted rows of U' in the tile, w = q, xoff = T slot,
+//         val = U' row u0, idx = aux offset of the row-id list at u0
+//  CSR:   cnt = tile rows, idx = aux offset of the row pointer of row lr0,
+//         idx2 = aux offset of the block's column indices, val = block values
 struct TileItem {
+    int32_t kind;
+    int32_t cnt;
+    int32_t w;
+    int32_t xoff;
+    int32_t idx;
+    int32_t idx2;
+    int64_t val;
     int32_t blk;
-    int32_t lr0;    // first row of the tile inside the block (dense/CSR)
-    int32_t u0, u1; // SVD: compacted-row range of the block inside the tile
+    int32_t pad;
 };
 
-// Phase-1 work item: rows [k0, k1) of an SVD block's V'.
+// Phase-1 work item: V' rows [j0, j1) of an SVD block, one warp.
 struct SvdChunk {
     int32_t blk;
-    int32_t k0, k1;
+    int32_t j0, j1;
     int32_t chunk;   // index of this chunk within its block
     int32_t nchunks; // chunks of the block
-    int32_t first_chunk_global;
+    int32_t first;   // slot of the block's first chunk in the partial buffer
 };
 
 }  // namespace vf
@@ -50,6 +63,8 @@ struct vf_hmat {
     std::vector<int32_t> h_perm;
     std::vector<int32_t> h_tile_first, h_tile_count;  // per row tile (tree leaf)
     std::vector<int32_t> h_tile_item_ptr;             // ntiles + 1
+    std::vector<int32_t> h_tile_order;                // launch order: heaviest tile first
+    int64_t n_part_slots = 0;                         // phase-1 partial slots (split blocks)
     std::vector<vf::TileItem> h_items;
     std::vector<vf::SvdChunk> h_chunks;
     std::vector<float> h_scale8;                      // FP8 per-block scale
@@ -66,7 +81,7 @@ struct vf_hmat {
     vf::dbuf<__nv_fp8_e4m3> val8;  // FP8 E4M3 copy (val / scale)
     vf::dbuf<float> scale8;        // per block
     vf::dbuf<int32_t> aux;
-    vf::dbuf<int32_t> tile_first, tile_count, tile_item_ptr;
+    vf::dbuf<int32_t> tile_first, tile_count, tile_item_ptr, tile_order;
     vf::dbuf<vf::TileItem> items;
     vf::dbuf<vf::SvdChunk> chunks;
     bool has_bf16 = false, has_fp8 = false;

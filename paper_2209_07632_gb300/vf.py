@@ -40,7 +40,8 @@ class PartitionOpts(ctypes.Structure):
 class AssembleOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("leaf_threshold", ctypes.c_int64), ("k0", ctypes.c_int32),
                 ("k_max", ctypes.c_int32), ("power_iters", ctypes.c_int32), ("verify", ctypes.c_int32),
-                ("precisions", ctypes.c_uint32), ("predictor", ctypes.c_void_p), ("seed", ctypes.c_uint64)]
+                ("precisions", ctypes.c_uint32), ("predictor", ctypes.c_void_p), ("seed", ctypes.c_uint64),
+                ("storage", ctypes.c_int32)]
 
 
 class AssembleStats(ctypes.Structure):
@@ -98,7 +99,9 @@ _SIGS = {
     "vf_hmat_blocks": ([_P, _P, _P], ctypes.c_int),
     "vf_hmat_bytes": ([_P, ctypes.c_int], _I64),
     "vf_apply": ([_P, ctypes.c_int, _P, _I64, _I32, _P, _I64, _P], ctypes.c_int),
+    "vf_apply_tree": ([_P, ctypes.c_int, _P, _I32, _P, _P], ctypes.c_int),
     "vf_solve": ([_P, _P, _P, _I64, _P, _I64, _I32, _P, _P, _P], ctypes.c_int),
+    "vf_solve_host": ([_P, _P, _P, _I64, _P, _I64, _I32, _P, _P, _P], ctypes.c_int),
     "vf_solve_batched": ([_P, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "vf_hmat_save": ([_P, ctypes.c_char_p], ctypes.c_int),
     "vf_hmat_load": ([ctypes.c_char_p, _I32, _P], ctypes.c_int),
@@ -268,14 +271,17 @@ def vf_tree_nodes(t: Tree) -> dict:
     return arrs
 
 
+STORAGE = {"compressed": 0, "dense": 1, "csr": 2}
+
+
 def vf_assemble(m: Mesh, t: Tree, tol: float = 1e-3, leaf_threshold: int = 4096, k0: int = 8, k_max: int = 128,
                 power_iters: int = 2, verify: bool = False, precisions=("fp32", "bf16"), predictor=None,
-                seed: int = 12345):
+                seed: int = 12345, storage: str = "compressed"):
     bits = 0
     for p in precisions:
         bits |= 1 << PREC[p]
     opts = AssembleOpts(tol, leaf_threshold, k0, k_max, power_iters, int(verify), bits,
-                        predictor.ptr if predictor is not None else None, seed)
+                        predictor.ptr if predictor is not None else None, seed, STORAGE[storage])
     st = AssembleStats()
     out = ctypes.c_void_p()
     _check(load().vf_assemble(m.ptr, t.ptr, ctypes.byref(opts), ctypes.byref(out), ctypes.byref(st)))
@@ -305,6 +311,15 @@ def vf_apply(h: HMat, X, Y, precision: str = "fp32", stream=None):
     return Y
 
 
+def vf_apply_tree(h: HMat, Xt, Yt, precision: str = "fp32", stream=None):
+    """The multiply alone on tree-ordered (R, N) tensors."""
+    n = h.n
+    R = 1 if Xt.dim() == 1 else Xt.shape[0]
+    _check(load().vf_apply_tree(h.ptr, PREC[precision], _dev_ptr(Xt, "Xt", n), R, _dev_ptr(Yt, "Yt", n),
+                                _stream(stream)))
+    return Yt
+
+
 def _solve_opts(rtol, max_iter, precision, refine, max_refine, inner_rtol, clamp, rho_uniform):
     return SolveOpts(rtol, max_iter, PREC[precision], int(refine), max_refine, inner_rtol, int(clamp),
                      float(rho_uniform))
@@ -328,6 +343,31 @@ def vf_solve(h: HMat, E, B, rho=0.12, rtol: float = 1e-6, max_iter: int = 100, p
     st = SolveStats()
     _check(load().vf_solve(h.ptr, rho_ptr, _dev_ptr(E, "E", n), n, _dev_ptr(B, "B", n), n, R, ctypes.byref(opts),
                            ctypes.byref(st), _stream(stream)), allow=(VF_E_NOCONV,))
+    return st.as_dict()
+
+
+def vf_solve_host(h: HMat, E: np.ndarray, B: np.ndarray, rho=0.12, rtol: float = 1e-6, max_iter: int = 100,
+                  precision: str = "fp32", refine: bool = False, max_refine: int = 8, inner_rtol: float = 1e-3,
+                  clamp: bool = False, stream=None) -> dict:
+    """vf_solve on host arrays E, B of shape (R, N) float32 (C-contiguous,
+    ideally pinned); the copies run inside the call."""
+    n = h.n
+    if E.dtype != np.float32 or B.dtype != np.float32 or E.shape != B.shape or E.shape[-1] != n:
+        raise VFError(VF_E_INVAL, "E, B: float32 arrays of shape (R, N)")
+    if not (E.flags.c_contiguous and B.flags.c_contiguous):
+        raise VFError(VF_E_INVAL, "E, B must be C-contiguous")
+    R = 1 if E.ndim == 1 else E.shape[0]
+    rho_ptr = None
+    rho_u = 0.0
+    if isinstance(rho, (int, float)):
+        rho_u = float(rho)
+    else:
+        rho = np.ascontiguousarray(rho, dtype=np.float32)
+        rho_ptr = _np_ptr(rho)
+    opts = _solve_opts(rtol, max_iter, precision, refine, max_refine, inner_rtol, clamp, rho_u)
+    st = SolveStats()
+    _check(load().vf_solve_host(h.ptr, rho_ptr, _np_ptr(E), n, _np_ptr(B), n, R, ctypes.byref(opts),
+                                ctypes.byref(st), _stream(stream)), allow=(VF_E_NOCONV,))
     return st.as_dict()
 
 
