@@ -15,6 +15,8 @@
 //            registers, so Y is written once, in a fixed order.
 // The Jacobi update, the per-column residual partials and (for refinement)
 // the FP64-accumulated residual are fused into the phase-2 epilogue.
+#include <cuda/atomic>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -22,171 +24,242 @@
 #include <memory>
 #include <mutex>
 
+#include "vf_bulk.cuh"
 #include "vf_hmat.cuh"
 
 namespace vf {
 
 constexpr int kTileRows = 64;
 constexpr int kWarps = 8;
-constexpr int kChunkElems = 8192;  // V' values per phase-1 chunk (one warp)
 
-// ------------------------------------------------------------ value loads
-template <class T> __device__ __forceinline__ float ld(const T* p);
-template <> __device__ __forceinline__ float ld<float>(const float* p) { return __ldg(p); }
-template <> __device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat16* p) {
-    return __bfloat162float(__ldg(p));
-}
-template <> __device__ __forceinline__ float ld<__nv_fp8_e4m3>(const __nv_fp8_e4m3* p) {
-    __nv_fp8_e4m3 v;
-    v.__x = __ldg(reinterpret_cast<const unsigned char*>(p));
-    return float(v);
-}
 
 struct ApplyArgs {
-    const HBlock* blocks;
-    const int32_t* aux;
-    const float* scale;        // per-block scale (FP8) or nullptr
     const int32_t* tile_first;
     const int32_t* tile_count;
-    const int32_t* tile_item_ptr;
-    const TileItem* items;
-    const SvdChunk* chunks;
+    const int32_t* tile_page_ptr;  // per (tile, warp): first page; ntiles * kWarps + 1 entries
     const int32_t* tile_order;
-    int64_t nparts;            // phase-1 partial slots per panel
-    int64_t n;                 // facets
-    int64_t nT;                // T slots per RHS column
-    int R;                     // total RHS columns
+    int64_t nparts;                // phase-1 partial slots per panel
+    int64_t n;                     // facets
+    int64_t nT;                    // T slots per RHS column
+    int R;                         // total RHS columns
 };
 
-// Both phases stream their data as flat, contiguous element ranges: the
-// lanes of a warp load consecutive values (fully coalesced), multiply by the
-// matching x (or T) entries, stage the products in a per-warp scratch of
-// 512 / RB elements, then sum whole rows (phase 2) or whole columns (phase 1)
-// out of the scratch in a fixed order.  Every sum therefore has one owner
-// and one order: results are bit-reproducible with no float atomics.
-// per-warp scratch: 512 products for all RHS panel widths
-template <int RB> struct Chunk {
-    static constexpr int p2 = 512 / RB;                 // phase 2 elements per pass
-    static constexpr int p1 = (512 / RB) < 128 ? 128 : 512 / RB;  // phase 1 (holds a whole V' row)
+// Both phases stream the matrix as pages (see vf_hmat.cuh) through per-warp
+// prefetch pipelines: lane 0 of each warp issues one bulk asynchronous copy
+// per page into one of kStages shared-memory stages (completion tracked by
+// an mbarrier per stage) while the warp computes on a page that has
+// arrived.  HBM latency is hidden by the copies in flight; records are read
+// from shared memory.  Every sum has one owner and one order, so results
+// are bit-reproducible with no float atomics:
+//  * dense slabs: lane r owns tile row r (and r + 32), x is loaded once per
+//    record and broadcast by shuffles;
+//  * CSR rows: lane r walks row r's nonzeros, 8 gathers in flight; a long
+//    row is split across lanes and reduced by a fixed butterfly;
+//  * SVD factors (row-major, rank q): a group of g = pow2ceil(min(q, 32))
+//    lanes shares one row, 32 / g rows per step, added by xor-shuffles.
+// Row sums go to per-warp row slots in shared memory; the CTA adds the
+// warps' slots in warp order.
+constexpr int kStages = 3;
+constexpr uint32_t kWaitLimit = 1u << 22;  // polls before a wait reports a timeout
+
+__device__ __forceinline__ int pow2ceil32(int q) {
+    int g = 1;
+    while (g < q && g < 32) g <<= 1;
+    return g;
+}
+
+template <class T> __device__ __forceinline__ float lds(const T* p);
+template <> __device__ __forceinline__ float lds<float>(const float* p) { return *p; }
+template <> __device__ __forceinline__ float lds<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+template <> __device__ __forceinline__ float lds<__nv_fp8_e4m3>(const __nv_fp8_e4m3* p) { return float(*p); }
+
+struct WarpPipe {
+    uint64_t bar[kStages];
+    __align__(16) unsigned char buf[kStages][kPage];
 };
 
-// row index of element e in rows of width w: (e + 0.5) / w is at least
-// 0.5 / w away from an integer and its FP32 error is below e / w * 2^-23,
-// so the truncation is exact for e < 2^22
-__device__ __forceinline__ int row_of(int e, float invw) { return (int)(((float)e + 0.5f) * invw); }
+struct PageArgs {
+    const unsigned char* pages;
+    const uint16_t* used;
+};
+
+__device__ __forceinline__ void issue_page(const PageArgs& pg, int64_t page, WarpPipe& wp, int s) {
+    const uint32_t bytes = ((uint32_t)pg.used[page] + 15u) & ~15u;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&wp.bar[s], bytes);
+    bulk_g2s(wp.buf[s], pg.pages + page * (int64_t)kPage, bytes, &wp.bar[s]);
+}
+
+__device__ __forceinline__ void pipe_init(WarpPipe& wp) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&wp.bar[s], 1);
+    mbar_init_fence();
+}
 
 // ------------------------------------------------------------ phase 1
-// T_b = V'_b^T X[cols_b] for one chunk of V' rows (one warp).  Input X: tree
-// order, column-major with leading dimension n, columns [p0, p0 + RB) of
-// the panel.  T: per panel RB x nT (column c at c * nT).  A block split into
-// several chunks writes chunk partials; the last chunk to finish (atomic
+// T_b = V'_b^T X[cols_b] from phase-1 records.  Input X: tree order,
+// column-major with leading dimension n, columns [p0, p0 + RB) of the
+// panel.  T: per panel RB x nT (column c at c * nT).  A block split into
+// several records writes chunk partials; the last chunk to finish (atomic
 // ticket) adds them in chunk order.
 template <class T, int RB>
-__device__ __forceinline__ void phase1_warp(const ApplyArgs& a, const T* __restrict__ val, const float* X,
-                                            float* __restrict__ Tbuf, float* __restrict__ part,
-                                            int* __restrict__ counters, int ci, int panel, float* scr) {
+__device__ __forceinline__ void p1_record(const ApplyArgs& a, const float* X, const unsigned char* rec,
+                                          float* __restrict__ Tbuf, float* __restrict__ part,
+                                          int* __restrict__ counters, int panel) {
     const int lane = threadIdx.x & 31;
-    const SvdChunk ch = a.chunks[ci];
-    const HBlock b = a.blocks[ch.blk];
-    const int q = b.q;
+    const uint32_t* h = reinterpret_cast<const uint32_t*>(rec);
+    const int nrows = (int)(h[0] >> 8), q = (int)h[1], offT = (int)h[2];
+    const float sc = __uint_as_float(h[3]);
+    const int chunk = (int)h[4], nch = (int)h[5], first = (int)h[6];
+    const int32_t* sC = reinterpret_cast<const int32_t*>(rec + kP1Hdr);
+    const T* sV = reinterpret_cast<const T*>(rec + kP1Hdr + 4 * nrows);
     const int p0 = panel * RB;
-    const T* Vp = val + b.off_val + (int64_t)b.m1 * q;
-    const int32_t* cols = a.aux + b.off_aux + b.m1;
-    const float sc = a.scale ? a.scale[ch.blk] : 1.f;
-    constexpr int kC = Chunk<RB>::p1;
-    const int rows_per = kC / q;  // q <= 128 <= kC
-    const float invq = 1.f / (float)q;
-    float tk[4][RB];
+    const int64_t panel_T = (int64_t)panel * RB * a.nT;
+    const int g = pow2ceil32(q);
+    const int step = 32 / g;
+    const int sub = lane / g, kk = lane - sub * g;
+    const int nk = (q + 31) / 32;
+    float acc[4][RB];
 #pragma unroll
     for (int t = 0; t < 4; ++t)
 #pragma unroll
-        for (int c = 0; c < RB; ++c) tk[t][c] = 0.f;
-    for (int j0 = ch.j0; j0 < ch.j1; j0 += rows_per) {
-        const int nr = min(rows_per, ch.j1 - j0);
-        const int L = nr * q;
-        const T* src = Vp + (int64_t)j0 * q;
-        float v[kC / 32];
-        int jl[kC / 32];
+        for (int c = 0; c < RB; ++c) acc[t][c] = 0.f;
+    // x of all rows (<= 128) gathered at once: lane l holds rows l + 32 t
+    float xr[4][RB];
 #pragma unroll
-        for (int i = 0; i < kC / 32; ++i) {
-            int e = lane + 32 * i;
-            v[i] = e < L ? ld(src + e) : 0.f;
-            jl[i] = e < L ? row_of(e, invq) : 0;
-        }
+    for (int t = 0; t < 4; ++t) {
+        const int j = lane + 32 * t;
+        const int col = j < nrows ? sC[j] : 0;
 #pragma unroll
-        for (int i = 0; i < kC / 32; ++i) {
-            int e = lane + 32 * i;
-            if (e < L) {
-                int col = __ldg(cols + j0 + jl[i]);
+        for (int c = 0; c < RB; ++c)
+            xr[t][c] = (j < nrows && p0 + c < a.R) ? __ldg(X + (int64_t)(p0 + c) * a.n + col) : 0.f;
+    }
+    if (q <= 32) {
+        // one k per lane: lane (sub, kk) takes rows sub, sub + step, ...
+        const bool kin = kk < q;
 #pragma unroll
-                for (int c = 0; c < RB; ++c) {
-                    float x = (p0 + c < a.R) ? __ldg(X + (int64_t)(p0 + c) * a.n + col) : 0.f;
-                    scr[c * kC + e] = v[i] * x;
+        for (int tj = 0; tj < 4; ++tj) {
+            if (32 * tj >= nrows) break;
+            const int jend = min(32 * tj + 32, nrows);
+#pragma unroll 2
+            for (int j0 = 32 * tj; j0 < jend; j0 += step) {
+                const int j = j0 + sub;
+                float x[RB];
+#pragma unroll
+                for (int c = 0; c < RB; ++c) x[c] = __shfl_sync(0xffffffffu, xr[tj][c], j & 31);
+                if (kin && j < nrows) {
+                    const float v = lds(sV + j * q + kk);
+#pragma unroll
+                    for (int c = 0; c < RB; ++c) acc[0][c] = fmaf(v, x[c], acc[0][c]);
                 }
             }
         }
-        __syncwarp();
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            int k = lane + 32 * t;
-            if (k < q)
-                for (int r = 0; r < nr; ++r)
-#pragma unroll
-                    for (int c = 0; c < RB; ++c) tk[t][c] += scr[c * kC + r * q + k];
-        }
-        __syncwarp();
-    }
-    const int64_t panel_T = (int64_t)panel * RB * a.nT;
-    if (ch.nchunks == 1) {
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            int k = lane + 32 * t;
-            if (k < q)
-#pragma unroll
-                for (int c = 0; c < RB; ++c) Tbuf[panel_T + (int64_t)c * a.nT + b.off_T + k] = tk[t][c] * sc;
-        }
-        return;
-    }
-    float* mypart = part + ((int64_t)panel * a.nparts + ch.first + ch.chunk) * (RB * 128);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        int k = lane + 32 * t;
-        if (k < q)
-#pragma unroll
-            for (int c = 0; c < RB; ++c) mypart[c * 128 + k] = tk[t][c];
-    }
-    __threadfence();
-    __syncwarp();
-    int last = 0;
-    if (lane == 0) last = atomicAdd(counters + (int64_t)panel * a.nT + b.off_T, 1) == ch.nchunks - 1;
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (!last) return;
-    __threadfence();
-    const float* pb = part + ((int64_t)panel * a.nparts + ch.first) * (RB * 128);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        int k = lane + 32 * t;
-        if (k < q)
+    } else {
+        for (int j = 0; j < nrows; ++j) {  // q > 32: the whole warp shares each row
+            const int tj = j >> 5;
+            float x[RB];
 #pragma unroll
             for (int c = 0; c < RB; ++c) {
-                float s = 0.f;
-                for (int cc = 0; cc < ch.nchunks; ++cc) s += __ldcg(pb + (int64_t)cc * (RB * 128) + c * 128 + k);
-                Tbuf[panel_T + (int64_t)c * a.nT + b.off_T + k] = s * sc;
+                float xs = xr[0][c];
+                if (tj == 1) xs = xr[1][c];
+                else if (tj == 2) xs = xr[2][c];
+                else if (tj == 3) xs = xr[3][c];
+                x[c] = __shfl_sync(0xffffffffu, xs, j & 31);
             }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int k = lane + 32 * t;
+                if (t < nk && k < q) {
+                    const float v = lds(sV + j * q + k);
+#pragma unroll
+                    for (int c = 0; c < RB; ++c) acc[t][c] = fmaf(v, x[c], acc[t][c]);
+                }
+            }
+        }
     }
-    if (lane == 0) counters[(int64_t)panel * a.nT + b.off_T] = 0;
+    for (int o = 16; o >= g; o >>= 1)
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int c = 0; c < RB; ++c) acc[t][c] += __shfl_xor_sync(0xffffffffu, acc[t][c], o);
+    if (nch == 1) {
+        if (sub == 0)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int k = kk + 32 * t;
+                if (t < nk && k < q)
+#pragma unroll
+                    for (int c = 0; c < RB; ++c) Tbuf[panel_T + (int64_t)c * a.nT + offT + k] = acc[t][c] * sc;
+            }
+        return;
+    }
+    float* mypart = part + ((int64_t)panel * a.nparts + first + chunk) * (RB * 128);
+    if (sub == 0)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int k = kk + 32 * t;
+            if (t < nk && k < q)
+#pragma unroll
+                for (int c = 0; c < RB; ++c) mypart[c * 128 + k] = acc[t][c];
+        }
+    // ticket: the partial stores (ordered before lane 0 by __syncwarp) are
+    // released with the increment; the last chunk acquires all of them
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) {
+        cuda::atomic_ref<int, cuda::thread_scope_device> ticket(counters[(int64_t)panel * a.nT + offT]);
+        last = ticket.fetch_add(1, cuda::memory_order_acq_rel) == nch - 1;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __syncwarp();
+    const float* pb = part + ((int64_t)panel * a.nparts + first) * (RB * 128);
+    for (int k = lane; k < q; k += 32)
+#pragma unroll
+        for (int c = 0; c < RB; ++c) {
+            float sum = 0.f;
+            for (int cc = 0; cc < nch; ++cc) sum += __ldcg(pb + (int64_t)cc * (RB * 128) + c * 128 + k);
+            Tbuf[panel_T + (int64_t)c * a.nT + offT + k] = sum * sc;
+        }
+    if (lane == 0) counters[(int64_t)panel * a.nT + offT] = 0;
 }
 
 template <class T, int RB>
-__global__ void __launch_bounds__(256, RB <= 2 ? 4 : 2) k_phase1(ApplyArgs a, const T* __restrict__ val,
-                                                                const float* const* xsel, const float* xd,
-                                                                float* __restrict__ Tbuf, float* __restrict__ part,
-                                                                int* __restrict__ counters, int nchunks) {
-    __shared__ float scr[kWarps][RB * Chunk<RB>::p1];
-    const int warp = threadIdx.x >> 5;
-    const int ci = blockIdx.x * kWarps + warp;
-    if (ci >= nchunks) return;
-    phase1_warp<T, RB>(a, val, xsel ? *xsel : xd, Tbuf, part, counters, ci, blockIdx.y, scr[warp]);
+__global__ void __launch_bounds__(256) k_phase1(ApplyArgs a, PageArgs pg, int64_t npages, const float* const* xsel,
+                                                const float* xd, float* __restrict__ Tbuf, float* __restrict__ part,
+                                                int* __restrict__ counters, int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WarpPipe* pipes = reinterpret_cast<WarpPipe*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpPipe& wp = pipes[warp];
+    const float* X = xsel ? *xsel : xd;
+    const int64_t wstride = (int64_t)gridDim.x * kWarps;
+    const int64_t p_first = (int64_t)blockIdx.x * kWarps + warp;
+    if (lane == 0) {
+        pipe_init(wp);
+        for (int s = 0; s < kStages; ++s)
+            if (p_first + s * wstride < npages) issue_page(pg, p_first + s * wstride, wp, s);
+    }
+    __syncwarp();
+    int n = 0;
+    for (int64_t p = p_first; p < npages; p += wstride, ++n) {
+        const int s = n % kStages;
+        // warp-uniform decision: a lane that gave up makes the whole warp stop
+        if (!__all_sync(0xffffffffu, mbar_wait(&wp.bar[s], (uint32_t)((n / kStages) & 1), kWaitLimit))) {
+            if (lane == 0) atomicExch(status, VF_E_TIMEOUT);
+            return;
+        }
+        const unsigned char* page = wp.buf[s];
+        const int nrec = (int)reinterpret_cast<const uint32_t*>(page)[0];
+        uint32_t off = kPageHdr;
+        for (int r = 0; r < nrec; ++r) {
+            const uint32_t* h = reinterpret_cast<const uint32_t*>(page + off);
+            const uint32_t sz = rec_bytes(REC_P1, (int)(h[0] >> 8), (int)h[1], (int)sizeof(T));
+            p1_record<T, RB>(a, X, page + off, Tbuf, part, counters, blockIdx.y);
+            off += sz;
+        }
+        __syncwarp();
+        if (lane == 0 && p + kStages * wstride < npages) issue_page(pg, p + kStages * wstride, wp, s);
+    }
 }
 
 // ------------------------------------------------------------ phase 2
@@ -201,102 +274,158 @@ struct SweepIO {
     const float* rho;          // tree order, n
     double* colpart;           // per (tile, column): sum of squares
     int64_t ntiles;
+    int* status;               // VF_E_TIMEOUT if a wait gave up
 };
 
-// One tile item, processed by one warp into the warp's row accumulators.
-template <class T, int RB, class acc_t>
-__device__ __forceinline__ void item_warp(const ApplyArgs& a, const T* __restrict__ val, const float* X,
-                                          const float* Tp, const TileItem& it, int tf, float* scr, acc_t* acc) {
+// A column-major slab (cnt <= 64 rows x w <= 128 columns, element (r, k) at
+// k * cnt + r) times an x slice: lane r owns slab row r (and r + 32); the x
+// slice is loaded once (x[k] by lane k % 32) and broadcast by shuffles.
+// Dense records read x from X, SVD records from T (U' stored as a slab, its
+// rows scattered over the tile through `rows8`).
+template <class T, int RB, class acc_t, bool SVD>
+__device__ __forceinline__ void slab_compute(const ApplyArgs& a, const float* xsrc, int64_t xstride,
+                                             const T* __restrict__ sA, int cnt, int w, int xo,
+                                             const unsigned char* rows8, float sc, acc_t* slot) {
     const int lane = threadIdx.x & 31;
-    const float sc = a.scale ? a.scale[it.blk] : 1.f;
     const int p0 = blockIdx.y * RB;
-    int L, base = 0;
-    const T* src;
-    const int32_t* cj = nullptr;
-    if (it.kind == VF_BLK_CSR) {
-        base = a.aux[it.idx];
-        L = a.aux[it.idx + it.cnt] - base;
-        src = val + it.val + base;
-        cj = a.aux + it.idx2 + base;
-    } else {
-        L = it.cnt * it.w;
-        src = val + it.val;
+    float xr[4][RB];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int k = lane + 32 * t;
+#pragma unroll
+        for (int c = 0; c < RB; ++c)
+            xr[t][c] = (k < w && p0 + c < a.R) ? __ldg(xsrc + (int64_t)c * xstride + xo + k) : 0.f;
     }
-    const float invw = it.kind == VF_BLK_CSR ? 0.f : 1.f / (float)it.w;
-    const bool wide = (int64_t)it.cnt * it.w >= (1 << 22);  // row_of is exact below 2^22 elements
-    constexpr int kC = Chunk<RB>::p2;
-    for (int cs = 0; cs < L; cs += kC) {
-        const int Lc = min(kC, L - cs);
-        float v[kC / 32];
-        int xi[kC / 32];
+    float q0[RB], q1[RB];
 #pragma unroll
-        for (int i = 0; i < kC / 32; ++i) {
-            int e = lane + 32 * i;
-            v[i] = e < Lc ? ld(src + cs + e) : 0.f;
+    for (int c = 0; c < RB; ++c) q0[c] = q1[c] = 0.f;
+    const bool h0 = lane < cnt;
+    if (cnt <= 32) {
+        const T* col = sA + lane;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (32 * t >= w) break;
+            const int kmax = min(32, w - 32 * t);
+#pragma unroll 4
+            for (int kl = 0; kl < kmax; ++kl) {
+                const float v0 = h0 ? lds(col + (32 * t + kl) * cnt) : 0.f;
+#pragma unroll
+                for (int c = 0; c < RB; ++c) q0[c] = fmaf(v0, __shfl_sync(0xffffffffu, xr[t][c], kl), q0[c]);
+            }
         }
+    } else {
+        const bool h1 = lane + 32 < cnt;
 #pragma unroll
-        for (int i = 0; i < kC / 32; ++i) {
-            int e = cs + lane + 32 * i;
-            if (it.kind == VF_BLK_CSR) xi[i] = (lane + 32 * i < Lc) ? __ldg(cj + e) : 0;
-            else xi[i] = it.xoff + (e - (wide ? e / it.w : row_of(e, invw)) * it.w);
-        }
-#pragma unroll
-        for (int i = 0; i < kC / 32; ++i) {
-            int e = lane + 32 * i;
-            if (e < Lc) {
+        for (int t = 0; t < 4; ++t) {
+            if (32 * t >= w) break;
+            const int kmax = min(32, w - 32 * t);
+#pragma unroll 2
+            for (int kl = 0; kl < kmax; ++kl) {
+                const int k = 32 * t + kl;
+                const float v0 = lds(sA + k * cnt + lane);
+                const float v1 = h1 ? lds(sA + k * cnt + lane + 32) : 0.f;
 #pragma unroll
                 for (int c = 0; c < RB; ++c) {
-                    float x;
-                    if (it.kind == VF_BLK_SVD) x = Tp[(int64_t)c * a.nT + xi[i]];
-                    else x = (p0 + c < a.R) ? __ldg(X + (int64_t)(p0 + c) * a.n + xi[i]) : 0.f;
-                    scr[c * kC + e] = v[i] * x;
+                    const float x = __shfl_sync(0xffffffffu, xr[t][c], kl);
+                    q0[c] = fmaf(v0, x, q0[c]);
+                    q1[c] = fmaf(v1, x, q1[c]);
                 }
             }
         }
-        __syncwarp();
-        // whole-row sums out of the scratch: item row j by lane j (and j + 32)
+        if (h1) {
+            const int d1 = SVD ? rows8[lane + 32] : lane + 32;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            int j = lane + 32 * h;
-            if (j < it.cnt) {
-                int rs, re;
-                if (it.kind == VF_BLK_CSR) {
-                    rs = a.aux[it.idx + j] - base;
-                    re = a.aux[it.idx + j + 1] - base;
-                } else {
-                    rs = j * it.w;
-                    re = rs + it.w;
-                }
-                int lo = max(rs, cs) - cs, hi = min(re, cs + Lc) - cs;
-                if (lo < hi) {
-                    int dest = it.kind == VF_BLK_SVD ? a.aux[it.idx + j] - tf : j;
-#pragma unroll
-                    for (int c = 0; c < RB; ++c) {
-                        float s = 0.f;
-                        for (int k = lo; k < hi; ++k) s += scr[c * kC + k];
-                        acc[dest * RB + c] += (acc_t)(s * sc);
-                    }
-                }
-            }
+            for (int c = 0; c < RB; ++c) slot[d1 * RB + c] += (acc_t)(q1[c] * sc);
         }
-        __syncwarp();
+    }
+    if (h0) {
+        const int d0 = SVD ? rows8[lane] : lane;
+#pragma unroll
+        for (int c = 0; c < RB; ++c) slot[d0 * RB + c] += (acc_t)(q0[c] * sc);
     }
 }
 
-// One CTA per row tile (heaviest first) and RHS panel.  Warp w takes the
-// tile's items w, w + 8, ... in order; the warps' row accumulators are then
-// added in warp order, and the epilogue applies the mode.
+// One record into the warp's row slots (slot[r * RB + c]); returns its size.
+template <class T, int RB, class acc_t>
+__device__ __forceinline__ uint32_t rec_compute(const ApplyArgs& a, const float* X, const float* Tp,
+                                                const unsigned char* rec, acc_t* slot) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t* h = reinterpret_cast<const uint32_t*>(rec);
+    const int kind = (int)(h[0] & 0xffu), cnt = (int)(h[0] >> 8), w = (int)h[1], xo = (int)h[2];
+    const float sc = __uint_as_float(h[3]);
+    const int p0 = blockIdx.y * RB;
+    const unsigned char* body = rec + kRecHdr;
+    if (kind == REC_DENSE) {
+        slab_compute<T, RB, acc_t, false>(a, X + (int64_t)p0 * a.n, a.n, reinterpret_cast<const T*>(body), cnt, w,
+                                          xo, nullptr, sc, slot);
+        return rec_bytes(REC_DENSE, cnt, w, (int)sizeof(T));
+    }
+    if (kind == REC_SVD) {
+        slab_compute<T, RB, acc_t, true>(a, Tp, a.nT, reinterpret_cast<const T*>(body + pad4((uint32_t)cnt)), cnt,
+                                         w, xo, body, sc, slot);
+        return rec_bytes(REC_SVD, cnt, w, (int)sizeof(T));
+    }
+    if (kind == REC_CSR) {
+        const int32_t* sPtr = reinterpret_cast<const int32_t*>(body);
+        const int32_t* sCol = sPtr + cnt + 1;
+        const T* sA = reinterpret_cast<const T*>(sCol + w);
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int r = lane + 32 * hh;
+            if (r >= cnt) continue;
+            const int k0 = sPtr[r], k1 = sPtr[r + 1];
+            float q[RB];
+#pragma unroll
+            for (int c = 0; c < RB; ++c) q[c] = 0.f;
+#pragma unroll 2
+            for (int k = k0; k < k1; ++k) {
+                const float v = lds(sA + k);
+                const int col = sCol[k];
+#pragma unroll
+                for (int c = 0; c < RB; ++c)
+                    if (p0 + c < a.R) q[c] = fmaf(v, __ldg(X + (int64_t)(p0 + c) * a.n + col), q[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < RB; ++c) slot[(xo + r) * RB + c] += (acc_t)(q[c] * sc);
+        }
+        return rec_bytes(REC_CSR, cnt, w, (int)sizeof(T));
+    }
+    // a long CSR row shared by the lanes, reduced by a fixed butterfly
+    const int32_t* sCol = reinterpret_cast<const int32_t*>(body);
+    const T* sA = reinterpret_cast<const T*>(sCol + w);
+    float q[RB];
+#pragma unroll
+    for (int c = 0; c < RB; ++c) q[c] = 0.f;
+    for (int k = lane; k < w; k += 32) {
+        const float v = lds(sA + k);
+        const int col = sCol[k];
+#pragma unroll
+        for (int c = 0; c < RB; ++c)
+            if (p0 + c < a.R) q[c] = fmaf(v, __ldg(X + (int64_t)(p0 + c) * a.n + col), q[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < RB; ++c)
+        for (int o = 16; o > 0; o >>= 1) q[c] += __shfl_xor_sync(0xffffffffu, q[c], o);
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < RB; ++c) slot[xo * RB + c] += (acc_t)(q[c] * sc);
+    return rec_bytes(REC_CSR_LONG, cnt, w, (int)sizeof(T));
+}
+
+// One CTA per row tile (heaviest first) and RHS panel.  Warp w streams the
+// tile's pages [ptr[w], ptr[w+1]) (balanced at build time) through its
+// prefetch pipeline; the warps' row slots are then added in warp order, and
+// the epilogue applies the mode.
 template <class T, int RB, int MODE>
-__global__ void __launch_bounds__(256, RB <= 2 ? 4 : 2) k_phase2(ApplyArgs a, const T* __restrict__ val,
-                                                                const float* __restrict__ Tbuf, SweepIO io) {
+__global__ void __launch_bounds__(256) k_phase2(ApplyArgs a, PageArgs pg, const float* __restrict__ Tbuf,
+                                                SweepIO io) {
     using acc_t = typename std::conditional<MODE == MODE_RESID, double, float>::type;
-    // dynamic shared memory: acc[kWarps][kTileRows * RB] (acc_t), colsum[kWarps][RB]
-    // (double), scr[kWarps][RB * chunk] (float)
+    // dynamic shared memory: pipes[kWarps], slots[kWarps][kTileRows * RB] (acc_t), colsum[kWarps][RB]
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto acc = reinterpret_cast<acc_t(*)[kTileRows * RB]>(smem_raw);
-    auto colsum = reinterpret_cast<double(*)[RB]>(smem_raw + sizeof(acc_t) * kWarps * kTileRows * RB);
-    auto scr = reinterpret_cast<float(*)[RB * Chunk<RB>::p2]>(smem_raw + sizeof(acc_t) * kWarps * kTileRows * RB +
-                                                                sizeof(double) * kWarps * RB);
+    WarpPipe* pipes = reinterpret_cast<WarpPipe*>(smem_raw);
+    auto slots = reinterpret_cast<acc_t(*)[kTileRows * RB]>(smem_raw + sizeof(WarpPipe) * kWarps);
+    auto colsum = reinterpret_cast<double(*)[RB]>(smem_raw + sizeof(WarpPipe) * kWarps +
+                                                  sizeof(acc_t) * kWarps * kTileRows * RB);
     const int tile = a.tile_order[blockIdx.x];
     const int panel = blockIdx.y;
     const int p0 = panel * RB;
@@ -304,18 +433,32 @@ __global__ void __launch_bounds__(256, RB <= 2 ? 4 : 2) k_phase2(ApplyArgs a, co
     const int tf = a.tile_first[tile], tc = a.tile_count[tile];
     const float* X = io.xsel ? *io.xsel : io.xd;
     const float* Tp = Tbuf + (int64_t)panel * RB * a.nT;
-    for (int i = lane; i < kTileRows * RB; i += 32) acc[warp][i] = 0;
-    __syncwarp();
-    const int i0 = a.tile_item_ptr[tile], i1 = a.tile_item_ptr[tile + 1];
-    int ii = i0 + warp;
-    TileItem nxt;
-    if (ii < i1) nxt = a.items[ii];
-    for (; ii < i1; ii += kWarps) {
-        const TileItem it = nxt;
-        if (ii + kWarps < i1) nxt = a.items[ii + kWarps];  // prefetch the next descriptor
-        item_warp<T, RB, acc_t>(a, val, X, Tp, it, tf, scr[warp], acc[warp]);
+    WarpPipe& wp = pipes[warp];
+    acc_t* slot = slots[warp];
+    for (int i = lane; i < kTileRows * RB; i += 32) slot[i] = 0;
+    const int pa = a.tile_page_ptr[tile * kWarps + warp], pb = a.tile_page_ptr[tile * kWarps + warp + 1];
+    if (lane == 0) {
+        pipe_init(wp);
+        for (int s = 0; s < kStages && pa + s < pb; ++s) issue_page(pg, pa + s, wp, s);
     }
+    __syncwarp();
+    bool ok = true;
+    for (int p = pa, n = 0; p < pb; ++p, ++n) {
+        const int s = n % kStages;
+        if (!__all_sync(0xffffffffu, mbar_wait(&wp.bar[s], (uint32_t)((n / kStages) & 1), kWaitLimit))) {
+            ok = false;  // warp-uniform: a lane that gave up makes the whole warp stop
+            break;
+        }
+        const unsigned char* page = wp.buf[s];
+        const int nrec = (int)reinterpret_cast<const uint32_t*>(page)[0];
+        uint32_t off = kPageHdr;
+        for (int r = 0; r < nrec; ++r) off += rec_compute<T, RB, acc_t>(a, X, Tp, page + off, slot);
+        __syncwarp();
+        if (lane == 0 && p + kStages < pb) issue_page(pg, p + kStages, wp, s);
+    }
+    if (!ok && lane == 0) atomicExch(io.status, VF_E_TIMEOUT);
     __syncthreads();
+    (void)tf;
     double mysum[RB];
 #pragma unroll
     for (int c = 0; c < RB; ++c) mysum[c] = 0.0;
@@ -325,18 +468,18 @@ __global__ void __launch_bounds__(256, RB <= 2 ? 4 : 2) k_phase2(ApplyArgs a, co
         if (p0 + c >= a.R) continue;
         acc_t y = 0;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) y += acc[w][r * RB + c];
+        for (int w = 0; w < kWarps; ++w) y += slots[w][r * RB + c];
         const int64_t p = tf + r;
         const int64_t o = (int64_t)(p0 + c) * a.n + p;
         if (MODE == MODE_APPLY) {
             Y[o] = (float)y;
         } else if (MODE == MODE_JACOBI) {
             float bn = io.E[o] + io.rho[p] * (float)y;
-            float d = bn - X[o];
+            float dd = bn - X[o];
             Y[o] = bn;
 #pragma unroll
             for (int cc = 0; cc < RB; ++cc)
-                if (cc == c) mysum[cc] += (double)d * d;
+                if (cc == c) mysum[cc] += (double)dd * dd;
         } else {
             double rr = (double)io.E[o] - (double)X[o] + (double)io.rho[p] * (double)y;
             Y[o] = (float)rr;
@@ -346,7 +489,6 @@ __global__ void __launch_bounds__(256, RB <= 2 ? 4 : 2) k_phase2(ApplyArgs a, co
         }
     }
     if (MODE != MODE_APPLY) {
-        // per-column sums: warp butterfly, then warps in order
 #pragma unroll
         for (int c = 0; c < RB; ++c)
             for (int o = 16; o > 0; o >>= 1) mysum[c] += __shfl_xor_sync(0xffffffffu, mysum[c], o);
@@ -355,11 +497,85 @@ __global__ void __launch_bounds__(256, RB <= 2 ? 4 : 2) k_phase2(ApplyArgs a, co
             for (int c = 0; c < RB; ++c) colsum[warp][c] = mysum[c];
         __syncthreads();
         if (threadIdx.x < RB && p0 + (int)threadIdx.x < a.R) {
-            double s = 0;
-            for (int w = 0; w < kWarps; ++w) s += colsum[w][threadIdx.x];
-            io.colpart[(int64_t)(p0 + threadIdx.x) * io.ntiles + tile] = s;
+            double sm = 0;
+            for (int w = 0; w < kWarps; ++w) sm += colsum[w][threadIdx.x];
+            io.colpart[(int64_t)(p0 + threadIdx.x) * io.ntiles + tile] = sm;
         }
     }
+}
+
+// ------------------------------------------------------------ page packing
+// One warp per record: copies its data from the block pools into the page
+// pool (element type T), converting row pointers to record-local offsets and
+// SVD row ids to tile-local bytes.
+template <class T>
+__global__ void k_pack_pages(const RecSrc* __restrict__ recs, int64_t nrec, const T* __restrict__ val,
+                             const int32_t* __restrict__ aux, const float* __restrict__ scales,
+                             unsigned char* __restrict__ pool) {
+    const int64_t ri = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (ri >= nrec) return;
+    const RecSrc r = recs[ri];
+    unsigned char* dst = pool + r.dst;
+    uint32_t* h = reinterpret_cast<uint32_t*>(dst);
+    const float sc = scales ? scales[r.blk] : 1.f;
+    if (lane == 0) {
+        h[0] = (uint32_t)r.kind | ((uint32_t)r.cnt << 8);
+        h[1] = (uint32_t)r.w;
+        h[2] = (uint32_t)r.x;
+        h[3] = __float_as_uint(sc);
+        if (r.kind == REC_P1) {
+            h[4] = (uint32_t)r.chunk;
+            h[5] = (uint32_t)r.nchunks;
+            h[6] = (uint32_t)r.first;
+            h[7] = 0u;
+        }
+    }
+    if (r.kind == REC_DENSE) {
+        T* o = reinterpret_cast<T*>(dst + kRecHdr);
+        for (int e = lane; e < r.cnt * r.w; e += 32) o[e] = val[r.val + e];
+    } else if (r.kind == REC_SVD) {
+        unsigned char* rows = dst + kRecHdr;
+        for (int u = lane; u < r.cnt; u += 32) rows[u] = (unsigned char)(aux[r.idx + u] - r.tile_first);
+        // U' rows (row-major in the block pool) become a column-major slab
+        T* o = reinterpret_cast<T*>(dst + kRecHdr + pad4((uint32_t)r.cnt));
+        for (int e = lane; e < r.cnt * r.w; e += 32) {
+            const int u = e / r.w, k = e - u * r.w;
+            o[k * r.cnt + u] = val[r.val + e];
+        }
+    } else if (r.kind == REC_CSR) {
+        int32_t* ptr = reinterpret_cast<int32_t*>(dst + kRecHdr);
+        for (int i = lane; i <= r.cnt; i += 32) ptr[i] = aux[r.idx + i] - r.nz0;
+        int32_t* cols = ptr + r.cnt + 1;
+        T* o = reinterpret_cast<T*>(cols + r.w);
+        for (int e = lane; e < r.w; e += 32) {
+            cols[e] = aux[r.idx2 + r.nz0 + e];
+            o[e] = val[r.val + r.nz0 + e];
+        }
+    } else if (r.kind == REC_CSR_LONG) {
+        int32_t* cols = reinterpret_cast<int32_t*>(dst + kRecHdr);
+        T* o = reinterpret_cast<T*>(cols + r.w);
+        for (int e = lane; e < r.w; e += 32) {
+            cols[e] = aux[r.idx2 + r.nz0 + e];
+            o[e] = val[r.val + r.nz0 + e];
+        }
+    } else {  // phase 1
+        int32_t* cols = reinterpret_cast<int32_t*>(dst + kP1Hdr);
+        for (int j = lane; j < r.cnt; j += 32) cols[j] = aux[r.idx2 + j];
+        T* o = reinterpret_cast<T*>(dst + kP1Hdr + 4 * r.cnt);
+        for (int e = lane; e < r.cnt * r.w; e += 32) o[e] = val[r.val + e];
+    }
+}
+
+__global__ void k_page_headers(const int32_t* __restrict__ nrec, const uint16_t* __restrict__ used, int64_t npages,
+                               unsigned char* __restrict__ pool) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= npages) return;
+    uint32_t* h = reinterpret_cast<uint32_t*>(pool + p * (int64_t)kPage);
+    h[0] = (uint32_t)nrec[p];
+    h[1] = used[p];
+    h[2] = 0u;
+    h[3] = 0u;
 }
 
 // ------------------------------------------------------------ small kernels
@@ -466,7 +682,75 @@ __global__ void k_axpy_inplace(float* __restrict__ y, const float* __restrict__ 
 
 using namespace vf;
 
-// ============================================================ work lists
+// ============================================================ page plan
+namespace {
+
+// Pack records (already in their order) into pages of kPage bytes with FP32
+// record sizes, which bound the BF16/FP8 sizes; returns the page of each
+// record.  A record never straddles pages.
+struct PagePlan {
+    std::vector<int64_t> page_of;  // per record
+    int64_t npages = 0;
+};
+
+}  // namespace
+
+static vf_status build_pages(vf_hmat* H, std::vector<vf::RecSrc>& recs, const std::vector<int64_t>& page_of,
+                             int64_t npages, bool phase1) {
+    // per element size: offsets inside pages, page headers, pack kernel
+    const int es_of[3] = {4, 2, 1};
+    for (int prec = 0; prec < 3; ++prec) {
+        if (prec == VF_PREC_BF16 && !H->has_bf16) continue;
+        if (prec == VF_PREC_FP8 && !H->has_fp8) continue;
+        const int es = es_of[prec];
+        std::vector<int32_t> nrec(npages, 0);
+        std::vector<uint16_t> used(npages, (uint16_t)kPageHdr);
+        for (size_t i = 0; i < recs.size(); ++i) {
+            const int64_t pg = page_of[i];
+            recs[i].dst = pg * (int64_t)kPage + used[pg];
+            used[pg] = (uint16_t)(used[pg] + vf::rec_bytes(recs[i].kind, recs[i].cnt, recs[i].w, es));
+            nrec[pg]++;
+        }
+        vf::dbuf<unsigned char>& pool = phase1 ? H->p1pages[prec] : H->pages[prec];
+        vf::dbuf<uint16_t>& u = phase1 ? H->p1_used[prec] : H->page_used[prec];
+        VF_TRY(pool.alloc(std::max<int64_t>(npages, 1) * kPage));
+        VF_TRY_CUDA(cudaMemset(pool.p, 0, std::max<int64_t>(npages, 1) * kPage));
+        VF_TRY(u.upload(used));
+        if (npages == 0) continue;
+        vf::dbuf<int32_t> dn;
+        VF_TRY(dn.upload(nrec));
+        vf::dbuf<vf::RecSrc> dr;
+        VF_TRY(dr.upload(recs));
+        const int64_t nr = (int64_t)recs.size();
+        const unsigned grid = (unsigned)vf::ceil_div(nr * 32, 256);
+        if (nr) {
+            if (prec == VF_PREC_FP32)
+                vf::k_pack_pages<float><<<grid, 256>>>(dr.p, nr, H->val.p, H->aux.p, nullptr, pool.p);
+            else if (prec == VF_PREC_BF16)
+                vf::k_pack_pages<__nv_bfloat16><<<grid, 256>>>(dr.p, nr, H->val16.p, H->aux.p, nullptr, pool.p);
+            else
+                vf::k_pack_pages<__nv_fp8_e4m3><<<grid, 256>>>(dr.p, nr, H->val8.p, H->aux.p, H->scale8.p, pool.p);
+            VF_TRY_CUDA(cudaGetLastError());
+        }
+        vf::k_page_headers<<<(unsigned)vf::ceil_div(npages, 256), 256>>>(dn.p, u.p, npages, pool.p);
+        VF_TRY_CUDA(cudaGetLastError());
+        VF_TRY_CUDA(cudaDeviceSynchronize());
+    }
+    return VF_OK;
+}
+
+int64_t vf_hmat::bytes_payload(int prec) const {
+    // the stored representation: values (element size es) and index bytes
+    const int64_t es = prec == VF_PREC_FP32 ? 4 : prec == VF_PREC_BF16 ? 2 : 1;
+    int64_t b = 0;
+    for (const vf::HBlock& k : h_blocks) {
+        if (k.kind == VF_BLK_DENSE) b += es * k.m * (int64_t)k.n;
+        else if (k.kind == VF_BLK_CSR) b += (es + 4) * (int64_t)k.m1 + 4 * ((int64_t)k.m + 1);
+        else if (k.kind == VF_BLK_SVD) b += (es * k.q + 4) * ((int64_t)k.m1 + k.n1);
+    }
+    return b;
+}
+
 vf_status vf_hmat::upload_all() {
     // Row tiles are the tree leaves (h_tile_first/count, filled by assembly or
     // load); every block's row range is a union of consecutive tiles.
@@ -477,79 +761,193 @@ vf_status vf_hmat::upload_all() {
     std::vector<int32_t> tile_of_row(nf, -1);
     for (int64_t k = 0; k < ntiles; ++k)
         for (int32_t r = h_tile_first[k]; r < h_tile_first[k] + h_tile_count[k]; ++r) tile_of_row[r] = (int32_t)k;
-    std::vector<std::vector<vf::TileItem>> per(ntiles);
+    // ---- phase-2 records per tile (FP32 sizes; each fits a page)
+    const int64_t cap = kPage - kPageHdr;
+    std::vector<std::vector<vf::RecSrc>> per(ntiles);
     std::vector<int64_t> cost(ntiles, 0);
     for (size_t bi = 0; bi < B.size(); ++bi) {
         const vf::HBlock& b = B[bi];
         for (int32_t r = b.r0; r < b.r0 + b.m;) {
             const int32_t k = tile_of_row[r];
             const int32_t tf = h_tile_first[k], tc = h_tile_count[k], lr0 = tf - b.r0;
-            vf::TileItem it{};
-            it.kind = b.kind;
-            it.blk = (int32_t)bi;
-            int64_t work = 0;
+            vf::RecSrc rs{};
+            rs.blk = (int32_t)bi;
+            rs.tile_first = tf;
             if (b.kind == VF_BLK_DENSE) {
-                it.cnt = tc;
-                it.w = b.n;
-                it.xoff = b.c0;
-                it.val = b.off_val + (int64_t)lr0 * b.n;
-                work = (int64_t)tc * b.n;
+                // the tile's column-major slab, split into column ranges of <= 128
+                const int32_t per_cols = (int32_t)std::min<int64_t>(128, (cap - kRecHdr) / (4 * (int64_t)tc));
+                for (int32_t c0 = 0; c0 < b.n; c0 += per_cols) {
+                    rs.kind = vf::REC_DENSE;
+                    rs.cnt = tc;
+                    rs.w = std::min(per_cols, b.n - c0);
+                    rs.x = b.c0 + c0;
+                    rs.val = b.off_val + (int64_t)lr0 * b.n + (int64_t)c0 * tc;
+                    per[k].push_back(rs);
+                }
             } else if (b.kind == VF_BLK_CSR) {
-                it.cnt = tc;
-                it.idx = (int32_t)(b.off_aux + lr0);
-                it.idx2 = (int32_t)(b.off_aux + b.m + 1);
-                it.val = b.off_val;
-                work = haux[b.off_aux + lr0 + tc] - haux[b.off_aux + lr0];
+                const int32_t* rp = haux.data() + b.off_aux;
+                rs.idx2 = (int32_t)(b.off_aux + b.m + 1);
+                rs.val = b.off_val;
+                int32_t i = 0;
+                while (i < tc) {
+                    const int32_t row = lr0 + i;
+                    const int64_t nz_row = rp[row + 1] - rp[row];
+                    if (vf::rec_bytes(vf::REC_CSR, 1, (int)nz_row, 4) > cap) {
+                        // a long row: lanes share it, in pieces that fit a page
+                        const int32_t piece = (int32_t)((cap - kRecHdr) / 8);
+                        for (int64_t z = rp[row]; z < rp[row + 1]; z += piece) {
+                            vf::RecSrc lr = rs;
+                            lr.kind = vf::REC_CSR_LONG;
+                            lr.cnt = 1;
+                            lr.x = i;
+                            lr.nz0 = (int32_t)z;
+                            lr.w = (int32_t)std::min<int64_t>(piece, rp[row + 1] - z);
+                            per[k].push_back(lr);
+                        }
+                        ++i;
+                        continue;
+                    }
+                    int32_t j = i + 1;
+                    while (j < tc && vf::rec_bytes(vf::REC_CSR, j + 1 - i, rp[lr0 + j + 1] - rp[lr0 + i], 4) <= cap)
+                        ++j;
+                    vf::RecSrc cr = rs;
+                    cr.kind = vf::REC_CSR;
+                    cr.cnt = j - i;
+                    cr.x = i;
+                    cr.idx = (int32_t)(b.off_aux + lr0 + i);
+                    cr.nz0 = rp[lr0 + i];
+                    cr.w = rp[lr0 + j] - rp[lr0 + i];
+                    if (cr.w > 0) per[k].push_back(cr);
+                    i = j;
+                }
             } else {
                 const int32_t* rows = haux.data() + b.off_aux;
                 int32_t u0 = (int32_t)(std::lower_bound(rows, rows + b.m1, tf) - rows);
                 int32_t u1 = (int32_t)(std::lower_bound(rows, rows + b.m1, tf + tc) - rows);
-                it.cnt = u1 - u0;
-                it.w = b.q;
-                it.xoff = (int32_t)b.off_T;
-                it.val = b.off_val + (int64_t)u0 * b.q;
-                it.idx = (int32_t)(b.off_aux + u0);
-                work = (int64_t)it.cnt * b.q;
-            }
-            if (it.cnt > 0 && !(b.kind == VF_BLK_CSR && work == 0)) {
-                per[k].push_back(it);
-                cost[k] += work + 32;
+                const int32_t per_rows =
+                    (int32_t)std::max<int64_t>(1, (cap - kRecHdr - 4) / (4 * (int64_t)b.q + 1));
+                for (int32_t u = u0; u < u1; u += per_rows) {
+                    rs.kind = vf::REC_SVD;
+                    rs.cnt = std::min(per_rows, u1 - u);
+                    rs.w = b.q;
+                    rs.x = (int32_t)b.off_T;
+                    rs.val = b.off_val + (int64_t)u * b.q;
+                    rs.idx = (int32_t)(b.off_aux + u);
+                    per[k].push_back(rs);
+                }
             }
             r = tf + tc;
         }
     }
-    h_items.clear();
-    h_tile_item_ptr.assign(ntiles + 1, 0);
+    // each tile's records go to its warps by longest-processing-time first
+    // (records by decreasing bytes, each to the least-loaded warp, lowest
+    // index on ties); each warp's records are then packed into its own pages
+    std::vector<vf::RecSrc> recs;
+    std::vector<int64_t> page_of;
+    h_tile_page_ptr.assign(ntiles * kWarps + 1, 0);
+    int64_t npages = 0;
     for (int64_t k = 0; k < ntiles; ++k) {
-        h_tile_item_ptr[k] = (int32_t)h_items.size();
-        h_items.insert(h_items.end(), per[k].begin(), per[k].end());
+        std::vector<int32_t> ord(per[k].size());
+        for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int32_t)i;
+        auto bytes_of = [&](int32_t i) {
+            return (int64_t)vf::rec_bytes(per[k][i].kind, per[k][i].cnt, per[k][i].w, 4);
+        };
+        std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return bytes_of(x) > bytes_of(y); });
+        std::vector<std::vector<int32_t>> lists(kWarps);
+        int64_t load[kWarps] = {0};
+        for (int32_t i : ord) {
+            int best = 0;
+            for (int w = 1; w < kWarps; ++w)
+                if (load[w] < load[best]) best = w;
+            lists[best].push_back(i);
+            load[best] += bytes_of(i) + 64;
+        }
+        for (int w = 0; w < kWarps; ++w) {
+            h_tile_page_ptr[k * kWarps + w] = (int32_t)npages;
+            int64_t fill = cap + 1;  // forces a new page for the first record
+            for (int32_t i : lists[w]) {
+                const int64_t bsz = bytes_of(i);
+                if (fill + bsz > cap) {
+                    ++npages;
+                    fill = 0;
+                }
+                recs.push_back(per[k][i]);
+                page_of.push_back(npages - 1);
+                fill += bsz;
+            }
+            cost[k] += load[w] > cost[k] ? load[w] - cost[k] : 0;  // the slowest warp bounds the tile
+        }
     }
-    h_tile_item_ptr[ntiles] = (int32_t)h_items.size();
+    h_tile_page_ptr[ntiles * kWarps] = (int32_t)npages;
+    n_pages = npages;
+    VF_TRY(build_pages(this, recs, page_of, npages, false));
     h_tile_order.resize(ntiles);
     for (int64_t k = 0; k < ntiles; ++k) h_tile_order[k] = (int32_t)k;
     std::stable_sort(h_tile_order.begin(), h_tile_order.end(),
                      [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
-    // phase-1 chunks of at most kChunkElems V' values, largest first
-    h_chunks.clear();
+    // ---- phase-1 records: V' rows of each SVD block, <= 128 rows per record
+    std::vector<vf::RecSrc> p1;
     n_part_slots = 0;
     for (size_t bi = 0; bi < B.size(); ++bi) {
         if (B[bi].kind != VF_BLK_SVD) continue;
-        const int32_t rows = std::max<int32_t>(1, kChunkElems / B[bi].q);
-        const int32_t nch = (int32_t)vf::ceil_div(B[bi].n1, rows);
+        const vf::HBlock& b = B[bi];
+        const int32_t rows = (int32_t)std::min<int64_t>(128, std::max<int64_t>(1, (cap - kP1Hdr) / (4 * (int64_t)b.q + 4)));
+        const int32_t nch = (int32_t)vf::ceil_div(b.n1, rows);
         const int32_t first = nch > 1 ? (int32_t)n_part_slots : 0;
         if (nch > 1) n_part_slots += nch;
-        for (int32_t c = 0; c < nch; ++c)
-            h_chunks.push_back(vf::SvdChunk{(int32_t)bi, c * rows, std::min(B[bi].n1, (c + 1) * rows), c, nch, first});
+        for (int32_t c = 0; c < nch; ++c) {
+            vf::RecSrc rs{};
+            rs.kind = vf::REC_P1;
+            rs.blk = (int32_t)bi;
+            rs.w = b.q;
+            rs.cnt = std::min(b.n1, (c + 1) * rows) - c * rows;
+            rs.x = (int32_t)b.off_T;
+            rs.val = b.off_val + (int64_t)b.m1 * b.q + (int64_t)c * rows * b.q;
+            rs.idx2 = (int32_t)(b.off_aux + b.m1 + (int64_t)c * rows);
+            rs.chunk = c;
+            rs.nchunks = nch;
+            rs.first = first;
+            p1.push_back(rs);
+        }
     }
-    std::stable_sort(h_chunks.begin(), h_chunks.end(), [&](const vf::SvdChunk& x, const vf::SvdChunk& y) {
-        return (int64_t)(x.j1 - x.j0) * B[x.blk].q > (int64_t)(y.j1 - y.j0) * B[y.blk].q;
+    // first-fit-decreasing into pages
+    std::stable_sort(p1.begin(), p1.end(), [&](const vf::RecSrc& x, const vf::RecSrc& y) {
+        return vf::rec_bytes(x.kind, x.cnt, x.w, 4) > vf::rec_bytes(y.kind, y.cnt, y.w, 4);
     });
+    std::vector<int64_t> p1_page;
+    {
+        std::vector<int64_t> fill;  // open pages
+        for (const auto& rs : p1) {
+            const int64_t bsz = vf::rec_bytes(rs.kind, rs.cnt, rs.w, 4);
+            int64_t pg = -1;
+            // the most recent few pages are tried (keeps the plan linear-time)
+            for (int64_t t = (int64_t)fill.size() - 1; t >= 0 && t >= (int64_t)fill.size() - 8; --t)
+                if (fill[t] + bsz <= cap) { pg = t; break; }
+            if (pg < 0) {
+                fill.push_back(0);
+                pg = (int64_t)fill.size() - 1;
+            }
+            fill[pg] += bsz;
+            p1_page.push_back(pg);
+        }
+        n_p1_pages = (int64_t)fill.size();
+    }
+    // records must be in page order within a page for the offsets: sort by page (stable)
+    {
+        std::vector<int64_t> ord(p1.size());
+        for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int64_t)i;
+        std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return p1_page[x] < p1_page[y]; });
+        std::vector<vf::RecSrc> p1s;
+        std::vector<int64_t> pgs;
+        for (int64_t i : ord) { p1s.push_back(p1[i]); pgs.push_back(p1_page[i]); }
+        p1.swap(p1s);
+        p1_page.swap(pgs);
+    }
+    VF_TRY(build_pages(this, p1, p1_page, n_p1_pages, true));
     VF_TRY(tile_first.upload(h_tile_first));
     VF_TRY(tile_count.upload(h_tile_count));
-    VF_TRY(tile_item_ptr.upload(h_tile_item_ptr));
+    VF_TRY(tile_page_ptr.upload(h_tile_page_ptr));
     VF_TRY(tile_order.upload(h_tile_order));
-    VF_TRY(items.upload(h_items));
-    VF_TRY(chunks.upload(h_chunks));
     return VF_OK;
 }
 
@@ -562,6 +960,7 @@ struct Workspace {
     int RB = 0, npanels = 0;
     dbuf<float> Xt, Yt, Et, Bt[2], rho_t, Tbuf, part, Rbuf;
     dbuf<int> counters;
+    dbuf<int> status;         // VF_OK, or VF_E_TIMEOUT if a bounded wait gave up
     dbuf<double> colpart, enorm2, colres;
     dbuf<LoopState> loop;
     dbuf<float*> bufs;        // [2] ping-pong pointers
@@ -604,15 +1003,11 @@ static int pick_rb(int R) {
 }
 
 static ApplyArgs make_args(const vf_hmat* h, int prec, int R) {
+    (void)prec;
     ApplyArgs a{};
-    a.blocks = h->blocks.p;
-    a.aux = h->aux.p;
-    a.scale = prec == VF_PREC_FP8 ? h->scale8.p : nullptr;
     a.tile_first = h->tile_first.p;
     a.tile_count = h->tile_count.p;
-    a.tile_item_ptr = h->tile_item_ptr.p;
-    a.items = h->items.p;
-    a.chunks = h->chunks.p;
+    a.tile_page_ptr = h->tile_page_ptr.p;
     a.tile_order = h->tile_order.p;
     a.nparts = std::max<int64_t>(h->n_part_slots, 1);
     a.n = h->nf;
@@ -622,6 +1017,18 @@ static ApplyArgs make_args(const vf_hmat* h, int prec, int R) {
 }
 
 static vf_status phase2_attrs(int device);
+
+static int num_sms(int device) {
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(device);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0) n = 148;
+    cache[device] = n;
+    return n;
+}
 
 static vf_status ws_get(const vf_hmat* h, int R, int prec, Workspace** out) {
     WsCache& c = cache_for(h);
@@ -656,6 +1063,8 @@ static vf_status ws_get(const vf_hmat* h, int R, int prec, Workspace** out) {
     VF_TRY(w->enorm2.alloc(R));
     VF_TRY(w->colres.alloc(R));
     VF_TRY(w->loop.alloc(1));
+    VF_TRY(w->status.alloc(1));
+    VF_TRY_CUDA(cudaMemset(w->status.p, 0, sizeof(int)));
     VF_TRY(w->bufs.alloc(2));
     VF_TRY(w->xsel.alloc(1));
     VF_TRY(w->ysel.alloc(1));
@@ -668,12 +1077,12 @@ static vf_status ws_get(const vf_hmat* h, int R, int prec, Workspace** out) {
 }
 
 template <class T, int RB, int MODE>
-static vf_status launch_phase2(dim3 grid, const ApplyArgs& a, const T* val, const float* Tbuf, const SweepIO& io,
+static vf_status launch_phase2(dim3 grid, const ApplyArgs& a, PageArgs pg, const float* Tbuf, const SweepIO& io,
                                cudaStream_t st) {
     using acc_t = typename std::conditional<MODE == MODE_RESID, double, float>::type;
-    const size_t smem = sizeof(acc_t) * kWarps * kTileRows * RB + sizeof(double) * kWarps * RB +
-                        sizeof(float) * kWarps * RB * Chunk<RB>::p2;
-    k_phase2<T, RB, MODE><<<grid, 256, smem, st>>>(a, val, Tbuf, io);
+    const size_t smem = sizeof(WarpPipe) * kWarps + sizeof(acc_t) * kWarps * kTileRows * RB +
+                        sizeof(double) * kWarps * RB;
+    k_phase2<T, RB, MODE><<<grid, 256, smem, st>>>(a, pg, Tbuf, io);
     return VF_OK;
 }
 
@@ -682,14 +1091,16 @@ static vf_status launch_phase2(dim3 grid, const ApplyArgs& a, const T* val, cons
 template <class T, int RB, int MODE>
 static cudaError_t phase2_attr() {
     using acc_t = typename std::conditional<MODE == MODE_RESID, double, float>::type;
-    const size_t smem = sizeof(acc_t) * kWarps * kTileRows * RB + sizeof(double) * kWarps * RB +
-                        sizeof(float) * kWarps * RB * Chunk<RB>::p2;
+    const size_t smem = sizeof(WarpPipe) * kWarps + sizeof(acc_t) * kWarps * kTileRows * RB +
+                        sizeof(double) * kWarps * RB;
     return cudaFuncSetAttribute(k_phase2<T, RB, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 template <class T, int RB>
 static cudaError_t phase2_attrs_rb() {
-    cudaError_t e = phase2_attr<T, RB, MODE_APPLY>();
+    cudaError_t e = cudaFuncSetAttribute(k_phase1<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(WarpPipe) * kWarps));
+    if (e == cudaSuccess) e = phase2_attr<T, RB, MODE_APPLY>();
     if (e == cudaSuccess) e = phase2_attr<T, RB, MODE_JACOBI>();
     if (e == cudaSuccess) e = phase2_attr<T, RB, MODE_RESID>();
     return e;
@@ -718,49 +1129,51 @@ static vf_status phase2_attrs(int device) {
 }
 
 template <class T, int RB>
-static vf_status launch_multiply_t(const vf_hmat* h, const T* val, const ApplyArgs& a, Workspace* w, int mode,
+static vf_status launch_multiply_t(const vf_hmat* h, int prec, const ApplyArgs& a, Workspace* w, int mode,
                                    const float* const* xsel, float* const* ysel, const float* xd, float* yd,
                                    const float* E, const float* rho, cudaStream_t st) {
     const int64_t ntiles = (int64_t)h->h_tile_first.size();
-    if (!h->h_chunks.empty()) {
-        const int nch = (int)h->h_chunks.size();
-        dim3 g1((unsigned)ceil_div(nch, kWarps), (unsigned)w->npanels);
-        k_phase1<T, RB><<<g1, 256, 0, st>>>(a, val, xsel, xd, w->Tbuf.p, w->part.p, w->counters.p, nch);
+    if (h->n_p1_pages > 0) {
+        const int64_t persistent = (int64_t)num_sms(h->device) * 4;
+        dim3 g1((unsigned)std::min<int64_t>(ceil_div(h->n_p1_pages, kWarps), persistent), (unsigned)w->npanels);
+        PageArgs p1{h->p1pages[prec].p, h->p1_used[prec].p};
+        k_phase1<T, RB><<<g1, 256, sizeof(WarpPipe) * kWarps, st>>>(a, p1, h->n_p1_pages, xsel, xd, w->Tbuf.p,
+                                                                   w->part.p, w->counters.p, w->status.p);
     }
-    SweepIO io{xsel, ysel, xd, yd, E, rho, w->colpart.p, ntiles};
+    SweepIO io{xsel, ysel, xd, yd, E, rho, w->colpart.p, ntiles, w->status.p};
     dim3 g2((unsigned)ntiles, (unsigned)w->npanels);
+    PageArgs pg{h->pages[prec].p, h->page_used[prec].p};
     vf_status s2;
-    if (mode == MODE_APPLY) s2 = launch_phase2<T, RB, MODE_APPLY>(g2, a, val, w->Tbuf.p, io, st);
-    else if (mode == MODE_JACOBI) s2 = launch_phase2<T, RB, MODE_JACOBI>(g2, a, val, w->Tbuf.p, io, st);
-    else s2 = launch_phase2<T, RB, MODE_RESID>(g2, a, val, w->Tbuf.p, io, st);
+    if (mode == MODE_APPLY) s2 = launch_phase2<T, RB, MODE_APPLY>(g2, a, pg, w->Tbuf.p, io, st);
+    else if (mode == MODE_JACOBI) s2 = launch_phase2<T, RB, MODE_JACOBI>(g2, a, pg, w->Tbuf.p, io, st);
+    else s2 = launch_phase2<T, RB, MODE_RESID>(g2, a, pg, w->Tbuf.p, io, st);
     VF_TRY(s2);
     VF_TRY_CUDA(cudaGetLastError());
     return VF_OK;
 }
 
 template <class T>
-static vf_status launch_multiply_rb(const vf_hmat* h, const T* val, const ApplyArgs& a, Workspace* w, int mode,
+static vf_status launch_multiply_rb(const vf_hmat* h, int prec, const ApplyArgs& a, Workspace* w, int mode,
                                     const float* const* xsel, float* const* ysel, const float* xd, float* yd,
                                     const float* E, const float* rho, cudaStream_t st) {
     switch (w->RB) {
-        case 1: return launch_multiply_t<T, 1>(h, val, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
-        case 2: return launch_multiply_t<T, 2>(h, val, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
-        case 4: return launch_multiply_t<T, 4>(h, val, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
-        default: return launch_multiply_t<T, 8>(h, val, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
+        case 1: return launch_multiply_t<T, 1>(h, prec, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
+        case 2: return launch_multiply_t<T, 2>(h, prec, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
+        case 4: return launch_multiply_t<T, 4>(h, prec, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
+        default: return launch_multiply_t<T, 8>(h, prec, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
     }
 }
 
 // One multiply (phase 1 + phase 2) with the given mode, input/output selected
-// through device pointers.
+// through device pointers (xsel/ysel) or given directly (xd/yd).
 static vf_status launch_multiply(const vf_hmat* h, int prec, Workspace* w, int mode, const float* const* xsel,
                                  float* const* ysel, const float* xd, float* yd, const float* E, const float* rho,
                                  cudaStream_t st) {
     ApplyArgs a = make_args(h, prec, w->R);
-    if (prec == VF_PREC_FP32)
-        return launch_multiply_rb<float>(h, h->val.p, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
+    if (prec == VF_PREC_FP32) return launch_multiply_rb<float>(h, prec, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
     if (prec == VF_PREC_BF16)
-        return launch_multiply_rb<__nv_bfloat16>(h, h->val16.p, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
-    return launch_multiply_rb<__nv_fp8_e4m3>(h, h->val8.p, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
+        return launch_multiply_rb<__nv_bfloat16>(h, prec, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
+    return launch_multiply_rb<__nv_fp8_e4m3>(h, prec, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
 }
 
 static vf_status check_prec(const vf_hmat* h, int prec) {

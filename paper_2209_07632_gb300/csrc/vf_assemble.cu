@@ -378,13 +378,21 @@ struct PackDesc {
     int64_t lists_off;  // SVD: rows/cols in the probe index list
 };
 
-// dense: one CTA per block, warps over rows
-__global__ void k_pack_dense(Geo g, const PackDesc* __restrict__ pk, float* __restrict__ val) {
+// dense: one CTA per block.  The values of the block's rows that fall in
+// one row tile (tree leaf) form a column-major slab at
+// off_val + (tile_first - r0) * n, so the multiply reads it with one lane per
+// row and coalesced loads: element (r, c) is at slab + c * tile_rows + (r - tile_first).
+__global__ void k_pack_dense(Geo g, const PackDesc* __restrict__ pk, const int32_t* __restrict__ tile_of_row,
+                             const int32_t* __restrict__ tile_first, const int32_t* __restrict__ tile_count,
+                             float* __restrict__ val) {
     const PackDesc d = pk[blockIdx.x];
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int r = warp; r < d.m; r += nw)
-        for (int c = lane; c < d.n; c += 32)
-            val[d.off_val + (int64_t)r * d.n + c] = entry(g, d.r0 + r, d.c0 + c);
+    for (int64_t e = threadIdx.x; e < (int64_t)d.m * d.n; e += blockDim.x) {
+        const int c = (int)(e / d.m), r = (int)(e - (int64_t)c * d.m);  // consecutive threads: consecutive rows
+        const int row = d.r0 + r;
+        const int t = tile_of_row[row];
+        const int tf = tile_first[t], tc = tile_count[t];
+        val[d.off_val + (int64_t)(tf - d.r0) * d.n + (int64_t)c * tc + (row - tf)] = entry(g, row, d.c0 + c);
+    }
 }
 
 // CSR: one CTA per block: row counts, exclusive scan, then the entries.
@@ -699,10 +707,6 @@ static vf_status run_probes(const Geo& g, ProbeBatch& B, int power_iters, cudaSt
 
 using namespace vf;
 
-int64_t vf_hmat::bytes_payload(int prec) const {
-    int64_t elt = prec == VF_PREC_FP32 ? 4 : prec == VF_PREC_BF16 ? 2 : 1;
-    return n_val * elt + n_aux * 4;
-}
 
 extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_assemble_opts* opts_in, vf_hmat** out,
                                  vf_assemble_stats* stats_out) {
@@ -1123,9 +1127,11 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
     H->n_aux = naux;
     H->n_T = nT;
     H->max_q = maxq;
-    VF_TRY(H->val.alloc(std::max<int64_t>(nval, 4)));
-    VF_TRY(H->aux.alloc(std::max<int64_t>(naux, 1)));
-    VF_TRY_CUDA(cudaMemsetAsync(H->val.p, 0, std::max<int64_t>(nval, 4) * 4, st));
+    // pools are padded by 16 elements: the multiply copies 16-byte aligned supersets
+    VF_TRY(H->val.alloc(nval + 16));
+    VF_TRY(H->aux.alloc(naux + 16));
+    VF_TRY_CUDA(cudaMemsetAsync(H->val.p, 0, (nval + 16) * 4, st));
+    VF_TRY_CUDA(cudaMemsetAsync(H->aux.p, 0, (naux + 16) * 4, st));
     // pack
     std::vector<PackDesc> pk_dense, pk_csr;
     std::vector<std::vector<PackDesc>> pk_svd(stage_bufs.size());
@@ -1155,8 +1161,15 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
     }
     if (!pk_dense.empty()) {
         dbuf<PackDesc> d;
+        dbuf<int32_t> d_tor, d_tf, d_tc;
+        std::vector<int32_t> tor(n);
+        for (size_t k = 0; k < Bd.leaf_first.size(); ++k)
+            for (int32_t r = Bd.leaf_first[k]; r < Bd.leaf_first[k] + Bd.leaf_count[k]; ++r) tor[r] = (int32_t)k;
+        VF_TRY(d_tor.upload(tor));
+        VF_TRY(d_tf.upload(Bd.leaf_first));
+        VF_TRY(d_tc.upload(Bd.leaf_count));
         VF_TRY(d.upload(pk_dense));
-        k_pack_dense<<<(unsigned)pk_dense.size(), 256, 0, st>>>(g, d.p, H->val.p);
+        k_pack_dense<<<(unsigned)pk_dense.size(), 256, 0, st>>>(g, d.p, d_tor.p, d_tf.p, d_tc.p, H->val.p);
         VF_TRY_CUDA(cudaGetLastError());
         VF_TRY_CUDA(cudaStreamSynchronize(st));
     }
@@ -1179,15 +1192,15 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
     VF_TRY(H->blocks.upload(HB));
     // low-precision copies
     if (o.precisions & (1u << VF_PREC_BF16)) {
-        VF_TRY(H->val16.alloc(std::max<int64_t>(nval, 4)));
-        k_to_bf16<<<1024, 256, 0, st>>>(H->val.p, H->val16.p, std::max<int64_t>(nval, 4));
+        VF_TRY(H->val16.alloc(nval + 16));
+        k_to_bf16<<<1024, 256, 0, st>>>(H->val.p, H->val16.p, nval + 16);
         VF_TRY_CUDA(cudaGetLastError());
         H->has_bf16 = true;
     }
     if (o.precisions & (1u << VF_PREC_FP8)) {
-        VF_TRY(H->val8.alloc(std::max<int64_t>(nval, 4)));
+        VF_TRY(H->val8.alloc(nval + 16));
         VF_TRY(H->scale8.alloc(std::max<size_t>(HB.size(), 1)));
-        VF_TRY_CUDA(cudaMemsetAsync(H->val8.p, 0, std::max<int64_t>(nval, 4), st));
+        VF_TRY_CUDA(cudaMemsetAsync(H->val8.p, 0, nval + 16, st));
         if (!HB.empty()) k_to_fp8<<<(unsigned)HB.size(), 256, 0, st>>>(H->blocks.p, H->val.p, H->val8.p, H->scale8.p);
         VF_TRY_CUDA(cudaGetLastError());
         H->has_fp8 = true;

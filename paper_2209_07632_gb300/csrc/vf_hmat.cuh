@@ -22,33 +22,50 @@ struct HBlock {
     int64_t off_T;        // SVD: offset of its q-vector slot in the T buffer (per RHS column)
 };
 
-// Row-tile work item (32 bytes): the part of one stored block that lies in
-// a tile's rows, as one contiguous range of values.
-//  dense: cnt = tile rows, w = n, xoff = tree column c0, val = first value
-//         (row lr0 of the block); element e is row e / w, column e % w
-//  SVD:   cnt = compacted rows of U' in the tile, w = q, xoff = T slot,
-//         val = U' row u0, idx = aux offset of the row-id list at u0
-//  CSR:   cnt = tile rows, idx = aux offset of the row pointer of row lr0,
-//         idx2 = aux offset of the block's column indices, val = block values
-struct TileItem {
-    int32_t kind;
-    int32_t cnt;
-    int32_t w;
-    int32_t xoff;
-    int32_t idx;
-    int32_t idx2;
-    int64_t val;
-    int32_t blk;
-    int32_t pad;
-};
+// The multiply streams the matrix from tile-major "pages": kPage-byte
+// blocks of self-describing records, built once from the block pools.  A
+// page is one bulk copy into a warp's prefetch stage; its records are then
+// read from shared memory.  Record layouts (4-byte aligned arrays):
+//   header (16 B): u32 kind | cnt << 8, u32 w, i32 x, f32 scale
+//   dense  (1): cnt x w column-major slab (element (r, k) at k * cnt + r) of
+//               tile rows 0..cnt-1, columns x .. x + w - 1
+//   CSR    (2): w = nnz, x = first tile row; row pointers (cnt + 1, from 0),
+//               column indices (nnz), values (nnz)
+//   SVD    (3): w = q, x = T slot; tile-local rows (cnt bytes), U' rows (cnt x q)
+//   long CSR row (5): w = nnz, x = tile row; column indices, values
+//   phase-1 (6): header + i32 chunk, nchunks, first partial slot, pad; then
+//               w = q, x = T slot, cnt = rows; column indices (cnt), V' rows (cnt x q)
+// A page starts with a 16-byte header: u32 number of records, u32 bytes used.
+constexpr int kPage = 2048;
+constexpr int kPageHdr = 16;
+constexpr int kRecHdr = 16;
+constexpr int kP1Hdr = 32;
+enum RecKind { REC_DENSE = 1, REC_CSR = 2, REC_SVD = 3, REC_CSR_LONG = 5, REC_P1 = 6 };
 
-// Phase-1 work item: V' rows [j0, j1) of an SVD block, one warp.
-struct SvdChunk {
+__host__ __device__ inline uint32_t pad4(uint32_t b) { return (b + 3u) & ~3u; }
+
+// bytes of a record with element size es
+__host__ __device__ inline uint32_t rec_bytes(int kind, int cnt, int w, int es) {
+    switch (kind) {
+        case REC_DENSE: return kRecHdr + pad4((uint32_t)(cnt * w * es));
+        case REC_SVD: return kRecHdr + pad4((uint32_t)cnt) + pad4((uint32_t)(cnt * w * es));
+        case REC_CSR: return kRecHdr + 4u * (cnt + 1) + 4u * w + pad4((uint32_t)(w * es));
+        case REC_CSR_LONG: return kRecHdr + 4u * w + pad4((uint32_t)(w * es));
+        default: return kP1Hdr + 4u * cnt + pad4((uint32_t)(cnt * w * es));
+    }
+}
+
+// Where one record's data comes from in the block pools (build time only).
+struct RecSrc {
+    int32_t kind, cnt, w, x;
     int32_t blk;
-    int32_t j0, j1;
-    int32_t chunk;   // index of this chunk within its block
-    int32_t nchunks; // chunks of the block
-    int32_t first;   // slot of the block's first chunk in the partial buffer
+    int32_t tile_first;  // SVD: row ids are stored relative to it
+    int64_t val;         // element offset of the first value in the block pool
+    int32_t idx;         // CSR: aux offset of the first row pointer; SVD: of the first row id
+    int32_t idx2;        // CSR / long row / phase 1: aux offset of the first column index
+    int32_t nz0;         // CSR: block-local offset of the first nonzero
+    int32_t chunk, nchunks, first;  // phase 1
+    int64_t dst;         // byte offset in the page pool (per element size)
 };
 
 }  // namespace vf
@@ -62,17 +79,15 @@ struct vf_hmat {
     std::vector<vf::HBlock> h_blocks;
     std::vector<int32_t> h_perm;
     std::vector<int32_t> h_tile_first, h_tile_count;  // per row tile (tree leaf)
-    std::vector<int32_t> h_tile_item_ptr;             // ntiles + 1
+    std::vector<int32_t> h_tile_page_ptr;             // ntiles * kWarps + 1: each warp's page range
     std::vector<int32_t> h_tile_order;                // launch order: heaviest tile first
+    int64_t n_pages = 0, n_p1_pages = 0;              // phase-2 / phase-1 pages
     int64_t n_part_slots = 0;                         // phase-1 partial slots (split blocks)
-    std::vector<vf::TileItem> h_items;
-    std::vector<vf::SvdChunk> h_chunks;
-    std::vector<float> h_scale8;                      // FP8 per-block scale
     int64_t n_val = 0, n_aux = 0, n_T = 0;            // pool sizes (elements); n_T per RHS column
     int32_t max_q = 0;
     int64_t n_hier = 0;
     vf_assemble_stats stats{};
-    // device
+    // device: block pools (the stored representation)
     vf::dbuf<int32_t> perm;        // tree position -> facet
     vf::dbuf<int32_t> iperm;       // facet -> tree position
     vf::dbuf<vf::HBlock> blocks;
@@ -81,10 +96,11 @@ struct vf_hmat {
     vf::dbuf<__nv_fp8_e4m3> val8;  // FP8 E4M3 copy (val / scale)
     vf::dbuf<float> scale8;        // per block
     vf::dbuf<int32_t> aux;
-    vf::dbuf<int32_t> tile_first, tile_count, tile_item_ptr, tile_order;
-    vf::dbuf<vf::TileItem> items;
-    vf::dbuf<vf::SvdChunk> chunks;
+    // device: the multiply's page pools per precision (FP32, BF16, FP8)
+    vf::dbuf<unsigned char> pages[3], p1pages[3];
+    vf::dbuf<uint16_t> page_used[3], p1_used[3];  // bytes used per page
+    vf::dbuf<int32_t> tile_first, tile_count, tile_page_ptr, tile_order;
     bool has_bf16 = false, has_fp8 = false;
-    int64_t bytes_payload(int prec) const;
+    int64_t bytes_payload(int prec) const;        // bytes of the stored representation
     vf_status upload_all();
 };

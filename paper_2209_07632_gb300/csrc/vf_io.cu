@@ -187,9 +187,10 @@ extern "C" vf_status vf_hmat_load(const char* path, int32_t device, vf_hmat** ou
     for (int64_t k = 0; k < hd.nf; ++k) ip[H->h_perm[k]] = (int32_t)k;
     VF_TRY(H->iperm.upload(ip));
     VF_TRY(H->blocks.upload(H->h_blocks));
-    val.resize(std::max<int64_t>(hd.n_val, 4), 0.f);
+    // pools are padded by 16 elements: the multiply copies 16-byte aligned supersets
+    val.resize(hd.n_val + 16, 0.f);
     VF_TRY(H->val.upload(val));
-    if (aux.empty()) aux.push_back(0);
+    aux.resize(hd.n_aux + 16, 0);
     VF_TRY(H->aux.upload(aux));
     if (hd.flags & 1u) {
         VF_TRY(H->val16.alloc(val.size()));
