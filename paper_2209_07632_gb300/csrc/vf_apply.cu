@@ -46,20 +46,27 @@ struct ApplyArgs {
 
 // Both phases stream the matrix as pages (see vf_hmat.cuh) through per-warp
 // prefetch pipelines: lane 0 of each warp issues one bulk asynchronous copy
-// per page into one of kStages shared-memory stages (completion tracked by
-// an mbarrier per stage) while the warp computes on a page that has
-// arrived.  HBM latency is hidden by the copies in flight; records are read
-// from shared memory.  Every sum has one owner and one order, so results
-// are bit-reproducible with no float atomics:
-//  * dense slabs: lane r owns tile row r (and r + 32), x is loaded once per
-//    record and broadcast by shuffles;
-//  * CSR rows: lane r walks row r's nonzeros, 8 gathers in flight; a long
-//    row is split across lanes and reduced by a fixed butterfly;
-//  * SVD factors (row-major, rank q): a group of g = pow2ceil(min(q, 32))
-//    lanes shares one row, 32 / g rows per step, added by xor-shuffles.
+// per page into one of kStages shared-memory stages (an mbarrier per stage
+// tracks the bytes) while the warp computes on a page that has arrived.  On
+// arrival the warp gathers every x (or T) value the page's records need in
+// one round, in place over the page's x list, so the records then compute
+// from shared memory only.  Few, large copies in flight per SM (kStages x
+// warps x CTAs ~ 48 of 4 KB) keep HBM streaming efficiently.  Every sum has
+// one owner and one order, so results are bit-reproducible with no float
+// atomics:
+//  * dense and SVD slabs (column-major): lane r owns slab row r (and r + 32);
+//  * CSR rows: lane r walks row r's nonzeros; a long row is split across
+//    lanes and reduced by a fixed butterfly;
+//  * phase-1 V' rows: a group of g = pow2ceil(min(q, 32)) lanes per row,
+//    lane (sub, k) accumulates column k over its rows, groups added by a
+//    fixed butterfly.
 // Row sums go to per-warp row slots in shared memory; the CTA adds the
-// warps' slots in warp order.
-constexpr int kStages = 3;
+// warps' slots in warp order.  Every wait is bounded, and a warp that stops
+// early first waits (bounded) for its own copies in flight.
+#ifndef VF_STAGES
+#define VF_STAGES 2
+#endif
+constexpr int kStages = VF_STAGES;
 constexpr uint32_t kWaitLimit = 1u << 22;  // polls before a wait reports a timeout
 
 __device__ __forceinline__ int pow2ceil32(int q) {
@@ -85,7 +92,6 @@ struct PageArgs {
 
 __device__ __forceinline__ void issue_page(const PageArgs& pg, int64_t page, WarpPipe& wp, int s) {
     const uint32_t bytes = ((uint32_t)pg.used[page] + 15u) & ~15u;
-    fence_proxy_async_smem();
     mbar_arrive_expect_tx(&wp.bar[s], bytes);
     bulk_g2s(wp.buf[s], pg.pages + page * (int64_t)kPage, bytes, &wp.bar[s]);
 }
@@ -95,143 +101,182 @@ __device__ __forceinline__ void pipe_init(WarpPipe& wp) {
     mbar_init_fence();
 }
 
+// Wait (bounded) for the copies this warp issued but did not consume, so a
+// warp that stops early never leaves bulk copies in flight into its stages.
+__device__ __forceinline__ void drain(WarpPipe& wp, int consumed, int issued) {
+    for (int j = consumed; j < issued; ++j) mbar_wait(&wp.bar[j % kStages], (uint32_t)((j / kStages) & 1), kWaitLimit);
+}
+
+// x source of entry v of a page's x list for RHS column c of the panel
+__device__ __forceinline__ float x_of(const ApplyArgs& a, const float* X, const float* Tp, int32_t v, int c) {
+    return v >= 0 ? __ldg(X + (int64_t)c * a.n + v) : Tp[(int64_t)c * a.nT + (-1 - v)];
+}
+
+// Panel column c of the x entries of a page, entry e = lane + 32 j in v[j]:
+// all loads issued before any is used.
+__device__ __forceinline__ void load_col(const ApplyArgs& a, const float* X, const float* Tp, const int32_t* xl,
+                                         int nx, int c, float (&v)[kXMax / 32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < kXMax / 32; ++j) {
+        const int e = lane + 32 * j;
+        v[j] = e < nx ? x_of(a, X, Tp, xl[e], c) : 0.f;
+    }
+}
+
+__device__ __forceinline__ void store_col(int nx, const float (&v)[kXMax / 32], float* xv) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < kXMax / 32; ++j) {
+        const int e = lane + 32 * j;
+        if (e < nx) xv[e] = v[j];
+    }
+}
+
+// Single column: gather the page's x list in place (each lane overwrites the
+// entries it read), so the records then read x values from the page itself.
+__device__ __forceinline__ void gather_in_place(const ApplyArgs& a, const float* X, const float* Tp,
+                                                unsigned char* page) {
+    const int nx = (int)reinterpret_cast<const uint32_t*>(page)[2];
+    int32_t* xl = reinterpret_cast<int32_t*>(page + kPageHdr);
+    float v[kXMax / 32];
+    load_col(a, X, Tp, xl, nx, 0, v);
+    store_col(nx, v, reinterpret_cast<float*>(xl));
+    __syncwarp();
+}
+
 // ------------------------------------------------------------ phase 1
-// T_b = V'_b^T X[cols_b] from phase-1 records.  Input X: tree order,
-// column-major with leading dimension n, columns [p0, p0 + RB) of the
-// panel.  T: per panel RB x nT (column c at c * nT).  A block split into
-// several records writes chunk partials; the last chunk to finish (atomic
-// ticket) adds them in chunk order.
+// T_b = V'_b^T X[cols_b] from phase-1 records, one panel column at a time
+// (xv: that column's x values, indexed by x-list entry).  T: per panel
+// RB x nT (column c at c * nT).  A block split into several records writes
+// one partial per chunk; k_p1_reduce adds them in chunk order.
 template <class T, int RB>
-__device__ __forceinline__ void p1_record(const ApplyArgs& a, const float* X, const unsigned char* rec,
-                                          float* __restrict__ Tbuf, float* __restrict__ part,
-                                          int* __restrict__ counters, int panel) {
+__device__ __forceinline__ void p1_column(const ApplyArgs& a, const float* xv, const unsigned char* rec, int c,
+                                          float* __restrict__ Tbuf, float* __restrict__ part, int panel) {
     const int lane = threadIdx.x & 31;
     const uint32_t* h = reinterpret_cast<const uint32_t*>(rec);
-    const int nrows = (int)(h[0] >> 8), q = (int)h[1], offT = (int)h[2];
+    const int nrows = (int)((h[0] >> 8) & 0xffu), q = (int)h[1], xb = (int)h[2];
     const float sc = __uint_as_float(h[3]);
-    const int chunk = (int)h[4], nch = (int)h[5], first = (int)h[6];
-    const int32_t* sC = reinterpret_cast<const int32_t*>(rec + kP1Hdr);
-    const T* sV = reinterpret_cast<const T*>(rec + kP1Hdr + 4 * nrows);
-    const int p0 = panel * RB;
-    const int64_t panel_T = (int64_t)panel * RB * a.nT;
+    const int chunk = (int)h[4], nch = (int)h[5], first = (int)h[6], offT = (int)h[7];
+    const T* sV = reinterpret_cast<const T*>(rec + kP1Hdr);
     const int g = pow2ceil32(q);
     const int step = 32 / g;
     const int sub = lane / g, kk = lane - sub * g;
     const int nk = (q + 31) / 32;
-    float acc[4][RB];
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-#pragma unroll
-        for (int c = 0; c < RB; ++c) acc[t][c] = 0.f;
-    // x of all rows (<= 128) gathered at once: lane l holds rows l + 32 t
-    float xr[4][RB];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        const int j = lane + 32 * t;
-        const int col = j < nrows ? sC[j] : 0;
-#pragma unroll
-        for (int c = 0; c < RB; ++c)
-            xr[t][c] = (j < nrows && p0 + c < a.R) ? __ldg(X + (int64_t)(p0 + c) * a.n + col) : 0.f;
-    }
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
     if (q <= 32) {
-        // one k per lane: lane (sub, kk) takes rows sub, sub + step, ...
-        const bool kin = kk < q;
-#pragma unroll
-        for (int tj = 0; tj < 4; ++tj) {
-            if (32 * tj >= nrows) break;
-            const int jend = min(32 * tj + 32, nrows);
-#pragma unroll 2
-            for (int j0 = 32 * tj; j0 < jend; j0 += step) {
-                const int j = j0 + sub;
-                float x[RB];
-#pragma unroll
-                for (int c = 0; c < RB; ++c) x[c] = __shfl_sync(0xffffffffu, xr[tj][c], j & 31);
-                if (kin && j < nrows) {
-                    const float v = lds(sV + j * q + kk);
-#pragma unroll
-                    for (int c = 0; c < RB; ++c) acc[0][c] = fmaf(v, x[c], acc[0][c]);
-                }
-            }
-        }
+        if (kk < q)
+#pragma unroll 4
+            for (int j = sub; j < nrows; j += step) acc[0] = fmaf(lds(sV + j * q + kk), xv[xb + j], acc[0]);
     } else {
         for (int j = 0; j < nrows; ++j) {  // q > 32: the whole warp shares each row
-            const int tj = j >> 5;
-            float x[RB];
-#pragma unroll
-            for (int c = 0; c < RB; ++c) {
-                float xs = xr[0][c];
-                if (tj == 1) xs = xr[1][c];
-                else if (tj == 2) xs = xr[2][c];
-                else if (tj == 3) xs = xr[3][c];
-                x[c] = __shfl_sync(0xffffffffu, xs, j & 31);
-            }
+            const float x = xv[xb + j];
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 const int k = lane + 32 * t;
-                if (t < nk && k < q) {
-                    const float v = lds(sV + j * q + k);
-#pragma unroll
-                    for (int c = 0; c < RB; ++c) acc[t][c] = fmaf(v, x[c], acc[t][c]);
-                }
+                if (t < nk && k < q) acc[t] = fmaf(lds(sV + j * q + k), x, acc[t]);
             }
         }
     }
     for (int o = 16; o >= g; o >>= 1)
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
-#pragma unroll
-            for (int c = 0; c < RB; ++c) acc[t][c] += __shfl_xor_sync(0xffffffffu, acc[t][c], o);
+        for (int t = 0; t < 4; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+    if (sub != 0) return;
     if (nch == 1) {
-        if (sub == 0)
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int k = kk + 32 * t;
-                if (t < nk && k < q)
-#pragma unroll
-                    for (int c = 0; c < RB; ++c) Tbuf[panel_T + (int64_t)c * a.nT + offT + k] = acc[t][c] * sc;
-            }
-        return;
-    }
-    float* mypart = part + ((int64_t)panel * a.nparts + first + chunk) * (RB * 128);
-    if (sub == 0)
+        float* dst = Tbuf + ((int64_t)panel * RB + c) * a.nT + offT;
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int k = kk + 32 * t;
-            if (t < nk && k < q)
-#pragma unroll
-                for (int c = 0; c < RB; ++c) mypart[c * 128 + k] = acc[t][c];
+            if (t < nk && k < q) dst[k] = acc[t] * sc;
         }
-    // ticket: the partial stores (ordered before lane 0 by __syncwarp) are
-    // released with the increment; the last chunk acquires all of them
-    __syncwarp();
-    int last = 0;
-    if (lane == 0) {
-        cuda::atomic_ref<int, cuda::thread_scope_device> ticket(counters[(int64_t)panel * a.nT + offT]);
-        last = ticket.fetch_add(1, cuda::memory_order_acq_rel) == nch - 1;
+        return;
     }
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (!last) return;
-    __syncwarp();
-    const float* pb = part + ((int64_t)panel * a.nparts + first) * (RB * 128);
-    for (int k = lane; k < q; k += 32)
+    float* mypart = part + ((int64_t)panel * a.nparts + first + chunk) * (RB * 128) + c * 128;
 #pragma unroll
-        for (int c = 0; c < RB; ++c) {
-            float sum = 0.f;
-            for (int cc = 0; cc < nch; ++cc) sum += __ldcg(pb + (int64_t)cc * (RB * 128) + c * 128 + k);
-            Tbuf[panel_T + (int64_t)c * a.nT + offT + k] = sum * sc;
-        }
-    if (lane == 0) counters[(int64_t)panel * a.nT + offT] = 0;
+    for (int t = 0; t < 4; ++t) {
+        const int k = kk + 32 * t;
+        if (t < nk && k < q) mypart[k] = acc[t];
+    }
+}
+
+// T of the blocks whose V' rows were split over several records: the chunk
+// partials added in chunk order, then scaled.  One CTA per (split block,
+// panel); split[5 i ..] = first partial slot, chunks, q, T slot, block.
+template <int RB>
+__global__ void k_p1_reduce(ApplyArgs a, const int32_t* __restrict__ split, const float* __restrict__ scales,
+                            const float* __restrict__ part, float* __restrict__ Tbuf) {
+    const int32_t* d = split + 5 * (int64_t)blockIdx.x;
+    const int first = d[0], nch = d[1], q = d[2], offT = d[3];
+    const float sc = scales ? scales[d[4]] : 1.f;
+    const int panel = blockIdx.y;
+    const float* pb = part + ((int64_t)panel * a.nparts + first) * (RB * 128);
+    for (int e = threadIdx.x; e < RB * 128; e += blockDim.x) {
+        const int c = e >> 7, k = e & 127;
+        if (k >= q || panel * RB + c >= a.R) continue;
+        float sum = 0.f;
+        for (int cc = 0; cc < nch; ++cc) sum += pb[(int64_t)cc * (RB * 128) + c * 128 + k];
+        Tbuf[((int64_t)panel * RB + c) * a.nT + offT + k] = sum * sc;
+    }
+}
+
+// Walk a page's records (after its header and x list); f(record) returns
+// nothing, the record sizes come from the headers.
+template <class T, class F>
+__device__ __forceinline__ void for_records(const unsigned char* page, F f) {
+    const uint32_t* ph = reinterpret_cast<const uint32_t*>(page);
+    const int nrec = (int)ph[0];
+    uint32_t off = kPageHdr + 4u * ph[2];
+    for (int r = 0; r < nrec; ++r) {
+        const uint32_t* h = reinterpret_cast<const uint32_t*>(page + off);
+        const int kind = (int)(h[0] & 0xffu), cnt = (int)((h[0] >> 8) & 0xffu);
+        f(page + off);
+        off += rec_bytes(kind, cnt, (int)h[1], (int)sizeof(T));
+    }
+}
+
+// Per-warp x buffers for panels of more than one column: two columns, so
+// the loads of column c + 1 are in flight while column c computes.
+struct XBuf {
+    float v[2][kXMax];
+};
+
+// Every panel column of one page: f(xv, c) computes column c from xv.  One
+// column gathers in place; more columns go through the warp's XBuf.
+template <int RB, class F>
+__device__ __forceinline__ void page_columns(const ApplyArgs& a, const float* X, const float* Tp, unsigned char* page,
+                                             XBuf* xb, int p0, F f) {
+    if (RB == 1) {
+        gather_in_place(a, X, Tp, page);
+        f(reinterpret_cast<const float*>(page + kPageHdr), 0);
+        return;
+    }
+    const int nx = (int)reinterpret_cast<const uint32_t*>(page)[2];
+    const int32_t* xl = reinterpret_cast<const int32_t*>(page + kPageHdr);
+    float v[kXMax / 32];
+    load_col(a, X, Tp, xl, nx, 0, v);
+    store_col(nx, v, xb->v[0]);
+    for (int c = 0; c < RB && p0 + c < a.R; ++c) {
+        const bool more = c + 1 < RB && p0 + c + 1 < a.R;
+        if (more) load_col(a, X, Tp, xl, nx, c + 1, v);
+        __syncwarp();
+        f(xb->v[c & 1], c);
+        if (more) store_col(nx, v, xb->v[(c + 1) & 1]);
+    }
+    __syncwarp();
 }
 
 template <class T, int RB>
 __global__ void __launch_bounds__(256) k_phase1(ApplyArgs a, PageArgs pg, int64_t npages, const float* const* xsel,
                                                 const float* xd, float* __restrict__ Tbuf, float* __restrict__ part,
-                                                int* __restrict__ counters, int* __restrict__ status) {
+                                                int* __restrict__ status) {
+    // dynamic shared memory: pipes[kWarps], then (RB > 1) xbufs[kWarps]
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpPipe* pipes = reinterpret_cast<WarpPipe*>(smem_raw);
+    XBuf* xbufs = reinterpret_cast<XBuf*>(smem_raw + sizeof(WarpPipe) * kWarps);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpPipe& wp = pipes[warp];
-    const float* X = xsel ? *xsel : xd;
+    const int panel = blockIdx.y, p0 = panel * RB;
+    const float* X = (xsel ? *xsel : xd) + (int64_t)p0 * a.n;
     const int64_t wstride = (int64_t)gridDim.x * kWarps;
     const int64_t p_first = (int64_t)blockIdx.x * kWarps + warp;
     if (lane == 0) {
@@ -240,25 +285,27 @@ __global__ void __launch_bounds__(256) k_phase1(ApplyArgs a, PageArgs pg, int64_
             if (p_first + s * wstride < npages) issue_page(pg, p_first + s * wstride, wp, s);
     }
     __syncwarp();
-    int n = 0;
+    int n = 0, issued = 0;
+    for (int s = 0; s < kStages; ++s)
+        if (p_first + s * wstride < npages) ++issued;
     for (int64_t p = p_first; p < npages; p += wstride, ++n) {
         const int s = n % kStages;
         // warp-uniform decision: a lane that gave up makes the whole warp stop
         if (!__all_sync(0xffffffffu, mbar_wait(&wp.bar[s], (uint32_t)((n / kStages) & 1), kWaitLimit))) {
+            drain(wp, n, issued);  // no bulk copy may stay in flight into this warp's stages
             if (lane == 0) atomicExch(status, VF_E_TIMEOUT);
             return;
         }
-        const unsigned char* page = wp.buf[s];
-        const int nrec = (int)reinterpret_cast<const uint32_t*>(page)[0];
-        uint32_t off = kPageHdr;
-        for (int r = 0; r < nrec; ++r) {
-            const uint32_t* h = reinterpret_cast<const uint32_t*>(page + off);
-            const uint32_t sz = rec_bytes(REC_P1, (int)(h[0] >> 8), (int)h[1], (int)sizeof(T));
-            p1_record<T, RB>(a, X, page + off, Tbuf, part, counters, blockIdx.y);
-            off += sz;
-        }
+        unsigned char* page = wp.buf[s];
+        page_columns<RB>(a, X, nullptr, page, xbufs + warp, p0, [&](const float* xv, int c) {
+            for_records<T>(page, [&](const unsigned char* rec) { p1_column<T, RB>(a, xv, rec, c, Tbuf, part, panel); });
+        });
+        if (RB == 1) fence_proxy_async_smem();  // the gather wrote the stage; the next copy refills it
         __syncwarp();
-        if (lane == 0 && p + kStages * wstride < npages) issue_page(pg, p + kStages * wstride, wp, s);
+        if (p + kStages * wstride < npages) {
+            if (lane == 0) issue_page(pg, p + kStages * wstride, wp, s);
+            ++issued;
+        }
     }
 }
 
@@ -277,139 +324,78 @@ struct SweepIO {
     int* status;               // VF_E_TIMEOUT if a wait gave up
 };
 
-// A column-major slab (cnt <= 64 rows x w <= 128 columns, element (r, k) at
-// k * cnt + r) times an x slice: lane r owns slab row r (and r + 32); the x
-// slice is loaded once (x[k] by lane k % 32) and broadcast by shuffles.
-// Dense records read x from X, SVD records from T (U' stored as a slab, its
-// rows scattered over the tile through `rows8`).
-template <class T, int RB, class acc_t, bool SVD>
-__device__ __forceinline__ void slab_compute(const ApplyArgs& a, const float* xsrc, int64_t xstride,
-                                             const T* __restrict__ sA, int cnt, int w, int xo,
+// A column-major slab (cnt <= 64 rows x w columns, element (r, k) at
+// k * cnt + r) times its x values: lane r owns slab row r (and r + 32).
+// slot: the warp's row slots of this column, stride S.
+template <class T, int S, class acc_t, bool SVD>
+__device__ __forceinline__ void slab_compute(const float* xv, const T* __restrict__ sA, int cnt, int w, int xb,
                                              const unsigned char* rows8, float sc, acc_t* slot) {
     const int lane = threadIdx.x & 31;
-    const int p0 = blockIdx.y * RB;
-    float xr[4][RB];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        const int k = lane + 32 * t;
-#pragma unroll
-        for (int c = 0; c < RB; ++c)
-            xr[t][c] = (k < w && p0 + c < a.R) ? __ldg(xsrc + (int64_t)c * xstride + xo + k) : 0.f;
-    }
-    float q0[RB], q1[RB];
-#pragma unroll
-    for (int c = 0; c < RB; ++c) q0[c] = q1[c] = 0.f;
-    const bool h0 = lane < cnt;
+    float q0 = 0.f, q1 = 0.f;
+    const bool h0 = lane < cnt, h1 = lane + 32 < cnt;
     if (cnt <= 32) {
-        const T* col = sA + lane;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            if (32 * t >= w) break;
-            const int kmax = min(32, w - 32 * t);
-#pragma unroll 4
-            for (int kl = 0; kl < kmax; ++kl) {
-                const float v0 = h0 ? lds(col + (32 * t + kl) * cnt) : 0.f;
-#pragma unroll
-                for (int c = 0; c < RB; ++c) q0[c] = fmaf(v0, __shfl_sync(0xffffffffu, xr[t][c], kl), q0[c]);
-            }
-        }
+        if (h0)
+#pragma unroll 8
+            for (int k = 0; k < w; ++k) q0 = fmaf(lds(sA + k * cnt + lane), xv[xb + k], q0);
     } else {
-        const bool h1 = lane + 32 < cnt;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            if (32 * t >= w) break;
-            const int kmax = min(32, w - 32 * t);
-#pragma unroll 2
-            for (int kl = 0; kl < kmax; ++kl) {
-                const int k = 32 * t + kl;
-                const float v0 = lds(sA + k * cnt + lane);
-                const float v1 = h1 ? lds(sA + k * cnt + lane + 32) : 0.f;
-#pragma unroll
-                for (int c = 0; c < RB; ++c) {
-                    const float x = __shfl_sync(0xffffffffu, xr[t][c], kl);
-                    q0[c] = fmaf(v0, x, q0[c]);
-                    q1[c] = fmaf(v1, x, q1[c]);
-                }
-            }
+#pragma unroll 4
+        for (int k = 0; k < w; ++k) {
+            const float x = xv[xb + k];
+            q0 = fmaf(lds(sA + k * cnt + lane), x, q0);
+            if (h1) q1 = fmaf(lds(sA + k * cnt + lane + 32), x, q1);
         }
-        if (h1) {
-            const int d1 = SVD ? rows8[lane + 32] : lane + 32;
-#pragma unroll
-            for (int c = 0; c < RB; ++c) slot[d1 * RB + c] += (acc_t)(q1[c] * sc);
-        }
+        if (h1) slot[(SVD ? rows8[lane + 32] : lane + 32) * S] += (acc_t)(q1 * sc);
     }
-    if (h0) {
-        const int d0 = SVD ? rows8[lane] : lane;
-#pragma unroll
-        for (int c = 0; c < RB; ++c) slot[d0 * RB + c] += (acc_t)(q0[c] * sc);
-    }
+    if (h0) slot[(SVD ? rows8[lane] : lane) * S] += (acc_t)(q0 * sc);
 }
 
-// One record into the warp's row slots (slot[r * RB + c]); returns its size.
-template <class T, int RB, class acc_t>
-__device__ __forceinline__ uint32_t rec_compute(const ApplyArgs& a, const float* X, const float* Tp,
-                                                const unsigned char* rec, acc_t* slot) {
+// One record, one panel column, into the warp's row slots.
+template <class T, int S, class acc_t>
+__device__ __forceinline__ void rec_compute(const float* xv, const unsigned char* rec, acc_t* slot) {
     const int lane = threadIdx.x & 31;
     const uint32_t* h = reinterpret_cast<const uint32_t*>(rec);
-    const int kind = (int)(h[0] & 0xffu), cnt = (int)(h[0] >> 8), w = (int)h[1], xo = (int)h[2];
+    const int kind = (int)(h[0] & 0xffu), cnt = (int)((h[0] >> 8) & 0xffu), roff = (int)(h[0] >> 16);
+    const int w = (int)h[1], xb = (int)h[2];
     const float sc = __uint_as_float(h[3]);
-    const int p0 = blockIdx.y * RB;
     const unsigned char* body = rec + kRecHdr;
     if (kind == REC_DENSE) {
-        slab_compute<T, RB, acc_t, false>(a, X + (int64_t)p0 * a.n, a.n, reinterpret_cast<const T*>(body), cnt, w,
-                                          xo, nullptr, sc, slot);
-        return rec_bytes(REC_DENSE, cnt, w, (int)sizeof(T));
-    }
-    if (kind == REC_SVD) {
-        slab_compute<T, RB, acc_t, true>(a, Tp, a.nT, reinterpret_cast<const T*>(body + pad4((uint32_t)cnt)), cnt,
-                                         w, xo, body, sc, slot);
-        return rec_bytes(REC_SVD, cnt, w, (int)sizeof(T));
-    }
-    if (kind == REC_CSR) {
+        slab_compute<T, S, acc_t, false>(xv, reinterpret_cast<const T*>(body), cnt, w, xb, nullptr, sc,
+                                         slot + roff * S);
+    } else if (kind == REC_SVD) {
+        slab_compute<T, S, acc_t, true>(xv, reinterpret_cast<const T*>(body + pad4((uint32_t)cnt)), cnt, w, xb, body,
+                                        sc, slot);
+    } else if (kind == REC_CSR) {
         const int32_t* sPtr = reinterpret_cast<const int32_t*>(body);
-        const int32_t* sCol = sPtr + cnt + 1;
-        const T* sA = reinterpret_cast<const T*>(sCol + w);
+        const T* sA = reinterpret_cast<const T*>(sPtr + cnt + 1);
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
             const int r = lane + 32 * hh;
             if (r >= cnt) continue;
             const int k0 = sPtr[r], k1 = sPtr[r + 1];
-            float q[RB];
-#pragma unroll
-            for (int c = 0; c < RB; ++c) q[c] = 0.f;
-#pragma unroll 2
-            for (int k = k0; k < k1; ++k) {
-                const float v = lds(sA + k);
-                const int col = sCol[k];
-#pragma unroll
-                for (int c = 0; c < RB; ++c)
-                    if (p0 + c < a.R) q[c] = fmaf(v, __ldg(X + (int64_t)(p0 + c) * a.n + col), q[c]);
-            }
-#pragma unroll
-            for (int c = 0; c < RB; ++c) slot[(xo + r) * RB + c] += (acc_t)(q[c] * sc);
+            float q = 0.f;
+#pragma unroll 4
+            for (int k = k0; k < k1; ++k) q = fmaf(lds(sA + k), xv[xb + k], q);
+            slot[(roff + r) * S] += (acc_t)(q * sc);
         }
-        return rec_bytes(REC_CSR, cnt, w, (int)sizeof(T));
+    } else {
+        // a long CSR row shared by the lanes, reduced by a fixed butterfly
+        const T* sA = reinterpret_cast<const T*>(body);
+        float q = 0.f;
+        for (int k = lane; k < w; k += 32) q = fmaf(lds(sA + k), xv[xb + k], q);
+        for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+        if (lane == 0) slot[roff * S] += (acc_t)(q * sc);
     }
-    // a long CSR row shared by the lanes, reduced by a fixed butterfly
-    const int32_t* sCol = reinterpret_cast<const int32_t*>(body);
-    const T* sA = reinterpret_cast<const T*>(sCol + w);
-    float q[RB];
-#pragma unroll
-    for (int c = 0; c < RB; ++c) q[c] = 0.f;
-    for (int k = lane; k < w; k += 32) {
-        const float v = lds(sA + k);
-        const int col = sCol[k];
-#pragma unroll
-        for (int c = 0; c < RB; ++c)
-            if (p0 + c < a.R) q[c] = fmaf(v, __ldg(X + (int64_t)(p0 + c) * a.n + col), q[c]);
-    }
-#pragma unroll
-    for (int c = 0; c < RB; ++c)
-        for (int o = 16; o > 0; o >>= 1) q[c] += __shfl_xor_sync(0xffffffffu, q[c], o);
-    if (lane == 0)
-#pragma unroll
-        for (int c = 0; c < RB; ++c) slot[xo * RB + c] += (acc_t)(q[c] * sc);
-    return rec_bytes(REC_CSR_LONG, cnt, w, (int)sizeof(T));
+}
+
+// Dynamic shared memory of the phase kernels.
+template <int RB, class acc_t>
+__host__ __device__ constexpr size_t phase2_smem() {
+    return sizeof(WarpPipe) * kWarps + (RB > 1 ? sizeof(XBuf) * kWarps : 0) +
+           sizeof(acc_t) * kWarps * kTileRows * RB + sizeof(double) * kWarps * RB;
+}
+template <int RB>
+__host__ __device__ constexpr size_t phase1_smem() {
+    return sizeof(WarpPipe) * kWarps + (RB > 1 ? sizeof(XBuf) * kWarps : 0);
 }
 
 // One CTA per row tile (heaviest first) and RHS panel.  Warp w streams the
@@ -417,21 +403,24 @@ __device__ __forceinline__ uint32_t rec_compute(const ApplyArgs& a, const float*
 // prefetch pipeline; the warps' row slots are then added in warp order, and
 // the epilogue applies the mode.
 template <class T, int RB, int MODE>
-__global__ void __launch_bounds__(256) k_phase2(ApplyArgs a, PageArgs pg, const float* __restrict__ Tbuf,
+__global__ void __launch_bounds__(256, RB == 1 ? 3 : 1) k_phase2(ApplyArgs a, PageArgs pg, const float* __restrict__ Tbuf,
                                                 SweepIO io) {
     using acc_t = typename std::conditional<MODE == MODE_RESID, double, float>::type;
-    // dynamic shared memory: pipes[kWarps], slots[kWarps][kTileRows * RB] (acc_t), colsum[kWarps][RB]
+    // dynamic shared memory: pipes[kWarps], (RB > 1) xbufs[kWarps],
+    // slots[kWarps][kTileRows * RB] (acc_t), colsum[kWarps][RB]
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpPipe* pipes = reinterpret_cast<WarpPipe*>(smem_raw);
-    auto slots = reinterpret_cast<acc_t(*)[kTileRows * RB]>(smem_raw + sizeof(WarpPipe) * kWarps);
-    auto colsum = reinterpret_cast<double(*)[RB]>(smem_raw + sizeof(WarpPipe) * kWarps +
-                                                  sizeof(acc_t) * kWarps * kTileRows * RB);
+    XBuf* xbufs = reinterpret_cast<XBuf*>(smem_raw + sizeof(WarpPipe) * kWarps);
+    const size_t o_slots = sizeof(WarpPipe) * kWarps + (RB > 1 ? sizeof(XBuf) * kWarps : 0);
+    auto slots = reinterpret_cast<acc_t(*)[kTileRows * RB]>(smem_raw + o_slots);
+    auto colsum = reinterpret_cast<double(*)[RB]>(smem_raw + o_slots + sizeof(acc_t) * kWarps * kTileRows * RB);
     const int tile = a.tile_order[blockIdx.x];
     const int panel = blockIdx.y;
     const int p0 = panel * RB;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tf = a.tile_first[tile], tc = a.tile_count[tile];
-    const float* X = io.xsel ? *io.xsel : io.xd;
+    const float* Xb = io.xsel ? *io.xsel : io.xd;
+    const float* X = Xb + (int64_t)p0 * a.n;  // this panel's columns
     const float* Tp = Tbuf + (int64_t)panel * RB * a.nT;
     WarpPipe& wp = pipes[warp];
     acc_t* slot = slots[warp];
@@ -443,22 +432,30 @@ __global__ void __launch_bounds__(256) k_phase2(ApplyArgs a, PageArgs pg, const 
     }
     __syncwarp();
     bool ok = true;
+    int consumed = 0, issued = min(kStages, pb - pa);
     for (int p = pa, n = 0; p < pb; ++p, ++n) {
         const int s = n % kStages;
         if (!__all_sync(0xffffffffu, mbar_wait(&wp.bar[s], (uint32_t)((n / kStages) & 1), kWaitLimit))) {
             ok = false;  // warp-uniform: a lane that gave up makes the whole warp stop
             break;
         }
-        const unsigned char* page = wp.buf[s];
-        const int nrec = (int)reinterpret_cast<const uint32_t*>(page)[0];
-        uint32_t off = kPageHdr;
-        for (int r = 0; r < nrec; ++r) off += rec_compute<T, RB, acc_t>(a, X, Tp, page + off, slot);
+        unsigned char* page = wp.buf[s];
+        page_columns<RB>(a, X, Tp, page, xbufs + warp, p0, [&](const float* xv, int c) {
+            for_records<T>(page, [&](const unsigned char* rec) { rec_compute<T, RB, acc_t>(xv, rec, slot + c); });
+        });
+        if (RB == 1) fence_proxy_async_smem();  // the gather wrote the stage; the next copy refills it
         __syncwarp();
-        if (lane == 0 && p + kStages < pb) issue_page(pg, p + kStages, wp, s);
+        consumed = n + 1;
+        if (p + kStages < pb) {
+            if (lane == 0) issue_page(pg, p + kStages, wp, s);
+            ++issued;
+        }
     }
-    if (!ok && lane == 0) atomicExch(io.status, VF_E_TIMEOUT);
+    if (!ok) {
+        drain(wp, consumed, issued);  // no bulk copy may stay in flight into this warp's stages
+        if (lane == 0) atomicExch(io.status, VF_E_TIMEOUT);
+    }
     __syncthreads();
-    (void)tf;
     double mysum[RB];
 #pragma unroll
     for (int c = 0; c < RB; ++c) mysum[c] = 0.0;
@@ -475,13 +472,13 @@ __global__ void __launch_bounds__(256) k_phase2(ApplyArgs a, PageArgs pg, const 
             Y[o] = (float)y;
         } else if (MODE == MODE_JACOBI) {
             float bn = io.E[o] + io.rho[p] * (float)y;
-            float dd = bn - X[o];
+            float dd = bn - Xb[o];
             Y[o] = bn;
 #pragma unroll
             for (int cc = 0; cc < RB; ++cc)
                 if (cc == c) mysum[cc] += (double)dd * dd;
         } else {
-            double rr = (double)io.E[o] - (double)X[o] + (double)io.rho[p] * (double)y;
+            double rr = (double)io.E[o] - (double)Xb[o] + (double)io.rho[p] * (double)y;
             Y[o] = (float)rr;
 #pragma unroll
             for (int cc = 0; cc < RB; ++cc)
@@ -505,9 +502,8 @@ __global__ void __launch_bounds__(256) k_phase2(ApplyArgs a, PageArgs pg, const 
 }
 
 // ------------------------------------------------------------ page packing
-// One warp per record: copies its data from the block pools into the page
-// pool (element type T), converting row pointers to record-local offsets and
-// SVD row ids to tile-local bytes.
+// One warp per record: writes its header, its body (from the block pools,
+// element type T) and its x-list entries into the page pool.
 template <class T>
 __global__ void k_pack_pages(const RecSrc* __restrict__ recs, int64_t nrec, const T* __restrict__ val,
                              const int32_t* __restrict__ aux, const float* __restrict__ scales,
@@ -517,23 +513,25 @@ __global__ void k_pack_pages(const RecSrc* __restrict__ recs, int64_t nrec, cons
     if (ri >= nrec) return;
     const RecSrc r = recs[ri];
     unsigned char* dst = pool + r.dst;
+    int32_t* xl = reinterpret_cast<int32_t*>(pool + r.xdst);
     uint32_t* h = reinterpret_cast<uint32_t*>(dst);
     const float sc = scales ? scales[r.blk] : 1.f;
     if (lane == 0) {
-        h[0] = (uint32_t)r.kind | ((uint32_t)r.cnt << 8);
+        h[0] = (uint32_t)r.kind | ((uint32_t)r.cnt << 8) | ((uint32_t)r.roff << 16);
         h[1] = (uint32_t)r.w;
-        h[2] = (uint32_t)r.x;
+        h[2] = (uint32_t)r.xbase;
         h[3] = __float_as_uint(sc);
         if (r.kind == REC_P1) {
             h[4] = (uint32_t)r.chunk;
             h[5] = (uint32_t)r.nchunks;
             h[6] = (uint32_t)r.first;
-            h[7] = 0u;
+            h[7] = (uint32_t)r.x;
         }
     }
     if (r.kind == REC_DENSE) {
         T* o = reinterpret_cast<T*>(dst + kRecHdr);
         for (int e = lane; e < r.cnt * r.w; e += 32) o[e] = val[r.val + e];
+        for (int k = lane; k < r.w; k += 32) xl[k] = r.x + k;
     } else if (r.kind == REC_SVD) {
         unsigned char* rows = dst + kRecHdr;
         for (int u = lane; u < r.cnt; u += 32) rows[u] = (unsigned char)(aux[r.idx + u] - r.tile_first);
@@ -543,38 +541,36 @@ __global__ void k_pack_pages(const RecSrc* __restrict__ recs, int64_t nrec, cons
             const int u = e / r.w, k = e - u * r.w;
             o[k * r.cnt + u] = val[r.val + e];
         }
+        for (int k = lane; k < r.w; k += 32) xl[k] = -1 - (r.x + k);
     } else if (r.kind == REC_CSR) {
         int32_t* ptr = reinterpret_cast<int32_t*>(dst + kRecHdr);
         for (int i = lane; i <= r.cnt; i += 32) ptr[i] = aux[r.idx + i] - r.nz0;
-        int32_t* cols = ptr + r.cnt + 1;
-        T* o = reinterpret_cast<T*>(cols + r.w);
+        T* o = reinterpret_cast<T*>(ptr + r.cnt + 1);
         for (int e = lane; e < r.w; e += 32) {
-            cols[e] = aux[r.idx2 + r.nz0 + e];
+            xl[e] = aux[r.idx2 + r.nz0 + e];
             o[e] = val[r.val + r.nz0 + e];
         }
     } else if (r.kind == REC_CSR_LONG) {
-        int32_t* cols = reinterpret_cast<int32_t*>(dst + kRecHdr);
-        T* o = reinterpret_cast<T*>(cols + r.w);
+        T* o = reinterpret_cast<T*>(dst + kRecHdr);
         for (int e = lane; e < r.w; e += 32) {
-            cols[e] = aux[r.idx2 + r.nz0 + e];
+            xl[e] = aux[r.idx2 + r.nz0 + e];
             o[e] = val[r.val + r.nz0 + e];
         }
     } else {  // phase 1
-        int32_t* cols = reinterpret_cast<int32_t*>(dst + kP1Hdr);
-        for (int j = lane; j < r.cnt; j += 32) cols[j] = aux[r.idx2 + j];
-        T* o = reinterpret_cast<T*>(dst + kP1Hdr + 4 * r.cnt);
+        for (int j = lane; j < r.cnt; j += 32) xl[j] = aux[r.idx2 + j];
+        T* o = reinterpret_cast<T*>(dst + kP1Hdr);
         for (int e = lane; e < r.cnt * r.w; e += 32) o[e] = val[r.val + e];
     }
 }
 
-__global__ void k_page_headers(const int32_t* __restrict__ nrec, const uint16_t* __restrict__ used, int64_t npages,
-                               unsigned char* __restrict__ pool) {
+__global__ void k_page_headers(const int32_t* __restrict__ nrec, const uint16_t* __restrict__ used,
+                               const int32_t* __restrict__ nx, int64_t npages, unsigned char* __restrict__ pool) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= npages) return;
     uint32_t* h = reinterpret_cast<uint32_t*>(pool + p * (int64_t)kPage);
     h[0] = (uint32_t)nrec[p];
     h[1] = used[p];
-    h[2] = 0u;
+    h[2] = (uint32_t)nx[p];
     h[3] = 0u;
 }
 
@@ -703,12 +699,21 @@ static vf_status build_pages(vf_hmat* H, std::vector<vf::RecSrc>& recs, const st
         if (prec == VF_PREC_BF16 && !H->has_bf16) continue;
         if (prec == VF_PREC_FP8 && !H->has_fp8) continue;
         const int es = es_of[prec];
-        std::vector<int32_t> nrec(npages, 0);
-        std::vector<uint16_t> used(npages, (uint16_t)kPageHdr);
+        // page = header | x list (nx entries) | records
+        std::vector<int32_t> nrec(npages, 0), nx(npages, 0), xcur(npages, 0);
+        for (size_t i = 0; i < recs.size(); ++i) nx[page_of[i]] += (int32_t)vf::rec_xn(recs[i].kind, recs[i].cnt, recs[i].w);
+        std::vector<uint16_t> used(npages);
+        for (int64_t pg = 0; pg < npages; ++pg) used[pg] = (uint16_t)(kPageHdr + 4 * nx[pg]);
         for (size_t i = 0; i < recs.size(); ++i) {
             const int64_t pg = page_of[i];
+            recs[i].xbase = xcur[pg];
+            recs[i].xdst = pg * (int64_t)kPage + kPageHdr + 4 * (int64_t)xcur[pg];
+            xcur[pg] += (int32_t)vf::rec_xn(recs[i].kind, recs[i].cnt, recs[i].w);
             recs[i].dst = pg * (int64_t)kPage + used[pg];
-            used[pg] = (uint16_t)(used[pg] + vf::rec_bytes(recs[i].kind, recs[i].cnt, recs[i].w, es));
+            const uint32_t u = used[pg] + vf::rec_bytes(recs[i].kind, recs[i].cnt, recs[i].w, es);
+            VF_CHECK(u <= (uint32_t)kPage && xcur[pg] <= kXMax, VF_E_INVAL,
+                     "page plan overflows a page (%u bytes, %d x entries)", u, xcur[pg]);
+            used[pg] = (uint16_t)u;
             nrec[pg]++;
         }
         vf::dbuf<unsigned char>& pool = phase1 ? H->p1pages[prec] : H->pages[prec];
@@ -717,8 +722,9 @@ static vf_status build_pages(vf_hmat* H, std::vector<vf::RecSrc>& recs, const st
         VF_TRY_CUDA(cudaMemset(pool.p, 0, std::max<int64_t>(npages, 1) * kPage));
         VF_TRY(u.upload(used));
         if (npages == 0) continue;
-        vf::dbuf<int32_t> dn;
+        vf::dbuf<int32_t> dn, dx;
         VF_TRY(dn.upload(nrec));
+        VF_TRY(dx.upload(nx));
         vf::dbuf<vf::RecSrc> dr;
         VF_TRY(dr.upload(recs));
         const int64_t nr = (int64_t)recs.size();
@@ -732,7 +738,7 @@ static vf_status build_pages(vf_hmat* H, std::vector<vf::RecSrc>& recs, const st
                 vf::k_pack_pages<__nv_fp8_e4m3><<<grid, 256>>>(dr.p, nr, H->val8.p, H->aux.p, H->scale8.p, pool.p);
             VF_TRY_CUDA(cudaGetLastError());
         }
-        vf::k_page_headers<<<(unsigned)vf::ceil_div(npages, 256), 256>>>(dn.p, u.p, npages, pool.p);
+        vf::k_page_headers<<<(unsigned)vf::ceil_div(npages, 256), 256>>>(dn.p, u.p, dx.p, npages, pool.p);
         VF_TRY_CUDA(cudaGetLastError());
         VF_TRY_CUDA(cudaDeviceSynchronize());
     }
@@ -763,43 +769,51 @@ vf_status vf_hmat::upload_all() {
         for (int32_t r = h_tile_first[k]; r < h_tile_first[k] + h_tile_count[k]; ++r) tile_of_row[r] = (int32_t)k;
     // ---- phase-2 records per tile (FP32 sizes; each fits a page)
     const int64_t cap = kPage - kPageHdr;
+    // FP32 bytes of a record in its page: header, body and its x-list entries
+    auto tot = [](int kind, int cnt, int w) {
+        return (int64_t)vf::rec_bytes(kind, cnt, w, 4) + 4 * (int64_t)vf::rec_xn(kind, cnt, w);
+    };
     std::vector<std::vector<vf::RecSrc>> per(ntiles);
     std::vector<int64_t> cost(ntiles, 0);
     for (size_t bi = 0; bi < B.size(); ++bi) {
         const vf::HBlock& b = B[bi];
         for (int32_t r = b.r0; r < b.r0 + b.m;) {
             const int32_t k = tile_of_row[r];
-            const int32_t tf = h_tile_first[k], tc = h_tile_count[k], lr0 = tf - b.r0;
-            vf::RecSrc rs{};
-            rs.blk = (int32_t)bi;
-            rs.tile_first = tf;
+            const int32_t tf = h_tile_first[k], tc = h_tile_count[k];
+            // the block's rows inside this tile: [rs, re)
+            const int32_t rs = std::max(b.r0, tf), re = std::min(b.r0 + b.m, tf + tc);
+            const int32_t cnt = re - rs, br = rs - b.r0, troff = rs - tf;
+            vf::RecSrc src{};
+            src.blk = (int32_t)bi;
+            src.tile_first = tf;
             if (b.kind == VF_BLK_DENSE) {
                 // the tile's column-major slab, split into column ranges of <= 128
-                const int32_t per_cols = (int32_t)std::min<int64_t>(128, (cap - kRecHdr) / (4 * (int64_t)tc));
+                const int32_t per_cols = (int32_t)std::min<int64_t>(128, (cap - kRecHdr) / (4 * (int64_t)cnt + 4));
                 for (int32_t c0 = 0; c0 < b.n; c0 += per_cols) {
-                    rs.kind = vf::REC_DENSE;
-                    rs.cnt = tc;
-                    rs.w = std::min(per_cols, b.n - c0);
-                    rs.x = b.c0 + c0;
-                    rs.val = b.off_val + (int64_t)lr0 * b.n + (int64_t)c0 * tc;
-                    per[k].push_back(rs);
+                    src.kind = vf::REC_DENSE;
+                    src.cnt = cnt;
+                    src.roff = troff;
+                    src.w = std::min(per_cols, b.n - c0);
+                    src.x = b.c0 + c0;
+                    src.val = b.off_val + (int64_t)br * b.n + (int64_t)c0 * cnt;
+                    per[k].push_back(src);
                 }
             } else if (b.kind == VF_BLK_CSR) {
                 const int32_t* rp = haux.data() + b.off_aux;
-                rs.idx2 = (int32_t)(b.off_aux + b.m + 1);
-                rs.val = b.off_val;
+                src.idx2 = (int32_t)(b.off_aux + b.m + 1);
+                src.val = b.off_val;
                 int32_t i = 0;
-                while (i < tc) {
-                    const int32_t row = lr0 + i;
+                while (i < cnt) {
+                    const int32_t row = br + i;
                     const int64_t nz_row = rp[row + 1] - rp[row];
-                    if (vf::rec_bytes(vf::REC_CSR, 1, (int)nz_row, 4) > cap) {
+                    if (tot(vf::REC_CSR, 1, (int)nz_row) > cap) {
                         // a long row: lanes share it, in pieces that fit a page
                         const int32_t piece = (int32_t)((cap - kRecHdr) / 8);
                         for (int64_t z = rp[row]; z < rp[row + 1]; z += piece) {
-                            vf::RecSrc lr = rs;
+                            vf::RecSrc lr = src;
                             lr.kind = vf::REC_CSR_LONG;
                             lr.cnt = 1;
-                            lr.x = i;
+                            lr.roff = troff + i;
                             lr.nz0 = (int32_t)z;
                             lr.w = (int32_t)std::min<int64_t>(piece, rp[row + 1] - z);
                             per[k].push_back(lr);
@@ -808,35 +822,35 @@ vf_status vf_hmat::upload_all() {
                         continue;
                     }
                     int32_t j = i + 1;
-                    while (j < tc && vf::rec_bytes(vf::REC_CSR, j + 1 - i, rp[lr0 + j + 1] - rp[lr0 + i], 4) <= cap)
+                    while (j < cnt && tot(vf::REC_CSR, j + 1 - i, rp[br + j + 1] - rp[br + i]) <= cap)
                         ++j;
-                    vf::RecSrc cr = rs;
+                    vf::RecSrc cr = src;
                     cr.kind = vf::REC_CSR;
                     cr.cnt = j - i;
-                    cr.x = i;
-                    cr.idx = (int32_t)(b.off_aux + lr0 + i);
-                    cr.nz0 = rp[lr0 + i];
-                    cr.w = rp[lr0 + j] - rp[lr0 + i];
+                    cr.roff = troff + i;
+                    cr.idx = (int32_t)(b.off_aux + br + i);
+                    cr.nz0 = rp[br + i];
+                    cr.w = rp[br + j] - rp[br + i];
                     if (cr.w > 0) per[k].push_back(cr);
                     i = j;
                 }
             } else {
                 const int32_t* rows = haux.data() + b.off_aux;
-                int32_t u0 = (int32_t)(std::lower_bound(rows, rows + b.m1, tf) - rows);
-                int32_t u1 = (int32_t)(std::lower_bound(rows, rows + b.m1, tf + tc) - rows);
+                int32_t u0 = (int32_t)(std::lower_bound(rows, rows + b.m1, rs) - rows);
+                int32_t u1 = (int32_t)(std::lower_bound(rows, rows + b.m1, re) - rows);
                 const int32_t per_rows =
-                    (int32_t)std::max<int64_t>(1, (cap - kRecHdr - 4) / (4 * (int64_t)b.q + 1));
+                    (int32_t)std::max<int64_t>(1, (cap - kRecHdr - 4 - 4 * (int64_t)b.q) / (4 * (int64_t)b.q + 1));
                 for (int32_t u = u0; u < u1; u += per_rows) {
-                    rs.kind = vf::REC_SVD;
-                    rs.cnt = std::min(per_rows, u1 - u);
-                    rs.w = b.q;
-                    rs.x = (int32_t)b.off_T;
-                    rs.val = b.off_val + (int64_t)u * b.q;
-                    rs.idx = (int32_t)(b.off_aux + u);
-                    per[k].push_back(rs);
+                    src.kind = vf::REC_SVD;
+                    src.cnt = std::min(per_rows, u1 - u);
+                    src.w = b.q;
+                    src.x = (int32_t)b.off_T;
+                    src.val = b.off_val + (int64_t)u * b.q;
+                    src.idx = (int32_t)(b.off_aux + u);
+                    per[k].push_back(src);
                 }
             }
-            r = tf + tc;
+            r = re;
         }
     }
     // each tile's records go to its warps by longest-processing-time first
@@ -849,9 +863,7 @@ vf_status vf_hmat::upload_all() {
     for (int64_t k = 0; k < ntiles; ++k) {
         std::vector<int32_t> ord(per[k].size());
         for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int32_t)i;
-        auto bytes_of = [&](int32_t i) {
-            return (int64_t)vf::rec_bytes(per[k][i].kind, per[k][i].cnt, per[k][i].w, 4);
-        };
+        auto bytes_of = [&](int32_t i) { return tot(per[k][i].kind, per[k][i].cnt, per[k][i].w); };
         std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return bytes_of(x) > bytes_of(y); });
         std::vector<std::vector<int32_t>> lists(kWarps);
         int64_t load[kWarps] = {0};
@@ -887,6 +899,7 @@ vf_status vf_hmat::upload_all() {
                      [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
     // ---- phase-1 records: V' rows of each SVD block, <= 128 rows per record
     std::vector<vf::RecSrc> p1;
+    std::vector<int32_t> split;  // per split block: first slot, chunks, q, T slot, block
     n_part_slots = 0;
     for (size_t bi = 0; bi < B.size(); ++bi) {
         if (B[bi].kind != VF_BLK_SVD) continue;
@@ -894,7 +907,10 @@ vf_status vf_hmat::upload_all() {
         const int32_t rows = (int32_t)std::min<int64_t>(128, std::max<int64_t>(1, (cap - kP1Hdr) / (4 * (int64_t)b.q + 4)));
         const int32_t nch = (int32_t)vf::ceil_div(b.n1, rows);
         const int32_t first = nch > 1 ? (int32_t)n_part_slots : 0;
-        if (nch > 1) n_part_slots += nch;
+        if (nch > 1) {
+            split.insert(split.end(), {first, nch, b.q, (int32_t)b.off_T, (int32_t)bi});
+            n_part_slots += nch;
+        }
         for (int32_t c = 0; c < nch; ++c) {
             vf::RecSrc rs{};
             rs.kind = vf::REC_P1;
@@ -912,13 +928,13 @@ vf_status vf_hmat::upload_all() {
     }
     // first-fit-decreasing into pages
     std::stable_sort(p1.begin(), p1.end(), [&](const vf::RecSrc& x, const vf::RecSrc& y) {
-        return vf::rec_bytes(x.kind, x.cnt, x.w, 4) > vf::rec_bytes(y.kind, y.cnt, y.w, 4);
+        return tot(x.kind, x.cnt, x.w) > tot(y.kind, y.cnt, y.w);
     });
     std::vector<int64_t> p1_page;
     {
         std::vector<int64_t> fill;  // open pages
         for (const auto& rs : p1) {
-            const int64_t bsz = vf::rec_bytes(rs.kind, rs.cnt, rs.w, 4);
+            const int64_t bsz = tot(rs.kind, rs.cnt, rs.w);
             int64_t pg = -1;
             // the most recent few pages are tried (keeps the plan linear-time)
             for (int64_t t = (int64_t)fill.size() - 1; t >= 0 && t >= (int64_t)fill.size() - 8; --t)
@@ -944,6 +960,8 @@ vf_status vf_hmat::upload_all() {
         p1_page.swap(pgs);
     }
     VF_TRY(build_pages(this, p1, p1_page, n_p1_pages, true));
+    n_split = (int64_t)split.size() / 5;
+    if (n_split > 0) VF_TRY(p1_split.upload(split));
     VF_TRY(tile_first.upload(h_tile_first));
     VF_TRY(tile_count.upload(h_tile_count));
     VF_TRY(tile_page_ptr.upload(h_tile_page_ptr));
@@ -959,7 +977,6 @@ struct Workspace {
     int prec = 0;
     int RB = 0, npanels = 0;
     dbuf<float> Xt, Yt, Et, Bt[2], rho_t, Tbuf, part, Rbuf;
-    dbuf<int> counters;
     dbuf<int> status;         // VF_OK, or VF_E_TIMEOUT if a bounded wait gave up
     dbuf<double> colpart, enorm2, colres;
     dbuf<LoopState> loop;
@@ -1057,8 +1074,6 @@ static vf_status ws_get(const vf_hmat* h, int R, int prec, Workspace** out) {
     int64_t nT = std::max<int64_t>(h->n_T, 1);
     VF_TRY(w->Tbuf.alloc((int64_t)w->npanels * w->RB * nT));
     VF_TRY(w->part.alloc(std::max<int64_t>((int64_t)w->npanels * std::max<int64_t>(h->n_part_slots, 1) * w->RB * 128, 1)));
-    VF_TRY(w->counters.alloc((int64_t)w->npanels * nT));
-    VF_TRY_CUDA(cudaMemset(w->counters.p, 0, (int64_t)w->npanels * nT * sizeof(int)));
     VF_TRY(w->colpart.alloc(std::max<int64_t>(ntiles * R, 1)));
     VF_TRY(w->enorm2.alloc(R));
     VF_TRY(w->colres.alloc(R));
@@ -1080,8 +1095,7 @@ template <class T, int RB, int MODE>
 static vf_status launch_phase2(dim3 grid, const ApplyArgs& a, PageArgs pg, const float* Tbuf, const SweepIO& io,
                                cudaStream_t st) {
     using acc_t = typename std::conditional<MODE == MODE_RESID, double, float>::type;
-    const size_t smem = sizeof(WarpPipe) * kWarps + sizeof(acc_t) * kWarps * kTileRows * RB +
-                        sizeof(double) * kWarps * RB;
+    const size_t smem = phase2_smem<RB, acc_t>();
     k_phase2<T, RB, MODE><<<grid, 256, smem, st>>>(a, pg, Tbuf, io);
     return VF_OK;
 }
@@ -1091,15 +1105,14 @@ static vf_status launch_phase2(dim3 grid, const ApplyArgs& a, PageArgs pg, const
 template <class T, int RB, int MODE>
 static cudaError_t phase2_attr() {
     using acc_t = typename std::conditional<MODE == MODE_RESID, double, float>::type;
-    const size_t smem = sizeof(WarpPipe) * kWarps + sizeof(acc_t) * kWarps * kTileRows * RB +
-                        sizeof(double) * kWarps * RB;
+    const size_t smem = phase2_smem<RB, acc_t>();
     return cudaFuncSetAttribute(k_phase2<T, RB, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 template <class T, int RB>
 static cudaError_t phase2_attrs_rb() {
     cudaError_t e = cudaFuncSetAttribute(k_phase1<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(WarpPipe) * kWarps));
+                                         (int)phase1_smem<RB>());
     if (e == cudaSuccess) e = phase2_attr<T, RB, MODE_APPLY>();
     if (e == cudaSuccess) e = phase2_attr<T, RB, MODE_JACOBI>();
     if (e == cudaSuccess) e = phase2_attr<T, RB, MODE_RESID>();
@@ -1134,11 +1147,16 @@ static vf_status launch_multiply_t(const vf_hmat* h, int prec, const ApplyArgs& 
                                    const float* E, const float* rho, cudaStream_t st) {
     const int64_t ntiles = (int64_t)h->h_tile_first.size();
     if (h->n_p1_pages > 0) {
-        const int64_t persistent = (int64_t)num_sms(h->device) * 4;
+        const int64_t persistent = (int64_t)num_sms(h->device) * 3;
         dim3 g1((unsigned)std::min<int64_t>(ceil_div(h->n_p1_pages, kWarps), persistent), (unsigned)w->npanels);
         PageArgs p1{h->p1pages[prec].p, h->p1_used[prec].p};
-        k_phase1<T, RB><<<g1, 256, sizeof(WarpPipe) * kWarps, st>>>(a, p1, h->n_p1_pages, xsel, xd, w->Tbuf.p,
-                                                                   w->part.p, w->counters.p, w->status.p);
+        k_phase1<T, RB><<<g1, 256, phase1_smem<RB>(), st>>>(a, p1, h->n_p1_pages, xsel, xd, w->Tbuf.p,
+                                                            w->part.p, w->status.p);
+        if (h->n_split > 0) {
+            dim3 gr((unsigned)h->n_split, (unsigned)w->npanels);
+            k_p1_reduce<RB><<<gr, 128, 0, st>>>(a, h->p1_split.p, prec == VF_PREC_FP8 ? h->scale8.p : nullptr,
+                                                w->part.p, w->Tbuf.p);
+        }
     }
     SweepIO io{xsel, ysel, xd, yd, E, rho, w->colpart.p, ntiles, w->status.p};
     dim3 g2((unsigned)ntiles, (unsigned)w->npanels);

@@ -378,10 +378,10 @@ struct PackDesc {
     int64_t lists_off;  // SVD: rows/cols in the probe index list
 };
 
-// dense: one CTA per block.  The values of the block's rows that fall in
-// one row tile (tree leaf) form a column-major slab at
-// off_val + (tile_first - r0) * n, so the multiply reads it with one lane per
-// row and coalesced loads: element (r, c) is at slab + c * tile_rows + (r - tile_first).
+// dense: one CTA per block.  The block's rows that fall in one row tile
+// [rs, re) form a column-major slab at off_val + (rs - r0) * n, so the
+// multiply reads it with one lane per row and coalesced loads: element
+// (row, c) is at slab + c * (re - rs) + (row - rs).
 __global__ void k_pack_dense(Geo g, const PackDesc* __restrict__ pk, const int32_t* __restrict__ tile_of_row,
                              const int32_t* __restrict__ tile_first, const int32_t* __restrict__ tile_count,
                              float* __restrict__ val) {
@@ -390,8 +390,8 @@ __global__ void k_pack_dense(Geo g, const PackDesc* __restrict__ pk, const int32
         const int c = (int)(e / d.m), r = (int)(e - (int64_t)c * d.m);  // consecutive threads: consecutive rows
         const int row = d.r0 + r;
         const int t = tile_of_row[row];
-        const int tf = tile_first[t], tc = tile_count[t];
-        val[d.off_val + (int64_t)(tf - d.r0) * d.n + (int64_t)c * tc + (row - tf)] = entry(g, row, d.c0 + c);
+        const int rs = max(d.r0, tile_first[t]), re = min(d.r0 + d.m, tile_first[t] + tile_count[t]);
+        val[d.off_val + (int64_t)(rs - d.r0) * d.n + (int64_t)c * (re - rs) + (row - rs)] = entry(g, row, d.c0 + c);
     }
 }
 
@@ -1159,15 +1159,26 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
             pk_svd[stage_ref[id].buf].push_back(p);
         }
     }
+    // row tiles of the multiply: runs of consecutive leaves holding <= 64 rows
+    H->h_tile_first.clear();
+    H->h_tile_count.clear();
+    for (size_t k = 0; k < Bd.leaf_first.size(); ++k) {
+        if (!H->h_tile_first.empty() && H->h_tile_count.back() + Bd.leaf_count[k] <= 64) {
+            H->h_tile_count.back() += Bd.leaf_count[k];
+        } else {
+            H->h_tile_first.push_back(Bd.leaf_first[k]);
+            H->h_tile_count.push_back(Bd.leaf_count[k]);
+        }
+    }
     if (!pk_dense.empty()) {
         dbuf<PackDesc> d;
         dbuf<int32_t> d_tor, d_tf, d_tc;
         std::vector<int32_t> tor(n);
-        for (size_t k = 0; k < Bd.leaf_first.size(); ++k)
-            for (int32_t r = Bd.leaf_first[k]; r < Bd.leaf_first[k] + Bd.leaf_count[k]; ++r) tor[r] = (int32_t)k;
+        for (size_t k = 0; k < H->h_tile_first.size(); ++k)
+            for (int32_t r = H->h_tile_first[k]; r < H->h_tile_first[k] + H->h_tile_count[k]; ++r) tor[r] = (int32_t)k;
         VF_TRY(d_tor.upload(tor));
-        VF_TRY(d_tf.upload(Bd.leaf_first));
-        VF_TRY(d_tc.upload(Bd.leaf_count));
+        VF_TRY(d_tf.upload(H->h_tile_first));
+        VF_TRY(d_tc.upload(H->h_tile_count));
         VF_TRY(d.upload(pk_dense));
         k_pack_dense<<<(unsigned)pk_dense.size(), 256, 0, st>>>(g, d.p, d_tor.p, d_tf.p, d_tc.p, H->val.p);
         VF_TRY_CUDA(cudaGetLastError());
@@ -1208,9 +1219,7 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
     VF_TRY_CUDA(cudaStreamSynchronize(st));
     double t4 = now_seconds();
     S.t_pack = t4 - t3;
-    // ---------------- apply work lists: row tiles are the tree leaves
-    H->h_tile_first = Bd.leaf_first;
-    H->h_tile_count = Bd.leaf_count;
+    // ---------------- the multiply's pages over the row tiles
     VF_TRY(H->upload_all());
     S.t_total = now_seconds() - t0;
     H->stats = S;

@@ -23,49 +23,72 @@ struct HBlock {
 };
 
 // The multiply streams the matrix from tile-major "pages": kPage-byte
-// blocks of self-describing records, built once from the block pools.  A
-// page is one bulk copy into a warp's prefetch stage; its records are then
-// read from shared memory.  Record layouts (4-byte aligned arrays):
-//   header (16 B): u32 kind | cnt << 8, u32 w, i32 x, f32 scale
+// blocks, built once from the block pools.  A page is one bulk copy into a
+// warp's prefetch stage.  Layout:
+//   page header (16 B): u32 number of records, u32 bytes used, u32 nx, u32 0
+//   x list (nx x i32): where each x value the page's records need comes from
+//               (>= 0: a tree-order row of X; < 0: T slot -1 - v); on arrival
+//               the warp gathers all of them in one round and overwrites the
+//               list with the values, so records compute from shared memory
+//   records, 4-byte aligned:
+//   header (16 B): u32 kind | cnt << 8 | roff << 16, u32 w, u32 xbase (first
+//               entry in the page's x list), f32 scale
 //   dense  (1): cnt x w column-major slab (element (r, k) at k * cnt + r) of
-//               tile rows 0..cnt-1, columns x .. x + w - 1
-//   CSR    (2): w = nnz, x = first tile row; row pointers (cnt + 1, from 0),
-//               column indices (nnz), values (nnz)
-//   SVD    (3): w = q, x = T slot; tile-local rows (cnt bytes), U' rows (cnt x q)
-//   long CSR row (5): w = nnz, x = tile row; column indices, values
-//   phase-1 (6): header + i32 chunk, nchunks, first partial slot, pad; then
-//               w = q, x = T slot, cnt = rows; column indices (cnt), V' rows (cnt x q)
-// A page starts with a 16-byte header: u32 number of records, u32 bytes used.
-constexpr int kPage = 2048;
+//               tile rows roff..roff+cnt-1; x entries: its w columns
+//   CSR    (2): tile rows roff..roff+cnt-1, w = nnz; row pointers (cnt + 1,
+//               from 0), values (nnz); x entries: the nonzeros' columns
+//   SVD    (3): w = q; tile-local rows (cnt bytes), U' (cnt x q) as a
+//               column-major slab; x entries: its q T slots
+//   long CSR row (5): tile row roff, w = nnz; values; x entries: columns
+//   phase-1 (6): header + i32 chunk, nchunks, first partial slot, T slot;
+//               cnt = rows, w = q; V' rows (cnt x q, row-major); x entries:
+//               the rows' columns
+#ifndef VF_PAGE_BYTES
+#define VF_PAGE_BYTES 4096
+#endif
+constexpr int kPage = VF_PAGE_BYTES;
 constexpr int kPageHdr = 16;
 constexpr int kRecHdr = 16;
 constexpr int kP1Hdr = 32;
+// Every x entry comes with at least 4 bytes of FP32 values in its record,
+// so a page planned with FP32 sizes holds fewer than kPage / 8 x entries;
+// the planner checks this bound.
+constexpr int kXMax = kPage / 8;
 enum RecKind { REC_DENSE = 1, REC_CSR = 2, REC_SVD = 3, REC_CSR_LONG = 5, REC_P1 = 6 };
 
 __host__ __device__ inline uint32_t pad4(uint32_t b) { return (b + 3u) & ~3u; }
 
-// bytes of a record with element size es
+// bytes of a record's body and header (not its x entries), element size es
 __host__ __device__ inline uint32_t rec_bytes(int kind, int cnt, int w, int es) {
     switch (kind) {
         case REC_DENSE: return kRecHdr + pad4((uint32_t)(cnt * w * es));
         case REC_SVD: return kRecHdr + pad4((uint32_t)cnt) + pad4((uint32_t)(cnt * w * es));
-        case REC_CSR: return kRecHdr + 4u * (cnt + 1) + 4u * w + pad4((uint32_t)(w * es));
-        case REC_CSR_LONG: return kRecHdr + 4u * w + pad4((uint32_t)(w * es));
-        default: return kP1Hdr + 4u * cnt + pad4((uint32_t)(cnt * w * es));
+        case REC_CSR: return kRecHdr + 4u * (cnt + 1) + pad4((uint32_t)(w * es));
+        case REC_CSR_LONG: return kRecHdr + pad4((uint32_t)(w * es));
+        default: return kP1Hdr + pad4((uint32_t)(cnt * w * es));
     }
+}
+
+// x entries a record adds to its page's x list
+__host__ __device__ inline uint32_t rec_xn(int kind, int cnt, int w) {
+    return kind == REC_P1 ? (uint32_t)cnt : (uint32_t)w;
 }
 
 // Where one record's data comes from in the block pools (build time only).
 struct RecSrc {
     int32_t kind, cnt, w, x;
     int32_t blk;
+    int32_t roff;        // dense: first tile row of the slab
     int32_t tile_first;  // SVD: row ids are stored relative to it
     int64_t val;         // element offset of the first value in the block pool
     int32_t idx;         // CSR: aux offset of the first row pointer; SVD: of the first row id
     int32_t idx2;        // CSR / long row / phase 1: aux offset of the first column index
     int32_t nz0;         // CSR: block-local offset of the first nonzero
     int32_t chunk, nchunks, first;  // phase 1
-    int64_t dst;         // byte offset in the page pool (per element size)
+    int64_t dst;         // byte offset of the record in the page pool (per element size)
+    int64_t xdst;        // byte offset of its first x-list entry in the page pool
+    int32_t xbase;       // its first x-list entry within the page
+    int32_t pad;
 };
 
 }  // namespace vf
@@ -83,6 +106,7 @@ struct vf_hmat {
     std::vector<int32_t> h_tile_order;                // launch order: heaviest tile first
     int64_t n_pages = 0, n_p1_pages = 0;              // phase-2 / phase-1 pages
     int64_t n_part_slots = 0;                         // phase-1 partial slots (split blocks)
+    int64_t n_split = 0;                              // blocks whose V' rows span several records
     int64_t n_val = 0, n_aux = 0, n_T = 0;            // pool sizes (elements); n_T per RHS column
     int32_t max_q = 0;
     int64_t n_hier = 0;
@@ -100,6 +124,7 @@ struct vf_hmat {
     vf::dbuf<unsigned char> pages[3], p1pages[3];
     vf::dbuf<uint16_t> page_used[3], p1_used[3];  // bytes used per page
     vf::dbuf<int32_t> tile_first, tile_count, tile_page_ptr, tile_order;
+    vf::dbuf<int32_t> p1_split;                       // n_split x {first slot, chunks, q, T slot, block}
     bool has_bf16 = false, has_fp8 = false;
     int64_t bytes_payload(int prec) const;        // bytes of the stored representation
     vf_status upload_all();
