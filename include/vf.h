@@ -219,6 +219,7 @@ typedef struct {
     int32_t sweeps;           /* low-precision (or FP32) sweeps */
     int32_t refinements;      /* outer refinement steps */
     int32_t converged;        /* 1 if every column met rtol */
+    int32_t kernels;          /* device kernels the call launched (graph body counted per sweep run) */
     double max_rel_residual;  /* max over columns of ||r||_2 / ||E||_2 */
 } vf_solve_stats;
 

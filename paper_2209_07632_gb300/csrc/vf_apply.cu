@@ -23,6 +23,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <queue>
 
 #include "vf_bulk.cuh"
 #include "vf_hmat.cuh"
@@ -69,12 +70,6 @@ struct ApplyArgs {
 constexpr int kStages = VF_STAGES;
 constexpr uint32_t kWaitLimit = 1u << 22;  // polls before a wait reports a timeout
 
-__device__ __forceinline__ int pow2ceil32(int q) {
-    int g = 1;
-    while (g < q && g < 32) g <<= 1;
-    return g;
-}
-
 template <class T> __device__ __forceinline__ float lds(const T* p);
 template <> __device__ __forceinline__ float lds<float>(const float* p) { return *p; }
 template <> __device__ __forceinline__ float lds<__nv_bfloat16>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
@@ -117,19 +112,25 @@ __device__ __forceinline__ float x_of(const ApplyArgs& a, const float* X, const 
 __device__ __forceinline__ void load_col(const ApplyArgs& a, const float* X, const float* Tp, const int32_t* xl,
                                          int nx, int c, float (&v)[kXMax / 32]) {
     const int lane = threadIdx.x & 31;
+    const int nj = (nx + 31) >> 5;  // warp-uniform: rounds past it are skipped
 #pragma unroll
     for (int j = 0; j < kXMax / 32; ++j) {
-        const int e = lane + 32 * j;
-        v[j] = e < nx ? x_of(a, X, Tp, xl[e], c) : 0.f;
+        if (j < nj) {
+            const int e = lane + 32 * j;
+            v[j] = e < nx ? x_of(a, X, Tp, xl[e], c) : 0.f;
+        }
     }
 }
 
 __device__ __forceinline__ void store_col(int nx, const float (&v)[kXMax / 32], float* xv) {
     const int lane = threadIdx.x & 31;
+    const int nj = (nx + 31) >> 5;
 #pragma unroll
     for (int j = 0; j < kXMax / 32; ++j) {
-        const int e = lane + 32 * j;
-        if (e < nx) xv[e] = v[j];
+        if (j < nj) {
+            const int e = lane + 32 * j;
+            if (e < nx) xv[e] = v[j];
+        }
     }
 }
 
@@ -148,26 +149,32 @@ __device__ __forceinline__ void gather_in_place(const ApplyArgs& a, const float*
 // ------------------------------------------------------------ phase 1
 // T_b = V'_b^T X[cols_b] from phase-1 records, one panel column at a time
 // (xv: that column's x values, indexed by x-list entry).  T: per panel
-// RB x nT (column c at c * nT).  A block split into several records writes
-// one partial per chunk; k_p1_reduce adds them in chunk order.
+// RB x nT (column c at c * nT).  A block whose V' rows span several records
+// (chunks) has them in one warp, in order: the warp carries the running
+// sum in shared memory (carry[c * 128 + k]) and writes T after the last
+// chunk.  A very large block is cut into several such units; each unit then
+// writes its sum to a partial slot and k_p1_reduce adds the units in order.
 template <class T, int RB>
 __device__ __forceinline__ void p1_column(const ApplyArgs& a, const float* xv, const unsigned char* rec, int c,
-                                          float* __restrict__ Tbuf, float* __restrict__ part, int panel) {
+                                          float* __restrict__ Tbuf, float* __restrict__ part,
+                                          float* __restrict__ carry, int panel) {
     const int lane = threadIdx.x & 31;
-    const uint32_t* h = reinterpret_cast<const uint32_t*>(rec);
-    const int nrows = (int)((h[0] >> 8) & 0xffu), q = (int)h[1], xb = (int)h[2];
-    const float sc = __uint_as_float(h[3]);
-    const int chunk = (int)h[4], nch = (int)h[5], first = (int)h[6], offT = (int)h[7];
+    const uint4 h0 = reinterpret_cast<const uint4*>(rec)[0], h1 = reinterpret_cast<const uint4*>(rec)[1];
+    const int nrows = (int)((h0.x >> 8) & 0xffu), q = (int)h0.y, xb = (int)h0.z;
+    const float sc = __uint_as_float(h0.w);
+    const int chunk = (int)h1.x, nch = (int)h1.y, slot = (int)h1.z, offT = (int)h1.w;
     const T* sV = reinterpret_cast<const T*>(rec + kP1Hdr);
-    const int g = pow2ceil32(q);
-    const int step = 32 / g;
-    const int sub = lane / g, kk = lane - sub * g;
-    const int nk = (q + 31) / 32;
+    const int lg = q >= 32 ? 5 : (q <= 1 ? 0 : 32 - __clz(q - 1));  // g = 2^lg lanes per row
+    const int g = 1 << lg;
+    const int step = 32 >> lg;
+    const int sub = lane >> lg, kk = lane & (g - 1);
+    const int nk = (q + 31) >> 5;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     if (q <= 32) {
         if (kk < q)
 #pragma unroll 4
             for (int j = sub; j < nrows; j += step) acc[0] = fmaf(lds(sV + j * q + kk), xv[xb + j], acc[0]);
+        for (int o = 16; o >= g; o >>= 1) acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
     } else {
         for (int j = 0; j < nrows; ++j) {  // q > 32: the whole warp shares each row
             const float x = xv[xb + j];
@@ -177,46 +184,46 @@ __device__ __forceinline__ void p1_column(const ApplyArgs& a, const float* xv, c
                 if (t < nk && k < q) acc[t] = fmaf(lds(sV + j * q + k), x, acc[t]);
             }
         }
+        // g = 32: the warp is one group, nothing to add across lanes
     }
-    for (int o = 16; o >= g; o >>= 1)
-#pragma unroll
-        for (int t = 0; t < 4; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
     if (sub != 0) return;
-    if (nch == 1) {
-        float* dst = Tbuf + ((int64_t)panel * RB + c) * a.nT + offT;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int k = kk + 32 * t;
-            if (t < nk && k < q) dst[k] = acc[t] * sc;
-        }
-        return;
-    }
-    float* mypart = part + ((int64_t)panel * a.nparts + first + chunk) * (RB * 128) + c * 128;
+    // the unit's result goes to T (scaled) or, for a unit of a cut block, to its partial slot
+    float* dst = slot < 0 ? Tbuf + ((int64_t)panel * RB + c) * a.nT + offT
+                          : part + ((int64_t)panel * a.nparts + slot) * (RB * 128) + c * 128;
+    const float f = slot < 0 ? sc : 1.f;
+    float* cr = carry + c * 128;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
         const int k = kk + 32 * t;
-        if (t < nk && k < q) mypart[k] = acc[t];
+        if (t < nk && k < q) {
+            const float v = chunk == 0 ? acc[t] : cr[k] + acc[t];
+            if (chunk == nch - 1) dst[k] = v * f;
+            else cr[k] = v;
+        }
     }
 }
 
-// T of the blocks whose V' rows were split over several records: the chunk
-// partials added in chunk order, then scaled.  One CTA per (split block,
-// panel); split[5 i ..] = first partial slot, chunks, q, T slot, block.
+// T of the blocks cut into several units: the unit sums added in unit
+// order, then scaled.  One warp per (cut block, panel); split[5 i ..] =
+// first partial slot, units, q, T slot, block.
 template <int RB>
-__global__ void k_p1_reduce(ApplyArgs a, const int32_t* __restrict__ split, const float* __restrict__ scales,
-                            const float* __restrict__ part, float* __restrict__ Tbuf) {
-    const int32_t* d = split + 5 * (int64_t)blockIdx.x;
+__global__ void __launch_bounds__(256) k_p1_reduce(ApplyArgs a, const int32_t* __restrict__ split, int64_t nsplit,
+                                                   const float* __restrict__ scales, const float* __restrict__ part,
+                                                   float* __restrict__ Tbuf) {
+    const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= nsplit) return;
+    const int32_t* d = split + 5 * i;
     const int first = d[0], nch = d[1], q = d[2], offT = d[3];
     const float sc = scales ? scales[d[4]] : 1.f;
     const int panel = blockIdx.y;
     const float* pb = part + ((int64_t)panel * a.nparts + first) * (RB * 128);
-    for (int e = threadIdx.x; e < RB * 128; e += blockDim.x) {
-        const int c = e >> 7, k = e & 127;
-        if (k >= q || panel * RB + c >= a.R) continue;
-        float sum = 0.f;
-        for (int cc = 0; cc < nch; ++cc) sum += pb[(int64_t)cc * (RB * 128) + c * 128 + k];
-        Tbuf[((int64_t)panel * RB + c) * a.nT + offT + k] = sum * sc;
-    }
+    for (int c = 0; c < RB && panel * RB + c < a.R; ++c)
+        for (int k = lane; k < q; k += 32) {
+            float sum = 0.f;
+            for (int cc = 0; cc < nch; ++cc) sum += pb[(int64_t)cc * (RB * 128) + c * 128 + k];
+            Tbuf[((int64_t)panel * RB + c) * a.nT + offT + k] = sum * sc;
+        }
 }
 
 // Walk a page's records (after its header and x list); f(record) returns
@@ -225,12 +232,12 @@ template <class T, class F>
 __device__ __forceinline__ void for_records(const unsigned char* page, F f) {
     const uint32_t* ph = reinterpret_cast<const uint32_t*>(page);
     const int nrec = (int)ph[0];
-    uint32_t off = kPageHdr + 4u * ph[2];
+    uint32_t off = page_rec0(ph[2]);
     for (int r = 0; r < nrec; ++r) {
-        const uint32_t* h = reinterpret_cast<const uint32_t*>(page + off);
-        const int kind = (int)(h[0] & 0xffu), cnt = (int)((h[0] >> 8) & 0xffu);
+        const uint2 h = *reinterpret_cast<const uint2*>(page + off);
+        const int kind = (int)(h.x & 0xffu), cnt = (int)((h.x >> 8) & 0xffu);
         f(page + off);
-        off += rec_bytes(kind, cnt, (int)h[1], (int)sizeof(T));
+        off += rec_bytes(kind, cnt, (int)h.y, (int)sizeof(T));
     }
 }
 
@@ -265,30 +272,33 @@ __device__ __forceinline__ void page_columns(const ApplyArgs& a, const float* X,
     __syncwarp();
 }
 
+// Phase 1: warp w of the grid streams pages [warp_ptr[w], warp_ptr[w + 1]),
+// balanced at build time.
 template <class T, int RB>
-__global__ void __launch_bounds__(256) k_phase1(ApplyArgs a, PageArgs pg, int64_t npages, const float* const* xsel,
+__global__ void __launch_bounds__(256) k_phase1(ApplyArgs a, PageArgs pg, const int32_t* __restrict__ warp_ptr,
+                                                const float* const* xsel,
                                                 const float* xd, float* __restrict__ Tbuf, float* __restrict__ part,
                                                 int* __restrict__ status) {
-    // dynamic shared memory: pipes[kWarps], then (RB > 1) xbufs[kWarps]
+    // dynamic shared memory: pipes[kWarps], (RB > 1) xbufs[kWarps], carry[kWarps][RB * 128]
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpPipe* pipes = reinterpret_cast<WarpPipe*>(smem_raw);
     XBuf* xbufs = reinterpret_cast<XBuf*>(smem_raw + sizeof(WarpPipe) * kWarps);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* carry = reinterpret_cast<float*>(smem_raw + sizeof(WarpPipe) * kWarps +
+                                            (RB > 1 ? sizeof(XBuf) * kWarps : 0)) +
+                   warp * RB * 128;
     WarpPipe& wp = pipes[warp];
     const int panel = blockIdx.y, p0 = panel * RB;
     const float* X = (xsel ? *xsel : xd) + (int64_t)p0 * a.n;
-    const int64_t wstride = (int64_t)gridDim.x * kWarps;
-    const int64_t p_first = (int64_t)blockIdx.x * kWarps + warp;
+    const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
+    const int pa = warp_ptr[gw], pb = warp_ptr[gw + 1];
     if (lane == 0) {
         pipe_init(wp);
-        for (int s = 0; s < kStages; ++s)
-            if (p_first + s * wstride < npages) issue_page(pg, p_first + s * wstride, wp, s);
+        for (int s = 0; s < kStages && pa + s < pb; ++s) issue_page(pg, pa + s, wp, s);
     }
     __syncwarp();
-    int n = 0, issued = 0;
-    for (int s = 0; s < kStages; ++s)
-        if (p_first + s * wstride < npages) ++issued;
-    for (int64_t p = p_first; p < npages; p += wstride, ++n) {
+    int n = 0, issued = min(kStages, pb - pa);
+    for (int p = pa; p < pb; ++p, ++n) {
         const int s = n % kStages;
         // warp-uniform decision: a lane that gave up makes the whole warp stop
         if (!__all_sync(0xffffffffu, mbar_wait(&wp.bar[s], (uint32_t)((n / kStages) & 1), kWaitLimit))) {
@@ -298,12 +308,14 @@ __global__ void __launch_bounds__(256) k_phase1(ApplyArgs a, PageArgs pg, int64_
         }
         unsigned char* page = wp.buf[s];
         page_columns<RB>(a, X, nullptr, page, xbufs + warp, p0, [&](const float* xv, int c) {
-            for_records<T>(page, [&](const unsigned char* rec) { p1_column<T, RB>(a, xv, rec, c, Tbuf, part, panel); });
+            for_records<T>(page, [&](const unsigned char* rec) {
+                p1_column<T, RB>(a, xv, rec, c, Tbuf, part, carry, panel);
+            });
         });
         if (RB == 1) fence_proxy_async_smem();  // the gather wrote the stage; the next copy refills it
         __syncwarp();
-        if (p + kStages * wstride < npages) {
-            if (lane == 0) issue_page(pg, p + kStages * wstride, wp, s);
+        if (p + kStages < pb) {
+            if (lane == 0) issue_page(pg, p + kStages, wp, s);
             ++issued;
         }
     }
@@ -353,10 +365,10 @@ __device__ __forceinline__ void slab_compute(const float* xv, const T* __restric
 template <class T, int S, class acc_t>
 __device__ __forceinline__ void rec_compute(const float* xv, const unsigned char* rec, acc_t* slot) {
     const int lane = threadIdx.x & 31;
-    const uint32_t* h = reinterpret_cast<const uint32_t*>(rec);
-    const int kind = (int)(h[0] & 0xffu), cnt = (int)((h[0] >> 8) & 0xffu), roff = (int)(h[0] >> 16);
-    const int w = (int)h[1], xb = (int)h[2];
-    const float sc = __uint_as_float(h[3]);
+    const uint4 h = *reinterpret_cast<const uint4*>(rec);
+    const int kind = (int)(h.x & 0xffu), cnt = (int)((h.x >> 8) & 0xffu), roff = (int)(h.x >> 16);
+    const int w = (int)h.y, xb = (int)h.z;
+    const float sc = __uint_as_float(h.w);
     const unsigned char* body = rec + kRecHdr;
     if (kind == REC_DENSE) {
         slab_compute<T, S, acc_t, false>(xv, reinterpret_cast<const T*>(body), cnt, w, xb, nullptr, sc,
@@ -395,7 +407,7 @@ __host__ __device__ constexpr size_t phase2_smem() {
 }
 template <int RB>
 __host__ __device__ constexpr size_t phase1_smem() {
-    return sizeof(WarpPipe) * kWarps + (RB > 1 ? sizeof(XBuf) * kWarps : 0);
+    return sizeof(WarpPipe) * kWarps + (RB > 1 ? sizeof(XBuf) * kWarps : 0) + sizeof(float) * kWarps * RB * 128;
 }
 
 // One CTA per row tile (heaviest first) and RHS panel.  Warp w streams the
@@ -601,17 +613,26 @@ __global__ void k_gather_rho(const float* __restrict__ rho, float rho_u, const i
     if (t < n) dst[t] = rho ? rho[perm[t]] : rho_u;
 }
 
-// per column: ||E_c||^2 in double, one warp per column
-__global__ void k_colnorm2(const float* __restrict__ E, int64_t n, int R, double* __restrict__ out) {
-    int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (c >= R) return;
+// per column: ||E_c||^2 in double, one 1024-thread CTA per column; thread
+// t sums elements t, t + 1024, ..., then a fixed tree (shuffles, then the
+// warps in order), so the result does not depend on scheduling
+__global__ void __launch_bounds__(1024) k_colnorm2(const float* __restrict__ E, int64_t n, double* __restrict__ out) {
+    __shared__ double ws[32];
+    const int c = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float* e = E + (int64_t)c * n;
     double s = 0;
-    for (int64_t t = lane; t < n; t += 32) {
-        double v = E[(int64_t)c * n + t];
+    for (int64_t t = threadIdx.x; t < n; t += 1024) {
+        const double v = e[t];
         s += v * v;
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[c] = s;
+    if (lane == 0) ws[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0;
+        for (int w = 0; w < 32; ++w) sum += ws[w];
+        out[c] = sum;
+    }
 }
 
 struct LoopState {
@@ -703,7 +724,7 @@ static vf_status build_pages(vf_hmat* H, std::vector<vf::RecSrc>& recs, const st
         std::vector<int32_t> nrec(npages, 0), nx(npages, 0), xcur(npages, 0);
         for (size_t i = 0; i < recs.size(); ++i) nx[page_of[i]] += (int32_t)vf::rec_xn(recs[i].kind, recs[i].cnt, recs[i].w);
         std::vector<uint16_t> used(npages);
-        for (int64_t pg = 0; pg < npages; ++pg) used[pg] = (uint16_t)(kPageHdr + 4 * nx[pg]);
+        for (int64_t pg = 0; pg < npages; ++pg) used[pg] = (uint16_t)vf::page_rec0((uint32_t)nx[pg]);
         for (size_t i = 0; i < recs.size(); ++i) {
             const int64_t pg = page_of[i];
             recs[i].xbase = xcur[pg];
@@ -767,8 +788,9 @@ vf_status vf_hmat::upload_all() {
     std::vector<int32_t> tile_of_row(nf, -1);
     for (int64_t k = 0; k < ntiles; ++k)
         for (int32_t r = h_tile_first[k]; r < h_tile_first[k] + h_tile_count[k]; ++r) tile_of_row[r] = (int32_t)k;
-    // ---- phase-2 records per tile (FP32 sizes; each fits a page)
-    const int64_t cap = kPage - kPageHdr;
+    // ---- phase-2 records per tile (FP32 sizes; each fits a page).  cap leaves
+    // room for the 16-byte padding of the page's x list.
+    const int64_t cap = kPage - kPageHdr - 16;
     // FP32 bytes of a record in its page: header, body and its x-list entries
     auto tot = [](int kind, int cnt, int w) {
         return (int64_t)vf::rec_bytes(kind, cnt, w, 4) + 4 * (int64_t)vf::rec_xn(kind, cnt, w);
@@ -788,7 +810,7 @@ vf_status vf_hmat::upload_all() {
             src.tile_first = tf;
             if (b.kind == VF_BLK_DENSE) {
                 // the tile's column-major slab, split into column ranges of <= 128
-                const int32_t per_cols = (int32_t)std::min<int64_t>(128, (cap - kRecHdr) / (4 * (int64_t)cnt + 4));
+                const int32_t per_cols = (int32_t)std::min<int64_t>(128, (cap - kRecHdr - 15) / (4 * (int64_t)cnt + 4));
                 for (int32_t c0 = 0; c0 < b.n; c0 += per_cols) {
                     src.kind = vf::REC_DENSE;
                     src.cnt = cnt;
@@ -808,7 +830,7 @@ vf_status vf_hmat::upload_all() {
                     const int64_t nz_row = rp[row + 1] - rp[row];
                     if (tot(vf::REC_CSR, 1, (int)nz_row) > cap) {
                         // a long row: lanes share it, in pieces that fit a page
-                        const int32_t piece = (int32_t)((cap - kRecHdr) / 8);
+                        const int32_t piece = (int32_t)((cap - kRecHdr - 15) / 8);
                         for (int64_t z = rp[row]; z < rp[row + 1]; z += piece) {
                             vf::RecSrc lr = src;
                             lr.kind = vf::REC_CSR_LONG;
@@ -839,7 +861,7 @@ vf_status vf_hmat::upload_all() {
                 int32_t u0 = (int32_t)(std::lower_bound(rows, rows + b.m1, rs) - rows);
                 int32_t u1 = (int32_t)(std::lower_bound(rows, rows + b.m1, re) - rows);
                 const int32_t per_rows =
-                    (int32_t)std::max<int64_t>(1, (cap - kRecHdr - 4 - 4 * (int64_t)b.q) / (4 * (int64_t)b.q + 1));
+                    (int32_t)std::max<int64_t>(1, (cap - kRecHdr - 4 - 15 - 4 * (int64_t)b.q) / (4 * (int64_t)b.q + 1));
                 for (int32_t u = u0; u < u1; u += per_rows) {
                     src.kind = vf::REC_SVD;
                     src.cnt = std::min(per_rows, u1 - u);
@@ -872,7 +894,7 @@ vf_status vf_hmat::upload_all() {
             for (int w = 1; w < kWarps; ++w)
                 if (load[w] < load[best]) best = w;
             lists[best].push_back(i);
-            load[best] += bytes_of(i) + 64;
+            load[best] += bytes_of(i) + vf::kRecCost;
         }
         for (int w = 0; w < kWarps; ++w) {
             h_tile_page_ptr[k * kWarps + w] = (int32_t)npages;
@@ -898,68 +920,119 @@ vf_status vf_hmat::upload_all() {
     std::stable_sort(h_tile_order.begin(), h_tile_order.end(),
                      [&](int32_t x, int32_t y) { return cost[x] > cost[y]; });
     // ---- phase-1 records: V' rows of each SVD block, <= 128 rows per record
-    std::vector<vf::RecSrc> p1;
-    std::vector<int32_t> split;  // per split block: first slot, chunks, q, T slot, block
+    // (chunk).  A block's chunks form units that one warp runs in order; a
+    // block heavier than a quarter of the mean warp load is cut into units of
+    // about that size, whose sums meet in k_p1_reduce.
+    struct Unit {
+        int32_t blk, c0, c1;  // chunks [c0, c1) of block blk
+        int64_t cost;
+    };
+    auto p1_rows = [&](const vf::HBlock& b) {
+        return (int32_t)std::min<int64_t>(128, std::max<int64_t>(1, (cap - kP1Hdr - 15) / (4 * (int64_t)b.q + 4)));
+    };
+    auto chunk_cost = [&](const vf::HBlock& b, int32_t c) {
+        const int32_t rows = p1_rows(b);
+        const int32_t cnt = std::min(b.n1, (c + 1) * rows) - c * rows;
+        return tot(vf::REC_P1, cnt, b.q) + vf::kRecCost;
+    };
+    int64_t total = 0, nchunks_all = 0;
+    for (const vf::HBlock& b : B)
+        if (b.kind == VF_BLK_SVD) {
+            const int32_t nch = (int32_t)vf::ceil_div(b.n1, p1_rows(b));
+            nchunks_all += nch;
+            for (int32_t c = 0; c < nch; ++c) total += chunk_cost(b, c);
+        }
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || nsm <= 0) nsm = 148;
+    n_p1_warps = std::min<int64_t>((int64_t)nsm * 3 * kWarps, vf::ceil_div(nchunks_all, kWarps) * kWarps);
+    n_p1_warps = std::max<int64_t>(n_p1_warps, kWarps);
+    const int64_t unit_cap = std::max<int64_t>(8192, total / n_p1_warps / 4);
+    std::vector<Unit> units;
+    std::vector<int32_t> split;  // per cut block: first slot, units, q, T slot, block
+    std::vector<int32_t> unit_slot;
     n_part_slots = 0;
     for (size_t bi = 0; bi < B.size(); ++bi) {
         if (B[bi].kind != VF_BLK_SVD) continue;
         const vf::HBlock& b = B[bi];
-        const int32_t rows = (int32_t)std::min<int64_t>(128, std::max<int64_t>(1, (cap - kP1Hdr) / (4 * (int64_t)b.q + 4)));
-        const int32_t nch = (int32_t)vf::ceil_div(b.n1, rows);
-        const int32_t first = nch > 1 ? (int32_t)n_part_slots : 0;
-        if (nch > 1) {
-            split.insert(split.end(), {first, nch, b.q, (int32_t)b.off_T, (int32_t)bi});
-            n_part_slots += nch;
-        }
+        const int32_t nch = (int32_t)vf::ceil_div(b.n1, p1_rows(b));
+        const size_t u0 = units.size();
+        Unit u{(int32_t)bi, 0, 0, 0};
         for (int32_t c = 0; c < nch; ++c) {
-            vf::RecSrc rs{};
-            rs.kind = vf::REC_P1;
-            rs.blk = (int32_t)bi;
-            rs.w = b.q;
-            rs.cnt = std::min(b.n1, (c + 1) * rows) - c * rows;
-            rs.x = (int32_t)b.off_T;
-            rs.val = b.off_val + (int64_t)b.m1 * b.q + (int64_t)c * rows * b.q;
-            rs.idx2 = (int32_t)(b.off_aux + b.m1 + (int64_t)c * rows);
-            rs.chunk = c;
-            rs.nchunks = nch;
-            rs.first = first;
-            p1.push_back(rs);
+            const int64_t cc = chunk_cost(b, c);
+            if (u.c1 > u.c0 && u.cost + cc > unit_cap) {
+                units.push_back(u);
+                u = Unit{(int32_t)bi, c, c, 0};
+            }
+            u.c1 = c + 1;
+            u.cost += cc;
+        }
+        units.push_back(u);
+        const int32_t nu = (int32_t)(units.size() - u0);
+        if (nu > 1) {
+            split.insert(split.end(), {(int32_t)n_part_slots, nu, b.q, (int32_t)b.off_T, (int32_t)bi});
+            for (int32_t k = 0; k < nu; ++k) unit_slot.push_back((int32_t)(n_part_slots + k));
+            n_part_slots += nu;
+        } else {
+            unit_slot.push_back(-1);
         }
     }
-    // first-fit-decreasing into pages
-    std::stable_sort(p1.begin(), p1.end(), [&](const vf::RecSrc& x, const vf::RecSrc& y) {
-        return tot(x.kind, x.cnt, x.w) > tot(y.kind, y.cnt, y.w);
-    });
+    // units to warps by longest-processing-time first (heaviest first, each to
+    // the least-loaded warp, lowest index on ties); each warp's units then
+    // fill its own pages in order
+    std::vector<vf::RecSrc> p1;
     std::vector<int64_t> p1_page;
     {
-        std::vector<int64_t> fill;  // open pages
-        for (const auto& rs : p1) {
-            const int64_t bsz = tot(rs.kind, rs.cnt, rs.w);
-            int64_t pg = -1;
-            // the most recent few pages are tried (keeps the plan linear-time)
-            for (int64_t t = (int64_t)fill.size() - 1; t >= 0 && t >= (int64_t)fill.size() - 8; --t)
-                if (fill[t] + bsz <= cap) { pg = t; break; }
-            if (pg < 0) {
-                fill.push_back(0);
-                pg = (int64_t)fill.size() - 1;
-            }
-            fill[pg] += bsz;
-            p1_page.push_back(pg);
+        std::vector<int32_t> ord(units.size());
+        for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int32_t)i;
+        std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return units[x].cost > units[y].cost; });
+        using Slot = std::pair<int64_t, int32_t>;  // (load, warp): the smallest load, then the lowest warp
+        std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+        for (int32_t w = 0; w < (int32_t)n_p1_warps; ++w) heap.push({0, w});
+        std::vector<std::vector<int32_t>> lists(n_p1_warps);
+        for (int32_t i : ord) {
+            Slot sl = heap.top();
+            heap.pop();
+            lists[sl.second].push_back(i);
+            sl.first += units[i].cost;
+            heap.push(sl);
         }
-        n_p1_pages = (int64_t)fill.size();
-    }
-    // records must be in page order within a page for the offsets: sort by page (stable)
-    {
-        std::vector<int64_t> ord(p1.size());
-        for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int64_t)i;
-        std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return p1_page[x] < p1_page[y]; });
-        std::vector<vf::RecSrc> p1s;
-        std::vector<int64_t> pgs;
-        for (int64_t i : ord) { p1s.push_back(p1[i]); pgs.push_back(p1_page[i]); }
-        p1.swap(p1s);
-        p1_page.swap(pgs);
+        h_p1_warp_ptr.assign(n_p1_warps + 1, 0);
+        int64_t np = 0;
+        for (int64_t w = 0; w < n_p1_warps; ++w) {
+            h_p1_warp_ptr[w] = (int32_t)np;
+            int64_t fill = cap + 1;  // forces a new page for the first record
+            for (int32_t ui : lists[w]) {
+                const Unit& u = units[ui];
+                const vf::HBlock& b = B[u.blk];
+                const int32_t rows = p1_rows(b);
+                for (int32_t c = u.c0; c < u.c1; ++c) {
+                    vf::RecSrc rs{};
+                    rs.kind = vf::REC_P1;
+                    rs.blk = u.blk;
+                    rs.w = b.q;
+                    rs.cnt = std::min(b.n1, (c + 1) * rows) - c * rows;
+                    rs.x = (int32_t)b.off_T;
+                    rs.val = b.off_val + (int64_t)b.m1 * b.q + (int64_t)c * rows * b.q;
+                    rs.idx2 = (int32_t)(b.off_aux + b.m1 + (int64_t)c * rows);
+                    rs.chunk = c - u.c0;
+                    rs.nchunks = u.c1 - u.c0;
+                    rs.first = unit_slot[ui];
+                    const int64_t bsz = tot(rs.kind, rs.cnt, rs.w);
+                    if (fill + bsz > cap) {
+                        ++np;
+                        fill = 0;
+                    }
+                    p1.push_back(rs);
+                    p1_page.push_back(np - 1);
+                    fill += bsz;
+                }
+            }
+        }
+        h_p1_warp_ptr[n_p1_warps] = (int32_t)np;
+        n_p1_pages = np;
     }
     VF_TRY(build_pages(this, p1, p1_page, n_p1_pages, true));
+    VF_TRY(p1_warp_ptr.upload(h_p1_warp_ptr));
     n_split = (int64_t)split.size() / 5;
     if (n_split > 0) VF_TRY(p1_split.upload(split));
     VF_TRY(tile_first.upload(h_tile_first));
@@ -1034,18 +1107,6 @@ static ApplyArgs make_args(const vf_hmat* h, int prec, int R) {
 }
 
 static vf_status phase2_attrs(int device);
-
-static int num_sms(int device) {
-    static std::mutex mu;
-    static std::map<int, int> cache;
-    std::lock_guard<std::mutex> lk(mu);
-    auto it = cache.find(device);
-    if (it != cache.end()) return it->second;
-    int n = 0;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0) n = 148;
-    cache[device] = n;
-    return n;
-}
 
 static vf_status ws_get(const vf_hmat* h, int R, int prec, Workspace** out) {
     WsCache& c = cache_for(h);
@@ -1147,15 +1208,14 @@ static vf_status launch_multiply_t(const vf_hmat* h, int prec, const ApplyArgs& 
                                    const float* E, const float* rho, cudaStream_t st) {
     const int64_t ntiles = (int64_t)h->h_tile_first.size();
     if (h->n_p1_pages > 0) {
-        const int64_t persistent = (int64_t)num_sms(h->device) * 3;
-        dim3 g1((unsigned)std::min<int64_t>(ceil_div(h->n_p1_pages, kWarps), persistent), (unsigned)w->npanels);
+        dim3 g1((unsigned)(h->n_p1_warps / kWarps), (unsigned)w->npanels);
         PageArgs p1{h->p1pages[prec].p, h->p1_used[prec].p};
-        k_phase1<T, RB><<<g1, 256, phase1_smem<RB>(), st>>>(a, p1, h->n_p1_pages, xsel, xd, w->Tbuf.p,
+        k_phase1<T, RB><<<g1, 256, phase1_smem<RB>(), st>>>(a, p1, h->p1_warp_ptr.p, xsel, xd, w->Tbuf.p,
                                                             w->part.p, w->status.p);
         if (h->n_split > 0) {
-            dim3 gr((unsigned)h->n_split, (unsigned)w->npanels);
-            k_p1_reduce<RB><<<gr, 128, 0, st>>>(a, h->p1_split.p, prec == VF_PREC_FP8 ? h->scale8.p : nullptr,
-                                                w->part.p, w->Tbuf.p);
+            dim3 gr((unsigned)ceil_div(h->n_split, 8), (unsigned)w->npanels);
+            k_p1_reduce<RB><<<gr, 256, 0, st>>>(a, h->p1_split.p, h->n_split,
+                                                prec == VF_PREC_FP8 ? h->scale8.p : nullptr, w->part.p, w->Tbuf.p);
         }
     }
     SweepIO io{xsel, ysel, xd, yd, E, rho, w->colpart.p, ntiles, w->status.p};
@@ -1192,6 +1252,12 @@ static vf_status launch_multiply(const vf_hmat* h, int prec, Workspace* w, int m
     if (prec == VF_PREC_BF16)
         return launch_multiply_rb<__nv_bfloat16>(h, prec, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
     return launch_multiply_rb<__nv_fp8_e4m3>(h, prec, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
+}
+
+// kernels of one multiply: phase 1 (if any SVD block), the chunk reduction
+// (if any block was split), phase 2
+static int multiply_kernels(const vf_hmat* h) {
+    return (h->n_p1_pages > 0 ? 1 : 0) + (h->n_split > 0 ? 1 : 0) + 1;
 }
 
 static vf_status check_prec(const vf_hmat* h, int prec) {
@@ -1250,7 +1316,7 @@ static vf_status jacobi_loop(const vf_hmat* h, Workspace* w, int max_iter, doubl
     VF_TRY(ensure_graph(h, w));
     // B_0 = E
     VF_TRY_CUDA(cudaMemcpyAsync(w->Bt[0].p, w->Et.p, nR * 4, cudaMemcpyDeviceToDevice, st));
-    k_colnorm2<<<(unsigned)ceil_div((int64_t)w->R * 32, 256), 256, 0, st>>>(w->Et.p, n, w->R, w->enorm2.p);
+    k_colnorm2<<<(unsigned)w->R, 1024, 0, st>>>(w->Et.p, n, w->enorm2.p);
     k_loop_init<<<1, 1, 0, st>>>(w->loop.p, max_iter, rtol * rtol, w->bufs.p, w->xsel.p, w->ysel.p);
     VF_TRY_CUDA(cudaGetLastError());
     if (max_iter > 0) VF_TRY_CUDA(cudaGraphLaunch(w->graph, st));
@@ -1371,9 +1437,12 @@ extern "C" vf_status vf_solve(const vf_hmat* h, const float* rho, const float* E
     const bool refine = o.refine && o.precision != VF_PREC_FP32;
     float* result = nullptr;
     vf_status status = VF_OK;
+    const int kps = vf::multiply_kernels(h) + 1;  // one sweep: the multiply and the column reduction
+    S.kernels = 3;                                // gather E, gather rho, scatter B
     if (!refine) {
         VF_TRY(vf::jacobi_loop(h, w, o.max_iter, o.rtol, st, &ls, &colres, &en2));
         S.sweeps = ls.iter;
+        S.kernels += 2 + ls.iter * kps;           // column norms, loop init, the sweeps
         result = w->Bt[ls.parity].p;
         double mx = 0;
         bool ok = true;
@@ -1392,7 +1461,8 @@ extern "C" vf_status vf_solve(const vf_hmat* h, const float* rho, const float* E
         VF_TRY_CUDA(cudaMemcpyAsync(w->Xt.p, w->Et.p, nR * 4, cudaMemcpyDeviceToDevice, st));  // E (tree order)
         VF_TRY_CUDA(cudaMemsetAsync(w->Yt.p, 0, nR * 4, st));                                 // B = 0
         std::vector<double> en(R);
-        vf::k_colnorm2<<<(unsigned)vf::ceil_div((int64_t)R * 32, 256), 256, 0, st>>>(w->Xt.p, n, R, w->enorm2.p);
+        vf::k_colnorm2<<<(unsigned)R, 1024, 0, st>>>(w->Xt.p, n, w->enorm2.p);
+        S.kernels += 1;
         VF_TRY_CUDA(cudaMemcpyAsync(en.data(), w->enorm2.p, R * 8, cudaMemcpyDeviceToHost, st));
         VF_TRY_CUDA(cudaStreamSynchronize(st));
         // residual workspace shares the FP32 factors; use w32's selection slots
@@ -1404,6 +1474,7 @@ extern "C" vf_status vf_solve(const vf_hmat* h, const float* rho, const float* E
             // the residual (written to Et) becomes the next inner right-hand side
             VF_TRY(vf::launch_multiply(h, VF_PREC_FP32, w32, vf::MODE_RESID, nullptr, nullptr, w->Yt.p, w->Et.p,
                                        w->Xt.p, w32->rho_t.p, st));
+            S.kernels += kps - 1;
             const int64_t ntiles = (int64_t)h->h_tile_first.size();
             std::vector<double> part((size_t)ntiles * R), rr(R, 0.0);
             VF_TRY_CUDA(cudaMemcpyAsync(part.data(), w32->colpart.p, part.size() * 8, cudaMemcpyDeviceToHost, st));
@@ -1420,11 +1491,11 @@ extern "C" vf_status vf_solve(const vf_hmat* h, const float* rho, const float* E
             S.refinements++;
             // delta = (I - rho F_lowprec)^{-1} r, then B += delta
             VF_TRY(vf::jacobi_loop(h, w, o.max_iter, o.inner_rtol, st, &ls, nullptr, nullptr));
-            S.sweeps += 0;
             vf::LoopState l2{};
             VF_TRY_CUDA(cudaMemcpyAsync(&l2, w->loop.p, sizeof(l2), cudaMemcpyDeviceToHost, st));
             VF_TRY_CUDA(cudaStreamSynchronize(st));
             S.sweeps += l2.iter;
+            S.kernels += 2 + l2.iter * kps + 1;  // column norms, loop init, sweeps, the update
             vf::k_axpy_inplace<<<1024, 256, 0, st>>>(w->Yt.p, w->Bt[l2.parity].p, nR);
             VF_TRY_CUDA(cudaGetLastError());
         }

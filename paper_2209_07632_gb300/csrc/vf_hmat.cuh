@@ -30,7 +30,7 @@ struct HBlock {
 //               (>= 0: a tree-order row of X; < 0: T slot -1 - v); on arrival
 //               the warp gathers all of them in one round and overwrites the
 //               list with the values, so records compute from shared memory
-//   records, 4-byte aligned:
+//   records, 16-byte aligned (from page_rec0(nx)), each padded to 16 bytes:
 //   header (16 B): u32 kind | cnt << 8 | roff << 16, u32 w, u32 xbase (first
 //               entry in the page's x list), f32 scale
 //   dense  (1): cnt x w column-major slab (element (r, k) at k * cnt + r) of
@@ -40,7 +40,8 @@ struct HBlock {
 //   SVD    (3): w = q; tile-local rows (cnt bytes), U' (cnt x q) as a
 //               column-major slab; x entries: its q T slots
 //   long CSR row (5): tile row roff, w = nnz; values; x entries: columns
-//   phase-1 (6): header + i32 chunk, nchunks, first partial slot, T slot;
+//   phase-1 (6): header + i32 chunk (within its unit), chunks in the unit,
+//               partial slot (-1: the unit is the whole block), T slot;
 //               cnt = rows, w = q; V' rows (cnt x q, row-major); x entries:
 //               the rows' columns
 #ifndef VF_PAGE_BYTES
@@ -57,17 +58,26 @@ constexpr int kXMax = kPage / 8;
 enum RecKind { REC_DENSE = 1, REC_CSR = 2, REC_SVD = 3, REC_CSR_LONG = 5, REC_P1 = 6 };
 
 __host__ __device__ inline uint32_t pad4(uint32_t b) { return (b + 3u) & ~3u; }
+__host__ __device__ inline uint32_t pad16(uint32_t b) { return (b + 15u) & ~15u; }
 
-// bytes of a record's body and header (not its x entries), element size es
+// bytes of a record's header and body (not its x entries), element size
+// es, padded to 16 so every record header is one vector load
 __host__ __device__ inline uint32_t rec_bytes(int kind, int cnt, int w, int es) {
     switch (kind) {
-        case REC_DENSE: return kRecHdr + pad4((uint32_t)(cnt * w * es));
-        case REC_SVD: return kRecHdr + pad4((uint32_t)cnt) + pad4((uint32_t)(cnt * w * es));
-        case REC_CSR: return kRecHdr + 4u * (cnt + 1) + pad4((uint32_t)(w * es));
-        case REC_CSR_LONG: return kRecHdr + pad4((uint32_t)(w * es));
-        default: return kP1Hdr + pad4((uint32_t)(cnt * w * es));
+        case REC_DENSE: return pad16(kRecHdr + (uint32_t)(cnt * w * es));
+        case REC_SVD: return pad16(kRecHdr + pad4((uint32_t)cnt) + (uint32_t)(cnt * w * es));
+        case REC_CSR: return pad16(kRecHdr + 4u * (cnt + 1) + (uint32_t)(w * es));
+        case REC_CSR_LONG: return pad16(kRecHdr + (uint32_t)(w * es));
+        default: return pad16(kP1Hdr + (uint32_t)(cnt * w * es));
     }
 }
+
+// offset of the first record in a page whose x list has nx entries
+__host__ __device__ inline uint32_t page_rec0(uint32_t nx) { return kPageHdr + pad16(4u * nx); }
+
+// Planning weight of one record beyond its bytes: the fixed work of
+// decoding and finishing it, in byte equivalents of streaming.
+constexpr int64_t kRecCost = 384;
 
 // x entries a record adds to its page's x list
 __host__ __device__ inline uint32_t rec_xn(int kind, int cnt, int w) {
@@ -84,7 +94,7 @@ struct RecSrc {
     int32_t idx;         // CSR: aux offset of the first row pointer; SVD: of the first row id
     int32_t idx2;        // CSR / long row / phase 1: aux offset of the first column index
     int32_t nz0;         // CSR: block-local offset of the first nonzero
-    int32_t chunk, nchunks, first;  // phase 1
+    int32_t chunk, nchunks, first;  // phase 1: chunk in its unit, unit chunks, partial slot or -1
     int64_t dst;         // byte offset of the record in the page pool (per element size)
     int64_t xdst;        // byte offset of its first x-list entry in the page pool
     int32_t xbase;       // its first x-list entry within the page
@@ -104,6 +114,8 @@ struct vf_hmat {
     std::vector<int32_t> h_tile_first, h_tile_count;  // per row tile (tree leaf)
     std::vector<int32_t> h_tile_page_ptr;             // ntiles * kWarps + 1: each warp's page range
     std::vector<int32_t> h_tile_order;                // launch order: heaviest tile first
+    std::vector<int32_t> h_p1_warp_ptr;               // phase 1: each warp's page range (n_p1_warps + 1)
+    int64_t n_p1_warps = 0;                           // a multiple of 8 (one CTA per 8 warps)
     int64_t n_pages = 0, n_p1_pages = 0;              // phase-2 / phase-1 pages
     int64_t n_part_slots = 0;                         // phase-1 partial slots (split blocks)
     int64_t n_split = 0;                              // blocks whose V' rows span several records
@@ -125,6 +137,7 @@ struct vf_hmat {
     vf::dbuf<uint16_t> page_used[3], p1_used[3];  // bytes used per page
     vf::dbuf<int32_t> tile_first, tile_count, tile_page_ptr, tile_order;
     vf::dbuf<int32_t> p1_split;                       // n_split x {first slot, chunks, q, T slot, block}
+    vf::dbuf<int32_t> p1_warp_ptr;
     bool has_bf16 = false, has_fp8 = false;
     int64_t bytes_payload(int prec) const;        // bytes of the stored representation
     vf_status upload_all();

@@ -66,7 +66,7 @@ class SolveOpts(ctypes.Structure):
 
 class SolveStats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int32), ("refinements", ctypes.c_int32), ("converged", ctypes.c_int32),
-                ("max_rel_residual", ctypes.c_double)]
+                ("kernels", ctypes.c_int32), ("max_rel_residual", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
