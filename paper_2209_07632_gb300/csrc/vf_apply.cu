@@ -1202,36 +1202,47 @@ static vf_status phase2_attrs(int device) {
     return VF_OK;
 }
 
+// The scratch one multiply uses: T vectors (npanels x RB x nT floats),
+// partial sums of cut blocks, the timeout status word and (sweep modes)
+// the per-tile residual partials.
+struct Scratch {
+    int R, RB, npanels;
+    float* T;
+    float* part;
+    int* status;
+    double* colpart;
+};
+
 template <class T, int RB>
-static vf_status launch_multiply_t(const vf_hmat* h, int prec, const ApplyArgs& a, Workspace* w, int mode,
+static vf_status launch_multiply_t(const vf_hmat* h, int prec, const ApplyArgs& a, const Scratch* w, int mode,
                                    const float* const* xsel, float* const* ysel, const float* xd, float* yd,
                                    const float* E, const float* rho, cudaStream_t st) {
     const int64_t ntiles = (int64_t)h->h_tile_first.size();
     if (h->n_p1_pages > 0) {
         dim3 g1((unsigned)(h->n_p1_warps / kWarps), (unsigned)w->npanels);
         PageArgs p1{h->p1pages[prec].p, h->p1_used[prec].p};
-        k_phase1<T, RB><<<g1, 256, phase1_smem<RB>(), st>>>(a, p1, h->p1_warp_ptr.p, xsel, xd, w->Tbuf.p,
-                                                            w->part.p, w->status.p);
+        k_phase1<T, RB><<<g1, 256, phase1_smem<RB>(), st>>>(a, p1, h->p1_warp_ptr.p, xsel, xd, w->T, w->part,
+                                                            w->status);
         if (h->n_split > 0) {
             dim3 gr((unsigned)ceil_div(h->n_split, 8), (unsigned)w->npanels);
             k_p1_reduce<RB><<<gr, 256, 0, st>>>(a, h->p1_split.p, h->n_split,
-                                                prec == VF_PREC_FP8 ? h->scale8.p : nullptr, w->part.p, w->Tbuf.p);
+                                                prec == VF_PREC_FP8 ? h->scale8.p : nullptr, w->part, w->T);
         }
     }
-    SweepIO io{xsel, ysel, xd, yd, E, rho, w->colpart.p, ntiles, w->status.p};
+    SweepIO io{xsel, ysel, xd, yd, E, rho, w->colpart, ntiles, w->status};
     dim3 g2((unsigned)ntiles, (unsigned)w->npanels);
     PageArgs pg{h->pages[prec].p, h->page_used[prec].p};
     vf_status s2;
-    if (mode == MODE_APPLY) s2 = launch_phase2<T, RB, MODE_APPLY>(g2, a, pg, w->Tbuf.p, io, st);
-    else if (mode == MODE_JACOBI) s2 = launch_phase2<T, RB, MODE_JACOBI>(g2, a, pg, w->Tbuf.p, io, st);
-    else s2 = launch_phase2<T, RB, MODE_RESID>(g2, a, pg, w->Tbuf.p, io, st);
+    if (mode == MODE_APPLY) s2 = launch_phase2<T, RB, MODE_APPLY>(g2, a, pg, w->T, io, st);
+    else if (mode == MODE_JACOBI) s2 = launch_phase2<T, RB, MODE_JACOBI>(g2, a, pg, w->T, io, st);
+    else s2 = launch_phase2<T, RB, MODE_RESID>(g2, a, pg, w->T, io, st);
     VF_TRY(s2);
     VF_TRY_CUDA(cudaGetLastError());
     return VF_OK;
 }
 
 template <class T>
-static vf_status launch_multiply_rb(const vf_hmat* h, int prec, const ApplyArgs& a, Workspace* w, int mode,
+static vf_status launch_multiply_rb(const vf_hmat* h, int prec, const ApplyArgs& a, const Scratch* w, int mode,
                                     const float* const* xsel, float* const* ysel, const float* xd, float* yd,
                                     const float* E, const float* rho, cudaStream_t st) {
     switch (w->RB) {
@@ -1244,14 +1255,21 @@ static vf_status launch_multiply_rb(const vf_hmat* h, int prec, const ApplyArgs&
 
 // One multiply (phase 1 + phase 2) with the given mode, input/output selected
 // through device pointers (xsel/ysel) or given directly (xd/yd).
-static vf_status launch_multiply(const vf_hmat* h, int prec, Workspace* w, int mode, const float* const* xsel,
-                                 float* const* ysel, const float* xd, float* yd, const float* E, const float* rho,
-                                 cudaStream_t st) {
+static vf_status launch_multiply_sc(const vf_hmat* h, int prec, const Scratch* w, int mode, const float* const* xsel,
+                                    float* const* ysel, const float* xd, float* yd, const float* E, const float* rho,
+                                    cudaStream_t st) {
     ApplyArgs a = make_args(h, prec, w->R);
     if (prec == VF_PREC_FP32) return launch_multiply_rb<float>(h, prec, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
     if (prec == VF_PREC_BF16)
         return launch_multiply_rb<__nv_bfloat16>(h, prec, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
     return launch_multiply_rb<__nv_fp8_e4m3>(h, prec, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
+}
+
+static vf_status launch_multiply(const vf_hmat* h, int prec, Workspace* w, int mode, const float* const* xsel,
+                                 float* const* ysel, const float* xd, float* yd, const float* E, const float* rho,
+                                 cudaStream_t st) {
+    const Scratch sc{w->R, w->RB, w->npanels, w->Tbuf.p, w->part.p, w->status.p, w->colpart.p};
+    return launch_multiply_sc(h, prec, &sc, mode, xsel, ysel, xd, yd, E, rho, st);
 }
 
 // kernels of one multiply: phase 1 (if any SVD block), the chunk reduction
