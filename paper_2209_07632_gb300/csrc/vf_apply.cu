@@ -39,7 +39,7 @@ struct ApplyArgs {
     const int32_t* tile_count;
     const int32_t* tile_page_ptr;  // per (tile, warp): first page; ntiles * kWarps + 1 entries
     const int32_t* tile_order;
-    int64_t nparts;                // phase-1 partial slots per panel
+    int64_t nparts;                // phase-1 partial floats per RHS column (units of cut blocks, q each)
     int64_t n;                     // facets
     int64_t nT;                    // T slots per RHS column
     int R;                         // total RHS columns
@@ -189,7 +189,7 @@ __device__ __forceinline__ void p1_column(const ApplyArgs& a, const float* xv, c
     if (sub != 0) return;
     // the unit's result goes to T (scaled) or, for a unit of a cut block, to its partial slot
     float* dst = slot < 0 ? Tbuf + ((int64_t)panel * RB + c) * a.nT + offT
-                          : part + ((int64_t)panel * a.nparts + slot) * (RB * 128) + c * 128;
+                          : part + ((int64_t)panel * RB + c) * a.nparts + slot;
     const float f = slot < 0 ? sc : 1.f;
     float* cr = carry + c * 128;
 #pragma unroll
@@ -205,7 +205,8 @@ __device__ __forceinline__ void p1_column(const ApplyArgs& a, const float* xv, c
 
 // T of the blocks cut into several units: the unit sums added in unit
 // order, then scaled.  One warp per (cut block, panel); split[5 i ..] =
-// first partial slot, units, q, T slot, block.
+// offset of the block's partials (unit u at offset + u q in each column's
+// partial area), units, q, T slot, block.
 template <int RB>
 __global__ void __launch_bounds__(256) k_p1_reduce(ApplyArgs a, const int32_t* __restrict__ split, int64_t nsplit,
                                                    const float* __restrict__ scales, const float* __restrict__ part,
@@ -217,11 +218,11 @@ __global__ void __launch_bounds__(256) k_p1_reduce(ApplyArgs a, const int32_t* _
     const int first = d[0], nch = d[1], q = d[2], offT = d[3];
     const float sc = scales ? scales[d[4]] : 1.f;
     const int panel = blockIdx.y;
-    const float* pb = part + ((int64_t)panel * a.nparts + first) * (RB * 128);
     for (int c = 0; c < RB && panel * RB + c < a.R; ++c)
         for (int k = lane; k < q; k += 32) {
+            const float* pb = part + ((int64_t)panel * RB + c) * a.nparts + first;
             float sum = 0.f;
-            for (int cc = 0; cc < nch; ++cc) sum += pb[(int64_t)cc * (RB * 128) + c * 128 + k];
+            for (int cc = 0; cc < nch; ++cc) sum += pb[cc * q + k];
             Tbuf[((int64_t)panel * RB + c) * a.nT + offT + k] = sum * sc;
         }
 }
@@ -946,7 +947,7 @@ vf_status vf_hmat::upload_all() {
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || nsm <= 0) nsm = 148;
     n_p1_warps = std::min<int64_t>((int64_t)nsm * 3 * kWarps, vf::ceil_div(nchunks_all, kWarps) * kWarps);
     n_p1_warps = std::max<int64_t>(n_p1_warps, kWarps);
-    const int64_t unit_cap = std::max<int64_t>(8192, total / n_p1_warps / 4);
+    const int64_t unit_cap = std::max<int64_t>(16384, total / n_p1_warps / 4);
     std::vector<Unit> units;
     std::vector<int32_t> split;  // per cut block: first slot, units, q, T slot, block
     std::vector<int32_t> unit_slot;
@@ -970,8 +971,8 @@ vf_status vf_hmat::upload_all() {
         const int32_t nu = (int32_t)(units.size() - u0);
         if (nu > 1) {
             split.insert(split.end(), {(int32_t)n_part_slots, nu, b.q, (int32_t)b.off_T, (int32_t)bi});
-            for (int32_t k = 0; k < nu; ++k) unit_slot.push_back((int32_t)(n_part_slots + k));
-            n_part_slots += nu;
+            for (int32_t k = 0; k < nu; ++k) unit_slot.push_back((int32_t)(n_part_slots + (int64_t)k * b.q));
+            n_part_slots += (int64_t)nu * b.q;
         } else {
             unit_slot.push_back(-1);
         }
@@ -1134,7 +1135,7 @@ static vf_status ws_get(const vf_hmat* h, int R, int prec, Workspace** out) {
     VF_TRY(w->rho_t.alloc(n));
     int64_t nT = std::max<int64_t>(h->n_T, 1);
     VF_TRY(w->Tbuf.alloc((int64_t)w->npanels * w->RB * nT));
-    VF_TRY(w->part.alloc(std::max<int64_t>((int64_t)w->npanels * std::max<int64_t>(h->n_part_slots, 1) * w->RB * 128, 1)));
+    VF_TRY(w->part.alloc((int64_t)w->npanels * w->RB * std::max<int64_t>(h->n_part_slots, 1)));
     VF_TRY(w->colpart.alloc(std::max<int64_t>(ntiles * R, 1)));
     VF_TRY(w->enorm2.alloc(R));
     VF_TRY(w->colres.alloc(R));

@@ -41,7 +41,7 @@ struct HBlock {
 //               column-major slab; x entries: its q T slots
 //   long CSR row (5): tile row roff, w = nnz; values; x entries: columns
 //   phase-1 (6): header + i32 chunk (within its unit), chunks in the unit,
-//               partial slot (-1: the unit is the whole block), T slot;
+//               partial offset (-1: the unit is the whole block), T slot;
 //               cnt = rows, w = q; V' rows (cnt x q, row-major); x entries:
 //               the rows' columns
 #ifndef VF_PAGE_BYTES
@@ -117,7 +117,7 @@ struct vf_hmat {
     std::vector<int32_t> h_p1_warp_ptr;               // phase 1: each warp's page range (n_p1_warps + 1)
     int64_t n_p1_warps = 0;                           // a multiple of 8 (one CTA per 8 warps)
     int64_t n_pages = 0, n_p1_pages = 0;              // phase-2 / phase-1 pages
-    int64_t n_part_slots = 0;                         // phase-1 partial slots (split blocks)
+    int64_t n_part_slots = 0;                         // phase-1 partial floats per RHS column (cut blocks)
     int64_t n_split = 0;                              // blocks whose V' rows span several records
     int64_t n_val = 0, n_aux = 0, n_T = 0;            // pool sizes (elements); n_T per RHS column
     int32_t max_q = 0;
