@@ -193,6 +193,42 @@ vf_status vf_apply(const vf_hmat* h, vf_precision p, const float* X, int64_t ldx
  * vf_apply.  Device FP32, column-major, leading dimension N. */
 vf_status vf_apply_tree(const vf_hmat* h, vf_precision p, const float* Xt, int32_t R, float* Yt, vf_stream stream);
 
+/* vf_apply_tree that allocates nothing, for callers that cannot allocate
+ * device memory at call time: a host program whose device memory is wholly
+ * committed to its own pool, or a time-critical loop that must not take an
+ * allocator's latency or locks.  The paper has no counterpart: this is an
+ * interface of this library, not a step of the method.
+ *
+ * Scratch: the multiply's T vectors, the partial sums of cut blocks and a
+ * status word live in fixed-size static device arrays of libvf, reserved
+ * when its multiply module loads on a device (17 MiB):
+ *   T floats       npanels x RB x n_T   <= VF_STATIC_T_FLOATS    (4,194,304)
+ *   partial floats npanels x RB x n_P   <= VF_STATIC_PART_FLOATS (262,144)
+ * where RB = 1, 2, 4 or 8 (the smallest >= min(R, 8)), npanels =
+ * ceil(R / RB), n_T = the sum of the SVD blocks' ranks and n_P = the sum of
+ * rank x pieces over the (few) SVD blocks whose V' rows are cut across
+ * several pieces of the multiply's work plan.  A matrix and R that need more return VF_E_INVAL with the
+ * sizes in the message, and nothing is launched.
+ * What must start at zero: only the status word; the call clears it itself
+ * (cudaMemsetAsync) before the kernels run.  T and the partial slots are
+ * written before they are read.
+ * The call is synchronous: it returns once the multiply has finished on
+ * `stream`, after reading the status word (VF_E_TIMEOUT if a bounded
+ * device-side wait gave up).
+ * The first call on a device resolves the static arrays' addresses
+ * (cudaGetSymbolAddress) and sets the kernels' shared-memory attributes;
+ * make that first call outside any stream capture.
+ * Concurrency: the arrays are shared by every caller in the process on a
+ * device, so calls that overlap in time (from other threads or streams)
+ * race on them and corrupt each other's results: serialise them.
+ * Xt, Yt: device FP32, column-major, leading dimension N, tree order.
+ * Errors: VF_E_INVAL (null, R < 1, precision not built, scratch too
+ * small), VF_E_TIMEOUT, VF_E_CUDA. */
+#define VF_STATIC_T_FLOATS 4194304
+#define VF_STATIC_PART_FLOATS 262144
+vf_status vf_apply_tree_static(const vf_hmat* h, vf_precision p, const float* Xt, int32_t R, float* Yt,
+                               vf_stream stream);
+
 /* ---------------------------------------------------------------- solve
  * B = (I - diag(rho) F)^{-1} E by Jacobi (Sections 3, 5.1): B_0 = E,
  * B_{k+1} = E + rho .* (F B_k); a column is done when

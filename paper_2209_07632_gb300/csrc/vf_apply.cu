@@ -1273,6 +1273,35 @@ static vf_status launch_multiply(const vf_hmat* h, int prec, Workspace* w, int m
     return launch_multiply_sc(h, prec, &sc, mode, xsel, ysel, xd, yd, E, rho, st);
 }
 
+// Fixed scratch for vf_apply_tree_static: module globals, never allocated at
+// call time.
+static __device__ __align__(256) float g_static_T[VF_STATIC_T_FLOATS];
+static __device__ __align__(256) float g_static_part[VF_STATIC_PART_FLOATS];
+static __device__ __align__(256) int g_static_status[4];
+
+struct StaticScratch {
+    float* T = nullptr;
+    float* part = nullptr;
+    int* status = nullptr;
+};
+
+// Addresses of the static scratch on a device, resolved once per device.
+static vf_status static_scratch(int device, StaticScratch* out) {
+    static std::mutex mu;
+    static std::map<int, StaticScratch> addrs;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = addrs.find(device);
+    if (it == addrs.end()) {
+        StaticScratch s;
+        VF_TRY_CUDA(cudaGetSymbolAddress((void**)&s.T, g_static_T));
+        VF_TRY_CUDA(cudaGetSymbolAddress((void**)&s.part, g_static_part));
+        VF_TRY_CUDA(cudaGetSymbolAddress((void**)&s.status, g_static_status));
+        it = addrs.emplace(device, s).first;
+    }
+    *out = it->second;
+    return VF_OK;
+}
+
 // kernels of one multiply: phase 1 (if any SVD block), the chunk reduction
 // (if any block was split), phase 2
 static int multiply_kernels(const vf_hmat* h) {
@@ -1418,6 +1447,34 @@ extern "C" vf_status vf_apply_tree(const vf_hmat* h, vf_precision prec, const fl
     VF_TRY_CUDA(cudaStreamWaitEvent(st, w->done, 0));
     VF_TRY(vf::launch_multiply(h, prec, w, vf::MODE_APPLY, nullptr, nullptr, Xt, Yt, nullptr, nullptr, st));
     VF_TRY_CUDA(cudaEventRecord(w->done, st));
+    return VF_OK;
+}
+
+extern "C" vf_status vf_apply_tree_static(const vf_hmat* h, vf_precision prec, const float* Xt, int32_t R, float* Yt,
+                                          vf_stream stream) {
+    clear_error();
+    VF_CHECK(h && Xt && Yt, VF_E_INVAL, "vf_apply_tree_static: null argument");
+    VF_CHECK(R >= 1, VF_E_INVAL, "vf_apply_tree_static: need R >= 1");
+    VF_TRY(vf::check_prec(h, prec));
+    const int RB = vf::pick_rb(R), npanels = (int)vf::ceil_div(R, RB);
+    const int64_t nT = std::max<int64_t>(h->n_T, 1);
+    const int64_t need_T = (int64_t)npanels * RB * nT;
+    const int64_t need_part = (int64_t)npanels * RB * std::max<int64_t>(h->n_part_slots, 1);
+    VF_CHECK(need_T <= VF_STATIC_T_FLOATS && need_part <= VF_STATIC_PART_FLOATS, VF_E_INVAL,
+             "vf_apply_tree_static: needs %lld T floats (limit %d) and %lld partial floats (limit %d) for R = %d",
+             (long long)need_T, VF_STATIC_T_FLOATS, (long long)need_part, VF_STATIC_PART_FLOATS, (int)R);
+    device_guard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    vf::StaticScratch ss;
+    VF_TRY(vf::static_scratch(h->device, &ss));
+    VF_TRY(vf::phase2_attrs(h->device));
+    VF_TRY_CUDA(cudaMemsetAsync(ss.status, 0, sizeof(int), st));
+    const vf::Scratch sc{R, RB, npanels, ss.T, ss.part, ss.status, nullptr};
+    VF_TRY(vf::launch_multiply_sc(h, prec, &sc, vf::MODE_APPLY, nullptr, nullptr, Xt, Yt, nullptr, nullptr, st));
+    int hs = 0;
+    VF_TRY_CUDA(cudaMemcpyAsync(&hs, ss.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VF_TRY_CUDA(cudaStreamSynchronize(st));
+    VF_CHECK(hs == 0, VF_E_TIMEOUT, "vf_apply_tree_static: a bounded device-side wait gave up");
     return VF_OK;
 }
 

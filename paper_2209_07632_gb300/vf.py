@@ -18,6 +18,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libvf.so")
 
 VF_OK, VF_E_INVAL, VF_E_NOMEM, VF_E_CUDA, VF_E_NOCONV, VF_E_TIMEOUT, VF_E_OOB, VF_E_IO, VF_E_CORRUPT = range(9)
+# static scratch of vf_apply_tree_static (include/vf.h)
+VF_STATIC_T_FLOATS = 4194304
+VF_STATIC_PART_FLOATS = 262144
 PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
 KIND_NAMES = {0: "zero", 1: "dense", 2: "csr", 3: "svd", 4: "hier"}
 
@@ -100,6 +103,7 @@ _SIGS = {
     "vf_hmat_bytes": ([_P, ctypes.c_int], _I64),
     "vf_apply": ([_P, ctypes.c_int, _P, _I64, _I32, _P, _I64, _P], ctypes.c_int),
     "vf_apply_tree": ([_P, ctypes.c_int, _P, _I32, _P, _P], ctypes.c_int),
+    "vf_apply_tree_static": ([_P, ctypes.c_int, _P, _I32, _P, _P], ctypes.c_int),
     "vf_solve": ([_P, _P, _P, _I64, _P, _I64, _I32, _P, _P, _P], ctypes.c_int),
     "vf_solve_host": ([_P, _P, _P, _I64, _P, _I64, _I32, _P, _P, _P], ctypes.c_int),
     "vf_solve_batched": ([_P, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
@@ -317,6 +321,16 @@ def vf_apply_tree(h: HMat, Xt, Yt, precision: str = "fp32", stream=None):
     R = 1 if Xt.dim() == 1 else Xt.shape[0]
     _check(load().vf_apply_tree(h.ptr, PREC[precision], _dev_ptr(Xt, "Xt", n), R, _dev_ptr(Yt, "Yt", n),
                                 _stream(stream)))
+    return Yt
+
+
+def vf_apply_tree_static(h: HMat, Xt, Yt, precision: str = "fp32", stream=None):
+    """vf_apply_tree with the library's fixed static scratch: no device
+    allocation; synchronous; calls must not overlap in time."""
+    n = h.n
+    R = 1 if Xt.dim() == 1 else Xt.shape[0]
+    _check(load().vf_apply_tree_static(h.ptr, PREC[precision], _dev_ptr(Xt, "Xt", n), R, _dev_ptr(Yt, "Yt", n),
+                                       _stream(stream)))
     return Yt
 
 

@@ -51,3 +51,11 @@ def test_host_side_errors_without_gpu(lib):
     assert b"null" in lib.vf_last_error()
     assert lib.vf_apply(None, 0, None, 0, 1, None, 0, None) == 1
     assert lib.vf_hmat_load(b"/nonexistent/file.vfh", 0, ctypes.byref(out)) == 7  # VF_E_IO
+
+
+def test_static_scratch_limits_match_header():
+    from paper_2209_07632_gb300 import vf
+    txt = open(os.path.join(ROOT, "include", "vf.h")).read()
+    for name in ("VF_STATIC_T_FLOATS", "VF_STATIC_PART_FLOATS"):
+        m = re.search(r"#define\s+" + name + r"\s+(\d+)", txt)
+        assert m and int(m.group(1)) == getattr(vf, name)
