@@ -1582,8 +1582,23 @@ extern "C" vf_status vf_solve(const vf_hmat* h, const float* rho, const float* E
     }
     vf::k_scatter_cols<<<1024, 256, 0, st>>>(result, h->perm.p, n, R, B, ldb, o.clamp);
     VF_TRY_CUDA(cudaGetLastError());
+    // a bounded device-side wait that gave up left VF_E_TIMEOUT in a status word
+    int ws[2] = {0, 0};
+    VF_TRY_CUDA(cudaMemcpyAsync(&ws[0], w->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    vf::Workspace* wr = nullptr;
+    if (refine) {
+        VF_TRY(vf::ws_get(h, R, VF_PREC_FP32, &wr));
+        VF_TRY_CUDA(cudaMemcpyAsync(&ws[1], wr->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
     VF_TRY_CUDA(cudaEventRecord(w->done, st));
     VF_TRY_CUDA(cudaStreamSynchronize(st));
+    if (ws[0] || ws[1]) {
+        cudaMemsetAsync(w->status.p, 0, sizeof(int), st);
+        if (wr) cudaMemsetAsync(wr->status.p, 0, sizeof(int), st);
+        cudaStreamSynchronize(st);
+        vf::set_error("vf_solve: a bounded device-side wait gave up");
+        return VF_E_TIMEOUT;
+    }
     if (stats) *stats = S;
     if (status == VF_E_NOCONV) vf::set_error("vf_solve: not converged (max rel residual %.3e)", S.max_rel_residual);
     return status;
