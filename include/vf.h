@@ -179,6 +179,61 @@ vf_status vf_hmat_blocks(const vf_hmat* h, int64_t* nblocks, int32_t* desc);
 /* Total device payload bytes for one precision. */
 int64_t vf_hmat_bytes(const vf_hmat* h, vf_precision p);
 
+/* Training data from an assembly: one row per SVD probe candidate (the
+ * candidates of Algorithm 3 whose byte bound allows an SVD), in the order
+ * they were probed.  feats: n x VF_PRED_NFEAT (host, row-major), labels: n
+ * classes (host); call with feats = labels = NULL to get n.  Features of a
+ * candidate block (I, J), all from the cluster geometry and the visibility
+ * counts the assembly already has:
+ *   0 log2 |I|   1 log2 |J|   2 |I'|/|I| (rows with a visible pair)
+ *   3 |J'|/|J|   4 nnz/(|I||J|) (visible fraction)
+ *   5 distance between the clusters' mean centroids / (diameter I +
+ *     diameter J) (diameters: bounding-box diagonals)
+ *   6 mean normal I . mean normal J   7 |mean normal I|   8 |mean normal J|
+ *   9 block height (levels above the leaf pairs)
+ * Labels: the probe outcome: 0..4 = an SVD accepted with rank q in
+ * (0, 8], (8, 16], (16, 32], (32, 64], (64, 128]; 5 = no SVD accepted (no
+ * rank met the tolerance or the SVD could not win on bytes). */
+#define VF_PRED_NFEAT 10
+#define VF_PRED_NCLASS 6
+vf_status vf_hmat_probe_log(const vf_hmat* h, int64_t* n, float* feats, int32_t* labels);
+
+/* ---------------------------------------------------------- rank predictor
+ * The learned part of assembly; the paper has none (it motivates it: the
+ * SVD probes dominate assembly time, Section 4.3).  A 3-layer MLP:
+ * standardised features -> 64 -> 64 -> VF_PRED_NCLASS, ReLU, softmax,
+ * mean cross-entropy loss.  The forward pass uses FP16-rounded weights with
+ * FP32 activations and accumulation; training keeps FP32 master weights
+ * (Adam, lr given, betas 0.9 / 0.999) and takes the gradient at the rounded
+ * weights.  Training and inference run in the library's own kernels, with
+ * fixed summation orders (bit-reproducible).
+ * Used by vf_assemble through opts.predictor: a candidate predicted class 5
+ * with probability >= 0.9 is not probed (counted in probes_predicted_skip);
+ * any other prediction c sets its first probe rank to max(k0, 8 << c).  The
+ * probe and the byte test still decide every block, so the matrix meets
+ * the tolerance whatever the network predicts.
+ * Parameters (flat FP32, VF_PRED_NPARAM): W1 (64 x 10, row-major), b1 (64),
+ * W2 (64 x 64), b2 (64), W3 (6 x 64), b3 (6); then the feature means and
+ * scales (10 + 10) in vf_predictor_params.
+ * A predictor handle is used by one thread at a time. */
+#define VF_PRED_NPARAM 5254
+vf_status vf_predictor_create(int32_t device, uint64_t seed, vf_rank_predictor** out);
+void vf_predictor_destroy(vf_rank_predictor* p);
+/* get / set: host arrays of VF_PRED_NPARAM + 2 * VF_PRED_NFEAT floats (either may be NULL). */
+vf_status vf_predictor_params(vf_rank_predictor* p, float* get, const float* set);
+/* Mean loss (FP64 sum of FP32 terms) and its gradient w.r.t. the parameters
+ * (host, VF_PRED_NPARAM) on n samples; feats, labels: host. */
+vf_status vf_predictor_grad(vf_rank_predictor* p, const float* feats, const int32_t* labels, int64_t n, double* loss,
+                            float* grad);
+/* Adam over shuffled mini-batches (a seeded order; the last partial batch of
+ * an epoch is dropped); the feature standardisation is set from the training
+ * set first.  final_loss: the mean loss over all n samples afterwards. */
+vf_status vf_predictor_train(vf_rank_predictor* p, const float* feats, const int32_t* labels, int64_t n,
+                             int32_t epochs, int32_t batch, float lr, double* final_loss);
+/* Classes (argmax, ties to the lower class) and, if prob != NULL,
+ * probabilities (n x VF_PRED_NCLASS) of n feature rows; host arrays. */
+vf_status vf_predictor_predict(const vf_rank_predictor* p, const float* feats, int64_t n, int32_t* cls, float* prob);
+
 /* ---------------------------------------------------------------- apply
  * Algorithm 5 (Section 4.4): Y = F_hat X for R columns.  X, Y: device FP32,
  * column-major, face order (the tree permutation is applied inside).

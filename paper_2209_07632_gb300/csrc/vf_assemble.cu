@@ -12,6 +12,7 @@
 #include <numeric>
 
 #include "vf_hmat.cuh"
+#include "vf_predictor.cuh"
 
 namespace vf {
 
@@ -866,11 +867,60 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
             d.st = Bd.rect_stats(d.I, d.J);
             maxh = std::max(maxh, d.height);
         }
+        // per tree node: mean centroid, bounding-box diagonal and mean unit
+        // normal (the predictor's features; FP64 from the snapped geometry)
+        std::vector<double> ncen(3 * (size_t)nnodes, 0.0), ndiam(nnodes, 0.0), nnrm(3 * (size_t)nnodes, 0.0);
+        {
+            std::vector<double> hn;
+            VF_TRY(m->nrm.download(hn));
+            const double s = m->unit / 3.0;
+            for (int32_t k = 0; k < nnodes; ++k) {
+                double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+                for (int32_t pos = t->first[k]; pos < t->first[k] + t->count[k]; ++pos) {
+                    const int32_t f = t->perm[pos];
+                    for (int a = 0; a < 3; ++a) {
+                        const double x = s * m->h_c3[3 * (size_t)f + a];
+                        ncen[3 * (size_t)k + a] += x;
+                        lo[a] = std::min(lo[a], x);
+                        hi[a] = std::max(hi[a], x);
+                        nnrm[3 * (size_t)k + a] += hn[3 * (size_t)f + a];
+                    }
+                }
+                const double c = (double)std::max(t->count[k], 1);
+                double d2 = 0;
+                for (int a = 0; a < 3; ++a) {
+                    ncen[3 * (size_t)k + a] /= c;
+                    nnrm[3 * (size_t)k + a] /= c;
+                    d2 += (hi[a] - lo[a]) * (hi[a] - lo[a]);
+                }
+                ndiam[k] = std::sqrt(d2);
+            }
+        }
+        auto features = [&](const DNode& d, float* f) {
+            const double mm = t->count[d.I], nn = t->count[d.J];
+            const double* ci = &ncen[3 * (size_t)d.I];
+            const double* cj = &ncen[3 * (size_t)d.J];
+            const double* ni = &nnrm[3 * (size_t)d.I];
+            const double* nj = &nnrm[3 * (size_t)d.J];
+            const double dist = std::sqrt((ci[0] - cj[0]) * (ci[0] - cj[0]) + (ci[1] - cj[1]) * (ci[1] - cj[1]) +
+                                          (ci[2] - cj[2]) * (ci[2] - cj[2]));
+            f[0] = (float)std::log2(mm);
+            f[1] = (float)std::log2(nn);
+            f[2] = (float)(d.st.m1 / mm);
+            f[3] = (float)(d.st.n1 / nn);
+            f[4] = (float)((double)d.st.nnz / (mm * nn));
+            f[5] = (float)(dist / std::max(ndiam[d.I] + ndiam[d.J], 1e-300));
+            f[6] = (float)(ni[0] * nj[0] + ni[1] * nj[1] + ni[2] * nj[2]);
+            f[7] = (float)std::sqrt(ni[0] * ni[0] + ni[1] * ni[1] + ni[2] * ni[2]);
+            f[8] = (float)std::sqrt(nj[0] * nj[0] + nj[1] * nj[1] + nj[2] * nj[2]);
+            f[9] = (float)d.height;
+        };
         t2 = now_seconds();
         S.t_stats = t2 - t1;
 
         // ---------------- DP bottom-up by height
         stage_ref.assign(N.size(), StageRef{-1, -1});
+        std::vector<int32_t> log_ids;  // probed candidates, in order (the probe log)
 
         for (int32_t h = 0; h <= maxh; ++h) {
             std::vector<int32_t> level;
@@ -904,6 +954,34 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
                 } else {
                     S.probes_skipped++;
                 }
+            }
+            // the candidates' features; the predictor (if any) picks each
+            // first probe rank or skips the probe
+            const size_t log0 = log_ids.size();
+            {
+                std::vector<float> fl(pending.size() * VF_PRED_NFEAT);
+                for (size_t i = 0; i < pending.size(); ++i) features(N[pending[i]], &fl[i * VF_PRED_NFEAT]);
+                std::vector<int32_t> keep;
+                if (o.predictor && !pending.empty()) {
+                    std::vector<int32_t> cls;
+                    std::vector<float> prob;
+                    VF_TRY(predictor_classify(o.predictor, fl, (int64_t)pending.size(), cls, prob));
+                    std::vector<float> fk;
+                    for (size_t i = 0; i < pending.size(); ++i) {
+                        DNode& d = N[pending[i]];
+                        if (cls[i] == VF_PRED_NCLASS - 1 && prob[i * VF_PRED_NCLASS + cls[i]] >= 0.9f) {
+                            S.probes_predicted_skip++;
+                            continue;
+                        }
+                        if (cls[i] < VF_PRED_NCLASS - 1) d.k = std::min(std::max(o.k0, 8 << cls[i]), o.k_max);
+                        keep.push_back(pending[i]);
+                        fk.insert(fk.end(), fl.begin() + i * VF_PRED_NFEAT, fl.begin() + (i + 1) * VF_PRED_NFEAT);
+                    }
+                    pending.swap(keep);
+                    fl.swap(fk);
+                }
+                log_ids.insert(log_ids.end(), pending.begin(), pending.end());
+                H->h_probe_feat.insert(H->h_probe_feat.end(), fl.begin(), fl.end());
             }
             // probe rounds (k doubling, Algorithm 3)
             while (!pending.empty()) {
@@ -1007,6 +1085,13 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
                     stage_bufs.push_back(std::move(buf));
                 }
                 pending.swap(next);
+            }
+            // the probe log's labels: the rank bin of an accepted SVD, else "no SVD"
+            for (size_t i = log0; i < log_ids.size(); ++i) {
+                const DNode& d = N[log_ids[i]];
+                int32_t c = VF_PRED_NCLASS - 1;
+                if (d.q > 0 && stage_ref[log_ids[i]].buf >= 0) c = d.q <= 8 ? 0 : d.q <= 16 ? 1 : d.q <= 32 ? 2 : d.q <= 64 ? 3 : 4;
+                H->h_probe_label.push_back(c);
             }
             // decisions for this level
             for (int32_t id : level) {
@@ -1225,5 +1310,14 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
     H->stats = S;
     if (stats_out) *stats_out = S;
     *out = H.release();
+    return VF_OK;
+}
+
+extern "C" vf_status vf_hmat_probe_log(const vf_hmat* h, int64_t* n, float* feats, int32_t* labels) {
+    clear_error();
+    VF_CHECK(h && n, VF_E_INVAL, "vf_hmat_probe_log: null argument");
+    *n = (int64_t)h->h_probe_label.size();
+    if (feats) std::copy(h->h_probe_feat.begin(), h->h_probe_feat.end(), feats);
+    if (labels) std::copy(h->h_probe_label.begin(), h->h_probe_label.end(), labels);
     return VF_OK;
 }

@@ -123,6 +123,8 @@ struct vf_hmat {
     int32_t max_q = 0;
     int64_t n_hier = 0;
     vf_assemble_stats stats{};
+    std::vector<float> h_probe_feat;                  // the probe log: VF_PRED_NFEAT per candidate
+    std::vector<int32_t> h_probe_label;               // its outcomes (classes)
     // device: block pools (the stored representation)
     vf::dbuf<int32_t> perm;        // tree position -> facet
     vf::dbuf<int32_t> iperm;       // facet -> tree position

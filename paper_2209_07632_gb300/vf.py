@@ -98,6 +98,13 @@ _SIGS = {
     "vf_tree_nodes": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "vf_assemble": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "vf_hmat_destroy": ([_P], None),
+    "vf_hmat_probe_log": ([_P, _P, _P, _P], ctypes.c_int),
+    "vf_predictor_create": ([_I32, ctypes.c_uint64, _P], ctypes.c_int),
+    "vf_predictor_destroy": ([_P], None),
+    "vf_predictor_params": ([_P, _P, _P], ctypes.c_int),
+    "vf_predictor_grad": ([_P, _P, _P, _I64, _P, _P], ctypes.c_int),
+    "vf_predictor_train": ([_P, _P, _P, _I64, _I32, _I32, ctypes.c_float, _P], ctypes.c_int),
+    "vf_predictor_predict": ([_P, _P, _I64, _P, _P], ctypes.c_int),
     "vf_hmat_nfacets": ([_P], _I64),
     "vf_hmat_blocks": ([_P, _P, _P], ctypes.c_int),
     "vf_hmat_bytes": ([_P, ctypes.c_int], _I64),
@@ -197,6 +204,16 @@ class HMat(_Handle):
     @property
     def n(self) -> int:
         return int(load().vf_hmat_nfacets(self.ptr))
+
+
+class Predictor(_Handle):
+    _destroy = "vf_predictor_destroy"
+
+
+# rank predictor sizes (include/vf.h)
+VF_PRED_NFEAT = 10
+VF_PRED_NCLASS = 6
+VF_PRED_NPARAM = 5254
 
 
 # ------------------------------------------------------------------ API
@@ -431,3 +448,77 @@ def build_problem(verts, faces, kind: str = "quad", leaf_size: int = 64, tol: fl
     t = vf_partition(m, kind, leaf_size)
     h, st = vf_assemble(m, t, tol=tol, **assemble_kw)
     return Problem(m, t, h, st)
+
+
+# ------------------------------------------------------------------ rank predictor
+def _f32(a, shape_tail=None):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a
+
+
+def vf_hmat_probe_log(h: HMat):
+    """The assembly's probe log: (features n x VF_PRED_NFEAT float32, labels n int32)."""
+    n = ctypes.c_int64(0)
+    _check(load().vf_hmat_probe_log(h.ptr, ctypes.byref(n), None, None))
+    X = np.zeros((n.value, VF_PRED_NFEAT), dtype=np.float32)
+    y = np.zeros(n.value, dtype=np.int32)
+    if n.value:
+        _check(load().vf_hmat_probe_log(h.ptr, ctypes.byref(n), X.ctypes.data_as(ctypes.c_void_p),
+                                        y.ctypes.data_as(ctypes.c_void_p)))
+    return X, y
+
+
+def vf_predictor_create(seed: int = 0, device: int = 0) -> Predictor:
+    out = ctypes.c_void_p()
+    _check(load().vf_predictor_create(device, ctypes.c_uint64(seed), ctypes.byref(out)))
+    return Predictor(out.value)
+
+
+def vf_predictor_params(p: Predictor, set_to=None) -> np.ndarray:
+    """Flat parameters + feature means and scales (VF_PRED_NPARAM + 20 float32);
+    with set_to, load those first."""
+    if set_to is not None:
+        s = _f32(set_to)
+        if s.size != VF_PRED_NPARAM + 2 * VF_PRED_NFEAT:
+            raise VFError(VF_E_INVAL, "parameter vector has the wrong size")
+        _check(load().vf_predictor_params(p.ptr, None, s.ctypes.data_as(ctypes.c_void_p)))
+    out = np.zeros(VF_PRED_NPARAM + 2 * VF_PRED_NFEAT, dtype=np.float32)
+    _check(load().vf_predictor_params(p.ptr, out.ctypes.data_as(ctypes.c_void_p), None))
+    return out
+
+
+def _xy(X, y):
+    X = _f32(X)
+    y = np.ascontiguousarray(y, dtype=np.int32)
+    if X.ndim != 2 or X.shape[1] != VF_PRED_NFEAT or y.shape != (X.shape[0],):
+        raise VFError(VF_E_INVAL, "features must be (n, VF_PRED_NFEAT) with n labels")
+    return X, y
+
+
+def vf_predictor_grad(p: Predictor, X, y):
+    """(mean loss, gradient VF_PRED_NPARAM float32) on the samples."""
+    X, y = _xy(X, y)
+    loss = ctypes.c_double(0.0)
+    g = np.zeros(VF_PRED_NPARAM, dtype=np.float32)
+    _check(load().vf_predictor_grad(p.ptr, X.ctypes.data_as(ctypes.c_void_p), y.ctypes.data_as(ctypes.c_void_p),
+                                    X.shape[0], ctypes.byref(loss), g.ctypes.data_as(ctypes.c_void_p)))
+    return loss.value, g
+
+
+def vf_predictor_train(p: Predictor, X, y, epochs: int = 20, batch: int = 1024, lr: float = 2e-3) -> float:
+    X, y = _xy(X, y)
+    loss = ctypes.c_double(0.0)
+    _check(load().vf_predictor_train(p.ptr, X.ctypes.data_as(ctypes.c_void_p), y.ctypes.data_as(ctypes.c_void_p),
+                                     X.shape[0], epochs, batch, ctypes.c_float(lr), ctypes.byref(loss)))
+    return loss.value
+
+
+def vf_predictor_predict(p: Predictor, X):
+    """(classes int32, probabilities n x VF_PRED_NCLASS float32)."""
+    X = _f32(X)
+    n = X.shape[0]
+    cls = np.zeros(n, dtype=np.int32)
+    prob = np.zeros((n, VF_PRED_NCLASS), dtype=np.float32)
+    _check(load().vf_predictor_predict(p.ptr, X.ctypes.data_as(ctypes.c_void_p), n,
+                                       cls.ctypes.data_as(ctypes.c_void_p), prob.ctypes.data_as(ctypes.c_void_p)))
+    return cls, prob

@@ -59,3 +59,13 @@ def test_static_scratch_limits_match_header():
     for name in ("VF_STATIC_T_FLOATS", "VF_STATIC_PART_FLOATS"):
         m = re.search(r"#define\s+" + name + r"\s+(\d+)", txt)
         assert m and int(m.group(1)) == getattr(vf, name)
+
+
+def test_predictor_sizes_match_header():
+    from oracle import mlp
+    from paper_2209_07632_gb300 import vf
+    txt = open(os.path.join(ROOT, "include", "vf.h")).read()
+    for name in ("VF_PRED_NFEAT", "VF_PRED_NCLASS", "VF_PRED_NPARAM"):
+        m = re.search(r"#define\s+" + name + r"\s+(\d+)", txt)
+        assert m and int(m.group(1)) == getattr(vf, name)
+    assert vf.VF_PRED_NPARAM == mlp.NPARAM and vf.VF_PRED_NFEAT == mlp.NF and vf.VF_PRED_NCLASS == mlp.NC
