@@ -27,6 +27,7 @@
 
 #include "vf_bulk.cuh"
 #include "vf_hmat.cuh"
+#include "vf_tensor.cuh"
 
 namespace vf {
 
@@ -1057,6 +1058,9 @@ struct Workspace {
     dbuf<float*> bufs;        // [2] ping-pong pointers
     dbuf<const float*> xsel;  // current input
     dbuf<float*> ysel;        // current output
+    // tensor-core path (BF16, R >= kTensorMinR): BF16 panels of 128 RHS, ping-pong, and the T panel
+    dbuf<unsigned char> xpan[2], tpan;
+    int tpanels = 0;
     cudaGraphExec_t graph = nullptr;
     cudaGraphConditionalHandle handle = 0;
     cudaEvent_t done = nullptr;
@@ -1308,6 +1312,47 @@ static int multiply_kernels(const vf_hmat* h) {
     return (h->n_p1_pages > 0 ? 1 : 0) + (h->n_split > 0 ? 1 : 0) + 1;
 }
 
+// BF16 multiplies of at least kTensorMinR columns run on the tensor cores.
+static bool use_tensor(const vf_hmat* h, int prec, int R) {
+    return prec == VF_PREC_BF16 && h->has_bf16 && R >= kTensorMinR;
+}
+
+// The tensor pages (built once per matrix; the handle's lazily built part)
+// and this workspace's panels.
+static vf_status tensor_ws(const vf_hmat* h, Workspace* w) {
+    VF_TRY(tensor_prepare(const_cast<vf_hmat*>(h)));
+    if (w->xpan[0].p) return VF_OK;
+    w->tpanels = (int)ceil_div(w->R, kTensorPanel);
+    const int64_t bx = tensor_panel_bytes_x(h), bt = tensor_panel_bytes_t(h);
+    for (int i = 0; i < 2; ++i) {
+        VF_TRY(w->xpan[i].alloc((size_t)w->tpanels * bx));
+        VF_TRY_CUDA(cudaMemset(w->xpan[i].p, 0, (size_t)w->tpanels * bx));
+    }
+    VF_TRY(w->tpan.alloc((size_t)bt));
+    VF_TRY_CUDA(cudaMemset(w->tpan.p, 0, (size_t)bt));
+    return VF_OK;
+}
+
+// Y (tree order, column-major, ld n) = F X on the tensor cores; X column-major
+// with ld, rows taken through perm (NULL: already tree order).
+static vf_status tensor_apply(const vf_hmat* h, Workspace* w, const float* X, int64_t ld, const int32_t* perm,
+                              float* Y, cudaStream_t st) {
+    VF_TRY(tensor_ws(h, w));
+    const int64_t bx = tensor_panel_bytes_x(h);
+    for (int p = 0; p < w->tpanels; ++p) {
+        unsigned char* xp = w->xpan[0].p + (size_t)p * bx;
+        VF_TRY(tensor_to_panel(h, X, ld, perm, w->R, p * kTensorPanel, xp, st));
+        TEpi ep{};
+        ep.mode = 0;
+        ep.n = h->nf;
+        ep.R = w->R;
+        ep.p0 = p * kTensorPanel;
+        ep.Y = Y;
+        VF_TRY(tensor_multiply(h, xp, w->tpan.p, ep, w->status.p, st));
+    }
+    return VF_OK;
+}
+
 static vf_status check_prec(const vf_hmat* h, int prec) {
     VF_CHECK(prec == VF_PREC_FP32 || (prec == VF_PREC_BF16 && h->has_bf16) || (prec == VF_PREC_FP8 && h->has_fp8),
              VF_E_INVAL, "precision %d was not built for this matrix", prec);
@@ -1426,8 +1471,12 @@ extern "C" vf_status vf_apply(const vf_hmat* h, vf_precision prec, const float* 
     VF_TRY(vf::ws_get(h, R, prec, &w));
     VF_TRY_CUDA(cudaStreamWaitEvent(st, w->done, 0));
     const int64_t n = h->nf;
-    vf::k_gather_cols<<<1024, 256, 0, st>>>(X, ldx, h->perm.p, n, R, w->Xt.p);
-    VF_TRY(vf::launch_multiply(h, prec, w, vf::MODE_APPLY, nullptr, nullptr, w->Xt.p, w->Yt.p, nullptr, nullptr, st));
+    if (vf::use_tensor(h, prec, R)) {
+        VF_TRY(vf::tensor_apply(h, w, X, ldx, h->perm.p, w->Yt.p, st));
+    } else {
+        vf::k_gather_cols<<<1024, 256, 0, st>>>(X, ldx, h->perm.p, n, R, w->Xt.p);
+        VF_TRY(vf::launch_multiply(h, prec, w, vf::MODE_APPLY, nullptr, nullptr, w->Xt.p, w->Yt.p, nullptr, nullptr, st));
+    }
     vf::k_scatter_cols<<<1024, 256, 0, st>>>(w->Yt.p, h->perm.p, n, R, Y, ldy, 0);
     VF_TRY_CUDA(cudaGetLastError());
     VF_TRY_CUDA(cudaEventRecord(w->done, st));
@@ -1445,7 +1494,10 @@ extern "C" vf_status vf_apply_tree(const vf_hmat* h, vf_precision prec, const fl
     vf::Workspace* w;
     VF_TRY(vf::ws_get(h, R, prec, &w));
     VF_TRY_CUDA(cudaStreamWaitEvent(st, w->done, 0));
-    VF_TRY(vf::launch_multiply(h, prec, w, vf::MODE_APPLY, nullptr, nullptr, Xt, Yt, nullptr, nullptr, st));
+    if (vf::use_tensor(h, prec, R))
+        VF_TRY(vf::tensor_apply(h, w, Xt, h->nf, nullptr, Yt, st));
+    else
+        VF_TRY(vf::launch_multiply(h, prec, w, vf::MODE_APPLY, nullptr, nullptr, Xt, Yt, nullptr, nullptr, st));
     VF_TRY_CUDA(cudaEventRecord(w->done, st));
     return VF_OK;
 }

@@ -6,7 +6,9 @@
 namespace vf {
 
 // One stored block (Algorithm 4 output after flattening the hierarchy).
-//  dense: val[off_val + r*n + c], row-major m x n
+//  dense: per row tile [rs, re) the block meets, a column-major slab at
+//         val[off_val + (rs - r0)*n]: element (row, c) at
+//         (rs - r0)*n + c*(re - rs) + (row - rs)
 //  CSR:   aux[off_aux .. +m] row pointers (local), aux[off_aux+m+1 ..] global
 //         tree-order column of each nonzero, val[off_val + k]
 //  SVD:   aux[off_aux .. +m1] global tree rows, aux[off_aux+m1 .. +n1] global
@@ -103,6 +105,11 @@ struct RecSrc {
 
 }  // namespace vf
 
+struct vf_tensor_plan;  // the tensor-core multiply's pages (vf_tensor.cu), built on first use
+namespace vf {
+void tensor_plan_free(vf_tensor_plan* p);
+}
+
 struct vf_hmat {
     int device = 0;
     int64_t nf = 0;
@@ -141,6 +148,8 @@ struct vf_hmat {
     vf::dbuf<int32_t> p1_split;                       // n_split x {first slot, chunks, q, T slot, block}
     vf::dbuf<int32_t> p1_warp_ptr;
     bool has_bf16 = false, has_fp8 = false;
+    vf_tensor_plan* tplan = nullptr;
+    ~vf_hmat() { vf::tensor_plan_free(tplan); }
     int64_t bytes_payload(int prec) const;        // bytes of the stored representation
     vf_status upload_all();
 };

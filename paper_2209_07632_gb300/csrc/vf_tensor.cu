@@ -1,0 +1,858 @@
+// The multiply on the 5th-generation tensor cores for panels of 128
+// right-hand sides (BF16 factors and BF16 right-hand sides, FP32
+// accumulation in tensor memory): Algorithm 5 with the block products as
+// tcgen05 MMAs.
+//
+// Formulation (transposed, so the RHS panel is the MMA's M = 128):
+//   phase 1, per SVD block:   T^T (128 x q16) = X^T[cols] (128 x K) . V' (K x q16)
+//   phase 2, per row tile:    Y^T (128 x 64)  += X^T[cols] (128 x K) . F_IJ^T (K x rows)
+//                                            += T^T[q]    (128 x q16) . U'^T (q16 x rows)
+// D lives in TMEM (lane = RHS column, column = output row or T slot).  CSR
+// blocks are densified; every operand is zero-padded to the MMA's shape.
+//
+// Operand layout (no swizzle, MN-major, core matrices of 8 K-rows x 16 bytes
+// of MN): element (k, mn) at (k / 8) * LBO + (mn / 8) * 128 + (k % 8) * 16 +
+// (mn % 8) * 2, with LBO = (MN / 8) * 128 the byte stride between core
+// matrices along K and SBO = 128 the stride along MN.  The RHS panels (X and
+// T) are kept in global memory in exactly this layout (MN = 128, row groups
+// of 8 = 2 KB), so the A operand of any block is one contiguous byte range:
+// its column range (or T slots) rounded to 8 rows, fetched by one bulk copy.
+// B operands (the matrix) are packed once into "tensor pages" in the same
+// layout.
+//
+// Each kernel is persistent (two CTAs per SM) with warp roles: warp 0 lane 0
+// copies pages and A operands (cp.async.bulk, mbarrier completion), warp 1
+// lane 0 issues the MMAs and commits them to mbarriers, warps 2-5 read the
+// finished accumulators (tcgen05.ld) and run the epilogue.  Two accumulator
+// regions alternate between tiles (units), so the epilogue of one overlaps
+// the MMAs of the next.  Every wait is bounded; a role that gives up records
+// VF_E_TIMEOUT and stops issuing, and the kernel waits (bounded) for work in
+// flight before it frees its tensor memory.
+#include <algorithm>
+#include <cmath>
+#include <functional>
+#include <memory>
+#include <numeric>
+#include <queue>
+#include <vector>
+
+#include "vf_bulk.cuh"
+#include "vf_hmat.cuh"
+#include "vf_tensor.cuh"
+
+namespace vf {
+
+constexpr int kTP = 16384;           // tensor page bytes
+constexpr int kTPHdr = 16;           // page header: nrec, used, 0, 0
+constexpr int kTRHdr = 32;           // record header (8 x u32)
+constexpr int kPanel = 128;          // right-hand sides per panel (MMA M)
+constexpr int kKMax = 64;            // largest K of one record (A slot = 64 x 256 B)
+constexpr int kASlots = 4;
+constexpr int kAStage = kKMax * kPanel * 2;
+constexpr int kRegionCols = 128;     // TMEM columns per accumulator region
+constexpr uint32_t kTWait = 1u << 22;
+enum { TR_FIRST = 1, TR_LAST = 2 };
+enum { TREC_DENSE = 0, TREC_CSR = 1, TREC_SVDU = 2, TREC_VT = 3, TREC_EMPTY = 4 };
+
+// ------------------------------------------------------------ plan
+struct TRec {        // where one tensor record's B operand comes from (build time)
+    int32_t kind, blk;
+    int32_t K16, N16;
+    int32_t row_base;  // absolute tree row of B column 0 (phase 2) -- unused for V'
+    int32_t rs, re;    // absolute rows of the block inside this record (phase 2)
+    int32_t k0;        // absolute column (phase 2 dense / CSR, phase 1) of B row 0
+    int32_t coloff;    // D column offset (phase 2)
+    int32_t a_src, a_row0;
+    int32_t flags, offT;
+    int64_t dst;
+};
+
+}  // namespace vf
+
+struct vf_tensor_plan {
+    int64_t n_rows_x = 0, n_rows_t = 0;  // panel rows (X, T), multiples of 16
+    int32_t ncta2 = 0, ncta1 = 0;
+    std::vector<int32_t> h_offT16;       // per block: first T row (SVD), else -1
+    vf::dbuf<unsigned char> pages2, pages1;
+    vf::dbuf<uint32_t> used2, used1;
+    vf::dbuf<int32_t> cta_pages2, cta_pages1;  // ncta + 1 each
+    vf::dbuf<int32_t> cta_tiles, cta_tile_ptr; // phase 2: each CTA's tiles in order
+    vf::dbuf<int32_t> cta_units, cta_unit_ptr; // phase 1: each CTA's units (offT16, N16 pairs)
+    int64_t bytes2 = 0, bytes1 = 0;
+};
+
+namespace vf {
+
+void tensor_plan_free(vf_tensor_plan* p) { delete p; }
+
+__device__ __forceinline__ void st_bf16(unsigned char* base, int64_t k, int mn, int lbo, float v) {
+    *reinterpret_cast<__nv_bfloat16*>(base + (k >> 3) * lbo + (mn >> 3) * 128 + (k & 7) * 16 + (mn & 7) * 2) =
+        __float2bfloat16_rn(v);
+}
+
+// One CTA per record: header, zero-filled B body, then the values.
+__global__ void k_tpack(const TRec* __restrict__ recs, const HBlock* __restrict__ blocks,
+                        const float* __restrict__ val, const int32_t* __restrict__ aux,
+                        unsigned char* __restrict__ pool) {
+    const TRec r = recs[blockIdx.x];
+    unsigned char* dst = pool + r.dst;
+    uint32_t* h = reinterpret_cast<uint32_t*>(dst);
+    if (threadIdx.x == 0) {
+        h[0] = (uint32_t)r.K16;
+        h[1] = (uint32_t)r.N16;
+        h[2] = (uint32_t)r.coloff;
+        h[3] = (uint32_t)r.a_src;
+        h[4] = (uint32_t)r.a_row0;
+        h[5] = (uint32_t)r.flags;
+        h[6] = (uint32_t)r.offT;
+        h[7] = 0u;
+    }
+    unsigned char* B = dst + kTRHdr;
+    const int lbo = (r.N16 / 8) * 128;
+    const int nwords = r.K16 * r.N16 / 2;
+    for (int i = threadIdx.x; i < nwords; i += blockDim.x) reinterpret_cast<uint32_t*>(B)[i] = 0u;
+    __syncthreads();
+    if (r.kind == TREC_EMPTY) return;  // a tile with no blocks: a zero product
+    const HBlock b = blocks[r.blk];
+    if (r.kind == TREC_DENSE) {
+        // rows [rs, re) of the block (its part in one row tile: a column-major
+        // slab at (rs - r0) * n in the pool), columns [max(k0, c0), min(k0 + K16, c0 + n))
+        const int c_lo = max(r.k0, b.c0), c_hi = min(r.k0 + r.K16, b.c0 + b.n);
+        const int nr = r.re - r.rs, nc = c_hi - c_lo;
+        const float* slab = val + b.off_val + (int64_t)(r.rs - b.r0) * b.n;
+        for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
+            const int j = e / nr, i = e - j * nr;
+            const int row = r.rs + i, col = c_lo + j;
+            st_bf16(B, col - r.k0, row - r.row_base, lbo, slab[(int64_t)(col - b.c0) * nr + i]);
+        }
+    } else if (r.kind == TREC_CSR) {
+        const int32_t* rp = aux + b.off_aux;
+        const int32_t* ci = aux + b.off_aux + b.m + 1;
+        for (int row = r.rs + (threadIdx.x >> 5); row < r.re; row += blockDim.x >> 5) {
+            const int lr = row - b.r0;
+            for (int z = rp[lr] + (threadIdx.x & 31); z < rp[lr + 1]; z += 32) {
+                const int col = ci[z];
+                if (col >= r.k0 && col < r.k0 + r.K16)
+                    st_bf16(B, col - r.k0, row - r.row_base, lbo, val[b.off_val + z]);
+            }
+        }
+    } else if (r.kind == TREC_SVDU) {
+        // U' rows (compacted, sorted) inside [rs, re); K = rank indices [k0, k0 + K16)
+        const int32_t* rows = aux + b.off_aux;
+        for (int e = threadIdx.x; e < b.m1 * b.q; e += blockDim.x) {
+            const int u = e / b.q, k = e - u * b.q;
+            const int row = rows[u];
+            if (row >= r.rs && row < r.re && k >= r.k0 && k < r.k0 + r.K16)
+                st_bf16(B, k - r.k0, row - r.row_base, lbo, val[b.off_val + (int64_t)u * b.q + k]);
+        }
+    } else {
+        // V' rows (compacted columns) inside [k0, k0 + K16); N = the rank
+        const int32_t* cols = aux + b.off_aux + b.m1;
+        const float* Vp = val + b.off_val + (int64_t)b.m1 * b.q;
+        for (int e = threadIdx.x; e < b.n1 * b.q; e += blockDim.x) {
+            const int j = e / b.q, k = e - j * b.q;
+            const int col = cols[j];
+            if (col >= r.k0 && col < r.k0 + r.K16) st_bf16(B, col - r.k0, k, lbo, Vp[(int64_t)j * b.q + k]);
+        }
+    }
+}
+
+__global__ void k_tpage_headers(const int32_t* __restrict__ nrec, const uint32_t* __restrict__ used, int64_t np,
+                                unsigned char* __restrict__ pool) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    uint32_t* h = reinterpret_cast<uint32_t*>(pool + p * (int64_t)kTP);
+    h[0] = (uint32_t)nrec[p];
+    h[1] = used[p];
+    h[2] = 0u;
+    h[3] = 0u;
+}
+
+// Longest-processing-time assignment of items (costs) to ncta lists.
+static std::vector<std::vector<int32_t>> lpt(const std::vector<int64_t>& cost, int32_t ncta) {
+    std::vector<int32_t> ord(cost.size());
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
+    using Slot = std::pair<int64_t, int32_t>;
+    std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+    for (int32_t c = 0; c < ncta; ++c) heap.push({0, c});
+    std::vector<std::vector<int32_t>> lists(ncta);
+    for (int32_t i : ord) {
+        Slot s = heap.top();
+        heap.pop();
+        lists[s.second].push_back(i);
+        s.first += cost[i];
+        heap.push(s);
+    }
+    return lists;
+}
+
+// Pack records (grouped: each group starts a new page) into pages per CTA.
+static vf_status pack_pages(vf_hmat* H, std::vector<TRec>& recs, const std::vector<std::vector<int32_t>>& cta_groups,
+                            const std::vector<std::pair<int64_t, int64_t>>& group_recs, dbuf<unsigned char>& pool,
+                            dbuf<uint32_t>& used_d, dbuf<int32_t>& cta_pages, int64_t* bytes) {
+    const int32_t ncta = (int32_t)cta_groups.size();
+    std::vector<int32_t> cp(ncta + 1, 0);
+    std::vector<uint32_t> used;
+    std::vector<int32_t> nrec;
+    std::vector<TRec> ordered;
+    for (int32_t c = 0; c < ncta; ++c) {
+        cp[c] = (int32_t)used.size();
+        for (int32_t gi : cta_groups[c]) {
+            bool fresh = true;
+            for (int64_t ri = group_recs[gi].first; ri < group_recs[gi].second; ++ri) {
+                TRec r = recs[ri];
+                const uint32_t sz = (uint32_t)(kTRHdr + r.K16 * r.N16 * 2);
+                if (fresh || used.back() + sz > (uint32_t)kTP) {
+                    used.push_back(kTPHdr);
+                    nrec.push_back(0);
+                    fresh = false;
+                }
+                r.dst = (int64_t)(used.size() - 1) * kTP + used.back();
+                used.back() += sz;
+                nrec.back()++;
+                ordered.push_back(r);
+            }
+        }
+    }
+    cp[ncta] = (int32_t)used.size();
+    const int64_t np = (int64_t)used.size();
+    VF_TRY(pool.alloc(std::max<int64_t>(np, 1) * kTP));
+    VF_TRY(used_d.upload(used));
+    VF_TRY(cta_pages.upload(cp));
+    *bytes = 0;
+    for (uint32_t u : used) *bytes += u;
+    if (np == 0) return VF_OK;
+    dbuf<TRec> dr;
+    VF_TRY(dr.upload(ordered));
+    dbuf<int32_t> dn;
+    VF_TRY(dn.upload(nrec));
+    k_tpack<<<(unsigned)ordered.size(), 256>>>(dr.p, H->blocks.p, H->val.p, H->aux.p, pool.p);
+    VF_TRY_CUDA(cudaGetLastError());
+    k_tpage_headers<<<(unsigned)ceil_div(np, 256), 256>>>(dn.p, used_d.p, np, pool.p);
+    VF_TRY_CUDA(cudaGetLastError());
+    VF_TRY_CUDA(cudaDeviceSynchronize());
+    return VF_OK;
+}
+
+static inline int32_t r16(int64_t x) { return (int32_t)((x + 15) / 16 * 16); }
+
+// The invariants every record must meet (checked on the host before upload).
+static vf_status check_records(const std::vector<TRec>& recs, int max_col, int64_t rows_x, int64_t rows_t) {
+    for (const TRec& r : recs) {
+        const bool ok = r.K16 >= 16 && r.K16 <= kKMax && r.K16 % 16 == 0 && r.N16 >= 16 && r.N16 <= kRegionCols &&
+                        r.N16 % 16 == 0 && r.coloff >= 0 && r.coloff % 16 == 0 && r.coloff + r.N16 <= max_col &&
+                        r.a_row0 >= 0 && r.a_row0 % 8 == 0 &&
+                        (int64_t)r.a_row0 + r.K16 <= (r.a_src ? rows_t : rows_x) &&
+                        kTPHdr + kTRHdr + r.K16 * r.N16 * 2 <= kTP;
+        VF_CHECK(ok, VF_E_INVAL,
+                 "tensor plan: bad record (kind %d, K %d, N %d, col %d, src %d, row %d)", r.kind, r.K16, r.N16,
+                 r.coloff, r.a_src, r.a_row0);
+    }
+    return VF_OK;
+}
+
+// Build the tensor pages of a matrix (once, on first use).
+vf_status tensor_plan_build(vf_hmat* H) {
+    if (H->tplan) return VF_OK;
+    device_guard g(H->device);
+    auto P = std::make_unique<vf_tensor_plan>();
+    const std::vector<HBlock>& B = H->h_blocks;
+    std::vector<int32_t> haux;
+    if (H->n_aux > 0) VF_TRY(H->aux.download(haux));
+    const int64_t n = H->nf;
+    const int64_t ntiles = (int64_t)H->h_tile_first.size();
+    P->n_rows_x = r16(n) + 32;
+    // T rows: q16 per SVD block
+    P->h_offT16.assign(B.size(), -1);
+    int64_t nt = 0;
+    for (size_t i = 0; i < B.size(); ++i)
+        if (B[i].kind == VF_BLK_SVD) {
+            P->h_offT16[i] = (int32_t)nt;
+            nt += r16(B[i].q);
+        }
+    P->n_rows_t = nt + 16;
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, H->device) != cudaSuccess || nsm <= 0) nsm = 148;
+    const int64_t rec_cost = 2048;  // fixed work of one record, in byte equivalents
+
+    // ---- phase 2: per tile, the blocks' pieces inside it, K-chunks of <= kKMax
+    std::vector<int32_t> tile_of_row(n, -1);
+    for (int64_t k = 0; k < ntiles; ++k)
+        for (int32_t r = H->h_tile_first[k]; r < H->h_tile_first[k] + H->h_tile_count[k]; ++r)
+            tile_of_row[r] = (int32_t)k;
+    std::vector<std::vector<TRec>> per(ntiles);
+    for (size_t bi = 0; bi < B.size(); ++bi) {
+        const HBlock& b = B[bi];
+        if (b.kind != VF_BLK_DENSE && b.kind != VF_BLK_CSR && b.kind != VF_BLK_SVD) continue;
+        for (int32_t r = b.r0; r < b.r0 + b.m;) {
+            const int32_t k = tile_of_row[r];
+            const int32_t tf = H->h_tile_first[k], tc = H->h_tile_count[k];
+            const int32_t rs = std::max(b.r0, tf), re = std::min(b.r0 + b.m, tf + tc);
+            r = re;
+            if (b.kind == VF_BLK_SVD) {
+                // any of the block's compacted rows in [rs, re)?
+                const int32_t* rows = haux.data() + b.off_aux;
+                const int32_t* lo = std::lower_bound(rows, rows + b.m1, rs);
+                if (lo == rows + b.m1 || *lo >= re) continue;
+            }
+            TRec t{};
+            t.blk = (int32_t)bi;
+            t.rs = rs;
+            t.re = re;
+            t.coloff = ((rs - tf) / 16) * 16;
+            t.row_base = tf + t.coloff;
+            t.N16 = r16(re - t.row_base);
+            if (b.kind == VF_BLK_SVD) {
+                // K = the rank, in chunks of <= kKMax (one A slot each)
+                t.kind = TREC_SVDU;
+                t.a_src = 1;
+                for (int32_t kc = 0; kc < r16(b.q); kc += kKMax) {
+                    TRec u = t;
+                    u.k0 = kc;
+                    u.K16 = std::min(kKMax, r16(b.q) - kc);
+                    u.a_row0 = P->h_offT16[bi] + kc;
+                    per[k].push_back(u);
+                }
+            } else {
+                t.kind = b.kind == VF_BLK_DENSE ? TREC_DENSE : TREC_CSR;
+                t.a_src = 0;
+                const int32_t c8 = (b.c0 / 8) * 8;
+                const int32_t ktot = r16(b.c0 + b.n - c8);
+                for (int32_t kc = 0; kc < ktot; kc += kKMax) {
+                    TRec u = t;
+                    u.k0 = c8 + kc;
+                    u.K16 = std::min(kKMax, ktot - kc);
+                    u.a_row0 = u.k0;
+                    per[k].push_back(u);
+                }
+            }
+        }
+    }
+    std::vector<TRec> recs2;
+    std::vector<std::pair<int64_t, int64_t>> tile_recs(ntiles);
+    std::vector<int64_t> tile_cost(ntiles, 0);
+    for (int64_t k = 0; k < ntiles; ++k) {
+        tile_recs[k].first = (int64_t)recs2.size();
+        for (size_t i = 0; i < per[k].size(); ++i) {
+            TRec t = per[k][i];
+            t.flags = (i == 0 ? TR_FIRST : 0) | (i + 1 == per[k].size() ? TR_LAST : 0);
+            recs2.push_back(t);
+            tile_cost[k] += (int64_t)t.K16 * t.N16 * 2 + (int64_t)t.K16 * kPanel * 2 + rec_cost;
+        }
+        tile_recs[k].second = (int64_t)recs2.size();
+    }
+    // a tile with no records still needs its epilogue: give it one empty record
+    for (int64_t k = 0; k < ntiles; ++k)
+        if (tile_recs[k].first == tile_recs[k].second) {
+            TRec t{};
+            t.kind = TREC_EMPTY;
+            t.blk = 0;
+            t.K16 = 16;
+            t.N16 = 16;
+            t.rs = t.re = H->h_tile_first[k];
+            t.row_base = t.rs;
+            t.k0 = 0;
+            t.a_src = 0;
+            t.a_row0 = 0;
+            t.flags = TR_FIRST | TR_LAST;
+            tile_recs[k].first = (int64_t)recs2.size();
+            recs2.push_back(t);
+            tile_recs[k].second = (int64_t)recs2.size();
+        }
+    VF_TRY(check_records(recs2, 64, P->n_rows_x, P->n_rows_t));
+    P->ncta2 = (int32_t)std::min<int64_t>((int64_t)nsm * 2, ntiles);
+    auto lists2 = lpt(tile_cost, P->ncta2);
+    {
+        std::vector<int32_t> tiles, ptr(P->ncta2 + 1, 0);
+        for (int32_t c = 0; c < P->ncta2; ++c) {
+            ptr[c] = (int32_t)tiles.size();
+            tiles.insert(tiles.end(), lists2[c].begin(), lists2[c].end());
+        }
+        ptr[P->ncta2] = (int32_t)tiles.size();
+        VF_TRY(P->cta_tiles.upload(tiles));
+        VF_TRY(P->cta_tile_ptr.upload(ptr));
+    }
+    VF_TRY(pack_pages(H, recs2, lists2, tile_recs, P->pages2, P->used2, P->cta_pages2, &P->bytes2));
+
+    // ---- phase 1: per SVD block (one unit), K-chunks over its column range
+    std::vector<TRec> recs1;
+    std::vector<std::pair<int64_t, int64_t>> unit_recs;
+    std::vector<int64_t> unit_cost;
+    std::vector<int32_t> unit_blk;
+    for (size_t bi = 0; bi < B.size(); ++bi) {
+        const HBlock& b = B[bi];
+        if (b.kind != VF_BLK_SVD) continue;
+        const int32_t q16 = r16(b.q);
+        const int32_t kmax = std::min<int32_t>(kKMax, ((kTP - kTPHdr - kTRHdr) / (q16 * 2)) / 16 * 16);
+        const int32_t c8 = (b.c0 / 8) * 8;
+        const int32_t ktot = r16(b.c0 + b.n - c8);
+        const int64_t first = (int64_t)recs1.size();
+        int64_t cost = 0;
+        for (int32_t kc = 0; kc < ktot; kc += kmax) {
+            TRec t{};
+            t.kind = TREC_VT;
+            t.blk = (int32_t)bi;
+            t.k0 = c8 + kc;
+            t.K16 = std::min(kmax, ktot - kc);
+            t.N16 = q16;
+            t.a_src = 0;
+            t.a_row0 = t.k0;
+            t.offT = P->h_offT16[bi];
+            recs1.push_back(t);
+            cost += (int64_t)t.K16 * t.N16 * 2 + (int64_t)t.K16 * kPanel * 2 + rec_cost;
+        }
+        recs1[first].flags |= TR_FIRST;
+        recs1.back().flags |= TR_LAST;
+        unit_recs.push_back({first, (int64_t)recs1.size()});
+        unit_cost.push_back(cost);
+        unit_blk.push_back((int32_t)bi);
+    }
+    VF_TRY(check_records(recs1, kRegionCols, P->n_rows_x, P->n_rows_t));
+    P->ncta1 = (int32_t)std::min<int64_t>((int64_t)nsm * 2, (int64_t)unit_cost.size());
+    if (P->ncta1 > 0) {
+        auto lists1 = lpt(unit_cost, P->ncta1);
+        std::vector<int32_t> units, ptr(P->ncta1 + 1, 0);
+        for (int32_t c = 0; c < P->ncta1; ++c) {
+            ptr[c] = (int32_t)(units.size() / 2);
+            for (int32_t u : lists1[c]) {
+                units.push_back(P->h_offT16[unit_blk[u]]);
+                units.push_back(r16(B[unit_blk[u]].q));
+            }
+        }
+        ptr[P->ncta1] = (int32_t)(units.size() / 2);
+        VF_TRY(P->cta_units.upload(units));
+        VF_TRY(P->cta_unit_ptr.upload(ptr));
+        VF_TRY(pack_pages(H, recs1, lists1, unit_recs, P->pages1, P->used1, P->cta_pages1, &P->bytes1));
+    }
+    H->tplan = P.release();
+    return VF_OK;
+}
+
+// ------------------------------------------------------------ device helpers
+__device__ __forceinline__ uint64_t mma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// kind::f16 instruction descriptor: D F32, A and B BF16, both MN-major, M = 128
+__device__ __forceinline__ uint32_t mma_idesc(int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(kPanel >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tm_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    __syncwarp();  // .sync.aligned: the whole warp, converged
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tm_zero16(uint32_t taddr) {
+    const uint32_t z = 0u;
+    __syncwarp();
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
+
+__device__ __forceinline__ void tm_wait_st() {
+    __syncwarp();
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ bool bwait(uint64_t* bar, uint32_t parity) {
+    return mbar_wait(bar, parity, kTWait);
+}
+
+// panel element (row, m) in the MN-major tiled layout (128 RHS)
+__device__ __forceinline__ int64_t panel_off(int64_t row, int m) {
+    return (row >> 3) * 2048 + (m >> 3) * 128 + (row & 7) * 16 + (m & 7) * 2;
+}
+
+struct TSmem {
+    uint64_t page_full[2], page_empty[2], a_full[kASlots], a_empty[kASlots], d_full[2], d_empty[2], done;
+    uint32_t tmem_base;
+    int32_t abort;
+};
+
+constexpr size_t kTSmemBytes = 2 * kTP + kASlots * kAStage + 1024;
+
+// The producer (warp 0, lane 0): pages [pa, pb) into two stages, and each
+// record's A operand (a contiguous panel range) into the A ring.
+__device__ void t_producer(TSmem& S, unsigned char* stages, unsigned char* abuf, const unsigned char* pages,
+                           const uint32_t* used, int pa, int pb, const unsigned char* Xp, const unsigned char* Tp,
+                           int64_t rows_x, int64_t rows_t, int max_col, int* status) {
+    int nrec_issued = 0;
+    for (int p = pa, li = 0; p < pb; ++p, ++li) {
+        const int s = li & 1;
+        if (li >= 2 && !bwait(&S.page_empty[s], (uint32_t)(((li >> 1) - 1) & 1))) goto fail;
+        {
+            const uint32_t bytes = used[p];
+            if (bytes < kTPHdr || bytes > (uint32_t)kTP || (bytes & 15u)) goto oob;
+            mbar_arrive_expect_tx(&S.page_full[s], bytes);
+            bulk_g2s(stages + s * kTP, pages + (int64_t)p * kTP, bytes, &S.page_full[s]);
+        }
+        if (!bwait(&S.page_full[s], (uint32_t)((li >> 1) & 1))) goto fail;
+        {
+            const unsigned char* pg = stages + s * kTP;
+            const int nrec = (int)reinterpret_cast<const uint32_t*>(pg)[0];
+            const uint32_t pused = reinterpret_cast<const uint32_t*>(pg)[1];
+            uint32_t off = kTPHdr;
+            for (int r = 0; r < nrec; ++r) {
+                const uint32_t* h = reinterpret_cast<const uint32_t*>(pg + off);
+                const int K16 = (int)h[0], N16 = (int)h[1];
+                // self-check: shapes, the record inside the page, the A range inside its panel
+                if (K16 < 16 || K16 > kKMax || (K16 & 15) || N16 < 16 || N16 > kRegionCols || (N16 & 15) ||
+                    (int)h[2] + N16 > max_col || off + kTRHdr + (uint32_t)(K16 * N16 * 2) > pused || (h[4] & 7u) ||
+                    (int64_t)h[4] + K16 > (h[3] ? rows_t : rows_x))
+                    goto oob;
+                const int j = nrec_issued % kASlots;
+                if (nrec_issued >= kASlots && !bwait(&S.a_empty[j], (uint32_t)(((nrec_issued / kASlots) - 1) & 1)))
+                    goto fail;
+                const unsigned char* src = (h[3] ? Tp : Xp) + (int64_t)(h[4] >> 3) * 2048;
+                const uint32_t bytes = (uint32_t)K16 * kPanel * 2;
+                mbar_arrive_expect_tx(&S.a_full[j], bytes);
+                bulk_g2s(abuf + (size_t)j * kAStage, src, bytes, &S.a_full[j]);
+                ++nrec_issued;
+                off += kTRHdr + (uint32_t)(K16 * N16 * 2);
+            }
+        }
+        if (S.abort) return;
+    }
+    return;
+fail:
+    atomicExch(status, VF_E_TIMEOUT);
+    atomicExch(&S.abort, 1);
+    return;
+oob:
+    atomicExch(status, VF_E_OOB);
+    atomicExch(&S.abort, 1);
+}
+
+// The MMA issuer (warp 1, lane 0).
+__device__ void t_issuer(TSmem& S, unsigned char* stages, unsigned char* abuf, int pa, int pb, int* status) {
+    int nrec = 0, dcount[2] = {0, 0}, d = 0;
+    for (int p = pa, li = 0; p < pb; ++p, ++li) {
+        const int s = li & 1;
+        if (!bwait(&S.page_full[s], (uint32_t)((li >> 1) & 1))) goto fail;
+        {
+            const unsigned char* pg = stages + s * kTP;
+            const int nr = (int)reinterpret_cast<const uint32_t*>(pg)[0];
+            uint32_t off = kTPHdr;
+            for (int r = 0; r < nr; ++r) {
+                const uint32_t* h = reinterpret_cast<const uint32_t*>(pg + off);
+                const int K16 = (int)h[0], N16 = (int)h[1], coloff = (int)h[2], flags = (int)h[5];
+                const int j = nrec % kASlots;
+                if (!bwait(&S.a_full[j], (uint32_t)((nrec / kASlots) & 1))) goto fail;
+                if (flags & TR_FIRST) {
+                    if (!bwait(&S.d_empty[d], (uint32_t)(dcount[d] & 1))) goto fail;
+                    tm_fence_after();
+                }
+                const uint32_t dt = S.tmem_base + (uint32_t)(d * kRegionCols + coloff);
+                const uint32_t bsa = smem_u32(pg + off + kTRHdr), asa = smem_u32(abuf + (size_t)j * kAStage);
+                const uint32_t blbo = (uint32_t)(N16 / 8) * 128;
+                const uint32_t idesc = mma_idesc(N16);
+                for (int kk = 0; kk < K16 / 16; ++kk)
+                    mma_bf16(dt, mma_desc(asa + kk * 4096, 2048, 128), mma_desc(bsa + kk * 2 * blbo, blbo, 128), idesc, 1);
+                mma_commit(&S.a_empty[j]);
+                if (flags & TR_LAST) {
+                    mma_commit(&S.d_full[d]);
+                    dcount[d]++;
+                    d ^= 1;
+                }
+                ++nrec;
+                off += kTRHdr + (uint32_t)(K16 * N16 * 2);
+            }
+        }
+        mma_commit(&S.page_empty[s]);
+        if (S.abort) break;
+    }
+    mma_commit(&S.done);
+    return;
+fail:
+    atomicExch(status, VF_E_TIMEOUT);
+    atomicExch(&S.abort, 1);
+    mma_commit(&S.done);
+}
+
+// Common prologue: barriers, TMEM allocation, both regions zeroed.
+__device__ void t_prologue(TSmem& S, int ncols) {
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&S.page_full[i], 1);
+            mbar_init(&S.page_empty[i], 1);
+            mbar_init(&S.d_full[i], 1);
+            mbar_init(&S.d_empty[i], 4);
+        }
+        for (int i = 0; i < kASlots; ++i) {
+            mbar_init(&S.a_full[i], 1);
+            mbar_init(&S.a_empty[i], 1);
+        }
+        mbar_init(&S.done, 1);
+        S.abort = 0;
+        mbar_init_fence();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S.tmem_base)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    if (warp >= 2) {
+        // zero both accumulator regions (this warp's 32 lanes), then release them
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        for (int c = 0; c < 2 * kRegionCols; c += 16) tm_zero16(S.tmem_base + lane_base + c);
+        tm_wait_st();
+        tm_fence_before();
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) {
+            mbar_arrive(&S.d_empty[0]);
+            mbar_arrive(&S.d_empty[1]);
+        }
+    }
+}
+
+// Common epilogue of a CTA: wait for the MMAs, free TMEM.
+__device__ void t_finish(TSmem& S, int ncols, int* status) {
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 32) {
+        if (!bwait(&S.done, 0)) atomicExch(status, VF_E_TIMEOUT);
+    }
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem_base), "r"(ncols));
+    }
+}
+
+// Release a region after the epilogue read it: zero it, then arrive.
+__device__ __forceinline__ void t_release(TSmem& S, int d) {
+    const int warp = threadIdx.x >> 5;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    for (int c = 0; c < kRegionCols; c += 16) tm_zero16(S.tmem_base + lane_base + d * kRegionCols + c);
+    tm_wait_st();
+    tm_fence_before();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&S.d_empty[d]);
+}
+
+// Drain (producer): wait for every copy it may have left in flight.
+__device__ void t_drain(TSmem& S) {
+    for (int s = 0; s < 2; ++s) mbar_wait(&S.page_full[s], 0, 1024), mbar_wait(&S.page_full[s], 1, 1024);
+    for (int j = 0; j < kASlots; ++j) mbar_wait(&S.a_full[j], 0, 1024), mbar_wait(&S.a_full[j], 1, 1024);
+}
+
+// ------------------------------------------------------------ phase 1
+// T panel rows offT16 .. + N16 of each unit = (V'^T X) for this panel.
+__global__ void __launch_bounds__(192, 1) k_tphase1(const unsigned char* __restrict__ pages,
+                                                    const uint32_t* __restrict__ used,
+                                                    const int32_t* __restrict__ cta_pages,
+                                                    const int32_t* __restrict__ cta_units,
+                                                    const int32_t* __restrict__ cta_unit_ptr,
+                                                    const unsigned char* __restrict__ Xp, unsigned char* __restrict__ Tp,
+                                                    int64_t rows_x, int64_t rows_t, int* __restrict__ status) {
+    constexpr int MAXCOL = kRegionCols;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* stages = smem;
+    unsigned char* abuf = smem + 2 * kTP;
+    TSmem& S = *reinterpret_cast<TSmem*>(smem + 2 * kTP + kASlots * kAStage);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    t_prologue(S, 2 * kRegionCols);
+    __syncthreads();
+    const int pa = cta_pages[blockIdx.x], pb = cta_pages[blockIdx.x + 1];
+    if (warp == 0) {
+        if (lane == 0) {
+            t_producer(S, stages, abuf, pages, used, pa, pb, Xp, Tp, rows_x, rows_t, MAXCOL, status);
+            if (S.abort) t_drain(S);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) t_issuer(S, stages, abuf, pa, pb, status);
+    } else {
+        const int m = 32 * (warp & 3) + lane;
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        const int u0 = cta_unit_ptr[blockIdx.x], u1 = cta_unit_ptr[blockIdx.x + 1];
+        for (int u = u0, k = 0; u < u1; ++u, ++k) {
+            const int d = k & 1;
+            if (!__all_sync(0xffffffffu, bwait(&S.d_full[d], (uint32_t)((k >> 1) & 1)))) {
+                if (lane == 0) atomicExch(status, VF_E_TIMEOUT), atomicExch(&S.abort, 1);
+                break;
+            }
+            tm_fence_after();
+            const int offT = cta_units[2 * u], N16 = cta_units[2 * u + 1];
+            for (int c0 = 0; c0 < N16; c0 += 16) {
+                float v[16];
+                tm_ld16(S.tmem_base + lane_base + d * kRegionCols + c0, v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    *reinterpret_cast<__nv_bfloat16*>(Tp + panel_off(offT + c0 + j, m)) = __float2bfloat16_rn(v[j]);
+            }
+            t_release(S, d);
+        }
+    }
+    t_finish(S, 2 * kRegionCols, status);
+}
+
+// ------------------------------------------------------------ phase 2
+__global__ void __launch_bounds__(192, 1) k_tphase2(const unsigned char* __restrict__ pages,
+                                                    const uint32_t* __restrict__ used,
+                                                    const int32_t* __restrict__ cta_pages,
+                                                    const int32_t* __restrict__ cta_tiles,
+                                                    const int32_t* __restrict__ cta_tile_ptr,
+                                                    const int32_t* __restrict__ tile_first,
+                                                    const int32_t* __restrict__ tile_count,
+                                                    const unsigned char* __restrict__ Xp,
+                                                    const unsigned char* __restrict__ Tp, TEpi ep, int64_t rows_x,
+                                                    int64_t rows_t, int* __restrict__ status) {
+    constexpr int MAXCOL = 64;  // phase 2: a tile's rows
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* stages = smem;
+    unsigned char* abuf = smem + 2 * kTP;
+    TSmem& S = *reinterpret_cast<TSmem*>(smem + 2 * kTP + kASlots * kAStage);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    t_prologue(S, 2 * kRegionCols);
+    __syncthreads();
+    const int pa = cta_pages[blockIdx.x], pb = cta_pages[blockIdx.x + 1];
+    if (warp == 0) {
+        if (lane == 0) {
+            t_producer(S, stages, abuf, pages, used, pa, pb, Xp, Tp, rows_x, rows_t, MAXCOL, status);
+            if (S.abort) t_drain(S);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) t_issuer(S, stages, abuf, pa, pb, status);
+    } else {
+        const int m = 32 * (warp & 3) + lane;
+        const int col = ep.p0 + m;  // RHS column
+        const bool live = col < ep.R;
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        const int t0 = cta_tile_ptr[blockIdx.x], t1 = cta_tile_ptr[blockIdx.x + 1];
+        for (int ti = t0, k = 0; ti < t1; ++ti, ++k) {
+            const int d = k & 1;
+            if (!__all_sync(0xffffffffu, bwait(&S.d_full[d], (uint32_t)((k >> 1) & 1)))) {
+                if (lane == 0) atomicExch(status, VF_E_TIMEOUT), atomicExch(&S.abort, 1);
+                break;
+            }
+            tm_fence_after();
+            const int tile = cta_tiles[ti];
+            const int tf = tile_first[tile], tc = tile_count[tile];
+            double ss = 0.0;
+            for (int c0 = 0; c0 < tc; c0 += 16) {
+                float v[16];
+                tm_ld16(S.tmem_base + lane_base + d * kRegionCols + c0, v);
+                if (!live) continue;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if (c0 + j >= tc) break;
+                    const int64_t p = tf + c0 + j;
+                    const int64_t o = (int64_t)col * ep.n + p;
+                    if (ep.mode == 0) {
+                        ep.Y[o] = v[j];
+                    } else {
+                        const float bn = ep.E[o] + ep.rho[p] * v[j];
+                        const float dd = bn - ep.Bold[o];
+                        ss += (double)dd * dd;
+                        ep.Y[o] = bn;
+                        if (ep.Xnext) *reinterpret_cast<__nv_bfloat16*>(ep.Xnext + panel_off(p, m)) = __float2bfloat16_rn(bn);
+                    }
+                }
+            }
+            if (ep.mode == 1 && live) ep.colpart[(int64_t)col * ep.ntiles + tile] = ss;
+            t_release(S, d);
+        }
+    }
+    t_finish(S, 2 * kRegionCols, status);
+}
+
+// FP32 column-major (tree order, or face order through perm) -> BF16 panel.
+__global__ void k_to_panel(const float* __restrict__ src, int64_t ld, const int32_t* __restrict__ perm, int64_t n,
+                           int R, int p0, int64_t rows, unsigned char* __restrict__ dst) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // (row, 8-column chunk)
+    if (e >= rows * 16) return;
+    const int64_t row = e >> 4;
+    const int m0 = (int)(e & 15) * 8;
+    __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int c = p0 + m0 + i;
+        float x = 0.f;
+        if (row < n && c < R) x = src[(int64_t)c * ld + (perm ? perm[row] : row)];
+        v[i] = __float2bfloat16_rn(x);
+    }
+    *reinterpret_cast<uint4*>(dst + (row >> 3) * 2048 + (m0 >> 3) * 128 + (row & 7) * 16) =
+        *reinterpret_cast<const uint4*>(v);
+}
+
+// ------------------------------------------------------------ host entry
+static vf_status tensor_attrs() {
+    static bool done = false;
+    if (done) return VF_OK;
+    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmemBytes));
+    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmemBytes));
+    done = true;
+    return VF_OK;
+}
+
+vf_status tensor_prepare(vf_hmat* H) {
+    VF_TRY(tensor_plan_build(H));
+    VF_TRY(tensor_attrs());
+    return VF_OK;
+}
+
+int64_t tensor_panel_bytes_x(const vf_hmat* H) { return H->tplan->n_rows_x * kPanel * 2; }
+int64_t tensor_panel_bytes_t(const vf_hmat* H) { return H->tplan->n_rows_t * kPanel * 2; }
+int64_t tensor_page_bytes(const vf_hmat* H) { return H->tplan->bytes1 + H->tplan->bytes2; }
+
+// X (FP32, column-major, ld) -> panel; perm maps tree row -> source row (or NULL)
+vf_status tensor_to_panel(const vf_hmat* H, const float* X, int64_t ld, const int32_t* perm, int R, int p0,
+                          unsigned char* panel, cudaStream_t st) {
+    const int64_t rows = H->tplan->n_rows_x;
+    k_to_panel<<<(unsigned)ceil_div(rows * 16, 256), 256, 0, st>>>(X, ld, perm, H->nf, R, p0, rows, panel);
+    VF_TRY_CUDA(cudaGetLastError());
+    return VF_OK;
+}
+
+// One multiply of one panel: phase 1 (T panel), then phase 2 with the epilogue.
+vf_status tensor_multiply(const vf_hmat* H, const unsigned char* Xpanel, unsigned char* Tpanel, const TEpi& ep,
+                          int* status, cudaStream_t st) {
+    const vf_tensor_plan* P = H->tplan;
+    if (P->ncta1 > 0)
+        k_tphase1<<<(unsigned)P->ncta1, 192, kTSmemBytes, st>>>(P->pages1.p, P->used1.p, P->cta_pages1.p,
+                                                                P->cta_units.p, P->cta_unit_ptr.p, Xpanel, Tpanel,
+                                                                P->n_rows_x, P->n_rows_t, status);
+    k_tphase2<<<(unsigned)P->ncta2, 192, kTSmemBytes, st>>>(P->pages2.p, P->used2.p, P->cta_pages2.p, P->cta_tiles.p,
+                                                            P->cta_tile_ptr.p, H->tile_first.p, H->tile_count.p,
+                                                            Xpanel, Tpanel, ep, P->n_rows_x, P->n_rows_t, status);
+    VF_TRY_CUDA(cudaGetLastError());
+    return VF_OK;
+}
+
+int tensor_kernels(const vf_hmat* H) { return (H->tplan->ncta1 > 0 ? 1 : 0) + 1; }
+
+}  // namespace vf
