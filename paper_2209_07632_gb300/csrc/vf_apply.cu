@@ -1060,6 +1060,8 @@ struct Workspace {
     dbuf<float*> ysel;        // current output
     // tensor-core path (BF16, R >= kTensorMinR): BF16 panels of 128 RHS, ping-pong, and the T panel
     dbuf<unsigned char> xpan[2], tpan;
+    dbuf<unsigned char> xsplit[2], tsplit[2];  // hi / lo panels of the split residual
+    dbuf<int> tcount;  // columns not converged after a tensor sweep
     int tpanels = 0;
     cudaGraphExec_t graph = nullptr;
     cudaGraphConditionalHandle handle = 0;
@@ -1320,7 +1322,7 @@ static bool use_tensor(const vf_hmat* h, int prec, int R) {
 // The tensor pages (built once per matrix; the handle's lazily built part)
 // and this workspace's panels.
 static vf_status tensor_ws(const vf_hmat* h, Workspace* w) {
-    VF_TRY(tensor_prepare(const_cast<vf_hmat*>(h)));
+    VF_TRY(tensor_prepare(const_cast<vf_hmat*>(h), 1));
     if (w->xpan[0].p) return VF_OK;
     w->tpanels = (int)ceil_div(w->R, kTensorPanel);
     const int64_t bx = tensor_panel_bytes_x(h), bt = tensor_panel_bytes_t(h);
@@ -1330,6 +1332,122 @@ static vf_status tensor_ws(const vf_hmat* h, Workspace* w) {
     }
     VF_TRY(w->tpan.alloc((size_t)bt));
     VF_TRY_CUDA(cudaMemset(w->tpan.p, 0, (size_t)bt));
+    VF_TRY(w->tcount.alloc(1));
+    return VF_OK;
+}
+
+// Columns whose last update exceeded rtol ||E|| (the sweep's residual
+// partials summed per column in a fixed order, as in k_sweep_reduce).
+__global__ void __launch_bounds__(1024) k_unconverged(const double* __restrict__ colpart, int64_t ntiles, int R,
+                                                      const double* __restrict__ enorm2, double rtol2,
+                                                      double* __restrict__ colres, int* __restrict__ count) {
+    __shared__ int s_unconv;
+    if (threadIdx.x == 0) s_unconv = 0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    int mine = 0;
+    for (int c = warp; c < R; c += nw) {
+        double s = 0;
+        for (int64_t t = lane; t < ntiles; t += 32) s += colpart[(int64_t)c * ntiles + t];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            colres[c] = s;
+            if (s > rtol2 * enorm2[c]) mine++;
+        }
+    }
+    if (lane == 0 && mine) atomicAdd(&s_unconv, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) *count = s_unconv;
+}
+
+// Jacobi on the tensor cores: B_0 = Et, B_{k+1} = Et + rho .* (F_bf16 B_k)
+// until every column's update is <= rtol ||Et|| or max_iter sweeps; the
+// result is in Bt[*par].  One host check per sweep.
+static vf_status tensor_jacobi_loop(const vf_hmat* h, Workspace* w, int max_iter, double rtol, cudaStream_t st,
+                                    int* iters, int* par, int* kernels) {
+    VF_TRY(tensor_ws(h, w));
+    const int64_t n = h->nf, nR = n * (int64_t)w->R;
+    const int64_t ntiles = (int64_t)h->h_tile_first.size();
+    const int64_t bx = tensor_panel_bytes_x(h);
+    VF_TRY_CUDA(cudaMemcpyAsync(w->Bt[0].p, w->Et.p, nR * 4, cudaMemcpyDeviceToDevice, st));
+    k_colnorm2<<<(unsigned)w->R, 1024, 0, st>>>(w->Et.p, n, w->enorm2.p);
+    for (int p = 0; p < w->tpanels; ++p)
+        VF_TRY(tensor_to_panel(h, w->Et.p, n, nullptr, w->R, p * kTensorPanel, w->xpan[0].p + (size_t)p * bx, nullptr,
+                               st));
+    *kernels += 1 + w->tpanels;
+    int it = 0, cur = 0;
+    while (it < max_iter) {
+        for (int p = 0; p < w->tpanels; ++p) {
+            TEpi ep{};
+            ep.mode = 1;
+            ep.n = n;
+            ep.R = w->R;
+            ep.p0 = p * kTensorPanel;
+            ep.Y = w->Bt[cur ^ 1].p;
+            ep.E = w->Et.p;
+            ep.rho = w->rho_t.p;
+            ep.Bold = w->Bt[cur].p;
+            ep.Xnext = w->xpan[cur ^ 1].p + (size_t)p * bx;
+            ep.colpart = w->colpart.p;
+            ep.ntiles = ntiles;
+            VF_TRY(tensor_multiply(h, 1, w->xpan[cur].p + (size_t)p * bx, nullptr, w->tpan.p, nullptr, ep,
+                                   w->status.p, st));
+        }
+        k_unconverged<<<1, 1024, 0, st>>>(w->colpart.p, ntiles, w->R, w->enorm2.p, rtol * rtol, w->colres.p,
+                                          w->tcount.p);
+        VF_TRY_CUDA(cudaGetLastError());
+        *kernels += w->tpanels * tensor_kernels(h, 1) + 1;
+        int hc = 0;
+        VF_TRY_CUDA(cudaMemcpyAsync(&hc, w->tcount.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        VF_TRY_CUDA(cudaStreamSynchronize(st));
+        cur ^= 1;
+        ++it;
+        if (hc == 0) break;
+    }
+    *iters = it;
+    *par = cur;
+    return VF_OK;
+}
+
+// The refinement residual on the tensor cores: r = E - B + rho .* (F B) with
+// F B formed from the FP32 factors split in two BF16 terms (three products
+// per block piece, FP32 accumulation; ~2^-16 relative) and r, its column
+// norms in FP64.  B, E: tree order, column-major (ld n); r -> rout;
+// per-column ||r||^2 -> w->colres (device).
+static vf_status tensor_residual(const vf_hmat* h, Workspace* w, const float* B, const float* E, float* rout,
+                                 cudaStream_t st, int* kernels) {
+    VF_TRY(tensor_ws(h, w));
+    VF_TRY(tensor_prepare(const_cast<vf_hmat*>(h), 2));
+    const int64_t n = h->nf, ntiles = (int64_t)h->h_tile_first.size();
+    const int64_t bx = tensor_panel_bytes_x(h), bt = tensor_panel_bytes_t(h);
+    if (!w->xsplit[0].p) {
+        for (int i = 0; i < 2; ++i) {
+            VF_TRY(w->xsplit[i].alloc((size_t)w->tpanels * bx));
+            VF_TRY_CUDA(cudaMemset(w->xsplit[i].p, 0, (size_t)w->tpanels * bx));
+            VF_TRY(w->tsplit[i].alloc((size_t)bt));
+            VF_TRY_CUDA(cudaMemset(w->tsplit[i].p, 0, (size_t)bt));
+        }
+    }
+    for (int p = 0; p < w->tpanels; ++p) {
+        unsigned char* xh = w->xsplit[0].p + (size_t)p * bx;
+        unsigned char* xl = w->xsplit[1].p + (size_t)p * bx;
+        VF_TRY(tensor_to_panel(h, B, n, nullptr, w->R, p * kTensorPanel, xh, xl, st));
+        TEpi ep{};
+        ep.mode = 2;
+        ep.n = n;
+        ep.R = w->R;
+        ep.p0 = p * kTensorPanel;
+        ep.Y = rout;
+        ep.E = E;
+        ep.rho = w->rho_t.p;
+        ep.Bold = B;
+        ep.colpart = w->colpart.p;
+        ep.ntiles = ntiles;
+        VF_TRY(tensor_multiply(h, 2, xh, xl, w->tsplit[0].p, w->tsplit[1].p, ep, w->status.p, st));
+    }
+    k_unconverged<<<1, 1024, 0, st>>>(w->colpart.p, ntiles, w->R, w->enorm2.p, 0.0, w->colres.p, w->tcount.p);
+    VF_TRY_CUDA(cudaGetLastError());
+    *kernels += w->tpanels * (1 + tensor_kernels(h, 2)) + 1;
     return VF_OK;
 }
 
@@ -1341,14 +1459,14 @@ static vf_status tensor_apply(const vf_hmat* h, Workspace* w, const float* X, in
     const int64_t bx = tensor_panel_bytes_x(h);
     for (int p = 0; p < w->tpanels; ++p) {
         unsigned char* xp = w->xpan[0].p + (size_t)p * bx;
-        VF_TRY(tensor_to_panel(h, X, ld, perm, w->R, p * kTensorPanel, xp, st));
+        VF_TRY(tensor_to_panel(h, X, ld, perm, w->R, p * kTensorPanel, xp, nullptr, st));
         TEpi ep{};
         ep.mode = 0;
         ep.n = h->nf;
         ep.R = w->R;
         ep.p0 = p * kTensorPanel;
         ep.Y = Y;
-        VF_TRY(tensor_multiply(h, xp, w->tpan.p, ep, w->status.p, st));
+        VF_TRY(tensor_multiply(h, 1, xp, nullptr, w->tpan.p, nullptr, ep, w->status.p, st));
     }
     return VF_OK;
 }
@@ -1597,20 +1715,34 @@ extern "C" vf_status vf_solve(const vf_hmat* h, const float* rho, const float* E
         VF_TRY_CUDA(cudaMemcpyAsync(w32->rho_t.p, w->rho_t.p, n * 4, cudaMemcpyDeviceToDevice, st));
         double mx = 0;
         bool ok = false;
+        const bool tensor = vf::use_tensor(h, o.precision, R);
         for (int ref = 0; ref <= o.max_refine; ++ref) {
-            // r = E - B + rho F B  (FP32 factors, FP64 accumulation)
-            // the residual (written to Et) becomes the next inner right-hand side
-            VF_TRY(vf::launch_multiply(h, VF_PREC_FP32, w32, vf::MODE_RESID, nullptr, nullptr, w->Yt.p, w->Et.p,
-                                       w->Xt.p, w32->rho_t.p, st));
-            S.kernels += kps - 1;
-            const int64_t ntiles = (int64_t)h->h_tile_first.size();
-            std::vector<double> part((size_t)ntiles * R), rr(R, 0.0);
-            VF_TRY_CUDA(cudaMemcpyAsync(part.data(), w32->colpart.p, part.size() * 8, cudaMemcpyDeviceToHost, st));
-            VF_TRY_CUDA(cudaStreamSynchronize(st));
+            // r = E - B + rho F B  (FP32 factors, FP64 accumulation); the
+            // residual (written to Et) becomes the next inner right-hand side.
+            // With B = 0 (the first pass) r = E exactly, already in Et.
+            std::vector<double> rr(R, 0.0);
+            if (ref == 0) {
+                rr = en;
+            } else if (tensor) {
+                int kk = 0;
+                VF_TRY(vf::tensor_residual(h, w, w->Yt.p, w->Xt.p, w->Et.p, st, &kk));
+                S.kernels += kk;
+                VF_TRY_CUDA(cudaMemcpyAsync(rr.data(), w->colres.p, R * 8, cudaMemcpyDeviceToHost, st));
+                VF_TRY_CUDA(cudaStreamSynchronize(st));
+            } else {
+                VF_TRY(vf::launch_multiply(h, VF_PREC_FP32, w32, vf::MODE_RESID, nullptr, nullptr, w->Yt.p, w->Et.p,
+                                           w->Xt.p, w32->rho_t.p, st));
+                S.kernels += kps - 1;
+                const int64_t ntiles = (int64_t)h->h_tile_first.size();
+                std::vector<double> part((size_t)ntiles * R);
+                VF_TRY_CUDA(cudaMemcpyAsync(part.data(), w32->colpart.p, part.size() * 8, cudaMemcpyDeviceToHost, st));
+                VF_TRY_CUDA(cudaStreamSynchronize(st));
+                for (int c = 0; c < R; ++c)
+                    for (int64_t tt = 0; tt < ntiles; ++tt) rr[c] += part[(size_t)c * ntiles + tt];
+            }
             mx = 0;
             ok = true;
             for (int c = 0; c < R; ++c) {
-                for (int64_t tt = 0; tt < ntiles; ++tt) rr[c] += part[(size_t)c * ntiles + tt];
                 double rel = en[c] > 0 ? std::sqrt(rr[c] / en[c]) : 0.0;
                 mx = std::max(mx, rel);
                 ok = ok && rr[c] <= o.rtol * o.rtol * en[c];
@@ -1618,12 +1750,18 @@ extern "C" vf_status vf_solve(const vf_hmat* h, const float* rho, const float* E
             if (ok || ref == o.max_refine) break;
             S.refinements++;
             // delta = (I - rho F_lowprec)^{-1} r, then B += delta
-            VF_TRY(vf::jacobi_loop(h, w, o.max_iter, o.inner_rtol, st, &ls, nullptr, nullptr));
             vf::LoopState l2{};
-            VF_TRY_CUDA(cudaMemcpyAsync(&l2, w->loop.p, sizeof(l2), cudaMemcpyDeviceToHost, st));
-            VF_TRY_CUDA(cudaStreamSynchronize(st));
+            if (tensor) {
+                int kk = 0;
+                VF_TRY(vf::tensor_jacobi_loop(h, w, o.max_iter, o.inner_rtol, st, &l2.iter, &l2.parity, &kk));
+                S.kernels += kk + 1;  // the tensor sweeps, then the update
+            } else {
+                VF_TRY(vf::jacobi_loop(h, w, o.max_iter, o.inner_rtol, st, &ls, nullptr, nullptr));
+                VF_TRY_CUDA(cudaMemcpyAsync(&l2, w->loop.p, sizeof(l2), cudaMemcpyDeviceToHost, st));
+                VF_TRY_CUDA(cudaStreamSynchronize(st));
+                S.kernels += 2 + l2.iter * kps + 1;  // column norms, loop init, sweeps, the update
+            }
             S.sweeps += l2.iter;
-            S.kernels += 2 + l2.iter * kps + 1;  // column norms, loop init, sweeps, the update
             vf::k_axpy_inplace<<<1024, 256, 0, st>>>(w->Yt.p, w->Bt[l2.parity].p, nR);
             VF_TRY_CUDA(cudaGetLastError());
         }

@@ -46,12 +46,16 @@ constexpr int kTP = 16384;           // tensor page bytes
 constexpr int kTPHdr = 16;           // page header: nrec, used, 0, 0
 constexpr int kTRHdr = 32;           // record header (8 x u32)
 constexpr int kPanel = 128;          // right-hand sides per panel (MMA M)
-constexpr int kKMax = 64;            // largest K of one record (A slot = 64 x 256 B)
-constexpr int kASlots = 4;
-constexpr int kAStage = kKMax * kPanel * 2;
+constexpr int kKMax = 64;            // largest K of one record (A operand <= 64 x 256 B)
+constexpr int kTickets = 16;         // records in flight (A operands in the ring)
+constexpr int kARing = 57344;        // A-operand ring bytes
+constexpr int kPStages = 3;          // page stages (the producer runs up to two pages ahead)
 constexpr int kRegionCols = 128;     // TMEM columns per accumulator region
 constexpr uint32_t kTWait = 1u << 22;
-enum { TR_FIRST = 1, TR_LAST = 2 };
+// record flags: FIRST / LAST record of its accumulator region's use (a
+// phase-2 tile, a phase-1 group of units); USTART: first record of a unit
+// (its first MMA overwrites D instead of accumulating)
+enum { TR_FIRST = 1, TR_LAST = 2, TR_USTART = 4 };
 enum { TREC_DENSE = 0, TREC_CSR = 1, TREC_SVDU = 2, TREC_VT = 3, TREC_EMPTY = 4 };
 
 // ------------------------------------------------------------ plan
@@ -64,15 +68,21 @@ struct TRec {        // where one tensor record's B operand comes from (build ti
     int32_t coloff;    // D column offset (phase 2)
     int32_t a_src, a_row0;
     int32_t flags, offT;
+    int32_t S;         // 1: BF16 body; 2: hi and lo bodies
+    int32_t ring;      // byte offset of its A operand(s) in the CTA's ring
+    int32_t dep;       // the record (CTA-local index) whose MMAs must finish before its copy, or -1
+    int32_t pad;
     int64_t dst;
 };
 
 }  // namespace vf
 
-struct vf_tensor_plan {
-    int64_t n_rows_x = 0, n_rows_t = 0;  // panel rows (X, T), multiples of 16
+// One set of tensor pages: S = 1 holds the BF16 factors; S = 2 holds each
+// FP32 factor split in two BF16 terms (hi = bf16(v), lo = bf16(v - hi)),
+// two B bodies per record.
+struct vf_tensor_set {
+    bool built = false;
     int32_t ncta2 = 0, ncta1 = 0;
-    std::vector<int32_t> h_offT16;       // per block: first T row (SVD), else -1
     vf::dbuf<unsigned char> pages2, pages1;
     vf::dbuf<uint32_t> used2, used1;
     vf::dbuf<int32_t> cta_pages2, cta_pages1;  // ncta + 1 each
@@ -81,13 +91,22 @@ struct vf_tensor_plan {
     int64_t bytes2 = 0, bytes1 = 0;
 };
 
+struct vf_tensor_plan {
+    int64_t n_rows_x = 0, n_rows_t = 0;  // panel rows (X, T), multiples of 16
+    std::vector<int32_t> h_offT16;       // per block: first T row (SVD), else -1
+    vf_tensor_set set[2];                // [S - 1]
+};
+
 namespace vf {
 
 void tensor_plan_free(vf_tensor_plan* p) { delete p; }
 
-__device__ __forceinline__ void st_bf16(unsigned char* base, int64_t k, int mn, int lbo, float v) {
-    *reinterpret_cast<__nv_bfloat16*>(base + (k >> 3) * lbo + (mn >> 3) * 128 + (k & 7) * 16 + (mn & 7) * 2) =
-        __float2bfloat16_rn(v);
+// B element (k, mn): the BF16 value, or (S = 2) hi and lo in two bodies `lo_off` bytes apart
+__device__ __forceinline__ void st_bf16(unsigned char* base, int64_t k, int mn, int lbo, float v, int lo_off) {
+    const int64_t o = (k >> 3) * lbo + (mn >> 3) * 128 + (k & 7) * 16 + (mn & 7) * 2;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    *reinterpret_cast<__nv_bfloat16*>(base + o) = hi;
+    if (lo_off) *reinterpret_cast<__nv_bfloat16*>(base + lo_off + o) = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
 // One CTA per record: header, zero-filled B body, then the values.
@@ -104,12 +123,13 @@ __global__ void k_tpack(const TRec* __restrict__ recs, const HBlock* __restrict_
         h[3] = (uint32_t)r.a_src;
         h[4] = (uint32_t)r.a_row0;
         h[5] = (uint32_t)r.flags;
-        h[6] = (uint32_t)r.offT;
-        h[7] = 0u;
+        h[6] = (uint32_t)r.ring;
+        h[7] = (uint32_t)r.dep;
     }
     unsigned char* B = dst + kTRHdr;
     const int lbo = (r.N16 / 8) * 128;
-    const int nwords = r.K16 * r.N16 / 2;
+    const int lo = r.S == 2 ? r.K16 * r.N16 * 2 : 0;
+    const int nwords = r.S * r.K16 * r.N16 / 2;
     for (int i = threadIdx.x; i < nwords; i += blockDim.x) reinterpret_cast<uint32_t*>(B)[i] = 0u;
     __syncthreads();
     if (r.kind == TREC_EMPTY) return;  // a tile with no blocks: a zero product
@@ -123,7 +143,7 @@ __global__ void k_tpack(const TRec* __restrict__ recs, const HBlock* __restrict_
         for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
             const int j = e / nr, i = e - j * nr;
             const int row = r.rs + i, col = c_lo + j;
-            st_bf16(B, col - r.k0, row - r.row_base, lbo, slab[(int64_t)(col - b.c0) * nr + i]);
+            st_bf16(B, col - r.k0, row - r.row_base, lbo, slab[(int64_t)(col - b.c0) * nr + i], lo);
         }
     } else if (r.kind == TREC_CSR) {
         const int32_t* rp = aux + b.off_aux;
@@ -133,7 +153,7 @@ __global__ void k_tpack(const TRec* __restrict__ recs, const HBlock* __restrict_
             for (int z = rp[lr] + (threadIdx.x & 31); z < rp[lr + 1]; z += 32) {
                 const int col = ci[z];
                 if (col >= r.k0 && col < r.k0 + r.K16)
-                    st_bf16(B, col - r.k0, row - r.row_base, lbo, val[b.off_val + z]);
+                    st_bf16(B, col - r.k0, row - r.row_base, lbo, val[b.off_val + z], lo);
             }
         }
     } else if (r.kind == TREC_SVDU) {
@@ -143,7 +163,7 @@ __global__ void k_tpack(const TRec* __restrict__ recs, const HBlock* __restrict_
             const int u = e / b.q, k = e - u * b.q;
             const int row = rows[u];
             if (row >= r.rs && row < r.re && k >= r.k0 && k < r.k0 + r.K16)
-                st_bf16(B, k - r.k0, row - r.row_base, lbo, val[b.off_val + (int64_t)u * b.q + k]);
+                st_bf16(B, k - r.k0, row - r.row_base, lbo, val[b.off_val + (int64_t)u * b.q + k], lo);
         }
     } else {
         // V' rows (compacted columns) inside [k0, k0 + K16); N = the rank
@@ -152,7 +172,7 @@ __global__ void k_tpack(const TRec* __restrict__ recs, const HBlock* __restrict_
         for (int e = threadIdx.x; e < b.n1 * b.q; e += blockDim.x) {
             const int j = e / b.q, k = e - j * b.q;
             const int col = cols[j];
-            if (col >= r.k0 && col < r.k0 + r.K16) st_bf16(B, col - r.k0, k, lbo, Vp[(int64_t)j * b.q + k]);
+            if (col >= r.k0 && col < r.k0 + r.K16) st_bf16(B, col - r.k0, k, lbo, Vp[(int64_t)j * b.q + k], lo);
         }
     }
 }
@@ -198,11 +218,45 @@ static vf_status pack_pages(vf_hmat* H, std::vector<TRec>& recs, const std::vect
     std::vector<TRec> ordered;
     for (int32_t c = 0; c < ncta; ++c) {
         cp[c] = (int32_t)used.size();
+        // The A-operand ring, planned here so the device only follows it: each
+        // record takes S x K x 256 contiguous bytes (wrapping to the start when
+        // the end is short) and may start its copy once `dep` (and so every
+        // earlier record: MMAs complete in order) has finished; dep is never
+        // more than kTickets records back, so each record's barrier ticket is free.
+        int32_t issued = 0, freed = 0;
+        uint32_t head = 0, tail = 0;
+        std::vector<uint32_t> start;
         for (int32_t gi : cta_groups[c]) {
             bool fresh = true;
             for (int64_t ri = group_recs[gi].first; ri < group_recs[gi].second; ++ri) {
                 TRec r = recs[ri];
-                const uint32_t sz = (uint32_t)(kTRHdr + r.K16 * r.N16 * 2);
+                const uint32_t bytes = (uint32_t)(r.S * r.K16 * kPanel * 2);
+                uint32_t at = 0;
+                for (;;) {
+                    if (issued == freed) {
+                        head = tail = 0;
+                        at = 0;
+                        break;
+                    }
+                    if (issued - freed < kTickets) {
+                        if (head >= tail) {
+                            if (head + bytes <= (uint32_t)kARing) { at = head; break; }
+                            if (bytes < tail) { at = 0; break; }
+                        } else if (head + bytes < tail) {
+                            at = head;
+                            break;
+                        }
+                    }
+                    ++freed;  // wait for the oldest record in flight
+                    tail = issued > freed ? start[freed] : head;
+                }
+                start.push_back(at);
+                head = at + bytes;
+                r.ring = (int32_t)at;
+                r.dep = std::max(freed - 1, issued - kTickets);
+                if (r.dep < 0) r.dep = -1;
+                ++issued;
+                const uint32_t sz = (uint32_t)(kTRHdr + r.S * r.K16 * r.N16 * 2);
                 if (fresh || used.back() + sz > (uint32_t)kTP) {
                     used.push_back(kTPHdr);
                     nrec.push_back(0);
@@ -244,7 +298,7 @@ static vf_status check_records(const std::vector<TRec>& recs, int max_col, int64
                         r.N16 % 16 == 0 && r.coloff >= 0 && r.coloff % 16 == 0 && r.coloff + r.N16 <= max_col &&
                         r.a_row0 >= 0 && r.a_row0 % 8 == 0 &&
                         (int64_t)r.a_row0 + r.K16 <= (r.a_src ? rows_t : rows_x) &&
-                        kTPHdr + kTRHdr + r.K16 * r.N16 * 2 <= kTP;
+                        (r.S == 1 || r.S == 2) && kTPHdr + kTRHdr + r.S * r.K16 * r.N16 * 2 <= kTP;
         VF_CHECK(ok, VF_E_INVAL,
                  "tensor plan: bad record (kind %d, K %d, N %d, col %d, src %d, row %d)", r.kind, r.K16, r.N16,
                  r.coloff, r.a_src, r.a_row0);
@@ -252,26 +306,33 @@ static vf_status check_records(const std::vector<TRec>& recs, int max_col, int64
     return VF_OK;
 }
 
-// Build the tensor pages of a matrix (once, on first use).
-vf_status tensor_plan_build(vf_hmat* H) {
-    if (H->tplan) return VF_OK;
+// Build one set of tensor pages of a matrix (once, on first use).
+vf_status tensor_plan_build(vf_hmat* H, int S) {
     device_guard g(H->device);
-    auto P = std::make_unique<vf_tensor_plan>();
+    if (!H->tplan) {
+        auto P0 = std::make_unique<vf_tensor_plan>();
+        P0->n_rows_x = r16(H->nf) + 32;
+        // T rows: q16 per SVD block
+        P0->h_offT16.assign(H->h_blocks.size(), -1);
+        int64_t nt = 0;
+        for (size_t i = 0; i < H->h_blocks.size(); ++i)
+            if (H->h_blocks[i].kind == VF_BLK_SVD) {
+                P0->h_offT16[i] = (int32_t)nt;
+                nt += r16(H->h_blocks[i].q);
+            }
+        P0->n_rows_t = nt + 16;
+        H->tplan = P0.release();
+    }
+    vf_tensor_plan* P = H->tplan;
+    vf_tensor_set* T = &P->set[S - 1];
+    if (T->built) return VF_OK;
     const std::vector<HBlock>& B = H->h_blocks;
     std::vector<int32_t> haux;
     if (H->n_aux > 0) VF_TRY(H->aux.download(haux));
     const int64_t n = H->nf;
     const int64_t ntiles = (int64_t)H->h_tile_first.size();
-    P->n_rows_x = r16(n) + 32;
-    // T rows: q16 per SVD block
-    P->h_offT16.assign(B.size(), -1);
-    int64_t nt = 0;
-    for (size_t i = 0; i < B.size(); ++i)
-        if (B[i].kind == VF_BLK_SVD) {
-            P->h_offT16[i] = (int32_t)nt;
-            nt += r16(B[i].q);
-        }
-    P->n_rows_t = nt + 16;
+    // largest K of a phase-2 record (N <= 64) so that it fits a page
+    const int32_t kk2 = std::min<int32_t>(kKMax, ((kTP - kTPHdr - kTRHdr) / (64 * 2 * S)) / 16 * 16);
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, H->device) != cudaSuccess || nsm <= 0) nsm = 148;
     const int64_t rec_cost = 2048;  // fixed work of one record, in byte equivalents
@@ -307,10 +368,10 @@ vf_status tensor_plan_build(vf_hmat* H) {
                 // K = the rank, in chunks of <= kKMax (one A slot each)
                 t.kind = TREC_SVDU;
                 t.a_src = 1;
-                for (int32_t kc = 0; kc < r16(b.q); kc += kKMax) {
+                for (int32_t kc = 0; kc < r16(b.q); kc += kk2) {
                     TRec u = t;
                     u.k0 = kc;
-                    u.K16 = std::min(kKMax, r16(b.q) - kc);
+                    u.K16 = std::min(kk2, r16(b.q) - kc);
                     u.a_row0 = P->h_offT16[bi] + kc;
                     per[k].push_back(u);
                 }
@@ -319,10 +380,10 @@ vf_status tensor_plan_build(vf_hmat* H) {
                 t.a_src = 0;
                 const int32_t c8 = (b.c0 / 8) * 8;
                 const int32_t ktot = r16(b.c0 + b.n - c8);
-                for (int32_t kc = 0; kc < ktot; kc += kKMax) {
+                for (int32_t kc = 0; kc < ktot; kc += kk2) {
                     TRec u = t;
                     u.k0 = c8 + kc;
-                    u.K16 = std::min(kKMax, ktot - kc);
+                    u.K16 = std::min(kk2, ktot - kc);
                     u.a_row0 = u.k0;
                     per[k].push_back(u);
                 }
@@ -337,8 +398,9 @@ vf_status tensor_plan_build(vf_hmat* H) {
         for (size_t i = 0; i < per[k].size(); ++i) {
             TRec t = per[k][i];
             t.flags = (i == 0 ? TR_FIRST : 0) | (i + 1 == per[k].size() ? TR_LAST : 0);
+            t.S = S;
             recs2.push_back(t);
-            tile_cost[k] += (int64_t)t.K16 * t.N16 * 2 + (int64_t)t.K16 * kPanel * 2 + rec_cost;
+            tile_cost[k] += S * ((int64_t)t.K16 * t.N16 * 2 + (int64_t)t.K16 * kPanel * 2) + rec_cost;
         }
         tile_recs[k].second = (int64_t)recs2.size();
     }
@@ -356,24 +418,25 @@ vf_status tensor_plan_build(vf_hmat* H) {
             t.a_src = 0;
             t.a_row0 = 0;
             t.flags = TR_FIRST | TR_LAST;
+            t.S = S;
             tile_recs[k].first = (int64_t)recs2.size();
             recs2.push_back(t);
             tile_recs[k].second = (int64_t)recs2.size();
         }
     VF_TRY(check_records(recs2, 64, P->n_rows_x, P->n_rows_t));
-    P->ncta2 = (int32_t)std::min<int64_t>((int64_t)nsm * 2, ntiles);
-    auto lists2 = lpt(tile_cost, P->ncta2);
+    T->ncta2 = (int32_t)std::min<int64_t>((int64_t)nsm * 2, ntiles);
+    auto lists2 = lpt(tile_cost, T->ncta2);
     {
-        std::vector<int32_t> tiles, ptr(P->ncta2 + 1, 0);
-        for (int32_t c = 0; c < P->ncta2; ++c) {
+        std::vector<int32_t> tiles, ptr(T->ncta2 + 1, 0);
+        for (int32_t c = 0; c < T->ncta2; ++c) {
             ptr[c] = (int32_t)tiles.size();
             tiles.insert(tiles.end(), lists2[c].begin(), lists2[c].end());
         }
-        ptr[P->ncta2] = (int32_t)tiles.size();
-        VF_TRY(P->cta_tiles.upload(tiles));
-        VF_TRY(P->cta_tile_ptr.upload(ptr));
+        ptr[T->ncta2] = (int32_t)tiles.size();
+        VF_TRY(T->cta_tiles.upload(tiles));
+        VF_TRY(T->cta_tile_ptr.upload(ptr));
     }
-    VF_TRY(pack_pages(H, recs2, lists2, tile_recs, P->pages2, P->used2, P->cta_pages2, &P->bytes2));
+    VF_TRY(pack_pages(H, recs2, lists2, tile_recs, T->pages2, T->used2, T->cta_pages2, &T->bytes2));
 
     // ---- phase 1: per SVD block (one unit), K-chunks over its column range
     std::vector<TRec> recs1;
@@ -384,7 +447,7 @@ vf_status tensor_plan_build(vf_hmat* H) {
         const HBlock& b = B[bi];
         if (b.kind != VF_BLK_SVD) continue;
         const int32_t q16 = r16(b.q);
-        const int32_t kmax = std::min<int32_t>(kKMax, ((kTP - kTPHdr - kTRHdr) / (q16 * 2)) / 16 * 16);
+        const int32_t kmax = std::min<int32_t>(kKMax, ((kTP - kTPHdr - kTRHdr) / (q16 * 2 * S)) / 16 * 16);
         const int32_t c8 = (b.c0 / 8) * 8;
         const int32_t ktot = r16(b.c0 + b.n - c8);
         const int64_t first = (int64_t)recs1.size();
@@ -399,8 +462,9 @@ vf_status tensor_plan_build(vf_hmat* H) {
             t.a_src = 0;
             t.a_row0 = t.k0;
             t.offT = P->h_offT16[bi];
+            t.S = S;
             recs1.push_back(t);
-            cost += (int64_t)t.K16 * t.N16 * 2 + (int64_t)t.K16 * kPanel * 2 + rec_cost;
+            cost += S * ((int64_t)t.K16 * t.N16 * 2 + (int64_t)t.K16 * kPanel * 2) + rec_cost;
         }
         recs1[first].flags |= TR_FIRST;
         recs1.back().flags |= TR_LAST;
@@ -409,23 +473,51 @@ vf_status tensor_plan_build(vf_hmat* H) {
         unit_blk.push_back((int32_t)bi);
     }
     VF_TRY(check_records(recs1, kRegionCols, P->n_rows_x, P->n_rows_t));
-    P->ncta1 = (int32_t)std::min<int64_t>((int64_t)nsm * 2, (int64_t)unit_cost.size());
-    if (P->ncta1 > 0) {
-        auto lists1 = lpt(unit_cost, P->ncta1);
-        std::vector<int32_t> units, ptr(P->ncta1 + 1, 0);
-        for (int32_t c = 0; c < P->ncta1; ++c) {
-            ptr[c] = (int32_t)(units.size() / 2);
+    T->ncta1 = (int32_t)std::min<int64_t>((int64_t)nsm * 2, (int64_t)unit_cost.size());
+    if (T->ncta1 > 0) {
+        auto lists1 = lpt(unit_cost, T->ncta1);
+        // consecutive units of a CTA share one accumulator region while their
+        // ranks fit its kRegionCols columns: one epilogue round per group.
+        // units[4 u ..] = T row, q16, region column, 1 if the unit ends its group
+        std::vector<int32_t> units, ptr(T->ncta1 + 1, 0);
+        for (int32_t c = 0; c < T->ncta1; ++c) {
+            ptr[c] = (int32_t)(units.size() / 4);
+            int32_t col = kRegionCols;  // forces a new group
+            int64_t prev_last = -1;     // last record of the previous unit
             for (int32_t u : lists1[c]) {
+                const int32_t q16 = r16(B[unit_blk[u]].q);
+                const bool fresh = col + q16 > kRegionCols;
+                if (fresh) {
+                    col = 0;
+                    if (prev_last >= 0) {
+                        recs1[prev_last].flags |= TR_LAST;
+                        units[units.size() - 1] = 1;  // the previous unit closes its group
+                    }
+                }
+                for (int64_t ri = unit_recs[u].first; ri < unit_recs[u].second; ++ri) {
+                    recs1[ri].flags &= ~(TR_FIRST | TR_LAST);
+                    recs1[ri].coloff = col;
+                }
+                recs1[unit_recs[u].first].flags |= TR_USTART | (fresh ? TR_FIRST : 0);
+                prev_last = unit_recs[u].second - 1;
                 units.push_back(P->h_offT16[unit_blk[u]]);
-                units.push_back(r16(B[unit_blk[u]].q));
+                units.push_back(q16);
+                units.push_back(col);
+                units.push_back(0);
+                col += q16;
+            }
+            if (prev_last >= 0) {
+                recs1[prev_last].flags |= TR_LAST;
+                units[units.size() - 1] = 1;
             }
         }
-        ptr[P->ncta1] = (int32_t)(units.size() / 2);
-        VF_TRY(P->cta_units.upload(units));
-        VF_TRY(P->cta_unit_ptr.upload(ptr));
-        VF_TRY(pack_pages(H, recs1, lists1, unit_recs, P->pages1, P->used1, P->cta_pages1, &P->bytes1));
+        ptr[T->ncta1] = (int32_t)(units.size() / 4);
+        VF_TRY(check_records(recs1, kRegionCols, P->n_rows_x, P->n_rows_t));
+        VF_TRY(T->cta_units.upload(units));
+        VF_TRY(T->cta_unit_ptr.upload(ptr));
+        VF_TRY(pack_pages(H, recs1, lists1, unit_recs, T->pages1, T->used1, T->cta_pages1, &T->bytes1));
     }
-    H->tplan = P.release();
+    T->built = true;
     return VF_OK;
 }
 
@@ -493,51 +585,73 @@ __device__ __forceinline__ int64_t panel_off(int64_t row, int m) {
 }
 
 struct TSmem {
-    uint64_t page_full[2], page_empty[2], a_full[kASlots], a_empty[kASlots], d_full[2], d_empty[2], done;
+    uint64_t page_full[kPStages], page_empty[kPStages], a_full[kTickets], a_empty[kTickets], d_full[2], d_empty[2],
+        done;
     uint32_t tmem_base;
     int32_t abort;
 };
 
-constexpr size_t kTSmemBytes = 2 * kTP + kASlots * kAStage + 1024;
+constexpr size_t kTSmemBytes = kPStages * kTP + kARing + 1024;
+static_assert(sizeof(TSmem) <= 1024, "barrier block");
 
 // The producer (warp 0, lane 0): pages [pa, pb) into two stages, and each
 // record's A operand (a contiguous panel range) into the A ring.
+// The RHS panels a kernel reads: X (hi, lo) and T (hi, lo); lo only with S = 2.
+struct TPanels {
+    const unsigned char* X[2];
+    unsigned char* T[2];
+    int64_t rows_x, rows_t;
+};
+
+// The producer (warp 0, lane 0): keeps up to kPStages pages in flight, and
+// for each record, in order, waits for its planned dependency (a record
+// whose MMAs free the ring bytes and the barrier ticket it reuses), then
+// copies its A operand(s) to the planned ring offset.
+template <int NS>
 __device__ void t_producer(TSmem& S, unsigned char* stages, unsigned char* abuf, const unsigned char* pages,
-                           const uint32_t* used, int pa, int pb, const unsigned char* Xp, const unsigned char* Tp,
-                           int64_t rows_x, int64_t rows_t, int max_col, int* status) {
-    int nrec_issued = 0;
-    for (int p = pa, li = 0; p < pb; ++p, ++li) {
-        const int s = li & 1;
-        if (li >= 2 && !bwait(&S.page_empty[s], (uint32_t)(((li >> 1) - 1) & 1))) goto fail;
-        {
-            const uint32_t bytes = used[p];
+                           const uint32_t* used, int pa, int pb, const TPanels& pn, int max_col, int* status) {
+    const int npl = pb - pa;
+    int pissued = 0, r = 0;  // pages copied; CTA-local record index
+    for (int li = 0; li < npl; ++li) {
+        while (pissued < npl && pissued < li + kPStages) {
+            const int s2 = pissued % kPStages;
+            if (pissued >= kPStages &&
+                !bwait(&S.page_empty[s2], (uint32_t)(((pissued / kPStages) - 1) & 1)))
+                goto fail;
+            const uint32_t bytes = used[pa + pissued];
             if (bytes < kTPHdr || bytes > (uint32_t)kTP || (bytes & 15u)) goto oob;
-            mbar_arrive_expect_tx(&S.page_full[s], bytes);
-            bulk_g2s(stages + s * kTP, pages + (int64_t)p * kTP, bytes, &S.page_full[s]);
+            mbar_arrive_expect_tx(&S.page_full[s2], bytes);
+            bulk_g2s(stages + s2 * kTP, pages + (int64_t)(pa + pissued) * kTP, bytes, &S.page_full[s2]);
+            ++pissued;
         }
-        if (!bwait(&S.page_full[s], (uint32_t)((li >> 1) & 1))) goto fail;
+        const int s = li % kPStages;
+        if (!bwait(&S.page_full[s], (uint32_t)((li / kPStages) & 1))) goto fail;
         {
             const unsigned char* pg = stages + s * kTP;
             const int nrec = (int)reinterpret_cast<const uint32_t*>(pg)[0];
             const uint32_t pused = reinterpret_cast<const uint32_t*>(pg)[1];
             uint32_t off = kTPHdr;
-            for (int r = 0; r < nrec; ++r) {
-                const uint32_t* h = reinterpret_cast<const uint32_t*>(pg + off);
-                const int K16 = (int)h[0], N16 = (int)h[1];
-                // self-check: shapes, the record inside the page, the A range inside its panel
+            for (int i = 0; i < nrec; ++i, ++r) {
+                const uint4 h0 = *reinterpret_cast<const uint4*>(pg + off);
+                const uint4 h1 = *reinterpret_cast<const uint4*>(pg + off + 16);
+                const int K16 = (int)h0.x, N16 = (int)h0.y;
+                const uint32_t abytes = (uint32_t)K16 * kPanel * 2, bytes = NS * abytes;
+                const int dep = (int)h1.w;
+                const uint32_t ring = h1.z;
+                // self-check: shapes, the record inside the page, the A range inside its panel, the plan
                 if (K16 < 16 || K16 > kKMax || (K16 & 15) || N16 < 16 || N16 > kRegionCols || (N16 & 15) ||
-                    (int)h[2] + N16 > max_col || off + kTRHdr + (uint32_t)(K16 * N16 * 2) > pused || (h[4] & 7u) ||
-                    (int64_t)h[4] + K16 > (h[3] ? rows_t : rows_x))
+                    (int)h0.z + N16 > max_col || off + kTRHdr + (uint32_t)(NS * K16 * N16 * 2) > pused ||
+                    (h1.x & 7u) || (int64_t)h1.x + K16 > (h0.w ? pn.rows_t : pn.rows_x) ||
+                    ring + bytes > (uint32_t)kARing || (ring & 15u) || dep >= r || dep < r - kTickets)
                     goto oob;
-                const int j = nrec_issued % kASlots;
-                if (nrec_issued >= kASlots && !bwait(&S.a_empty[j], (uint32_t)(((nrec_issued / kASlots) - 1) & 1)))
-                    goto fail;
-                const unsigned char* src = (h[3] ? Tp : Xp) + (int64_t)(h[4] >> 3) * 2048;
-                const uint32_t bytes = (uint32_t)K16 * kPanel * 2;
+                if (dep >= 0 && !bwait(&S.a_empty[dep % kTickets], (uint32_t)((dep / kTickets) & 1))) goto fail;
+                const int j = r % kTickets;
                 mbar_arrive_expect_tx(&S.a_full[j], bytes);
-                bulk_g2s(abuf + (size_t)j * kAStage, src, bytes, &S.a_full[j]);
-                ++nrec_issued;
-                off += kTRHdr + (uint32_t)(K16 * N16 * 2);
+                for (int t = 0; t < NS; ++t) {
+                    const unsigned char* src = (h0.w ? pn.T[t] : pn.X[t]) + (int64_t)(h1.x >> 3) * 2048;
+                    bulk_g2s(abuf + ring + t * abytes, src, abytes, &S.a_full[j]);
+                }
+                off += kTRHdr + (uint32_t)(NS * K16 * N16 * 2);
             }
         }
         if (S.abort) return;
@@ -552,12 +666,15 @@ oob:
     atomicExch(&S.abort, 1);
 }
 
-// The MMA issuer (warp 1, lane 0).
+// The MMA issuer (warp 1, lane 0).  With NS = 2 each K step is three MMAs,
+// A_hi B_hi + A_lo B_hi + A_hi B_lo (the lo x lo term, ~2^-16 of the
+// product, is dropped), all into the same FP32 accumulator.
+template <int NS>
 __device__ void t_issuer(TSmem& S, unsigned char* stages, unsigned char* abuf, int pa, int pb, int* status) {
     int nrec = 0, dcount[2] = {0, 0}, d = 0;
     for (int p = pa, li = 0; p < pb; ++p, ++li) {
-        const int s = li & 1;
-        if (!bwait(&S.page_full[s], (uint32_t)((li >> 1) & 1))) goto fail;
+        const int s = li % kPStages;
+        if (!bwait(&S.page_full[s], (uint32_t)((li / kPStages) & 1))) goto fail;
         {
             const unsigned char* pg = stages + s * kTP;
             const int nr = (int)reinterpret_cast<const uint32_t*>(pg)[0];
@@ -565,18 +682,26 @@ __device__ void t_issuer(TSmem& S, unsigned char* stages, unsigned char* abuf, i
             for (int r = 0; r < nr; ++r) {
                 const uint32_t* h = reinterpret_cast<const uint32_t*>(pg + off);
                 const int K16 = (int)h[0], N16 = (int)h[1], coloff = (int)h[2], flags = (int)h[5];
-                const int j = nrec % kASlots;
-                if (!bwait(&S.a_full[j], (uint32_t)((nrec / kASlots) & 1))) goto fail;
+                const int j = nrec % kTickets;
+                if (!bwait(&S.a_full[j], (uint32_t)((nrec / kTickets) & 1))) goto fail;
                 if (flags & TR_FIRST) {
                     if (!bwait(&S.d_empty[d], (uint32_t)(dcount[d] & 1))) goto fail;
                     tm_fence_after();
                 }
                 const uint32_t dt = S.tmem_base + (uint32_t)(d * kRegionCols + coloff);
-                const uint32_t bsa = smem_u32(pg + off + kTRHdr), asa = smem_u32(abuf + (size_t)j * kAStage);
+                const uint32_t bsa = smem_u32(pg + off + kTRHdr), asa = smem_u32(abuf + h[6]);
                 const uint32_t blbo = (uint32_t)(N16 / 8) * 128;
                 const uint32_t idesc = mma_idesc(N16);
-                for (int kk = 0; kk < K16 / 16; ++kk)
-                    mma_bf16(dt, mma_desc(asa + kk * 4096, 2048, 128), mma_desc(bsa + kk * 2 * blbo, blbo, 128), idesc, 1);
+                const uint32_t alo = (uint32_t)K16 * kPanel * 2, blo = (uint32_t)(K16 * N16 * 2);
+                for (int kk = 0; kk < K16 / 16; ++kk) {
+                    const uint64_t ah = mma_desc(asa + kk * 4096, 2048, 128);
+                    const uint64_t bh = mma_desc(bsa + kk * 2 * blbo, blbo, 128);
+                    mma_bf16(dt, ah, bh, idesc, (kk == 0 && (flags & TR_USTART)) ? 0 : 1);
+                    if (NS == 2) {
+                        mma_bf16(dt, mma_desc(asa + alo + kk * 4096, 2048, 128), bh, idesc, 1);
+                        mma_bf16(dt, ah, mma_desc(bsa + blo + kk * 2 * blbo, blbo, 128), idesc, 1);
+                    }
+                }
                 mma_commit(&S.a_empty[j]);
                 if (flags & TR_LAST) {
                     mma_commit(&S.d_full[d]);
@@ -584,7 +709,7 @@ __device__ void t_issuer(TSmem& S, unsigned char* stages, unsigned char* abuf, i
                     d ^= 1;
                 }
                 ++nrec;
-                off += kTRHdr + (uint32_t)(K16 * N16 * 2);
+                off += kTRHdr + (uint32_t)(NS * K16 * N16 * 2);
             }
         }
         mma_commit(&S.page_empty[s]);
@@ -602,13 +727,15 @@ fail:
 __device__ void t_prologue(TSmem& S, int ncols) {
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kPStages; ++i) {
             mbar_init(&S.page_full[i], 1);
             mbar_init(&S.page_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
             mbar_init(&S.d_full[i], 1);
             mbar_init(&S.d_empty[i], 4);
         }
-        for (int i = 0; i < kASlots; ++i) {
+        for (int i = 0; i < kTickets; ++i) {
             mbar_init(&S.a_full[i], 1);
             mbar_init(&S.a_empty[i], 1);
         }
@@ -653,12 +780,15 @@ __device__ void t_finish(TSmem& S, int ncols, int* status) {
     }
 }
 
-// Release a region after the epilogue read it: zero it, then arrive.
-__device__ __forceinline__ void t_release(TSmem& S, int d) {
+// Release a region after the epilogue read it (zeroing it first when the
+// next use accumulates into it), then arrive.
+__device__ __forceinline__ void t_release(TSmem& S, int d, bool zero) {
     const int warp = threadIdx.x >> 5;
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-    for (int c = 0; c < kRegionCols; c += 16) tm_zero16(S.tmem_base + lane_base + d * kRegionCols + c);
-    tm_wait_st();
+    if (zero) {
+        for (int c = 0; c < kRegionCols; c += 16) tm_zero16(S.tmem_base + lane_base + d * kRegionCols + c);
+        tm_wait_st();
+    }
     tm_fence_before();
     __syncwarp();
     if ((threadIdx.x & 31) == 0) mbar_arrive(&S.d_empty[d]);
@@ -666,87 +796,99 @@ __device__ __forceinline__ void t_release(TSmem& S, int d) {
 
 // Drain (producer): wait for every copy it may have left in flight.
 __device__ void t_drain(TSmem& S) {
-    for (int s = 0; s < 2; ++s) mbar_wait(&S.page_full[s], 0, 1024), mbar_wait(&S.page_full[s], 1, 1024);
-    for (int j = 0; j < kASlots; ++j) mbar_wait(&S.a_full[j], 0, 1024), mbar_wait(&S.a_full[j], 1, 1024);
+    for (int s = 0; s < kPStages; ++s) mbar_wait(&S.page_full[s], 0, 1024), mbar_wait(&S.page_full[s], 1, 1024);
+    for (int j = 0; j < kTickets; ++j) mbar_wait(&S.a_full[j], 0, 1024), mbar_wait(&S.a_full[j], 1, 1024);
 }
 
 // ------------------------------------------------------------ phase 1
 // T panel rows offT16 .. + N16 of each unit = (V'^T X) for this panel.
+template <int NS>
 __global__ void __launch_bounds__(192, 1) k_tphase1(const unsigned char* __restrict__ pages,
                                                     const uint32_t* __restrict__ used,
                                                     const int32_t* __restrict__ cta_pages,
                                                     const int32_t* __restrict__ cta_units,
-                                                    const int32_t* __restrict__ cta_unit_ptr,
-                                                    const unsigned char* __restrict__ Xp, unsigned char* __restrict__ Tp,
-                                                    int64_t rows_x, int64_t rows_t, int* __restrict__ status) {
+                                                    const int32_t* __restrict__ cta_unit_ptr, TPanels pn,
+                                                    int* __restrict__ status) {
     constexpr int MAXCOL = kRegionCols;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* stages = smem;
-    unsigned char* abuf = smem + 2 * kTP;
-    TSmem& S = *reinterpret_cast<TSmem*>(smem + 2 * kTP + kASlots * kAStage);
+    unsigned char* abuf = smem + kPStages * kTP;
+    TSmem& S = *reinterpret_cast<TSmem*>(smem + kPStages * kTP + kARing);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     t_prologue(S, 2 * kRegionCols);
     __syncthreads();
     const int pa = cta_pages[blockIdx.x], pb = cta_pages[blockIdx.x + 1];
     if (warp == 0) {
         if (lane == 0) {
-            t_producer(S, stages, abuf, pages, used, pa, pb, Xp, Tp, rows_x, rows_t, MAXCOL, status);
+            t_producer<NS>(S, stages, abuf, pages, used, pa, pb, pn, MAXCOL, status);
             if (S.abort) t_drain(S);
         }
     } else if (warp == 1) {
-        if (lane == 0) t_issuer(S, stages, abuf, pa, pb, status);
+        if (lane == 0) t_issuer<NS>(S, stages, abuf, pa, pb, status);
     } else {
         const int m = 32 * (warp & 3) + lane;
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         const int u0 = cta_unit_ptr[blockIdx.x], u1 = cta_unit_ptr[blockIdx.x + 1];
-        for (int u = u0, k = 0; u < u1; ++u, ++k) {
+        bool open = false;  // inside a group (its region filled)
+        for (int u = u0, k = 0; u < u1; ++u) {
             const int d = k & 1;
-            if (!__all_sync(0xffffffffu, bwait(&S.d_full[d], (uint32_t)((k >> 1) & 1)))) {
-                if (lane == 0) atomicExch(status, VF_E_TIMEOUT), atomicExch(&S.abort, 1);
-                break;
+            if (!open) {
+                if (!__all_sync(0xffffffffu, bwait(&S.d_full[d], (uint32_t)((k >> 1) & 1)))) {
+                    if (lane == 0) atomicExch(status, VF_E_TIMEOUT), atomicExch(&S.abort, 1);
+                    break;
+                }
+                tm_fence_after();
+                open = true;
             }
-            tm_fence_after();
-            const int offT = cta_units[2 * u], N16 = cta_units[2 * u + 1];
+            const int offT = cta_units[4 * u], N16 = cta_units[4 * u + 1], col = cta_units[4 * u + 2];
+            const bool gend = cta_units[4 * u + 3] != 0;
             for (int c0 = 0; c0 < N16; c0 += 16) {
                 float v[16];
-                tm_ld16(S.tmem_base + lane_base + d * kRegionCols + c0, v);
+                tm_ld16(S.tmem_base + lane_base + d * kRegionCols + col + c0, v);
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    *reinterpret_cast<__nv_bfloat16*>(Tp + panel_off(offT + c0 + j, m)) = __float2bfloat16_rn(v[j]);
+                for (int j = 0; j < 16; ++j) {
+                    const int64_t o = panel_off(offT + c0 + j, m);
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(v[j]);
+                    *reinterpret_cast<__nv_bfloat16*>(pn.T[0] + o) = hi;
+                    if (NS == 2) *reinterpret_cast<__nv_bfloat16*>(pn.T[1] + o) = __float2bfloat16_rn(v[j] - __bfloat162float(hi));
+                }
             }
-            t_release(S, d);
+            if (gend) {
+                t_release(S, d, false);  // each unit's first MMA overwrites its columns
+                open = false;
+                ++k;
+            }
         }
     }
     t_finish(S, 2 * kRegionCols, status);
 }
 
 // ------------------------------------------------------------ phase 2
+template <int NS>
 __global__ void __launch_bounds__(192, 1) k_tphase2(const unsigned char* __restrict__ pages,
                                                     const uint32_t* __restrict__ used,
                                                     const int32_t* __restrict__ cta_pages,
                                                     const int32_t* __restrict__ cta_tiles,
                                                     const int32_t* __restrict__ cta_tile_ptr,
                                                     const int32_t* __restrict__ tile_first,
-                                                    const int32_t* __restrict__ tile_count,
-                                                    const unsigned char* __restrict__ Xp,
-                                                    const unsigned char* __restrict__ Tp, TEpi ep, int64_t rows_x,
-                                                    int64_t rows_t, int* __restrict__ status) {
+                                                    const int32_t* __restrict__ tile_count, TPanels pn, TEpi ep,
+                                                    int* __restrict__ status) {
     constexpr int MAXCOL = 64;  // phase 2: a tile's rows
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* stages = smem;
-    unsigned char* abuf = smem + 2 * kTP;
-    TSmem& S = *reinterpret_cast<TSmem*>(smem + 2 * kTP + kASlots * kAStage);
+    unsigned char* abuf = smem + kPStages * kTP;
+    TSmem& S = *reinterpret_cast<TSmem*>(smem + kPStages * kTP + kARing);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     t_prologue(S, 2 * kRegionCols);
     __syncthreads();
     const int pa = cta_pages[blockIdx.x], pb = cta_pages[blockIdx.x + 1];
     if (warp == 0) {
         if (lane == 0) {
-            t_producer(S, stages, abuf, pages, used, pa, pb, Xp, Tp, rows_x, rows_t, MAXCOL, status);
+            t_producer<NS>(S, stages, abuf, pages, used, pa, pb, pn, MAXCOL, status);
             if (S.abort) t_drain(S);
         }
     } else if (warp == 1) {
-        if (lane == 0) t_issuer(S, stages, abuf, pa, pb, status);
+        if (lane == 0) t_issuer<NS>(S, stages, abuf, pa, pb, status);
     } else {
         const int m = 32 * (warp & 3) + lane;
         const int col = ep.p0 + m;  // RHS column
@@ -774,6 +916,11 @@ __global__ void __launch_bounds__(192, 1) k_tphase2(const unsigned char* __restr
                     const int64_t o = (int64_t)col * ep.n + p;
                     if (ep.mode == 0) {
                         ep.Y[o] = v[j];
+                    } else if (ep.mode == 2) {
+                        // residual r = E - B + rho .* y in FP64
+                        const double r = (double)ep.E[o] - (double)ep.Bold[o] + (double)ep.rho[p] * (double)v[j];
+                        ss += r * r;
+                        ep.Y[o] = (float)r;
                     } else {
                         const float bn = ep.E[o] + ep.rho[p] * v[j];
                         const float dd = bn - ep.Bold[o];
@@ -783,76 +930,96 @@ __global__ void __launch_bounds__(192, 1) k_tphase2(const unsigned char* __restr
                     }
                 }
             }
-            if (ep.mode == 1 && live) ep.colpart[(int64_t)col * ep.ntiles + tile] = ss;
-            t_release(S, d);
+            if (ep.mode != 0 && live) ep.colpart[(int64_t)col * ep.ntiles + tile] = ss;
+            t_release(S, d, true);
         }
     }
     t_finish(S, 2 * kRegionCols, status);
 }
 
-// FP32 column-major (tree order, or face order through perm) -> BF16 panel.
+// FP32 column-major (tree order, or face order through perm) -> BF16 panel
+// (or, with lo != NULL, the hi and lo panels of the two-term split).
 __global__ void k_to_panel(const float* __restrict__ src, int64_t ld, const int32_t* __restrict__ perm, int64_t n,
-                           int R, int p0, int64_t rows, unsigned char* __restrict__ dst) {
+                           int R, int p0, int64_t rows, unsigned char* __restrict__ hi, unsigned char* __restrict__ lo) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // (row, 8-column chunk)
     if (e >= rows * 16) return;
     const int64_t row = e >> 4;
     const int m0 = (int)(e & 15) * 8;
-    __align__(16) __nv_bfloat16 v[8];
+    __align__(16) __nv_bfloat16 vh[8], vl[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int c = p0 + m0 + i;
         float x = 0.f;
         if (row < n && c < R) x = src[(int64_t)c * ld + (perm ? perm[row] : row)];
-        v[i] = __float2bfloat16_rn(x);
+        vh[i] = __float2bfloat16_rn(x);
+        vl[i] = __float2bfloat16_rn(x - __bfloat162float(vh[i]));
     }
-    *reinterpret_cast<uint4*>(dst + (row >> 3) * 2048 + (m0 >> 3) * 128 + (row & 7) * 16) =
-        *reinterpret_cast<const uint4*>(v);
+    const int64_t o = (row >> 3) * 2048 + (m0 >> 3) * 128 + (row & 7) * 16;
+    *reinterpret_cast<uint4*>(hi + o) = *reinterpret_cast<const uint4*>(vh);
+    if (lo) *reinterpret_cast<uint4*>(lo + o) = *reinterpret_cast<const uint4*>(vl);
 }
 
 // ------------------------------------------------------------ host entry
 static vf_status tensor_attrs() {
     static bool done = false;
     if (done) return VF_OK;
-    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmemBytes));
-    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmemBytes));
+    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase1<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmemBytes));
+    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase2<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmemBytes));
+    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase1<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmemBytes));
+    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase2<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmemBytes));
     done = true;
     return VF_OK;
 }
 
-vf_status tensor_prepare(vf_hmat* H) {
-    VF_TRY(tensor_plan_build(H));
+vf_status tensor_prepare(vf_hmat* H, int S) {
+    VF_TRY(tensor_plan_build(H, S));
     VF_TRY(tensor_attrs());
     return VF_OK;
 }
 
 int64_t tensor_panel_bytes_x(const vf_hmat* H) { return H->tplan->n_rows_x * kPanel * 2; }
 int64_t tensor_panel_bytes_t(const vf_hmat* H) { return H->tplan->n_rows_t * kPanel * 2; }
-int64_t tensor_page_bytes(const vf_hmat* H) { return H->tplan->bytes1 + H->tplan->bytes2; }
+int64_t tensor_page_bytes(const vf_hmat* H, int S) { return H->tplan->set[S - 1].bytes1 + H->tplan->set[S - 1].bytes2; }
 
-// X (FP32, column-major, ld) -> panel; perm maps tree row -> source row (or NULL)
 vf_status tensor_to_panel(const vf_hmat* H, const float* X, int64_t ld, const int32_t* perm, int R, int p0,
-                          unsigned char* panel, cudaStream_t st) {
+                          unsigned char* hi, unsigned char* lo, cudaStream_t st) {
     const int64_t rows = H->tplan->n_rows_x;
-    k_to_panel<<<(unsigned)ceil_div(rows * 16, 256), 256, 0, st>>>(X, ld, perm, H->nf, R, p0, rows, panel);
+    k_to_panel<<<(unsigned)ceil_div(rows * 16, 256), 256, 0, st>>>(X, ld, perm, H->nf, R, p0, rows, hi, lo);
     VF_TRY_CUDA(cudaGetLastError());
     return VF_OK;
 }
 
-// One multiply of one panel: phase 1 (T panel), then phase 2 with the epilogue.
-vf_status tensor_multiply(const vf_hmat* H, const unsigned char* Xpanel, unsigned char* Tpanel, const TEpi& ep,
-                          int* status, cudaStream_t st) {
+// One multiply of one panel: phase 1 (T panels), then phase 2 with the epilogue.
+vf_status tensor_multiply(const vf_hmat* H, int S, const unsigned char* Xhi, const unsigned char* Xlo,
+                          unsigned char* Thi, unsigned char* Tlo, const TEpi& ep, int* status, cudaStream_t st) {
     const vf_tensor_plan* P = H->tplan;
-    if (P->ncta1 > 0)
-        k_tphase1<<<(unsigned)P->ncta1, 192, kTSmemBytes, st>>>(P->pages1.p, P->used1.p, P->cta_pages1.p,
-                                                                P->cta_units.p, P->cta_unit_ptr.p, Xpanel, Tpanel,
-                                                                P->n_rows_x, P->n_rows_t, status);
-    k_tphase2<<<(unsigned)P->ncta2, 192, kTSmemBytes, st>>>(P->pages2.p, P->used2.p, P->cta_pages2.p, P->cta_tiles.p,
-                                                            P->cta_tile_ptr.p, H->tile_first.p, H->tile_count.p,
-                                                            Xpanel, Tpanel, ep, P->n_rows_x, P->n_rows_t, status);
+    const vf_tensor_set& T = P->set[S - 1];
+    TPanels pn{};
+    pn.X[0] = Xhi;
+    pn.X[1] = Xlo;
+    pn.T[0] = Thi;
+    pn.T[1] = Tlo;
+    pn.rows_x = P->n_rows_x;
+    pn.rows_t = P->n_rows_t;
+    if (S == 1) {
+        if (T.ncta1 > 0)
+            k_tphase1<1><<<(unsigned)T.ncta1, 192, kTSmemBytes, st>>>(T.pages1.p, T.used1.p, T.cta_pages1.p,
+                                                                      T.cta_units.p, T.cta_unit_ptr.p, pn, status);
+        k_tphase2<1><<<(unsigned)T.ncta2, 192, kTSmemBytes, st>>>(T.pages2.p, T.used2.p, T.cta_pages2.p,
+                                                                  T.cta_tiles.p, T.cta_tile_ptr.p, H->tile_first.p,
+                                                                  H->tile_count.p, pn, ep, status);
+    } else {
+        if (T.ncta1 > 0)
+            k_tphase1<2><<<(unsigned)T.ncta1, 192, kTSmemBytes, st>>>(T.pages1.p, T.used1.p, T.cta_pages1.p,
+                                                                      T.cta_units.p, T.cta_unit_ptr.p, pn, status);
+        k_tphase2<2><<<(unsigned)T.ncta2, 192, kTSmemBytes, st>>>(T.pages2.p, T.used2.p, T.cta_pages2.p,
+                                                                  T.cta_tiles.p, T.cta_tile_ptr.p, H->tile_first.p,
+                                                                  H->tile_count.p, pn, ep, status);
+    }
     VF_TRY_CUDA(cudaGetLastError());
     return VF_OK;
 }
 
-int tensor_kernels(const vf_hmat* H) { return (H->tplan->ncta1 > 0 ? 1 : 0) + 1; }
+int tensor_kernels(const vf_hmat* H, int S) { return (H->tplan->set[S - 1].ncta1 > 0 ? 1 : 0) + 1; }
 
 }  // namespace vf

@@ -10,28 +10,34 @@ constexpr int kTensorMinR = 16;    // BF16 multiplies with at least this many co
 
 // What phase 2's epilogue does with the finished rows of a tile.
 struct TEpi {
-    int mode;              // 0: Y = F X;  1: Jacobi B' = E + rho .* (F X)
+    int mode;              // 0: Y = F X;  1: Jacobi B' = E + rho .* (F X);
+                           // 2: residual r = E - B + rho .* (F B) in FP64 (Y = r, colpart = r^2)
     int64_t n;             // facets (column stride of the FP32 arrays)
     int R, p0;             // total RHS, first RHS of this panel
     float* Y;              // FP32, column-major tree order (mode 0: F X; mode 1: B')
     const float* E;        // mode 1
     const float* rho;      // mode 1
-    const float* Bold;     // mode 1: the previous iterate
+    const float* Bold;     // mode 1: the previous iterate; mode 2: B
     unsigned char* Xnext;  // mode 1: the next BF16 panel (or NULL)
-    double* colpart;       // mode 1: per (RHS, tile) sum of squared updates
+    double* colpart;       // modes 1, 2: per (RHS, tile) sums of squares
     int64_t ntiles;
 };
 
-// Build the tensor pages once and set the kernels' attributes.
-vf_status tensor_prepare(vf_hmat* H);
+// Build one page set of the matrix once (S = 1: BF16 factors; S = 2: each
+// FP32 factor as two BF16 terms hi + lo) and set the kernels' attributes.
+vf_status tensor_prepare(vf_hmat* H, int S);
 int64_t tensor_panel_bytes_x(const vf_hmat* H);
 int64_t tensor_panel_bytes_t(const vf_hmat* H);
-int64_t tensor_page_bytes(const vf_hmat* H);
-// FP32 column-major X (ld; row k of the panel = X row perm[k], or k) -> BF16 panel of columns [p0, p0 + 128)
+int64_t tensor_page_bytes(const vf_hmat* H, int S);
+// FP32 column-major X (ld; panel row k = X row perm[k], or k) -> the BF16
+// panel of columns [p0, p0 + 128), and with lo != NULL also the lo panel of
+// the two-term split (x = hi + lo + O(2^-16 x))
 vf_status tensor_to_panel(const vf_hmat* H, const float* X, int64_t ld, const int32_t* perm, int R, int p0,
-                          unsigned char* panel, cudaStream_t st);
-vf_status tensor_multiply(const vf_hmat* H, const unsigned char* Xpanel, unsigned char* Tpanel, const TEpi& ep,
-                          int* status, cudaStream_t st);
-int tensor_kernels(const vf_hmat* H);
+                          unsigned char* hi, unsigned char* lo, cudaStream_t st);
+// One multiply of one panel.  S = 1: BF16 products; S = 2: the split
+// products A_hi B_hi + A_lo B_hi + A_hi B_lo (FP32-factor accuracy to ~2^-16).
+vf_status tensor_multiply(const vf_hmat* H, int S, const unsigned char* Xhi, const unsigned char* Xlo,
+                          unsigned char* Thi, unsigned char* Tlo, const TEpi& ep, int* status, cudaStream_t st);
+int tensor_kernels(const vf_hmat* H, int S);
 
 }  // namespace vf
