@@ -50,7 +50,14 @@ def parse():
     p.add_argument("--no-dense", action="store_true", help="skip the dense-F comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--cpu-rows", type=int, default=128, help="rows of F in the CPU oracle sample")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched (tensor-core) section")
+    p.add_argument("--batch-rhs", type=int, default=128, help="RHS of the batched section")
     return p.parse_args()
+
+
+def synth_dirs(R: int):
+    import synth
+    return synth.sun_directions(R, 10.0)
 
 
 def workload_inputs(R: int, side: int = 200):
@@ -293,6 +300,59 @@ def main():
     e2e = {"value": world * R / e2e_s, "unit": "RHS/s", "h2d_bytes_per_step": n * R * 4,
            "d2h_bytes_per_step": n * R * 4}
 
+    # ---- batched: many sun positions at once, BF16 sweeps on the tensor cores
+    # (tcgen05, FP32 accumulation) with split-BF16 residual refinement
+    batched = None
+    if not a.no_batched and rank == 0:
+        Rb = a.batch_rhs
+        Eb = torch.empty((Rb, n), device="cuda", dtype=torch.float32)
+        vf.vf_mesh_insolation(prob.mesh, synth_dirs(Rb), 1365.0, Eb)
+        Bb = torch.empty_like(Eb)
+        Bref = torch.empty_like(Eb)
+        vf.vf_solve(prob.hmat, Eb, Bref, rho=rho, rtol=rtol)  # FP32 CUDA-core solve: the accuracy reference
+        bkw = dict(rho=rho, rtol=1e-4, precision="bf16", refine=True)
+        for _ in range(3):
+            sb = vf.vf_solve(prob.hmat, Eb, Bb, **bkw)
+        torch.cuda.synchronize()
+        bsteps = max(5, min(a.steps, 50))
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(st)
+        for _ in range(bsteps):
+            sb = vf.vf_solve(prob.hmat, Eb, Bb, **bkw)
+        b1.record(st)
+        torch.cuda.synchronize()
+        bms = b0.elapsed_time(b1) / bsteps
+        live = Bref.norm(dim=1) > 0
+        brel = float(((Bb - Bref).norm(dim=1)[live] / Bref.norm(dim=1)[live]).max().item())
+        # the tensor-core multiply alone (one panel of 128, BF16), tree order
+        Xb = Eb.clone()
+        Yb = torch.empty_like(Xb)
+        for _ in range(3):
+            vf.vf_apply_tree(prob.hmat, Xb, Yb, precision="bf16")
+        torch.cuda.synchronize()
+        m0 = torch.cuda.Event(enable_timing=True)
+        m1 = torch.cuda.Event(enable_timing=True)
+        m0.record(st)
+        for _ in range(20):
+            vf.vf_apply_tree(prob.hmat, Xb, Yb, precision="bf16")
+        m1.record(st)
+        torch.cuda.synchronize()
+        tms = m0.elapsed_time(m1) / 20
+        bf16_bytes = vf.vf_hmat_bytes(prob.hmat, "bf16") + n * Rb * (2 + 4)
+        single_apply = 1.0 / (mult_ms / 1000.0)  # FP32 single-RHS multiply, RHS/s
+        batched = {"value": round(Rb / (bms / 1000.0), 1), "unit": "RHS/s", "rhs": Rb, "ms_per_solve": round(bms, 3),
+                   "precision": "bf16 factors and RHS on tcgen05 tensor cores, FP32 accumulation; "
+                                "split-BF16 residual refinement with FP64 update",
+                   "rtol": 1e-4, "sweeps": sb["sweeps"], "refinements": sb["refinements"],
+                   "max_rel_diff_vs_fp32_solve": brel,
+                   "x_fp32_single_rhs_apply": round(Rb / (bms / 1000.0) / single_apply, 2),
+                   "x_fp32_single_rhs_solve": round(Rb / (bms / 1000.0) / (value / world), 2),
+                   "tensor_multiply": {"ms": round(tms, 4), "rhs": Rb,
+                                       "alg_bytes": bf16_bytes,
+                                       "hbm_frac": round(bf16_bytes / (tms / 1000.0) / 1e9 / peak, 4)}}
+        del Eb, Bb, Bref, Xb, Yb
+
     # ---- the uncompressed dense FP32 F on the same GPU
     dense = None
     if not a.no_dense and rank == 0:
@@ -330,7 +390,7 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "setup_s": round(t_setup, 2)},
             "roofline": roofline, "e2e": e2e, "gpu_launches": kernels, "clocks": clk,
-            "dense_fp32": dense, "cpu_baseline": cpu,
+            "batched": batched, "dense_fp32": dense, "cpu_baseline": cpu,
             "assembly": {k: prob.stats[k] for k in ("nblocks", "bytes", "probes", "max_rank", "t_visibility",
                                                     "t_probe", "t_total")}}
     if rank == 0:
