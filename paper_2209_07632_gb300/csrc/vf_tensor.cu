@@ -48,9 +48,25 @@ constexpr int kTRHdr = 32;           // record header (8 x u32)
 constexpr int kPanel = 128;          // right-hand sides per panel (MMA M)
 constexpr int kKMax = 64;            // largest K of one record (A operand <= 64 x 256 B)
 constexpr int kTickets = 16;         // records in flight (A operands in the ring)
-constexpr int kARing = 57344;        // A-operand ring bytes
-constexpr int kPStages = 3;          // page stages (the producer runs up to two pages ahead)
-constexpr int kRegionCols = 128;     // TMEM columns per accumulator region
+// Per page set: S = 1 (BF16) runs four CTAs per SM (each: two page stages,
+// a 20 KB A ring, two 64-column accumulator regions), since the multiply is
+// bound by independent pipelines per SM; S = 2 (split residual, twice the
+// A bytes) runs two (three page stages, a 56 KB ring, 128-column regions).
+template <int NS> struct TCfg;
+template <> struct TCfg<1> {
+    static constexpr int PSTAGES = 2, RING = 20480, CTAS = 4, REGION = 64;
+};
+template <> struct TCfg<2> {
+    static constexpr int PSTAGES = 3, RING = 57344, CTAS = 2, REGION = 128;
+};
+constexpr int kMaxPStages = 3;
+static int cfg_ring(int S) { return S == 1 ? TCfg<1>::RING : TCfg<2>::RING; }
+static int cfg_ctas(int S) { return S == 1 ? TCfg<1>::CTAS : TCfg<2>::CTAS; }
+static int cfg_region(int S) { return S == 1 ? TCfg<1>::REGION : TCfg<2>::REGION; }
+template <int NS>
+constexpr size_t tsmem_bytes() {
+    return (size_t)TCfg<NS>::PSTAGES * 16384 + TCfg<NS>::RING + 1024;
+}
 constexpr uint32_t kTWait = 1u << 22;
 // record flags: FIRST / LAST record of its accumulator region's use (a
 // phase-2 tile, a phase-1 group of units); USTART: first record of a unit
@@ -71,7 +87,7 @@ struct TRec {        // where one tensor record's B operand comes from (build ti
     int32_t S;         // 1: BF16 body; 2: hi and lo bodies
     int32_t ring;      // byte offset of its A operand(s) in the CTA's ring
     int32_t dep;       // the record (CTA-local index) whose MMAs must finish before its copy, or -1
-    int32_t pad;
+    int32_t n0;        // V' records: first rank index of the B columns
     int64_t dst;
 };
 
@@ -172,7 +188,8 @@ __global__ void k_tpack(const TRec* __restrict__ recs, const HBlock* __restrict_
         for (int e = threadIdx.x; e < b.n1 * b.q; e += blockDim.x) {
             const int j = e / b.q, k = e - j * b.q;
             const int col = cols[j];
-            if (col >= r.k0 && col < r.k0 + r.K16) st_bf16(B, col - r.k0, k, lbo, Vp[(int64_t)j * b.q + k], lo);
+            if (col >= r.k0 && col < r.k0 + r.K16 && k >= r.n0 && k < r.n0 + r.N16)
+                st_bf16(B, col - r.k0, k - r.n0, lbo, Vp[(int64_t)j * b.q + k], lo);
         }
     }
 }
@@ -240,7 +257,7 @@ static vf_status pack_pages(vf_hmat* H, std::vector<TRec>& recs, const std::vect
                     }
                     if (issued - freed < kTickets) {
                         if (head >= tail) {
-                            if (head + bytes <= (uint32_t)kARing) { at = head; break; }
+                            if (head + bytes <= (uint32_t)cfg_ring(r.S)) { at = head; break; }
                             if (bytes < tail) { at = 0; break; }
                         } else if (head + bytes < tail) {
                             at = head;
@@ -294,7 +311,7 @@ static inline int32_t r16(int64_t x) { return (int32_t)((x + 15) / 16 * 16); }
 // The invariants every record must meet (checked on the host before upload).
 static vf_status check_records(const std::vector<TRec>& recs, int max_col, int64_t rows_x, int64_t rows_t) {
     for (const TRec& r : recs) {
-        const bool ok = r.K16 >= 16 && r.K16 <= kKMax && r.K16 % 16 == 0 && r.N16 >= 16 && r.N16 <= kRegionCols &&
+        const bool ok = r.K16 >= 16 && r.K16 <= kKMax && r.K16 % 16 == 0 && r.N16 >= 16 && r.N16 <= cfg_region(r.S) &&
                         r.N16 % 16 == 0 && r.coloff >= 0 && r.coloff % 16 == 0 && r.coloff + r.N16 <= max_col &&
                         r.a_row0 >= 0 && r.a_row0 % 8 == 0 &&
                         (int64_t)r.a_row0 + r.K16 <= (r.a_src ? rows_t : rows_x) &&
@@ -424,7 +441,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
             tile_recs[k].second = (int64_t)recs2.size();
         }
     VF_TRY(check_records(recs2, 64, P->n_rows_x, P->n_rows_t));
-    T->ncta2 = (int32_t)std::min<int64_t>((int64_t)nsm * 2, ntiles);
+    T->ncta2 = (int32_t)std::min<int64_t>((int64_t)nsm * cfg_ctas(S), ntiles);
     auto lists2 = lpt(tile_cost, T->ncta2);
     {
         std::vector<int32_t> tiles, ptr(T->ncta2 + 1, 0);
@@ -438,55 +455,64 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
     }
     VF_TRY(pack_pages(H, recs2, lists2, tile_recs, T->pages2, T->used2, T->cta_pages2, &T->bytes2));
 
-    // ---- phase 1: per SVD block (one unit), K-chunks over its column range
+    // ---- phase 1: per SVD block, K-chunks over its column range; a unit is
+    // a block's T columns [n0, n0 + N) with N <= the region width (blocks
+    // of larger rank become several units reading the same X rows)
     std::vector<TRec> recs1;
     std::vector<std::pair<int64_t, int64_t>> unit_recs;
     std::vector<int64_t> unit_cost;
-    std::vector<int32_t> unit_blk;
+    std::vector<int32_t> unit_blk, unit_n0, unit_n16;
     for (size_t bi = 0; bi < B.size(); ++bi) {
         const HBlock& b = B[bi];
         if (b.kind != VF_BLK_SVD) continue;
         const int32_t q16 = r16(b.q);
-        const int32_t kmax = std::min<int32_t>(kKMax, ((kTP - kTPHdr - kTRHdr) / (q16 * 2 * S)) / 16 * 16);
         const int32_t c8 = (b.c0 / 8) * 8;
         const int32_t ktot = r16(b.c0 + b.n - c8);
-        const int64_t first = (int64_t)recs1.size();
-        int64_t cost = 0;
-        for (int32_t kc = 0; kc < ktot; kc += kmax) {
-            TRec t{};
-            t.kind = TREC_VT;
-            t.blk = (int32_t)bi;
-            t.k0 = c8 + kc;
-            t.K16 = std::min(kmax, ktot - kc);
-            t.N16 = q16;
-            t.a_src = 0;
-            t.a_row0 = t.k0;
-            t.offT = P->h_offT16[bi];
-            t.S = S;
-            recs1.push_back(t);
-            cost += S * ((int64_t)t.K16 * t.N16 * 2 + (int64_t)t.K16 * kPanel * 2) + rec_cost;
+        for (int32_t n0 = 0; n0 < q16; n0 += cfg_region(S)) {
+            const int32_t n16 = std::min(cfg_region(S), q16 - n0);
+            const int32_t kmax = std::min<int32_t>(kKMax, ((kTP - kTPHdr - kTRHdr) / (n16 * 2 * S)) / 16 * 16);
+            const int64_t first = (int64_t)recs1.size();
+            int64_t cost = 0;
+            for (int32_t kc = 0; kc < ktot; kc += kmax) {
+                TRec t{};
+                t.kind = TREC_VT;
+                t.blk = (int32_t)bi;
+                t.k0 = c8 + kc;
+                t.K16 = std::min(kmax, ktot - kc);
+                t.N16 = n16;
+                t.n0 = n0;
+                t.a_src = 0;
+                t.a_row0 = t.k0;
+                t.offT = P->h_offT16[bi] + n0;
+                t.S = S;
+                recs1.push_back(t);
+                cost += S * ((int64_t)t.K16 * t.N16 * 2 + (int64_t)t.K16 * kPanel * 2) + rec_cost;
+            }
+            recs1[first].flags |= TR_FIRST;
+            recs1.back().flags |= TR_LAST;
+            unit_recs.push_back({first, (int64_t)recs1.size()});
+            unit_cost.push_back(cost);
+            unit_blk.push_back((int32_t)bi);
+            unit_n0.push_back(n0);
+            unit_n16.push_back(n16);
         }
-        recs1[first].flags |= TR_FIRST;
-        recs1.back().flags |= TR_LAST;
-        unit_recs.push_back({first, (int64_t)recs1.size()});
-        unit_cost.push_back(cost);
-        unit_blk.push_back((int32_t)bi);
     }
-    VF_TRY(check_records(recs1, kRegionCols, P->n_rows_x, P->n_rows_t));
-    T->ncta1 = (int32_t)std::min<int64_t>((int64_t)nsm * 2, (int64_t)unit_cost.size());
+    VF_TRY(check_records(recs1, cfg_region(S), P->n_rows_x, P->n_rows_t));
+    T->ncta1 = (int32_t)std::min<int64_t>((int64_t)nsm * cfg_ctas(S), (int64_t)unit_cost.size());
     if (T->ncta1 > 0) {
         auto lists1 = lpt(unit_cost, T->ncta1);
         // consecutive units of a CTA share one accumulator region while their
-        // ranks fit its kRegionCols columns: one epilogue round per group.
+        // ranks fit a region's columns: one epilogue round per group.
         // units[4 u ..] = T row, q16, region column, 1 if the unit ends its group
         std::vector<int32_t> units, ptr(T->ncta1 + 1, 0);
         for (int32_t c = 0; c < T->ncta1; ++c) {
             ptr[c] = (int32_t)(units.size() / 4);
-            int32_t col = kRegionCols;  // forces a new group
+            const int32_t region = cfg_region(S);
+            int32_t col = region;       // forces a new group
             int64_t prev_last = -1;     // last record of the previous unit
             for (int32_t u : lists1[c]) {
-                const int32_t q16 = r16(B[unit_blk[u]].q);
-                const bool fresh = col + q16 > kRegionCols;
+                const int32_t q16 = unit_n16[u];
+                const bool fresh = col + q16 > region;
                 if (fresh) {
                     col = 0;
                     if (prev_last >= 0) {
@@ -500,7 +526,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
                 }
                 recs1[unit_recs[u].first].flags |= TR_USTART | (fresh ? TR_FIRST : 0);
                 prev_last = unit_recs[u].second - 1;
-                units.push_back(P->h_offT16[unit_blk[u]]);
+                units.push_back(P->h_offT16[unit_blk[u]] + unit_n0[u]);
                 units.push_back(q16);
                 units.push_back(col);
                 units.push_back(0);
@@ -512,7 +538,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
             }
         }
         ptr[T->ncta1] = (int32_t)(units.size() / 4);
-        VF_TRY(check_records(recs1, kRegionCols, P->n_rows_x, P->n_rows_t));
+        VF_TRY(check_records(recs1, cfg_region(S), P->n_rows_x, P->n_rows_t));
         VF_TRY(T->cta_units.upload(units));
         VF_TRY(T->cta_unit_ptr.upload(ptr));
         VF_TRY(pack_pages(H, recs1, lists1, unit_recs, T->pages1, T->used1, T->cta_pages1, &T->bytes1));
@@ -585,13 +611,13 @@ __device__ __forceinline__ int64_t panel_off(int64_t row, int m) {
 }
 
 struct TSmem {
-    uint64_t page_full[kPStages], page_empty[kPStages], a_full[kTickets], a_empty[kTickets], d_full[2], d_empty[2],
-        done;
+    uint64_t page_full[kMaxPStages], page_empty[kMaxPStages], a_full[kTickets], a_empty[kTickets], d_full[2],
+        d_empty[2], done;
     uint32_t tmem_base;
     int32_t abort;
 };
 
-constexpr size_t kTSmemBytes = kPStages * kTP + kARing + 1024;
+
 static_assert(sizeof(TSmem) <= 1024, "barrier block");
 
 // The producer (warp 0, lane 0): pages [pa, pb) into two stages, and each
@@ -613,10 +639,10 @@ __device__ void t_producer(TSmem& S, unsigned char* stages, unsigned char* abuf,
     const int npl = pb - pa;
     int pissued = 0, r = 0;  // pages copied; CTA-local record index
     for (int li = 0; li < npl; ++li) {
-        while (pissued < npl && pissued < li + kPStages) {
-            const int s2 = pissued % kPStages;
-            if (pissued >= kPStages &&
-                !bwait(&S.page_empty[s2], (uint32_t)(((pissued / kPStages) - 1) & 1)))
+        constexpr int PS = TCfg<NS>::PSTAGES;
+        while (pissued < npl && pissued < li + PS) {
+            const int s2 = pissued % PS;
+            if (pissued >= PS && !bwait(&S.page_empty[s2], (uint32_t)(((pissued / PS) - 1) & 1)))
                 goto fail;
             const uint32_t bytes = used[pa + pissued];
             if (bytes < kTPHdr || bytes > (uint32_t)kTP || (bytes & 15u)) goto oob;
@@ -624,8 +650,8 @@ __device__ void t_producer(TSmem& S, unsigned char* stages, unsigned char* abuf,
             bulk_g2s(stages + s2 * kTP, pages + (int64_t)(pa + pissued) * kTP, bytes, &S.page_full[s2]);
             ++pissued;
         }
-        const int s = li % kPStages;
-        if (!bwait(&S.page_full[s], (uint32_t)((li / kPStages) & 1))) goto fail;
+        const int s = li % PS;
+        if (!bwait(&S.page_full[s], (uint32_t)((li / PS) & 1))) goto fail;
         {
             const unsigned char* pg = stages + s * kTP;
             const int nrec = (int)reinterpret_cast<const uint32_t*>(pg)[0];
@@ -639,10 +665,10 @@ __device__ void t_producer(TSmem& S, unsigned char* stages, unsigned char* abuf,
                 const int dep = (int)h1.w;
                 const uint32_t ring = h1.z;
                 // self-check: shapes, the record inside the page, the A range inside its panel, the plan
-                if (K16 < 16 || K16 > kKMax || (K16 & 15) || N16 < 16 || N16 > kRegionCols || (N16 & 15) ||
+                if (K16 < 16 || K16 > kKMax || (K16 & 15) || N16 < 16 || N16 > TCfg<NS>::REGION || (N16 & 15) ||
                     (int)h0.z + N16 > max_col || off + kTRHdr + (uint32_t)(NS * K16 * N16 * 2) > pused ||
                     (h1.x & 7u) || (int64_t)h1.x + K16 > (h0.w ? pn.rows_t : pn.rows_x) ||
-                    ring + bytes > (uint32_t)kARing || (ring & 15u) || dep >= r || dep < r - kTickets)
+                    ring + bytes > (uint32_t)TCfg<NS>::RING || (ring & 15u) || dep >= r || dep < r - kTickets)
                     goto oob;
                 if (dep >= 0 && !bwait(&S.a_empty[dep % kTickets], (uint32_t)((dep / kTickets) & 1))) goto fail;
                 const int j = r % kTickets;
@@ -673,8 +699,8 @@ template <int NS>
 __device__ void t_issuer(TSmem& S, unsigned char* stages, unsigned char* abuf, int pa, int pb, int* status) {
     int nrec = 0, dcount[2] = {0, 0}, d = 0;
     for (int p = pa, li = 0; p < pb; ++p, ++li) {
-        const int s = li % kPStages;
-        if (!bwait(&S.page_full[s], (uint32_t)((li / kPStages) & 1))) goto fail;
+        const int s = li % TCfg<NS>::PSTAGES;
+        if (!bwait(&S.page_full[s], (uint32_t)((li / TCfg<NS>::PSTAGES) & 1))) goto fail;
         {
             const unsigned char* pg = stages + s * kTP;
             const int nr = (int)reinterpret_cast<const uint32_t*>(pg)[0];
@@ -688,7 +714,7 @@ __device__ void t_issuer(TSmem& S, unsigned char* stages, unsigned char* abuf, i
                     if (!bwait(&S.d_empty[d], (uint32_t)(dcount[d] & 1))) goto fail;
                     tm_fence_after();
                 }
-                const uint32_t dt = S.tmem_base + (uint32_t)(d * kRegionCols + coloff);
+                const uint32_t dt = S.tmem_base + (uint32_t)(d * TCfg<NS>::REGION + coloff);
                 const uint32_t bsa = smem_u32(pg + off + kTRHdr), asa = smem_u32(abuf + h[6]);
                 const uint32_t blbo = (uint32_t)(N16 / 8) * 128;
                 const uint32_t idesc = mma_idesc(N16);
@@ -724,10 +750,12 @@ fail:
 }
 
 // Common prologue: barriers, TMEM allocation, both regions zeroed.
-__device__ void t_prologue(TSmem& S, int ncols) {
+template <int NS>
+__device__ void t_prologue(TSmem& S) {
+    constexpr int ncols = 2 * TCfg<NS>::REGION;
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kPStages; ++i) {
+        for (int i = 0; i < TCfg<NS>::PSTAGES; ++i) {
             mbar_init(&S.page_full[i], 1);
             mbar_init(&S.page_empty[i], 1);
         }
@@ -754,7 +782,7 @@ __device__ void t_prologue(TSmem& S, int ncols) {
     if (warp >= 2) {
         // zero both accumulator regions (this warp's 32 lanes), then release them
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-        for (int c = 0; c < 2 * kRegionCols; c += 16) tm_zero16(S.tmem_base + lane_base + c);
+        for (int c = 0; c < ncols; c += 16) tm_zero16(S.tmem_base + lane_base + c);
         tm_wait_st();
         tm_fence_before();
         __syncwarp();
@@ -766,7 +794,9 @@ __device__ void t_prologue(TSmem& S, int ncols) {
 }
 
 // Common epilogue of a CTA: wait for the MMAs, free TMEM.
-__device__ void t_finish(TSmem& S, int ncols, int* status) {
+template <int NS>
+__device__ void t_finish(TSmem& S, int* status) {
+    constexpr int ncols = 2 * TCfg<NS>::REGION;
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 32) {
         if (!bwait(&S.done, 0)) atomicExch(status, VF_E_TIMEOUT);
@@ -782,11 +812,13 @@ __device__ void t_finish(TSmem& S, int ncols, int* status) {
 
 // Release a region after the epilogue read it (zeroing it first when the
 // next use accumulates into it), then arrive.
+template <int NS>
 __device__ __forceinline__ void t_release(TSmem& S, int d, bool zero) {
     const int warp = threadIdx.x >> 5;
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     if (zero) {
-        for (int c = 0; c < kRegionCols; c += 16) tm_zero16(S.tmem_base + lane_base + d * kRegionCols + c);
+        for (int c = 0; c < TCfg<NS>::REGION; c += 16)
+            tm_zero16(S.tmem_base + lane_base + d * TCfg<NS>::REGION + c);
         tm_wait_st();
     }
     tm_fence_before();
@@ -795,33 +827,35 @@ __device__ __forceinline__ void t_release(TSmem& S, int d, bool zero) {
 }
 
 // Drain (producer): wait for every copy it may have left in flight.
+template <int NS>
 __device__ void t_drain(TSmem& S) {
-    for (int s = 0; s < kPStages; ++s) mbar_wait(&S.page_full[s], 0, 1024), mbar_wait(&S.page_full[s], 1, 1024);
+    for (int s = 0; s < TCfg<NS>::PSTAGES; ++s)
+        mbar_wait(&S.page_full[s], 0, 1024), mbar_wait(&S.page_full[s], 1, 1024);
     for (int j = 0; j < kTickets; ++j) mbar_wait(&S.a_full[j], 0, 1024), mbar_wait(&S.a_full[j], 1, 1024);
 }
 
 // ------------------------------------------------------------ phase 1
 // T panel rows offT16 .. + N16 of each unit = (V'^T X) for this panel.
 template <int NS>
-__global__ void __launch_bounds__(192, 1) k_tphase1(const unsigned char* __restrict__ pages,
+__global__ void __launch_bounds__(192, TCfg<NS>::CTAS) k_tphase1(const unsigned char* __restrict__ pages,
                                                     const uint32_t* __restrict__ used,
                                                     const int32_t* __restrict__ cta_pages,
                                                     const int32_t* __restrict__ cta_units,
                                                     const int32_t* __restrict__ cta_unit_ptr, TPanels pn,
                                                     int* __restrict__ status) {
-    constexpr int MAXCOL = kRegionCols;
+    constexpr int MAXCOL = TCfg<NS>::REGION;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* stages = smem;
-    unsigned char* abuf = smem + kPStages * kTP;
-    TSmem& S = *reinterpret_cast<TSmem*>(smem + kPStages * kTP + kARing);
+    unsigned char* abuf = smem + TCfg<NS>::PSTAGES * kTP;
+    TSmem& S = *reinterpret_cast<TSmem*>(smem + TCfg<NS>::PSTAGES * kTP + TCfg<NS>::RING);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    t_prologue(S, 2 * kRegionCols);
+    t_prologue<NS>(S);
     __syncthreads();
     const int pa = cta_pages[blockIdx.x], pb = cta_pages[blockIdx.x + 1];
     if (warp == 0) {
         if (lane == 0) {
             t_producer<NS>(S, stages, abuf, pages, used, pa, pb, pn, MAXCOL, status);
-            if (S.abort) t_drain(S);
+            if (S.abort) t_drain<NS>(S);
         }
     } else if (warp == 1) {
         if (lane == 0) t_issuer<NS>(S, stages, abuf, pa, pb, status);
@@ -844,7 +878,7 @@ __global__ void __launch_bounds__(192, 1) k_tphase1(const unsigned char* __restr
             const bool gend = cta_units[4 * u + 3] != 0;
             for (int c0 = 0; c0 < N16; c0 += 16) {
                 float v[16];
-                tm_ld16(S.tmem_base + lane_base + d * kRegionCols + col + c0, v);
+                tm_ld16(S.tmem_base + lane_base + d * TCfg<NS>::REGION + col + c0, v);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int64_t o = panel_off(offT + c0 + j, m);
@@ -854,18 +888,18 @@ __global__ void __launch_bounds__(192, 1) k_tphase1(const unsigned char* __restr
                 }
             }
             if (gend) {
-                t_release(S, d, false);  // each unit's first MMA overwrites its columns
+                t_release<NS>(S, d, false);  // each unit's first MMA overwrites its columns
                 open = false;
                 ++k;
             }
         }
     }
-    t_finish(S, 2 * kRegionCols, status);
+    t_finish<NS>(S, status);
 }
 
 // ------------------------------------------------------------ phase 2
 template <int NS>
-__global__ void __launch_bounds__(192, 1) k_tphase2(const unsigned char* __restrict__ pages,
+__global__ void __launch_bounds__(192, TCfg<NS>::CTAS) k_tphase2(const unsigned char* __restrict__ pages,
                                                     const uint32_t* __restrict__ used,
                                                     const int32_t* __restrict__ cta_pages,
                                                     const int32_t* __restrict__ cta_tiles,
@@ -876,16 +910,16 @@ __global__ void __launch_bounds__(192, 1) k_tphase2(const unsigned char* __restr
     constexpr int MAXCOL = 64;  // phase 2: a tile's rows
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* stages = smem;
-    unsigned char* abuf = smem + kPStages * kTP;
-    TSmem& S = *reinterpret_cast<TSmem*>(smem + kPStages * kTP + kARing);
+    unsigned char* abuf = smem + TCfg<NS>::PSTAGES * kTP;
+    TSmem& S = *reinterpret_cast<TSmem*>(smem + TCfg<NS>::PSTAGES * kTP + TCfg<NS>::RING);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    t_prologue(S, 2 * kRegionCols);
+    t_prologue<NS>(S);
     __syncthreads();
     const int pa = cta_pages[blockIdx.x], pb = cta_pages[blockIdx.x + 1];
     if (warp == 0) {
         if (lane == 0) {
             t_producer<NS>(S, stages, abuf, pages, used, pa, pb, pn, MAXCOL, status);
-            if (S.abort) t_drain(S);
+            if (S.abort) t_drain<NS>(S);
         }
     } else if (warp == 1) {
         if (lane == 0) t_issuer<NS>(S, stages, abuf, pa, pb, status);
@@ -907,7 +941,7 @@ __global__ void __launch_bounds__(192, 1) k_tphase2(const unsigned char* __restr
             double ss = 0.0;
             for (int c0 = 0; c0 < tc; c0 += 16) {
                 float v[16];
-                tm_ld16(S.tmem_base + lane_base + d * kRegionCols + c0, v);
+                tm_ld16(S.tmem_base + lane_base + d * TCfg<NS>::REGION + c0, v);
                 if (!live) continue;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -931,10 +965,10 @@ __global__ void __launch_bounds__(192, 1) k_tphase2(const unsigned char* __restr
                 }
             }
             if (ep.mode != 0 && live) ep.colpart[(int64_t)col * ep.ntiles + tile] = ss;
-            t_release(S, d, true);
+            t_release<NS>(S, d, true);
         }
     }
-    t_finish(S, 2 * kRegionCols, status);
+    t_finish<NS>(S, status);
 }
 
 // FP32 column-major (tree order, or face order through perm) -> BF16 panel
@@ -963,10 +997,10 @@ __global__ void k_to_panel(const float* __restrict__ src, int64_t ld, const int3
 static vf_status tensor_attrs() {
     static bool done = false;
     if (done) return VF_OK;
-    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase1<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmemBytes));
-    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase2<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmemBytes));
-    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase1<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmemBytes));
-    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase2<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTSmemBytes));
+    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase1<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem_bytes<1>()));
+    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase2<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem_bytes<1>()));
+    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase1<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem_bytes<2>()));
+    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase2<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem_bytes<2>()));
     done = true;
     return VF_OK;
 }
@@ -1003,16 +1037,16 @@ vf_status tensor_multiply(const vf_hmat* H, int S, const unsigned char* Xhi, con
     pn.rows_t = P->n_rows_t;
     if (S == 1) {
         if (T.ncta1 > 0)
-            k_tphase1<1><<<(unsigned)T.ncta1, 192, kTSmemBytes, st>>>(T.pages1.p, T.used1.p, T.cta_pages1.p,
+            k_tphase1<1><<<(unsigned)T.ncta1, 192, tsmem_bytes<1>(), st>>>(T.pages1.p, T.used1.p, T.cta_pages1.p,
                                                                       T.cta_units.p, T.cta_unit_ptr.p, pn, status);
-        k_tphase2<1><<<(unsigned)T.ncta2, 192, kTSmemBytes, st>>>(T.pages2.p, T.used2.p, T.cta_pages2.p,
+        k_tphase2<1><<<(unsigned)T.ncta2, 192, tsmem_bytes<1>(), st>>>(T.pages2.p, T.used2.p, T.cta_pages2.p,
                                                                   T.cta_tiles.p, T.cta_tile_ptr.p, H->tile_first.p,
                                                                   H->tile_count.p, pn, ep, status);
     } else {
         if (T.ncta1 > 0)
-            k_tphase1<2><<<(unsigned)T.ncta1, 192, kTSmemBytes, st>>>(T.pages1.p, T.used1.p, T.cta_pages1.p,
+            k_tphase1<2><<<(unsigned)T.ncta1, 192, tsmem_bytes<2>(), st>>>(T.pages1.p, T.used1.p, T.cta_pages1.p,
                                                                       T.cta_units.p, T.cta_unit_ptr.p, pn, status);
-        k_tphase2<2><<<(unsigned)T.ncta2, 192, kTSmemBytes, st>>>(T.pages2.p, T.used2.p, T.cta_pages2.p,
+        k_tphase2<2><<<(unsigned)T.ncta2, 192, tsmem_bytes<2>(), st>>>(T.pages2.p, T.used2.p, T.cta_pages2.p,
                                                                   T.cta_tiles.p, T.cta_tile_ptr.p, H->tile_first.p,
                                                                   H->tile_count.p, pn, ep, status);
     }
