@@ -48,21 +48,22 @@ constexpr int kTRHdr = 32;           // record header (8 x u32)
 constexpr int kPanel = 128;          // right-hand sides per panel (MMA M)
 constexpr int kKMax = 64;            // largest K of one record (A operand <= 64 x 256 B)
 constexpr int kTickets = 16;         // records in flight (A operands in the ring)
-// Per page set: S = 1 (BF16) runs four CTAs per SM (each: two page stages,
-// a 20 KB A ring, two 64-column accumulator regions), since the multiply is
-// bound by independent pipelines per SM; S = 2 (split residual, twice the
-// A bytes) runs two (three page stages, a 56 KB ring, 128-column regions).
+// Both page sets run four CTAs per SM (each: two page stages, a 20 KB A
+// ring, two 64-column accumulator regions), since the multiply is bound by
+// independent pipelines per SM; the split set (S = 2, hi and lo A operands)
+// caps a record's K at 32 so its A operands still fit the ring.
 template <int NS> struct TCfg;
 template <> struct TCfg<1> {
-    static constexpr int PSTAGES = 2, RING = 20480, CTAS = 4, REGION = 64;
+    static constexpr int PSTAGES = 2, RING = 20480, CTAS = 4, REGION = 64, KMAX = 64;
 };
 template <> struct TCfg<2> {
-    static constexpr int PSTAGES = 3, RING = 57344, CTAS = 2, REGION = 128;
+    static constexpr int PSTAGES = 2, RING = 20480, CTAS = 4, REGION = 64, KMAX = 32;
 };
 constexpr int kMaxPStages = 3;
 static int cfg_ring(int S) { return S == 1 ? TCfg<1>::RING : TCfg<2>::RING; }
 static int cfg_ctas(int S) { return S == 1 ? TCfg<1>::CTAS : TCfg<2>::CTAS; }
 static int cfg_region(int S) { return S == 1 ? TCfg<1>::REGION : TCfg<2>::REGION; }
+static int cfg_kmax(int S) { return S == 1 ? TCfg<1>::KMAX : TCfg<2>::KMAX; }
 template <int NS>
 constexpr size_t tsmem_bytes() {
     return (size_t)TCfg<NS>::PSTAGES * 16384 + TCfg<NS>::RING + 1024;
@@ -311,7 +312,7 @@ static inline int32_t r16(int64_t x) { return (int32_t)((x + 15) / 16 * 16); }
 // The invariants every record must meet (checked on the host before upload).
 static vf_status check_records(const std::vector<TRec>& recs, int max_col, int64_t rows_x, int64_t rows_t) {
     for (const TRec& r : recs) {
-        const bool ok = r.K16 >= 16 && r.K16 <= kKMax && r.K16 % 16 == 0 && r.N16 >= 16 && r.N16 <= cfg_region(r.S) &&
+        const bool ok = r.K16 >= 16 && r.K16 <= cfg_kmax(r.S) && r.K16 % 16 == 0 && r.N16 >= 16 && r.N16 <= cfg_region(r.S) &&
                         r.N16 % 16 == 0 && r.coloff >= 0 && r.coloff % 16 == 0 && r.coloff + r.N16 <= max_col &&
                         r.a_row0 >= 0 && r.a_row0 % 8 == 0 &&
                         (int64_t)r.a_row0 + r.K16 <= (r.a_src ? rows_t : rows_x) &&
@@ -349,7 +350,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
     const int64_t n = H->nf;
     const int64_t ntiles = (int64_t)H->h_tile_first.size();
     // largest K of a phase-2 record (N <= 64) so that it fits a page
-    const int32_t kk2 = std::min<int32_t>(kKMax, ((kTP - kTPHdr - kTRHdr) / (64 * 2 * S)) / 16 * 16);
+    const int32_t kk2 = std::min<int32_t>(cfg_kmax(S), ((kTP - kTPHdr - kTRHdr) / (64 * 2 * S)) / 16 * 16);
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, H->device) != cudaSuccess || nsm <= 0) nsm = 148;
     const int64_t rec_cost = 2048;  // fixed work of one record, in byte equivalents
@@ -470,7 +471,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
         const int32_t ktot = r16(b.c0 + b.n - c8);
         for (int32_t n0 = 0; n0 < q16; n0 += cfg_region(S)) {
             const int32_t n16 = std::min(cfg_region(S), q16 - n0);
-            const int32_t kmax = std::min<int32_t>(kKMax, ((kTP - kTPHdr - kTRHdr) / (n16 * 2 * S)) / 16 * 16);
+            const int32_t kmax = std::min<int32_t>(cfg_kmax(S), ((kTP - kTPHdr - kTRHdr) / (n16 * 2 * S)) / 16 * 16);
             const int64_t first = (int64_t)recs1.size();
             int64_t cost = 0;
             for (int32_t kc = 0; kc < ktot; kc += kmax) {
@@ -665,7 +666,7 @@ __device__ void t_producer(TSmem& S, unsigned char* stages, unsigned char* abuf,
                 const int dep = (int)h1.w;
                 const uint32_t ring = h1.z;
                 // self-check: shapes, the record inside the page, the A range inside its panel, the plan
-                if (K16 < 16 || K16 > kKMax || (K16 & 15) || N16 < 16 || N16 > TCfg<NS>::REGION || (N16 & 15) ||
+                if (K16 < 16 || K16 > TCfg<NS>::KMAX || (K16 & 15) || N16 < 16 || N16 > TCfg<NS>::REGION || (N16 & 15) ||
                     (int)h0.z + N16 > max_col || off + kTRHdr + (uint32_t)(NS * K16 * N16 * 2) > pused ||
                     (h1.x & 7u) || (int64_t)h1.x + K16 > (h0.w ? pn.rows_t : pn.rows_x) ||
                     ring + bytes > (uint32_t)TCfg<NS>::RING || (ring & 15u) || dep >= r || dep < r - kTickets)
