@@ -46,7 +46,6 @@ constexpr int kTP = 16384;           // tensor page bytes
 constexpr int kTPHdr = 16;           // page header: nrec, used, 0, 0
 constexpr int kTRHdr = 32;           // record header (8 x u32)
 constexpr int kPanel = 128;          // right-hand sides per panel (MMA M)
-constexpr int kKMax = 64;            // largest K of one record (A operand <= 64 x 256 B)
 constexpr int kTickets = 16;         // records in flight (A operands in the ring)
 // Both page sets run four CTAs per SM (each: two page stages, a 20 KB A
 // ring, two 64-column accumulator regions), since the multiply is bound by
@@ -88,7 +87,11 @@ struct TRec {        // where one tensor record's B operand comes from (build ti
     int32_t S;         // 1: BF16 body; 2: hi and lo bodies
     int32_t ring;      // byte offset of its A operand(s) in the CTA's ring
     int32_t dep;       // the record (CTA-local index) whose MMAs must finish before its copy, or -1
-    int32_t n0;        // V' records: first rank index of the B columns
+    int32_t n0;        // V' fills: first rank index of this block's columns
+    int32_t nsub;      // V' fills: how many of the block's rank columns
+    int32_t bcol;      // V' fills: their first column in the record's B
+    int32_t hdr;       // 1: this entry starts a page record (writes its header); 0: another fill of it
+    int32_t pad2;
     int64_t dst;
 };
 
@@ -133,7 +136,7 @@ __global__ void k_tpack(const TRec* __restrict__ recs, const HBlock* __restrict_
     const TRec r = recs[blockIdx.x];
     unsigned char* dst = pool + r.dst;
     uint32_t* h = reinterpret_cast<uint32_t*>(dst);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && r.hdr) {
         h[0] = (uint32_t)r.K16;
         h[1] = (uint32_t)r.N16;
         h[2] = (uint32_t)r.coloff;
@@ -146,9 +149,7 @@ __global__ void k_tpack(const TRec* __restrict__ recs, const HBlock* __restrict_
     unsigned char* B = dst + kTRHdr;
     const int lbo = (r.N16 / 8) * 128;
     const int lo = r.S == 2 ? r.K16 * r.N16 * 2 : 0;
-    const int nwords = r.S * r.K16 * r.N16 / 2;
-    for (int i = threadIdx.x; i < nwords; i += blockDim.x) reinterpret_cast<uint32_t*>(B)[i] = 0u;
-    __syncthreads();
+    // the pool was cleared: B is zero wherever no fill writes
     if (r.kind == TREC_EMPTY) return;  // a tile with no blocks: a zero product
     const HBlock b = blocks[r.blk];
     if (r.kind == TREC_DENSE) {
@@ -189,8 +190,8 @@ __global__ void k_tpack(const TRec* __restrict__ recs, const HBlock* __restrict_
         for (int e = threadIdx.x; e < b.n1 * b.q; e += blockDim.x) {
             const int j = e / b.q, k = e - j * b.q;
             const int col = cols[j];
-            if (col >= r.k0 && col < r.k0 + r.K16 && k >= r.n0 && k < r.n0 + r.N16)
-                st_bf16(B, col - r.k0, k - r.n0, lbo, Vp[(int64_t)j * b.q + k], lo);
+            if (col >= r.k0 && col < r.k0 + r.K16 && k >= r.n0 && k < r.n0 + r.nsub)
+                st_bf16(B, col - r.k0, r.bcol + k - r.n0, lbo, Vp[(int64_t)j * b.q + k], lo);
         }
     }
 }
@@ -248,6 +249,14 @@ static vf_status pack_pages(vf_hmat* H, std::vector<TRec>& recs, const std::vect
             bool fresh = true;
             for (int64_t ri = group_recs[gi].first; ri < group_recs[gi].second; ++ri) {
                 TRec r = recs[ri];
+                if (!r.hdr) {  // another fill of the previous record
+                    const TRec& prev = ordered.back();
+                    r.dst = prev.dst;
+                    r.ring = prev.ring;
+                    r.dep = prev.dep;
+                    ordered.push_back(r);
+                    continue;
+                }
                 const uint32_t bytes = (uint32_t)(r.S * r.K16 * kPanel * 2);
                 uint32_t at = 0;
                 for (;;) {
@@ -290,6 +299,7 @@ static vf_status pack_pages(vf_hmat* H, std::vector<TRec>& recs, const std::vect
     cp[ncta] = (int32_t)used.size();
     const int64_t np = (int64_t)used.size();
     VF_TRY(pool.alloc(std::max<int64_t>(np, 1) * kTP));
+    VF_TRY_CUDA(cudaMemset(pool.p, 0, std::max<int64_t>(np, 1) * kTP));
     VF_TRY(used_d.upload(used));
     VF_TRY(cta_pages.upload(cp));
     *bytes = 0;
@@ -355,7 +365,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, H->device) != cudaSuccess || nsm <= 0) nsm = 148;
     const int64_t rec_cost = 2048;  // fixed work of one record, in byte equivalents
 
-    // ---- phase 2: per tile, the blocks' pieces inside it, K-chunks of <= kKMax
+    // ---- phase 2: per tile, the blocks' pieces inside it, K-chunks of <= the set's KMAX
     std::vector<int32_t> tile_of_row(n, -1);
     for (int64_t k = 0; k < ntiles; ++k)
         for (int32_t r = H->h_tile_first[k]; r < H->h_tile_first[k] + H->h_tile_count[k]; ++r)
@@ -383,7 +393,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
             t.row_base = tf + t.coloff;
             t.N16 = r16(re - t.row_base);
             if (b.kind == VF_BLK_SVD) {
-                // K = the rank, in chunks of <= kKMax (one A slot each)
+                // K = the rank, in chunks of <= the set's KMAX
                 t.kind = TREC_SVDU;
                 t.a_src = 1;
                 for (int32_t kc = 0; kc < r16(b.q); kc += kk2) {
@@ -417,6 +427,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
             TRec t = per[k][i];
             t.flags = (i == 0 ? TR_FIRST : 0) | (i + 1 == per[k].size() ? TR_LAST : 0);
             t.S = S;
+            t.hdr = 1;
             recs2.push_back(t);
             tile_cost[k] += S * ((int64_t)t.K16 * t.N16 * 2 + (int64_t)t.K16 * kPanel * 2) + rec_cost;
         }
@@ -437,6 +448,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
             t.a_row0 = 0;
             t.flags = TR_FIRST | TR_LAST;
             t.S = S;
+            t.hdr = 1;
             tile_recs[k].first = (int64_t)recs2.size();
             recs2.push_back(t);
             tile_recs[k].second = (int64_t)recs2.size();
@@ -456,93 +468,113 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
     }
     VF_TRY(pack_pages(H, recs2, lists2, tile_recs, T->pages2, T->used2, T->cta_pages2, &T->bytes2));
 
-    // ---- phase 1: per SVD block, K-chunks over its column range; a unit is
-    // a block's T columns [n0, n0 + N) with N <= the region width (blocks
-    // of larger rank become several units reading the same X rows)
+    // ---- phase 1: SVD blocks with the same column cluster (the same X rows)
+    // form groups whose ranks fit one accumulator region; a group's records
+    // are K-chunks over the cluster's column range, each holding all its
+    // blocks' V' side by side (one A copy serves the whole group).  A block
+    // of rank above the region width becomes several parts.
+    struct Part {
+        int32_t blk, n0, nsub;  // rank columns [n0, n0 + nsub) of block blk (nsub a multiple of 16)
+    };
+    std::vector<std::vector<Part>> groups;
+    {
+        std::vector<int32_t> order;
+        for (size_t bi = 0; bi < B.size(); ++bi)
+            if (B[bi].kind == VF_BLK_SVD) order.push_back((int32_t)bi);
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+            return B[x].c0 != B[y].c0 ? B[x].c0 < B[y].c0 : B[x].n < B[y].n;
+        });
+        const int32_t region = cfg_region(S);
+        for (size_t i = 0; i < order.size();) {
+            size_t j = i;
+            while (j < order.size() && B[order[j]].c0 == B[order[i]].c0 && B[order[j]].n == B[order[i]].n) ++j;
+            std::vector<Part> cur;
+            int32_t used_cols = 0;
+            for (size_t t = i; t < j; ++t) {
+                const int32_t bi = order[t], q16 = r16(B[bi].q);
+                for (int32_t n0 = 0; n0 < q16; n0 += region) {
+                    const int32_t nsub = std::min(region, q16 - n0);
+                    if (used_cols + nsub > region) {
+                        groups.push_back(cur);
+                        cur.clear();
+                        used_cols = 0;
+                    }
+                    cur.push_back(Part{bi, n0, nsub});
+                    used_cols += nsub;
+                }
+            }
+            if (!cur.empty()) groups.push_back(cur);
+            i = j;
+        }
+    }
     std::vector<TRec> recs1;
-    std::vector<std::pair<int64_t, int64_t>> unit_recs;
-    std::vector<int64_t> unit_cost;
-    std::vector<int32_t> unit_blk, unit_n0, unit_n16;
-    for (size_t bi = 0; bi < B.size(); ++bi) {
-        const HBlock& b = B[bi];
-        if (b.kind != VF_BLK_SVD) continue;
-        const int32_t q16 = r16(b.q);
-        const int32_t c8 = (b.c0 / 8) * 8;
-        const int32_t ktot = r16(b.c0 + b.n - c8);
-        for (int32_t n0 = 0; n0 < q16; n0 += cfg_region(S)) {
-            const int32_t n16 = std::min(cfg_region(S), q16 - n0);
-            const int32_t kmax = std::min<int32_t>(cfg_kmax(S), ((kTP - kTPHdr - kTRHdr) / (n16 * 2 * S)) / 16 * 16);
-            const int64_t first = (int64_t)recs1.size();
-            int64_t cost = 0;
-            for (int32_t kc = 0; kc < ktot; kc += kmax) {
+    std::vector<std::pair<int64_t, int64_t>> group_recs1;
+    std::vector<int64_t> group_cost;
+    for (const auto& g : groups) {
+        const HBlock& b0 = B[g[0].blk];
+        int32_t n16 = 0;
+        for (const Part& pt : g) n16 += pt.nsub;
+        const int32_t kmax = std::min<int32_t>(cfg_kmax(S), ((kTP - kTPHdr - kTRHdr) / (n16 * 2 * S)) / 16 * 16);
+        const int32_t c8 = (b0.c0 / 8) * 8;
+        const int32_t ktot = r16(b0.c0 + b0.n - c8);
+        const int64_t first = (int64_t)recs1.size();
+        int64_t cost = 0;
+        for (int32_t kc = 0; kc < ktot; kc += kmax) {
+            int32_t bcol = 0;
+            for (size_t pi = 0; pi < g.size(); ++pi) {
                 TRec t{};
                 t.kind = TREC_VT;
-                t.blk = (int32_t)bi;
+                t.blk = g[pi].blk;
                 t.k0 = c8 + kc;
                 t.K16 = std::min(kmax, ktot - kc);
                 t.N16 = n16;
-                t.n0 = n0;
+                t.n0 = g[pi].n0;
+                t.nsub = g[pi].nsub;
+                t.bcol = bcol;
                 t.a_src = 0;
                 t.a_row0 = t.k0;
-                t.offT = P->h_offT16[bi] + n0;
                 t.S = S;
+                t.hdr = pi == 0;
+                t.flags = (kc == 0 && pi == 0) ? (TR_FIRST | TR_USTART) : 0;
+                if (kc + kmax >= ktot && pi == 0) t.flags |= TR_LAST;
                 recs1.push_back(t);
-                cost += S * ((int64_t)t.K16 * t.N16 * 2 + (int64_t)t.K16 * kPanel * 2) + rec_cost;
+                bcol += g[pi].nsub;
             }
-            recs1[first].flags |= TR_FIRST;
-            recs1.back().flags |= TR_LAST;
-            unit_recs.push_back({first, (int64_t)recs1.size()});
-            unit_cost.push_back(cost);
-            unit_blk.push_back((int32_t)bi);
-            unit_n0.push_back(n0);
-            unit_n16.push_back(n16);
+            cost += S * ((int64_t)std::min(kmax, ktot - kc) * n16 * 2 + (int64_t)std::min(kmax, ktot - kc) * kPanel * 2) +
+                    rec_cost;
         }
+        group_recs1.push_back({first, (int64_t)recs1.size()});
+        group_cost.push_back(cost);
     }
-    VF_TRY(check_records(recs1, cfg_region(S), P->n_rows_x, P->n_rows_t));
-    T->ncta1 = (int32_t)std::min<int64_t>((int64_t)nsm * cfg_ctas(S), (int64_t)unit_cost.size());
+    {
+        std::vector<TRec> heads;
+        for (const TRec& t : recs1)
+            if (t.hdr) heads.push_back(t);
+        VF_TRY(check_records(heads, cfg_region(S), P->n_rows_x, P->n_rows_t));
+    }
+    T->ncta1 = (int32_t)std::min<int64_t>((int64_t)nsm * cfg_ctas(S), (int64_t)group_cost.size());
     if (T->ncta1 > 0) {
-        auto lists1 = lpt(unit_cost, T->ncta1);
-        // consecutive units of a CTA share one accumulator region while their
-        // ranks fit a region's columns: one epilogue round per group.
-        // units[4 u ..] = T row, q16, region column, 1 if the unit ends its group
+        auto lists1 = lpt(group_cost, T->ncta1);
+        // the epilogue's list: per part, T row, columns, region column, 1 if it ends its group
         std::vector<int32_t> units, ptr(T->ncta1 + 1, 0);
         for (int32_t c = 0; c < T->ncta1; ++c) {
             ptr[c] = (int32_t)(units.size() / 4);
-            const int32_t region = cfg_region(S);
-            int32_t col = region;       // forces a new group
-            int64_t prev_last = -1;     // last record of the previous unit
-            for (int32_t u : lists1[c]) {
-                const int32_t q16 = unit_n16[u];
-                const bool fresh = col + q16 > region;
-                if (fresh) {
-                    col = 0;
-                    if (prev_last >= 0) {
-                        recs1[prev_last].flags |= TR_LAST;
-                        units[units.size() - 1] = 1;  // the previous unit closes its group
-                    }
+            for (int32_t gi : lists1[c]) {
+                int32_t col = 0;
+                for (size_t pi = 0; pi < groups[gi].size(); ++pi) {
+                    const Part& pt = groups[gi][pi];
+                    units.push_back(P->h_offT16[pt.blk] + pt.n0);
+                    units.push_back(pt.nsub);
+                    units.push_back(col);
+                    units.push_back(pi + 1 == groups[gi].size() ? 1 : 0);
+                    col += pt.nsub;
                 }
-                for (int64_t ri = unit_recs[u].first; ri < unit_recs[u].second; ++ri) {
-                    recs1[ri].flags &= ~(TR_FIRST | TR_LAST);
-                    recs1[ri].coloff = col;
-                }
-                recs1[unit_recs[u].first].flags |= TR_USTART | (fresh ? TR_FIRST : 0);
-                prev_last = unit_recs[u].second - 1;
-                units.push_back(P->h_offT16[unit_blk[u]] + unit_n0[u]);
-                units.push_back(q16);
-                units.push_back(col);
-                units.push_back(0);
-                col += q16;
-            }
-            if (prev_last >= 0) {
-                recs1[prev_last].flags |= TR_LAST;
-                units[units.size() - 1] = 1;
             }
         }
         ptr[T->ncta1] = (int32_t)(units.size() / 4);
-        VF_TRY(check_records(recs1, cfg_region(S), P->n_rows_x, P->n_rows_t));
         VF_TRY(T->cta_units.upload(units));
         VF_TRY(T->cta_unit_ptr.upload(ptr));
-        VF_TRY(pack_pages(H, recs1, lists1, unit_recs, T->pages1, T->used1, T->cta_pages1, &T->bytes1));
+        VF_TRY(pack_pages(H, recs1, lists1, group_recs1, T->pages1, T->used1, T->cta_pages1, &T->bytes1));
     }
     T->built = true;
     return VF_OK;
