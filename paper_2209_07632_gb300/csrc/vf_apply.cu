@@ -1061,7 +1061,7 @@ struct Workspace {
     // tensor-core path (BF16, R >= kTensorMinR): BF16 panels of 128 RHS, ping-pong, and the T panel
     dbuf<unsigned char> xpan[2], tpan;
     dbuf<unsigned char> xsplit[2], tsplit[2];  // hi / lo panels of the split residual
-    dbuf<int> tcount;  // columns not converged after a tensor sweep
+    dbuf<int> tcount;  // [0]: columns not converged after a tensor sweep; [1]: the reduction's ticket
     int tpanels = 0;
     cudaGraphExec_t graph = nullptr;
     cudaGraphConditionalHandle handle = 0;
@@ -1332,32 +1332,50 @@ static vf_status tensor_ws(const vf_hmat* h, Workspace* w) {
     }
     VF_TRY(w->tpan.alloc((size_t)bt));
     VF_TRY_CUDA(cudaMemset(w->tpan.p, 0, (size_t)bt));
-    VF_TRY(w->tcount.alloc(1));
+    VF_TRY(w->tcount.alloc(2));
+    VF_TRY_CUDA(cudaMemset(w->tcount.p, 0, 2 * sizeof(int)));
     return VF_OK;
 }
 
-// Columns whose last update exceeded rtol ||E|| (the sweep's residual
-// partials summed per column in a fixed order, as in k_sweep_reduce).
-__global__ void __launch_bounds__(1024) k_unconverged(const double* __restrict__ colpart, int64_t ntiles, int R,
-                                                      const double* __restrict__ enorm2, double rtol2,
-                                                      double* __restrict__ colres, int* __restrict__ count) {
-    __shared__ int s_unconv;
-    if (threadIdx.x == 0) s_unconv = 0;
+// Columns whose last update exceeded rtol ||E||: one CTA per column sums
+// the sweep's per-tile partials in a fixed order (threads stride the
+// tiles, then shuffles, then the warps in order) into colres[c], and the
+// last CTA to finish (an acq_rel ticket) counts the unconverged columns.
+__global__ void __launch_bounds__(256) k_unconverged(const double* __restrict__ colpart, int64_t ntiles, int R,
+                                                     const double* __restrict__ enorm2, double rtol2,
+                                                     double* __restrict__ colres, int* __restrict__ count,
+                                                     int* __restrict__ ticket) {
+    __shared__ double ws[8];
+    __shared__ int s_last;
+    const int c = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double s = 0;
+    for (int64_t t = threadIdx.x; t < ntiles; t += blockDim.x) s += colpart[(int64_t)c * ntiles + t];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) ws[warp] = s;
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    int mine = 0;
-    for (int c = warp; c < R; c += nw) {
-        double s = 0;
-        for (int64_t t = lane; t < ntiles; t += 32) s += colpart[(int64_t)c * ntiles + t];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) {
-            colres[c] = s;
-            if (s > rtol2 * enorm2[c]) mine++;
-        }
+    if (threadIdx.x == 0) {
+        double sum = 0;
+        for (int w = 0; w < 8; ++w) sum += ws[w];
+        colres[c] = sum;
+        cuda::atomic_ref<int, cuda::thread_scope_device> tk(*ticket);
+        s_last = tk.fetch_add(1, cuda::memory_order_acq_rel) == R - 1;
     }
-    if (lane == 0 && mine) atomicAdd(&s_unconv, mine);
     __syncthreads();
-    if (threadIdx.x == 0) *count = s_unconv;
+    if (!s_last) return;
+    // the last CTA: every colres is visible (acquired through the ticket)
+    int mine = 0;
+    for (int cc = threadIdx.x; cc < R; cc += blockDim.x)
+        if (__ldcg(colres + cc) > rtol2 * enorm2[cc]) mine++;
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    __shared__ int wc[8];
+    if (lane == 0) wc[warp] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < 8; ++w) tot += wc[w];
+        *count = tot;
+        *ticket = 0;  // ready for the next sweep
+    }
 }
 
 // Jacobi on the tensor cores: B_0 = Et, B_{k+1} = Et + rho .* (F_bf16 B_k)
@@ -1367,7 +1385,7 @@ static vf_status tensor_jacobi_loop(const vf_hmat* h, Workspace* w, int max_iter
                                     int* iters, int* par, int* kernels) {
     VF_TRY(tensor_ws(h, w));
     const int64_t n = h->nf, nR = n * (int64_t)w->R;
-    const int64_t ntiles = (int64_t)h->h_tile_first.size();
+    const int64_t ntiles = tensor_parts(h, 1);
     const int64_t bx = tensor_panel_bytes_x(h);
     VF_TRY_CUDA(cudaMemcpyAsync(w->Bt[0].p, w->Et.p, nR * 4, cudaMemcpyDeviceToDevice, st));
     k_colnorm2<<<(unsigned)w->R, 1024, 0, st>>>(w->Et.p, n, w->enorm2.p);
@@ -1393,8 +1411,8 @@ static vf_status tensor_jacobi_loop(const vf_hmat* h, Workspace* w, int max_iter
             VF_TRY(tensor_multiply(h, 1, w->xpan[cur].p + (size_t)p * bx, nullptr, w->tpan.p, nullptr, ep,
                                    w->status.p, st));
         }
-        k_unconverged<<<1, 1024, 0, st>>>(w->colpart.p, ntiles, w->R, w->enorm2.p, rtol * rtol, w->colres.p,
-                                          w->tcount.p);
+        k_unconverged<<<(unsigned)w->R, 256, 0, st>>>(w->colpart.p, ntiles, w->R, w->enorm2.p, rtol * rtol,
+                                                      w->colres.p, w->tcount.p, w->tcount.p + 1);
         VF_TRY_CUDA(cudaGetLastError());
         *kernels += w->tpanels * tensor_kernels(h, 1) + 1;
         int hc = 0;
@@ -1418,7 +1436,7 @@ static vf_status tensor_residual(const vf_hmat* h, Workspace* w, const float* B,
                                  cudaStream_t st, int* kernels) {
     VF_TRY(tensor_ws(h, w));
     VF_TRY(tensor_prepare(const_cast<vf_hmat*>(h), 2));
-    const int64_t n = h->nf, ntiles = (int64_t)h->h_tile_first.size();
+    const int64_t n = h->nf, ntiles = tensor_parts(h, 2);
     const int64_t bx = tensor_panel_bytes_x(h), bt = tensor_panel_bytes_t(h);
     if (!w->xsplit[0].p) {
         for (int i = 0; i < 2; ++i) {
@@ -1445,7 +1463,8 @@ static vf_status tensor_residual(const vf_hmat* h, Workspace* w, const float* B,
         ep.ntiles = ntiles;
         VF_TRY(tensor_multiply(h, 2, xh, xl, w->tsplit[0].p, w->tsplit[1].p, ep, w->status.p, st));
     }
-    k_unconverged<<<1, 1024, 0, st>>>(w->colpart.p, ntiles, w->R, w->enorm2.p, 0.0, w->colres.p, w->tcount.p);
+    k_unconverged<<<(unsigned)w->R, 256, 0, st>>>(w->colpart.p, ntiles, w->R, w->enorm2.p, 0.0, w->colres.p,
+                                                  w->tcount.p, w->tcount.p + 1);
     VF_TRY_CUDA(cudaGetLastError());
     *kernels += w->tpanels * (1 + tensor_kernels(h, 2)) + 1;
     return VF_OK;

@@ -52,17 +52,41 @@ constexpr int kTickets = 16;         // records in flight (A operands in the rin
 // independent pipelines per SM; the split set (S = 2, hi and lo A operands)
 // caps a record's K at 32 so its A operands still fit the ring.
 template <int NS> struct TCfg;
+// Phase 2 accumulates a (super-)tile of consecutive row tiles, up to R2
+// rows, in NREG2 regions of R2 TMEM columns used in turn.  Tiles (R2 = 64,
+// two regions, 128 columns, four CTAs per SM) measured faster than
+// super-tiles of 128 rows in one region (1.52 against 1.81 ms for a 128-RHS
+// multiply of the 79k-facet terrain) or in two regions at two CTAs per SM
+// (2.1 ms): the number of independent pipelines per SM decides.  The
+// VF_T1_* macros select the BF16 set's configuration at build time.
+#ifndef VF_T1_R2
+#define VF_T1_R2 64
+#endif
+#ifndef VF_T1_NREG2
+#define VF_T1_NREG2 2
+#endif
+#ifndef VF_T1_CTAS
+#define VF_T1_CTAS 4
+#endif
+#ifndef VF_T1_PSTAGES
+#define VF_T1_PSTAGES 2
+#endif
+#ifndef VF_T1_RING
+#define VF_T1_RING 20480
+#endif
 template <> struct TCfg<1> {
-    static constexpr int PSTAGES = 2, RING = 20480, CTAS = 4, REGION = 64, KMAX = 64;
+    static constexpr int PSTAGES = VF_T1_PSTAGES, RING = VF_T1_RING, CTAS = VF_T1_CTAS, REGION = 64, KMAX = 64,
+                         R2 = VF_T1_R2, NREG2 = VF_T1_NREG2, TMEM = R2 * NREG2 > 128 ? 256 : 128;
 };
 template <> struct TCfg<2> {
-    static constexpr int PSTAGES = 2, RING = 20480, CTAS = 4, REGION = 64, KMAX = 32;
+    static constexpr int PSTAGES = 2, RING = 20480, CTAS = 4, REGION = 64, KMAX = 32, R2 = 64, NREG2 = 2, TMEM = 128;
 };
 constexpr int kMaxPStages = 3;
 static int cfg_ring(int S) { return S == 1 ? TCfg<1>::RING : TCfg<2>::RING; }
 static int cfg_ctas(int S) { return S == 1 ? TCfg<1>::CTAS : TCfg<2>::CTAS; }
 static int cfg_region(int S) { return S == 1 ? TCfg<1>::REGION : TCfg<2>::REGION; }
 static int cfg_kmax(int S) { return S == 1 ? TCfg<1>::KMAX : TCfg<2>::KMAX; }
+static int cfg_r2(int S) { return S == 1 ? TCfg<1>::R2 : TCfg<2>::R2; }
 template <int NS>
 constexpr size_t tsmem_bytes() {
     return (size_t)TCfg<NS>::PSTAGES * 16384 + TCfg<NS>::RING + 1024;
@@ -106,7 +130,9 @@ struct vf_tensor_set {
     vf::dbuf<unsigned char> pages2, pages1;
     vf::dbuf<uint32_t> used2, used1;
     vf::dbuf<int32_t> cta_pages2, cta_pages1;  // ncta + 1 each
-    vf::dbuf<int32_t> cta_tiles, cta_tile_ptr; // phase 2: each CTA's tiles in order
+    vf::dbuf<int32_t> cta_tiles, cta_tile_ptr; // phase 2: each CTA's (super-)tiles in order
+    vf::dbuf<int32_t> st_first, st_count;      // phase 2: rows of each (super-)tile
+    int64_t nst = 0;                           // (super-)tiles
     vf::dbuf<int32_t> cta_units, cta_unit_ptr; // phase 1: each CTA's units (offT16, N16 pairs)
     int64_t bytes2 = 0, bytes1 = 0;
 };
@@ -322,7 +348,7 @@ static inline int32_t r16(int64_t x) { return (int32_t)((x + 15) / 16 * 16); }
 // The invariants every record must meet (checked on the host before upload).
 static vf_status check_records(const std::vector<TRec>& recs, int max_col, int64_t rows_x, int64_t rows_t) {
     for (const TRec& r : recs) {
-        const bool ok = r.K16 >= 16 && r.K16 <= cfg_kmax(r.S) && r.K16 % 16 == 0 && r.N16 >= 16 && r.N16 <= cfg_region(r.S) &&
+        const bool ok = r.K16 >= 16 && r.K16 <= cfg_kmax(r.S) && r.K16 % 16 == 0 && r.N16 >= 16 && r.N16 <= max_col &&
                         r.N16 % 16 == 0 && r.coloff >= 0 && r.coloff % 16 == 0 && r.coloff + r.N16 <= max_col &&
                         r.a_row0 >= 0 && r.a_row0 % 8 == 0 &&
                         (int64_t)r.a_row0 + r.K16 <= (r.a_src ? rows_t : rows_x) &&
@@ -359,102 +385,160 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
     if (H->n_aux > 0) VF_TRY(H->aux.download(haux));
     const int64_t n = H->nf;
     const int64_t ntiles = (int64_t)H->h_tile_first.size();
-    // largest K of a phase-2 record (N <= 64) so that it fits a page
-    const int32_t kk2 = std::min<int32_t>(cfg_kmax(S), ((kTP - kTPHdr - kTRHdr) / (64 * 2 * S)) / 16 * 16);
     int nsm = 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, H->device) != cudaSuccess || nsm <= 0) nsm = 148;
     const int64_t rec_cost = 2048;  // fixed work of one record, in byte equivalents
 
-    // ---- phase 2: per tile, the blocks' pieces inside it, K-chunks of <= the set's KMAX
-    std::vector<int32_t> tile_of_row(n, -1);
-    for (int64_t k = 0; k < ntiles; ++k)
-        for (int32_t r = H->h_tile_first[k]; r < H->h_tile_first[k] + H->h_tile_count[k]; ++r)
-            tile_of_row[r] = (int32_t)k;
-    std::vector<std::vector<TRec>> per(ntiles);
+    // ---- phase 2: (super-)tiles of consecutive row tiles up to R2 rows; in
+    // each, the pieces of dense and CSR blocks with the same column cluster
+    // share records (their rows side by side in B, one copy of the X rows per
+    // K-chunk); SVD pieces (A = the block's own T rows) get their own records
+    const int32_t r2 = cfg_r2(S);
+    std::vector<int32_t> stf, stc, st_of_row(n, -1), tile_of_row(n, -1);
+    for (int64_t k = 0; k < ntiles; ++k) {
+        const int32_t tf = H->h_tile_first[k], tc = H->h_tile_count[k];
+        if (stf.empty() || stc.back() + tc > r2) {
+            stf.push_back(tf);
+            stc.push_back(0);
+        }
+        stc.back() += tc;
+        for (int32_t r = tf; r < tf + tc; ++r) st_of_row[r] = (int32_t)stf.size() - 1, tile_of_row[r] = (int32_t)k;
+    }
+    const int64_t nst = (int64_t)stf.size();
+    struct Piece {
+        int32_t blk, rs, re;
+    };
+    std::vector<std::vector<Piece>> dpieces(nst), spieces(nst);
     for (size_t bi = 0; bi < B.size(); ++bi) {
         const HBlock& b = B[bi];
         if (b.kind != VF_BLK_DENSE && b.kind != VF_BLK_CSR && b.kind != VF_BLK_SVD) continue;
         for (int32_t r = b.r0; r < b.r0 + b.m;) {
-            const int32_t k = tile_of_row[r];
-            const int32_t tf = H->h_tile_first[k], tc = H->h_tile_count[k];
-            const int32_t rs = std::max(b.r0, tf), re = std::min(b.r0 + b.m, tf + tc);
+            // a dense block's values sit in one slab per row tile, so its
+            // pieces end at row tiles; the others' at (super-)tiles
+            const int32_t k = st_of_row[r];
+            int32_t rs = std::max(b.r0, stf[k]), re = std::min(b.r0 + b.m, stf[k] + stc[k]);
+            if (b.kind == VF_BLK_DENSE) {
+                const int32_t t = tile_of_row[r];
+                rs = std::max(b.r0, H->h_tile_first[t]);
+                re = std::min(b.r0 + b.m, H->h_tile_first[t] + H->h_tile_count[t]);
+            }
             r = re;
             if (b.kind == VF_BLK_SVD) {
                 // any of the block's compacted rows in [rs, re)?
                 const int32_t* rows = haux.data() + b.off_aux;
                 const int32_t* lo = std::lower_bound(rows, rows + b.m1, rs);
                 if (lo == rows + b.m1 || *lo >= re) continue;
-            }
-            TRec t{};
-            t.blk = (int32_t)bi;
-            t.rs = rs;
-            t.re = re;
-            t.coloff = ((rs - tf) / 16) * 16;
-            t.row_base = tf + t.coloff;
-            t.N16 = r16(re - t.row_base);
-            if (b.kind == VF_BLK_SVD) {
-                // K = the rank, in chunks of <= the set's KMAX
-                t.kind = TREC_SVDU;
-                t.a_src = 1;
-                for (int32_t kc = 0; kc < r16(b.q); kc += kk2) {
-                    TRec u = t;
-                    u.k0 = kc;
-                    u.K16 = std::min(kk2, r16(b.q) - kc);
-                    u.a_row0 = P->h_offT16[bi] + kc;
-                    per[k].push_back(u);
-                }
+                spieces[k].push_back(Piece{(int32_t)bi, rs, re});
             } else {
-                t.kind = b.kind == VF_BLK_DENSE ? TREC_DENSE : TREC_CSR;
-                t.a_src = 0;
-                const int32_t c8 = (b.c0 / 8) * 8;
-                const int32_t ktot = r16(b.c0 + b.n - c8);
-                for (int32_t kc = 0; kc < ktot; kc += kk2) {
-                    TRec u = t;
-                    u.k0 = c8 + kc;
-                    u.K16 = std::min(kk2, ktot - kc);
-                    u.a_row0 = u.k0;
-                    per[k].push_back(u);
-                }
+                dpieces[k].push_back(Piece{(int32_t)bi, rs, re});
             }
         }
     }
     std::vector<TRec> recs2;
-    std::vector<std::pair<int64_t, int64_t>> tile_recs(ntiles);
-    std::vector<int64_t> tile_cost(ntiles, 0);
-    for (int64_t k = 0; k < ntiles; ++k) {
+    std::vector<std::pair<int64_t, int64_t>> tile_recs(nst);
+    std::vector<int64_t> tile_cost(nst, 0);
+    for (int64_t k = 0; k < nst; ++k) {
         tile_recs[k].first = (int64_t)recs2.size();
-        for (size_t i = 0; i < per[k].size(); ++i) {
-            TRec t = per[k][i];
-            t.flags = (i == 0 ? TR_FIRST : 0) | (i + 1 == per[k].size() ? TR_LAST : 0);
+        const int64_t first = (int64_t)recs2.size();
+        auto add_cost = [&](const TRec& t) {
+            tile_cost[k] += S * ((int64_t)t.K16 * t.N16 * 2 + (int64_t)t.K16 * kPanel * 2) + rec_cost;
+        };
+        // dense / CSR pieces grouped by column cluster
+        std::vector<Piece>& dp = dpieces[k];
+        std::stable_sort(dp.begin(), dp.end(), [&](const Piece& x, const Piece& y) {
+            const HBlock &bx = B[x.blk], &by = B[y.blk];
+            return bx.c0 != by.c0 ? bx.c0 < by.c0 : (bx.n != by.n ? bx.n < by.n : x.rs < y.rs);
+        });
+        for (size_t i = 0; i < dp.size();) {
+            size_t j = i;
+            int32_t lo = dp[i].rs, hi = dp[i].re;
+            while (j < dp.size() && B[dp[j].blk].c0 == B[dp[i].blk].c0 && B[dp[j].blk].n == B[dp[i].blk].n) {
+                lo = std::min(lo, dp[j].rs);
+                hi = std::max(hi, dp[j].re);
+                ++j;
+            }
+            const HBlock& b0 = B[dp[i].blk];
+            const int32_t coloff = ((lo - stf[k]) / 16) * 16;
+            const int32_t row_base = stf[k] + coloff;
+            const int32_t n16 = r16(hi - row_base);
+            const int32_t kmax = std::min<int32_t>(cfg_kmax(S), ((kTP - kTPHdr - kTRHdr) / (n16 * 2 * S)) / 16 * 16);
+            const int32_t c8 = (b0.c0 / 8) * 8;
+            const int32_t ktot = r16(b0.c0 + b0.n - c8);
+            for (int32_t kc = 0; kc < ktot; kc += kmax) {
+                for (size_t t = i; t < j; ++t) {
+                    TRec u{};
+                    u.kind = B[dp[t].blk].kind == VF_BLK_DENSE ? TREC_DENSE : TREC_CSR;
+                    u.blk = dp[t].blk;
+                    u.rs = dp[t].rs;
+                    u.re = dp[t].re;
+                    u.coloff = coloff;
+                    u.row_base = row_base;
+                    u.N16 = n16;
+                    u.k0 = c8 + kc;
+                    u.K16 = std::min(kmax, ktot - kc);
+                    u.a_src = 0;
+                    u.a_row0 = u.k0;
+                    u.S = S;
+                    u.hdr = t == i;
+                    recs2.push_back(u);
+                    if (u.hdr) add_cost(u);
+                }
+            }
+            i = j;
+        }
+        // SVD pieces: K = the rank, in chunks
+        for (const Piece& pc : spieces[k]) {
+            const HBlock& b = B[pc.blk];
+            TRec t{};
+            t.kind = TREC_SVDU;
+            t.blk = pc.blk;
+            t.rs = pc.rs;
+            t.re = pc.re;
+            t.coloff = ((pc.rs - stf[k]) / 16) * 16;
+            t.row_base = stf[k] + t.coloff;
+            t.N16 = r16(pc.re - t.row_base);
+            t.a_src = 1;
             t.S = S;
             t.hdr = 1;
-            recs2.push_back(t);
-            tile_cost[k] += S * ((int64_t)t.K16 * t.N16 * 2 + (int64_t)t.K16 * kPanel * 2) + rec_cost;
+            const int32_t kmax = std::min<int32_t>(cfg_kmax(S), ((kTP - kTPHdr - kTRHdr) / (t.N16 * 2 * S)) / 16 * 16);
+            for (int32_t kc = 0; kc < r16(b.q); kc += kmax) {
+                TRec u = t;
+                u.k0 = kc;
+                u.K16 = std::min(kmax, r16(b.q) - kc);
+                u.a_row0 = P->h_offT16[pc.blk] + kc;
+                recs2.push_back(u);
+                add_cost(u);
+            }
         }
-        tile_recs[k].second = (int64_t)recs2.size();
-    }
-    // a tile with no records still needs its epilogue: give it one empty record
-    for (int64_t k = 0; k < ntiles; ++k)
-        if (tile_recs[k].first == tile_recs[k].second) {
+        if ((int64_t)recs2.size() == first) {
+            // a (super-)tile with no blocks still needs its epilogue: one empty record
             TRec t{};
             t.kind = TREC_EMPTY;
-            t.blk = 0;
             t.K16 = 16;
             t.N16 = 16;
-            t.rs = t.re = H->h_tile_first[k];
+            t.rs = t.re = stf[k];
             t.row_base = t.rs;
-            t.k0 = 0;
-            t.a_src = 0;
-            t.a_row0 = 0;
-            t.flags = TR_FIRST | TR_LAST;
             t.S = S;
             t.hdr = 1;
-            tile_recs[k].first = (int64_t)recs2.size();
             recs2.push_back(t);
-            tile_recs[k].second = (int64_t)recs2.size();
         }
-    VF_TRY(check_records(recs2, 64, P->n_rows_x, P->n_rows_t));
-    T->ncta2 = (int32_t)std::min<int64_t>((int64_t)nsm * cfg_ctas(S), ntiles);
+        // FIRST on the first record's header entry, LAST on the last record's
+        recs2[first].flags |= TR_FIRST;
+        int64_t last_hdr = (int64_t)recs2.size() - 1;
+        while (!recs2[last_hdr].hdr) --last_hdr;
+        recs2[last_hdr].flags |= TR_LAST;
+        tile_recs[k].second = (int64_t)recs2.size();
+    }
+    {
+        std::vector<TRec> heads;
+        for (const TRec& t : recs2)
+            if (t.hdr) heads.push_back(t);
+        VF_TRY(check_records(heads, r2, P->n_rows_x, P->n_rows_t));
+    }
+    T->nst = nst;
+    VF_TRY(T->st_first.upload(stf));
+    VF_TRY(T->st_count.upload(stc));
+    T->ncta2 = (int32_t)std::min<int64_t>((int64_t)nsm * cfg_ctas(S), nst);
     auto lists2 = lpt(tile_cost, T->ncta2);
     {
         std::vector<int32_t> tiles, ptr(T->ncta2 + 1, 0);
@@ -698,7 +782,7 @@ __device__ void t_producer(TSmem& S, unsigned char* stages, unsigned char* abuf,
                 const int dep = (int)h1.w;
                 const uint32_t ring = h1.z;
                 // self-check: shapes, the record inside the page, the A range inside its panel, the plan
-                if (K16 < 16 || K16 > TCfg<NS>::KMAX || (K16 & 15) || N16 < 16 || N16 > TCfg<NS>::REGION || (N16 & 15) ||
+                if (K16 < 16 || K16 > TCfg<NS>::KMAX || (K16 & 15) || N16 < 16 || N16 > max_col || (N16 & 15) ||
                     (int)h0.z + N16 > max_col || off + kTRHdr + (uint32_t)(NS * K16 * N16 * 2) > pused ||
                     (h1.x & 7u) || (int64_t)h1.x + K16 > (h0.w ? pn.rows_t : pn.rows_x) ||
                     ring + bytes > (uint32_t)TCfg<NS>::RING || (ring & 15u) || dep >= r || dep < r - kTickets)
@@ -727,9 +811,11 @@ oob:
 
 // The MMA issuer (warp 1, lane 0).  With NS = 2 each K step is three MMAs,
 // A_hi B_hi + A_lo B_hi + A_hi B_lo (the lo x lo term, ~2^-16 of the
-// product, is dropped), all into the same FP32 accumulator.
-template <int NS>
+// product, is dropped), all into the same FP32 accumulator.  The
+// accumulator is NREG regions of REG columns, used in turn.
+template <int NS, int REG, int NREG>
 __device__ void t_issuer(TSmem& S, unsigned char* stages, unsigned char* abuf, int pa, int pb, int* status) {
+    static_assert(REG * NREG <= TCfg<NS>::TMEM && NREG <= 2, "accumulator regions");
     int nrec = 0, dcount[2] = {0, 0}, d = 0;
     for (int p = pa, li = 0; p < pb; ++p, ++li) {
         const int s = li % TCfg<NS>::PSTAGES;
@@ -747,7 +833,7 @@ __device__ void t_issuer(TSmem& S, unsigned char* stages, unsigned char* abuf, i
                     if (!bwait(&S.d_empty[d], (uint32_t)(dcount[d] & 1))) goto fail;
                     tm_fence_after();
                 }
-                const uint32_t dt = S.tmem_base + (uint32_t)(d * TCfg<NS>::REGION + coloff);
+                const uint32_t dt = S.tmem_base + (uint32_t)(d * REG + coloff);
                 const uint32_t bsa = smem_u32(pg + off + kTRHdr), asa = smem_u32(abuf + h[6]);
                 const uint32_t blbo = (uint32_t)(N16 / 8) * 128;
                 const uint32_t idesc = mma_idesc(N16);
@@ -765,7 +851,7 @@ __device__ void t_issuer(TSmem& S, unsigned char* stages, unsigned char* abuf, i
                 if (flags & TR_LAST) {
                     mma_commit(&S.d_full[d]);
                     dcount[d]++;
-                    d ^= 1;
+                    d = NREG == 1 ? 0 : d ^ 1;
                 }
                 ++nrec;
                 off += kTRHdr + (uint32_t)(NS * K16 * N16 * 2);
@@ -785,7 +871,7 @@ fail:
 // Common prologue: barriers, TMEM allocation, both regions zeroed.
 template <int NS>
 __device__ void t_prologue(TSmem& S) {
-    constexpr int ncols = 2 * TCfg<NS>::REGION;
+    constexpr int ncols = TCfg<NS>::TMEM;
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         for (int i = 0; i < TCfg<NS>::PSTAGES; ++i) {
@@ -829,7 +915,7 @@ __device__ void t_prologue(TSmem& S) {
 // Common epilogue of a CTA: wait for the MMAs, free TMEM.
 template <int NS>
 __device__ void t_finish(TSmem& S, int* status) {
-    constexpr int ncols = 2 * TCfg<NS>::REGION;
+    constexpr int ncols = TCfg<NS>::TMEM;
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 32) {
         if (!bwait(&S.done, 0)) atomicExch(status, VF_E_TIMEOUT);
@@ -845,13 +931,13 @@ __device__ void t_finish(TSmem& S, int* status) {
 
 // Release a region after the epilogue read it (zeroing it first when the
 // next use accumulates into it), then arrive.
-template <int NS>
+template <int REG>
 __device__ __forceinline__ void t_release(TSmem& S, int d, bool zero) {
     const int warp = threadIdx.x >> 5;
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     if (zero) {
-        for (int c = 0; c < TCfg<NS>::REGION; c += 16)
-            tm_zero16(S.tmem_base + lane_base + d * TCfg<NS>::REGION + c);
+        for (int c = 0; c < REG; c += 16)
+            tm_zero16(S.tmem_base + lane_base + d * REG + c);
         tm_wait_st();
     }
     tm_fence_before();
@@ -891,7 +977,7 @@ __global__ void __launch_bounds__(192, TCfg<NS>::CTAS) k_tphase1(const unsigned 
             if (S.abort) t_drain<NS>(S);
         }
     } else if (warp == 1) {
-        if (lane == 0) t_issuer<NS>(S, stages, abuf, pa, pb, status);
+        if (lane == 0) t_issuer<NS, TCfg<NS>::REGION, 2>(S, stages, abuf, pa, pb, status);
     } else {
         const int m = 32 * (warp & 3) + lane;
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
@@ -921,7 +1007,7 @@ __global__ void __launch_bounds__(192, TCfg<NS>::CTAS) k_tphase1(const unsigned 
                 }
             }
             if (gend) {
-                t_release<NS>(S, d, false);  // each unit's first MMA overwrites its columns
+                t_release<TCfg<NS>::REGION>(S, d, false);  // each unit's first MMA overwrites its columns
                 open = false;
                 ++k;
             }
@@ -940,7 +1026,8 @@ __global__ void __launch_bounds__(192, TCfg<NS>::CTAS) k_tphase2(const unsigned 
                                                     const int32_t* __restrict__ tile_first,
                                                     const int32_t* __restrict__ tile_count, TPanels pn, TEpi ep,
                                                     int* __restrict__ status) {
-    constexpr int MAXCOL = 64;  // phase 2: a tile's rows
+    constexpr int REG = TCfg<NS>::R2, NREG = TCfg<NS>::NREG2;
+    constexpr int MAXCOL = REG;  // phase 2: a (super-)tile's rows
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* stages = smem;
     unsigned char* abuf = smem + TCfg<NS>::PSTAGES * kTP;
@@ -955,7 +1042,7 @@ __global__ void __launch_bounds__(192, TCfg<NS>::CTAS) k_tphase2(const unsigned 
             if (S.abort) t_drain<NS>(S);
         }
     } else if (warp == 1) {
-        if (lane == 0) t_issuer<NS>(S, stages, abuf, pa, pb, status);
+        if (lane == 0) t_issuer<NS, REG, NREG>(S, stages, abuf, pa, pb, status);
     } else {
         const int m = 32 * (warp & 3) + lane;
         const int col = ep.p0 + m;  // RHS column
@@ -963,8 +1050,8 @@ __global__ void __launch_bounds__(192, TCfg<NS>::CTAS) k_tphase2(const unsigned 
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         const int t0 = cta_tile_ptr[blockIdx.x], t1 = cta_tile_ptr[blockIdx.x + 1];
         for (int ti = t0, k = 0; ti < t1; ++ti, ++k) {
-            const int d = k & 1;
-            if (!__all_sync(0xffffffffu, bwait(&S.d_full[d], (uint32_t)((k >> 1) & 1)))) {
+            const int d = NREG == 1 ? 0 : (k & 1);
+            if (!__all_sync(0xffffffffu, bwait(&S.d_full[d], (uint32_t)((k / NREG) & 1)))) {
                 if (lane == 0) atomicExch(status, VF_E_TIMEOUT), atomicExch(&S.abort, 1);
                 break;
             }
@@ -974,7 +1061,7 @@ __global__ void __launch_bounds__(192, TCfg<NS>::CTAS) k_tphase2(const unsigned 
             double ss = 0.0;
             for (int c0 = 0; c0 < tc; c0 += 16) {
                 float v[16];
-                tm_ld16(S.tmem_base + lane_base + d * TCfg<NS>::REGION + c0, v);
+                tm_ld16(S.tmem_base + lane_base + d * REG + c0, v);
                 if (!live) continue;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -998,7 +1085,7 @@ __global__ void __launch_bounds__(192, TCfg<NS>::CTAS) k_tphase2(const unsigned 
                 }
             }
             if (ep.mode != 0 && live) ep.colpart[(int64_t)col * ep.ntiles + tile] = ss;
-            t_release<NS>(S, d, true);
+            t_release<REG>(S, d, true);
         }
     }
     t_finish<NS>(S, status);
@@ -1073,19 +1160,21 @@ vf_status tensor_multiply(const vf_hmat* H, int S, const unsigned char* Xhi, con
             k_tphase1<1><<<(unsigned)T.ncta1, 192, tsmem_bytes<1>(), st>>>(T.pages1.p, T.used1.p, T.cta_pages1.p,
                                                                       T.cta_units.p, T.cta_unit_ptr.p, pn, status);
         k_tphase2<1><<<(unsigned)T.ncta2, 192, tsmem_bytes<1>(), st>>>(T.pages2.p, T.used2.p, T.cta_pages2.p,
-                                                                  T.cta_tiles.p, T.cta_tile_ptr.p, H->tile_first.p,
-                                                                  H->tile_count.p, pn, ep, status);
+                                                                  T.cta_tiles.p, T.cta_tile_ptr.p, T.st_first.p,
+                                                                  T.st_count.p, pn, ep, status);
     } else {
         if (T.ncta1 > 0)
             k_tphase1<2><<<(unsigned)T.ncta1, 192, tsmem_bytes<2>(), st>>>(T.pages1.p, T.used1.p, T.cta_pages1.p,
                                                                       T.cta_units.p, T.cta_unit_ptr.p, pn, status);
         k_tphase2<2><<<(unsigned)T.ncta2, 192, tsmem_bytes<2>(), st>>>(T.pages2.p, T.used2.p, T.cta_pages2.p,
-                                                                  T.cta_tiles.p, T.cta_tile_ptr.p, H->tile_first.p,
-                                                                  H->tile_count.p, pn, ep, status);
+                                                                  T.cta_tiles.p, T.cta_tile_ptr.p, T.st_first.p,
+                                                                  T.st_count.p, pn, ep, status);
     }
     VF_TRY_CUDA(cudaGetLastError());
     return VF_OK;
 }
+
+int64_t tensor_parts(const vf_hmat* H, int S) { return H->tplan->set[S - 1].nst; }
 
 int tensor_kernels(const vf_hmat* H, int S) { return (H->tplan->set[S - 1].ncta1 > 0 ? 1 : 0) + 1; }
 

@@ -39,5 +39,7 @@ vf_status tensor_to_panel(const vf_hmat* H, const float* X, int64_t ld, const in
 vf_status tensor_multiply(const vf_hmat* H, int S, const unsigned char* Xhi, const unsigned char* Xlo,
                           unsigned char* Thi, unsigned char* Tlo, const TEpi& ep, int* status, cudaStream_t st);
 int tensor_kernels(const vf_hmat* H, int S);
+// per-column partial sums a phase-2 epilogue writes (one per row part)
+int64_t tensor_parts(const vf_hmat* H, int S);
 
 }  // namespace vf
