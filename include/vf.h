@@ -138,8 +138,12 @@ vf_status vf_tree_nodes(const vf_tree* t, int32_t* first, int32_t* count, int32_
  * dense or CSR.  Ties: zero < dense < CSR < SVD < hierarchical.  A
  * hierarchical block whose nonzero children are all CSR (all dense) is
  * coalesced into one CSR (dense) block.  The SVD probe starts at rank k0
- * and doubles up to k_max; a block needing more fails the probe.  Factors
- * are verified by an FP64-accumulated check of ||F_IJ - U'V'^T||_2.
+ * and doubles up to k_max; a block needing more fails the probe.  With
+ * verify = 1 each accepted factorisation is checked against Algorithm 3's
+ * criterion (Section 3): ||F_IJ - U'V'^T||_2 <= tol ||F_IJ||_2 (by
+ * Eckart-Young the left side is sigma_{q+1}), both norms estimated by eight
+ * FP64 power iterations on the GPU from one seeded start; a block that
+ * fails goes back to the rank doubling (counted in verify_failed).
  * Errors: VF_E_INVAL, VF_E_NOMEM, VF_E_CUDA. */
 typedef struct {
     double tol;             /* compression tolerance, e.g. 1e-3 */
@@ -147,7 +151,7 @@ typedef struct {
     int32_t k0;             /* initial probe rank, default 8 */
     int32_t k_max;          /* largest probe rank, default 128 */
     int32_t power_iters;    /* subspace iterations of the probe, default 2 */
-    int32_t verify;         /* 1: FP64 truncation check on accepted SVD blocks */
+    int32_t verify;         /* 1: FP64 truncation check on accepted SVD blocks (default 0) */
     uint32_t precisions;    /* bit (1 << vf_precision): copies to build; FP32 always */
     const vf_rank_predictor* predictor; /* NULL: plain probe path */
     uint64_t seed;

@@ -370,6 +370,190 @@ __global__ void k_form_factors(const ProbeDesc* __restrict__ pd, const FactorDes
     }
 }
 
+// ------------------------------------------------------------ FP64 truncation check
+// For an accepted q-term factorisation U' V'^T of a block A (compacted rows
+// and columns), the truncation criterion of Algorithm 3 is
+// sigma_{q+1}(A) < tol sigma_1(A); by Eckart-Young sigma_{q+1}(A) is the
+// spectral norm of A - A_q, so the check estimates ||A - U' V'^T||_2 and
+// ||A||_2 by power iteration on E^T E and A^T A (E = A - U' V'^T) from one
+// seeded start, with every product and sum in FP64 (entries as assembly
+// evaluates them), and accepts iff the first <= tol x the second.  A
+// failed check sends the block back to Algorithm 3's rank doubling.
+constexpr int kVerifyIters = 8;
+
+struct VerDesc {
+    int32_t probe, q;
+    int64_t u_off;  // U' (m1 x q, row-major) in the staging buffer; V' (n1 x q) follows
+    int64_t s_off;  // FP64 scratch: xE, xA (n1 each), yE, yA (m1 each), t (q)
+    uint64_t seed;
+};
+
+struct VerItem {
+    int32_t v, o0;  // candidate, first output row (32 per item)
+};
+
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+    // 256 threads
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) red[32] = s;
+    __syncthreads();
+    return red[32];
+}
+
+// out[k] = sum_r Fm[r q + k] x[r], k < q (Fm row-major rows x q, FP32; FP64 sums)
+__device__ void ver_tdot(const float* Fm, int rows, int q, const double* x, double* out, double* red) {
+    for (int k = 0; k < q; ++k) {
+        double a = 0.0;
+        for (int r = threadIdx.x; r < rows; r += blockDim.x) a += (double)Fm[(int64_t)r * q + k] * x[r];
+        a = block_sum_d(a, red);
+        if (threadIdx.x == 0) out[k] = a;
+    }
+}
+
+// Start: xE = xA = a seeded uniform(-1, 1) vector, normalised; t = V'^T xE.
+__global__ void __launch_bounds__(256) k_ver_start(const ProbeDesc* __restrict__ pd, const VerDesc* __restrict__ vd,
+                                                   const float* __restrict__ stage, double* __restrict__ sc) {
+    __shared__ double red[33];
+    const VerDesc v = vd[blockIdx.x];
+    const ProbeDesc d = pd[v.probe];
+    double* xE = sc + v.s_off;
+    double* xA = xE + d.n1;
+    double* t = xA + 2 * (int64_t)d.m1 + d.n1;
+    double nn = 0.0;
+    for (int j = threadIdx.x; j < d.n1; j += blockDim.x) {
+        const uint64_t h = splitmix64(v.seed ^ ((uint64_t)j * 0x9E3779B97F4A7C15ull));
+        const double r = ((double)(h >> 11) + 0.5) * (2.0 / 9007199254740992.0) - 1.0;
+        xE[j] = r;
+        nn += r * r;
+    }
+    nn = block_sum_d(nn, red);
+    const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+    for (int j = threadIdx.x; j < d.n1; j += blockDim.x) {
+        xE[j] *= inv;
+        xA[j] = xE[j];
+    }
+    __syncthreads();
+    ver_tdot(stage + v.u_off + (int64_t)d.m1 * v.q, d.n1, v.q, xE, t, red);
+}
+
+// TRANS = false: yE = A xE - U' t, yA = A xA; TRANS = true: xE = A^T yE - V' t,
+// xA = A^T yA.  One CTA (128 threads) per 32 output rows; entries in tiles
+// of 32 x 32, four partial sums per output.
+template <bool TRANS>
+__global__ void __launch_bounds__(128) k_ver_pass(Geo g, const ProbeDesc* __restrict__ pd,
+                                                  const VerDesc* __restrict__ vd, const VerItem* __restrict__ items,
+                                                  const int32_t* __restrict__ idx, const float* __restrict__ stage,
+                                                  double* __restrict__ sc) {
+    __shared__ float As[32][33];
+    __shared__ double vs[2][32];
+    __shared__ double red[4][2][32];
+    const VerItem it = items[blockIdx.x];
+    const VerDesc v = vd[it.v];
+    const ProbeDesc d = pd[v.probe];
+    const int out_n = TRANS ? d.n1 : d.m1;
+    const int con_n = TRANS ? d.m1 : d.n1;
+    const int32_t* out_idx = idx + (TRANS ? d.cols_off : d.rows_off);
+    const int32_t* con_idx = idx + (TRANS ? d.rows_off : d.cols_off);
+    double* xE = sc + v.s_off;
+    double* xA = xE + d.n1;
+    double* yE = xA + d.n1;
+    double* yA = yE + d.m1;
+    const double* tq = yA + d.m1;
+    const double* inE = TRANS ? yE : xE;
+    const double* inA = TRANS ? yA : xA;
+    double* outE = TRANS ? xE : yE;
+    double* outA = TRANS ? xA : yA;
+    const float* Fc = stage + v.u_off + (TRANS ? (int64_t)d.m1 * v.q : 0);  // the correction's factor
+    const int t = threadIdx.x, row = t & 31, part = t >> 5;
+    double accE = 0.0, accA = 0.0;
+    for (int k0 = 0; k0 < con_n; k0 += 32) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int id = t + 128 * e;
+            int o, c;
+            if (TRANS) { o = id & 31; c = id >> 5; } else { o = id >> 5; c = id & 31; }
+            const int go = it.o0 + o, gc = k0 + c;
+            float a = 0.f;
+            if (go < out_n && gc < con_n)
+                a = TRANS ? entry(g, con_idx[gc], out_idx[go]) : entry(g, out_idx[go], con_idx[gc]);
+            As[o][c] = a;
+        }
+        if (t < 64) {
+            const int gk = k0 + (t & 31);
+            vs[t >> 5][t & 31] = gk < con_n ? (t < 32 ? inE : inA)[gk] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = part * 8; kk < part * 8 + 8; ++kk) {
+            const double a = (double)As[row][kk];
+            accE = fma(a, vs[0][kk], accE);
+            accA = fma(a, vs[1][kk], accA);
+        }
+        __syncthreads();
+    }
+    red[part][0][row] = accE;
+    red[part][1][row] = accA;
+    __syncthreads();
+    if (t < 32) {
+        const int go = it.o0 + t;
+        if (go < out_n) {
+            double sE = red[0][0][t] + red[1][0][t] + red[2][0][t] + red[3][0][t];
+            const double sA = red[0][1][t] + red[1][1][t] + red[2][1][t] + red[3][1][t];
+            for (int k = 0; k < v.q; ++k) sE -= (double)Fc[(int64_t)go * v.q + k] * tq[k];
+            outE[go] = sE;
+            outA[go] = sA;
+        }
+    }
+}
+
+// t = U'^T yE
+__global__ void __launch_bounds__(256) k_ver_ut(const ProbeDesc* __restrict__ pd, const VerDesc* __restrict__ vd,
+                                                const float* __restrict__ stage, double* __restrict__ sc) {
+    __shared__ double red[33];
+    const VerDesc v = vd[blockIdx.x];
+    const ProbeDesc d = pd[v.probe];
+    double* yE = sc + v.s_off + 2 * (int64_t)d.n1;
+    ver_tdot(stage + v.u_off, d.m1, v.q, yE, yE + 2 * (int64_t)d.m1, red);
+}
+
+// After a T pass xE = E^T E x, xA = A^T A x for the previous unit x: record
+// their norms (estimates of sigma_max^2), normalise, and form t = V'^T xE.
+__global__ void __launch_bounds__(256) k_ver_norm(const ProbeDesc* __restrict__ pd, const VerDesc* __restrict__ vd,
+                                                  const float* __restrict__ stage, double* __restrict__ sc,
+                                                  double* __restrict__ lam) {
+    __shared__ double red[33];
+    const VerDesc v = vd[blockIdx.x];
+    const ProbeDesc d = pd[v.probe];
+    double* xE = sc + v.s_off;
+    double* xA = xE + d.n1;
+    double* t = xA + 2 * (int64_t)d.m1 + d.n1;
+    double nE = 0.0, nA = 0.0;
+    for (int j = threadIdx.x; j < d.n1; j += blockDim.x) {
+        nE += xE[j] * xE[j];
+        nA += xA[j] * xA[j];
+    }
+    nE = sqrt(block_sum_d(nE, red));
+    nA = sqrt(block_sum_d(nA, red));
+    if (threadIdx.x == 0) {
+        lam[2 * blockIdx.x] = nE;
+        lam[2 * blockIdx.x + 1] = nA;
+    }
+    const double iE = nE > 0.0 ? 1.0 / nE : 0.0, iA = nA > 0.0 ? 1.0 / nA : 0.0;
+    for (int j = threadIdx.x; j < d.n1; j += blockDim.x) {
+        xE[j] *= iE;
+        xA[j] *= iA;
+    }
+    __syncthreads();
+    ver_tdot(stage + v.u_off + (int64_t)d.m1 * v.q, d.n1, v.q, xE, t, red);
+}
+
 // ------------------------------------------------------------ packing
 struct PackDesc {
     int32_t kind, r0, m, c0, n;
@@ -701,6 +885,53 @@ static vf_status run_probes(const Geo& g, ProbeBatch& B, int power_iters, cudaSt
     VF_TRY_CUDA(cudaFuncSetAttribute(k_small_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_small_svd<<<(unsigned)np, 512, smem, st>>>(B.d_pd.p, B.small.p);
     VF_TRY_CUDA(cudaGetLastError());
+    return VF_OK;
+}
+
+// The FP64 truncation check of the factorisations fds (formed into stage)
+// of batch B: ok[f] = 1 iff ||A - U' V'^T||_2 <= tol ||A||_2 (estimates);
+// est[2 f], est[2 f + 1] = the two norms.
+static vf_status verify_factors(const Geo& g, const ProbeBatch& B, const std::vector<FactorDesc>& fds,
+                                const float* stage, double tol, uint64_t seed, std::vector<uint8_t>& ok,
+                                std::vector<double>& est, cudaStream_t st) {
+    const size_t nv = fds.size();
+    ok.assign(nv, 1);
+    est.assign(2 * nv, 0.0);
+    if (nv == 0) return VF_OK;
+    std::vector<VerDesc> vd(nv);
+    std::vector<VerItem> itn, itt;
+    int64_t ns = 0;
+    for (size_t f = 0; f < nv; ++f) {
+        const ProbeDesc& p = B.pd[fds[f].probe];
+        vd[f] = VerDesc{fds[f].probe, fds[f].q, fds[f].u_off, ns, splitmix64(seed ^ (0xC0FFEEull + f))};
+        ns += 2 * (int64_t)(p.m1 + p.n1) + fds[f].q;
+        for (int32_t o = 0; o < p.m1; o += 32) itn.push_back(VerItem{(int32_t)f, o});
+        for (int32_t o = 0; o < p.n1; o += 32) itt.push_back(VerItem{(int32_t)f, o});
+    }
+    dbuf<VerDesc> dvd;
+    dbuf<VerItem> din, dit;
+    dbuf<double> sc, lam;
+    VF_TRY(dvd.upload(vd));
+    VF_TRY(din.upload(itn));
+    VF_TRY(dit.upload(itt));
+    VF_TRY(sc.alloc(std::max<int64_t>(ns, 1)));
+    VF_TRY(lam.alloc(2 * (int64_t)nv));
+    k_ver_start<<<(unsigned)nv, 256, 0, st>>>(B.d_pd.p, dvd.p, stage, sc.p);
+    VF_CHECK(!itn.empty() && !itt.empty(), VF_E_INVAL, "truncation check: empty candidate");
+    for (int it = 0; it < kVerifyIters; ++it) {
+        k_ver_pass<false><<<(unsigned)itn.size(), 128, 0, st>>>(g, B.d_pd.p, dvd.p, din.p, B.d_lists.p, stage, sc.p);
+        k_ver_ut<<<(unsigned)nv, 256, 0, st>>>(B.d_pd.p, dvd.p, stage, sc.p);
+        k_ver_pass<true><<<(unsigned)itt.size(), 128, 0, st>>>(g, B.d_pd.p, dvd.p, dit.p, B.d_lists.p, stage, sc.p);
+        k_ver_norm<<<(unsigned)nv, 256, 0, st>>>(B.d_pd.p, dvd.p, stage, sc.p, lam.p);
+    }
+    VF_TRY_CUDA(cudaGetLastError());
+    VF_TRY_CUDA(cudaMemcpyAsync(est.data(), lam.p, 2 * nv * sizeof(double), cudaMemcpyDeviceToHost, st));
+    VF_TRY_CUDA(cudaStreamSynchronize(st));
+    for (size_t f = 0; f < nv; ++f) {
+        est[2 * f] = std::sqrt(est[2 * f]);  // sigma_max(E), sigma_max(A)
+        est[2 * f + 1] = std::sqrt(est[2 * f + 1]);
+        ok[f] = est[2 * f] <= tol * est[2 * f + 1] ? 1 : 0;
+    }
     return VF_OK;
 }
 
@@ -1070,9 +1301,29 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
                     k_form_factors<<<(unsigned)fds.size(), 256, 0, st>>>(B.d_pd.p, dfd.p, dsel.p, B.Y.p, B.Z.p, B.small.p, buf->p);
                     VF_TRY_CUDA(cudaGetLastError());
                     VF_TRY_CUDA(cudaStreamSynchronize(st));
+                    std::vector<uint8_t> ver_ok(fds.size(), 1);
+                    if (o.verify) {
+                        std::vector<double> ver_est;
+                        VF_TRY(verify_factors(g, B, fds, buf->p, o.tol, o.seed ^ (uint64_t)h, ver_ok, ver_est, st));
+                    }
                     int32_t bi = (int32_t)stage_bufs.size();
                     for (size_t f = 0; f < fds.size(); ++f) {
                         int32_t id = fd_owner[f];
+                        if (!ver_ok[f]) {
+                            // the check failed: back to the rank doubling
+                            DNode& d = N[id];
+                            const ProbeDesc& p = B.pd[fds[f].probe];
+                            S.verify_failed++;
+                            d.q = 0;
+                            const bool full = p.ell == std::min(p.m1, p.n1);
+                            if (!full && 2 * d.k <= o.k_max && svd_bytes(d.k, d.st.m1, d.st.n1) < d.best_alt) {
+                                d.k *= 2;
+                                next.push_back(id);
+                            } else {
+                                S.probes_failed++;
+                            }
+                            continue;
+                        }
                         stage_ref[id] = StageRef{bi, fds[f].u_off};
                         // keep the compacted lists of this candidate
                         const ProbeDesc& p = B.pd[fds[f].probe];

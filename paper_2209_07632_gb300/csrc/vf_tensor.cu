@@ -74,8 +74,11 @@ template <int NS> struct TCfg;
 #ifndef VF_T1_RING
 #define VF_T1_RING 20480
 #endif
+#ifndef VF_T1_KMAX
+#define VF_T1_KMAX 64
+#endif
 template <> struct TCfg<1> {
-    static constexpr int PSTAGES = VF_T1_PSTAGES, RING = VF_T1_RING, CTAS = VF_T1_CTAS, REGION = 64, KMAX = 64,
+    static constexpr int PSTAGES = VF_T1_PSTAGES, RING = VF_T1_RING, CTAS = VF_T1_CTAS, REGION = 64, KMAX = VF_T1_KMAX,
                          R2 = VF_T1_R2, NREG2 = VF_T1_NREG2, TMEM = R2 * NREG2 > 128 ? 256 : 128;
 };
 template <> struct TCfg<2> {
@@ -201,7 +204,9 @@ __global__ void k_tpack(const TRec* __restrict__ recs, const HBlock* __restrict_
             }
         }
     } else if (r.kind == TREC_SVDU) {
-        // U' rows (compacted, sorted) inside [rs, re); K = rank indices [k0, k0 + K16)
+        // U' rows (compacted, sorted) inside [rs, re); B row k - k0 holds rank
+        // index k, for k in [k0, k0 + K16) (k0 < 0 when the block's T rows
+        // start inside the record)
         const int32_t* rows = aux + b.off_aux;
         for (int e = threadIdx.x; e < b.m1 * b.q; e += blockDim.x) {
             const int u = e / b.q, k = e - u * b.q;
@@ -366,14 +371,23 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
     if (!H->tplan) {
         auto P0 = std::make_unique<vf_tensor_plan>();
         P0->n_rows_x = r16(H->nf) + 32;
-        // T rows: q16 per SVD block
-        P0->h_offT16.assign(H->h_blocks.size(), -1);
+        // T rows: q16 per SVD block, the blocks of one row cluster
+        // consecutive (phase 2 reads their T rows as one A operand)
+        const std::vector<HBlock>& hb = H->h_blocks;
+        std::vector<int32_t> svd;
+        for (size_t i = 0; i < hb.size(); ++i)
+            if (hb[i].kind == VF_BLK_SVD) svd.push_back((int32_t)i);
+        std::stable_sort(svd.begin(), svd.end(), [&](int32_t x, int32_t y) {
+            if (hb[x].r0 != hb[y].r0) return hb[x].r0 < hb[y].r0;
+            if (hb[x].m != hb[y].m) return hb[x].m < hb[y].m;
+            return hb[x].c0 < hb[y].c0;
+        });
+        P0->h_offT16.assign(hb.size(), -1);
         int64_t nt = 0;
-        for (size_t i = 0; i < H->h_blocks.size(); ++i)
-            if (H->h_blocks[i].kind == VF_BLK_SVD) {
-                P0->h_offT16[i] = (int32_t)nt;
-                nt += r16(H->h_blocks[i].q);
-            }
+        for (int32_t i : svd) {
+            P0->h_offT16[i] = (int32_t)nt;
+            nt += r16(hb[i].q);
+        }
         P0->n_rows_t = nt + 16;
         H->tplan = P0.release();
     }
@@ -486,29 +500,47 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
             }
             i = j;
         }
-        // SVD pieces: K = the rank, in chunks
-        for (const Piece& pc : spieces[k]) {
-            const HBlock& b = B[pc.blk];
+        // SVD pieces: blocks of one row cluster with adjacent T rows form a
+        // run; K = the run's T rows, in chunks, each block's U' rows filling
+        // its own K range (B row = T row - the chunk's first)
+        std::vector<Piece>& sp = spieces[k];
+        std::stable_sort(sp.begin(), sp.end(),
+                         [&](const Piece& x, const Piece& y) { return P->h_offT16[x.blk] < P->h_offT16[y.blk]; });
+        for (size_t i = 0; i < sp.size();) {
+            size_t j = i + 1;
+            while (j < sp.size() && B[sp[j].blk].r0 == B[sp[i].blk].r0 && B[sp[j].blk].m == B[sp[i].blk].m &&
+                   P->h_offT16[sp[j].blk] == P->h_offT16[sp[j - 1].blk] + r16(B[sp[j - 1].blk].q))
+                ++j;
             TRec t{};
             t.kind = TREC_SVDU;
-            t.blk = pc.blk;
-            t.rs = pc.rs;
-            t.re = pc.re;
-            t.coloff = ((pc.rs - stf[k]) / 16) * 16;
+            t.rs = sp[i].rs;
+            t.re = sp[i].re;
+            t.coloff = ((t.rs - stf[k]) / 16) * 16;
             t.row_base = stf[k] + t.coloff;
-            t.N16 = r16(pc.re - t.row_base);
+            t.N16 = r16(t.re - t.row_base);
             t.a_src = 1;
             t.S = S;
-            t.hdr = 1;
             const int32_t kmax = std::min<int32_t>(cfg_kmax(S), ((kTP - kTPHdr - kTRHdr) / (t.N16 * 2 * S)) / 16 * 16);
-            for (int32_t kc = 0; kc < r16(b.q); kc += kmax) {
-                TRec u = t;
-                u.k0 = kc;
-                u.K16 = std::min(kmax, r16(b.q) - kc);
-                u.a_row0 = P->h_offT16[pc.blk] + kc;
-                recs2.push_back(u);
-                add_cost(u);
+            const int32_t base = P->h_offT16[sp[i].blk];
+            const int32_t ktot = P->h_offT16[sp[j - 1].blk] + r16(B[sp[j - 1].blk].q) - base;
+            for (int32_t kc = 0; kc < ktot; kc += kmax) {
+                const int32_t a0 = base + kc, kk = std::min(kmax, ktot - kc);
+                bool head = true;
+                for (size_t u = i; u < j; ++u) {
+                    const int32_t o = P->h_offT16[sp[u].blk], q16 = r16(B[sp[u].blk].q);
+                    if (o + q16 <= a0 || o >= a0 + kk) continue;
+                    TRec f = t;
+                    f.blk = sp[u].blk;
+                    f.K16 = kk;
+                    f.a_row0 = a0;
+                    f.k0 = a0 - o;  // rank index of B row 0 (negative when the block starts later)
+                    f.hdr = head;
+                    recs2.push_back(f);
+                    if (head) add_cost(f);
+                    head = false;
+                }
             }
+            i = j;
         }
         if ((int64_t)recs2.size() == first) {
             // a (super-)tile with no blocks still needs its epilogue: one empty record
