@@ -328,14 +328,34 @@ vf_status vf_solve(const vf_hmat* h, const float* rho, const float* E, int64_t l
 vf_status vf_solve_host(const vf_hmat* h, const float* rho, const float* E, int64_t lde, float* B, int64_t ldb,
                         int32_t R, const vf_solve_opts* opts, vf_solve_stats* stats, vf_stream stream);
 
-/* Many meshes in one persistent launch per sweep (the batching workload):
- * nmeshes problems, each with its own F, rho (device or NULL), E, B
- * (device, column-major) and R; one shared work list over all meshes' row
- * tiles.  stats: host array of nmeshes entries or NULL. */
+/* Many meshes in one launch per phase and sweep (the batching workload of
+ * Section 1's many right-hand sides, over many meshes): nmeshes problems,
+ * each with its own F, rho (device or NULL: opts->rho), E, B (device,
+ * column-major, facet order) and R.  The call solves the block-diagonal
+ * system diag(F_1 ... F_k) (vf_hmat_stack, built on the first call for
+ * this list of handles and kept until one of them is destroyed) with R =
+ * max R_k columns, so every multiply is one work list over all meshes' row
+ * tiles; convergence is judged per mesh and per column.  stats: host array
+ * of nmeshes entries (sweeps and kernels are the shared ones) or NULL.
+ * Errors: VF_E_INVAL (null or mismatched arguments), VF_E_NOCONV (B still
+ * written), VF_E_NOMEM, VF_E_CUDA, VF_E_TIMEOUT. */
 vf_status vf_solve_batched(const vf_hmat* const* F, int32_t nmeshes, const float* const* rho,
                            const float* const* E, const int64_t* lde, float* const* B, const int64_t* ldb,
                            const int32_t* R, const vf_solve_opts* opts, vf_solve_stats* stats,
                            vf_stream stream);
+
+/* The block-diagonal composition of nmeshes matrices on one device (no
+ * counterpart in the paper; it batches many meshes): facets numbered mesh
+ * after mesh (facet f of mesh k is row off_k + f, off_k = the sizes of the
+ * meshes before it), payloads copied, one segment per mesh.  A multiply or
+ * solve of the result runs all meshes in the same launches, and solves judge
+ * convergence per segment and column.  The inputs stay owned by the caller;
+ * the result is a new handle (vf_hmat_destroy).  A stacked matrix saved to a
+ * file loads back as one segment.  Errors: VF_E_INVAL, VF_E_NOMEM, VF_E_CUDA. */
+vf_status vf_hmat_stack(const vf_hmat* const* F, int32_t nmeshes, vf_hmat** out);
+
+/* Number of segments (stacked meshes) of a matrix; 1 for an assembled one, -1 for NULL. */
+int32_t vf_hmat_nsegments(const vf_hmat* h);
 
 /* ------------------------------------------------------------ save/load
  * Versioned binary file: header, block table and payload sections, each with

@@ -615,15 +615,22 @@ __global__ void k_gather_rho(const float* __restrict__ rho, float rho_u, const i
     if (t < n) dst[t] = rho ? rho[perm[t]] : rho_u;
 }
 
-// per column: ||E_c||^2 in double, one 1024-thread CTA per column; thread
-// t sums elements t, t + 1024, ..., then a fixed tree (shuffles, then the
-// warps in order), so the result does not depend on scheduling
-__global__ void __launch_bounds__(1024) k_colnorm2(const float* __restrict__ E, int64_t n, double* __restrict__ out) {
+// Convergence is tracked per "virtual column" v = s R + c: column c of the
+// rows of segment s (one mesh of a stacked matrix; a plain matrix is one
+// segment), so every mesh and every right-hand side meets its own tolerance.
+//
+// per virtual column: ||E||^2 over the segment's rows in double, one
+// 1024-thread CTA each; thread t sums elements t, t + 1024, ..., then a
+// fixed tree (shuffles, then the warps in order), so the result does not
+// depend on scheduling
+__global__ void __launch_bounds__(1024) k_colnorm2(const float* __restrict__ E, int64_t n, int R,
+                                                   const int32_t* __restrict__ seg_row0, double* __restrict__ out) {
     __shared__ double ws[32];
-    const int c = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int v = blockIdx.x, c = v % R, sg = v / R, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float* e = E + (int64_t)c * n;
+    const int64_t r1 = seg_row0[sg + 1];
     double s = 0;
-    for (int64_t t = threadIdx.x; t < n; t += 1024) {
+    for (int64_t t = seg_row0[sg] + threadIdx.x; t < r1; t += 1024) {
         const double v = e[t];
         s += v * v;
     }
@@ -633,7 +640,7 @@ __global__ void __launch_bounds__(1024) k_colnorm2(const float* __restrict__ E, 
     if (threadIdx.x == 0) {
         double sum = 0;
         for (int w = 0; w < 32; ++w) sum += ws[w];
-        out[c] = sum;
+        out[v] = sum;
     }
 }
 
@@ -650,6 +657,7 @@ struct LoopState {
 // CTA (one warp per column, fixed order): the CTA always sets the while
 // condition, and `iter < max_iter` bounds the loop.
 __global__ void __launch_bounds__(1024) k_sweep_reduce(const double* __restrict__ colpart, int64_t ntiles, int R,
+                                                       int nseg, const int32_t* __restrict__ seg_tile0,
                                                        const double* __restrict__ enorm2, double* __restrict__ colres,
                                                        LoopState* st, float* const* bufs, const float** xsel,
                                                        float** ysel, cudaGraphConditionalHandle handle,
@@ -659,13 +667,14 @@ __global__ void __launch_bounds__(1024) k_sweep_reduce(const double* __restrict_
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     int mine = 0;
-    for (int c = warp; c < R; c += nw) {
+    for (int v = warp; v < R * nseg; v += nw) {
+        const int c = v % R, sg = v / R;
         double s = 0;
-        for (int64_t t = lane; t < ntiles; t += 32) s += colpart[(int64_t)c * ntiles + t];
+        for (int64_t t = seg_tile0[sg] + lane; t < seg_tile0[sg + 1]; t += 32) s += colpart[(int64_t)c * ntiles + t];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) {
-            colres[c] = s;
-            if (s > st->rtol2 * enorm2[c]) mine++;
+            colres[v] = s;
+            if (s > st->rtol2 * enorm2[v]) mine++;
         }
     }
     if (lane == 0 && mine) atomicAdd(&s_unconv, mine);
@@ -785,6 +794,12 @@ vf_status vf_hmat::upload_all() {
     // load); every block's row range is a union of consecutive tiles.
     std::vector<vf::HBlock>& B = h_blocks;
     const int64_t ntiles = (int64_t)h_tile_first.size();
+    if (h_seg_row0.empty()) {
+        h_seg_row0 = {0, (int32_t)nf};
+        h_seg_tile0 = {0, (int32_t)ntiles};
+    }
+    VF_TRY(seg_row0.upload(h_seg_row0));
+    VF_TRY(seg_tile0.upload(h_seg_tile0));
     std::vector<int32_t> haux;
     if (n_aux > 0) VF_TRY(aux.download(haux));
     std::vector<int32_t> tile_of_row(nf, -1);
@@ -1143,8 +1158,8 @@ static vf_status ws_get(const vf_hmat* h, int R, int prec, Workspace** out) {
     VF_TRY(w->Tbuf.alloc((int64_t)w->npanels * w->RB * nT));
     VF_TRY(w->part.alloc((int64_t)w->npanels * w->RB * std::max<int64_t>(h->n_part_slots, 1)));
     VF_TRY(w->colpart.alloc(std::max<int64_t>(ntiles * R, 1)));
-    VF_TRY(w->enorm2.alloc(R));
-    VF_TRY(w->colres.alloc(R));
+    VF_TRY(w->enorm2.alloc((int64_t)R * h->nseg()));
+    VF_TRY(w->colres.alloc((int64_t)R * h->nseg()));
     VF_TRY(w->loop.alloc(1));
     VF_TRY(w->status.alloc(1));
     VF_TRY_CUDA(cudaMemset(w->status.p, 0, sizeof(int)));
@@ -1337,35 +1352,39 @@ static vf_status tensor_ws(const vf_hmat* h, Workspace* w) {
     return VF_OK;
 }
 
-// Columns whose last update exceeded rtol ||E||: one CTA per column sums
-// the sweep's per-tile partials in a fixed order (threads stride the
-// tiles, then shuffles, then the warps in order) into colres[c], and the
-// last CTA to finish (an acq_rel ticket) counts the unconverged columns.
+// Virtual columns whose last update exceeded rtol ||E||: one CTA per
+// virtual column sums the sweep's per-part partials of its segment in a
+// fixed order (threads stride the parts, then shuffles, then the warps in
+// order) into colres[v], and the last CTA to finish (an acq_rel ticket)
+// counts the unconverged ones.
 __global__ void __launch_bounds__(256) k_unconverged(const double* __restrict__ colpart, int64_t ntiles, int R,
+                                                     int nseg, const int32_t* __restrict__ seg_part0,
                                                      const double* __restrict__ enorm2, double rtol2,
                                                      double* __restrict__ colres, int* __restrict__ count,
                                                      int* __restrict__ ticket) {
     __shared__ double ws[8];
     __shared__ int s_last;
-    const int c = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int v = blockIdx.x, c = v % R, sg = v / R, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int NV = R * nseg;
     double s = 0;
-    for (int64_t t = threadIdx.x; t < ntiles; t += blockDim.x) s += colpart[(int64_t)c * ntiles + t];
+    for (int64_t t = seg_part0[sg] + threadIdx.x; t < seg_part0[sg + 1]; t += blockDim.x)
+        s += colpart[(int64_t)c * ntiles + t];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) ws[warp] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
         double sum = 0;
         for (int w = 0; w < 8; ++w) sum += ws[w];
-        colres[c] = sum;
+        colres[v] = sum;
         cuda::atomic_ref<int, cuda::thread_scope_device> tk(*ticket);
-        s_last = tk.fetch_add(1, cuda::memory_order_acq_rel) == R - 1;
+        s_last = tk.fetch_add(1, cuda::memory_order_acq_rel) == NV - 1;
     }
     __syncthreads();
     if (!s_last) return;
     // the last CTA: every colres is visible (acquired through the ticket)
     int mine = 0;
-    for (int cc = threadIdx.x; cc < R; cc += blockDim.x)
-        if (__ldcg(colres + cc) > rtol2 * enorm2[cc]) mine++;
+    for (int vv = threadIdx.x; vv < NV; vv += blockDim.x)
+        if (__ldcg(colres + vv) > rtol2 * enorm2[vv]) mine++;
     for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
     __shared__ int wc[8];
     if (lane == 0) wc[warp] = mine;
@@ -1387,8 +1406,9 @@ static vf_status tensor_jacobi_loop(const vf_hmat* h, Workspace* w, int max_iter
     const int64_t n = h->nf, nR = n * (int64_t)w->R;
     const int64_t ntiles = tensor_parts(h, 1);
     const int64_t bx = tensor_panel_bytes_x(h);
+    const int NV = w->R * h->nseg();
     VF_TRY_CUDA(cudaMemcpyAsync(w->Bt[0].p, w->Et.p, nR * 4, cudaMemcpyDeviceToDevice, st));
-    k_colnorm2<<<(unsigned)w->R, 1024, 0, st>>>(w->Et.p, n, w->enorm2.p);
+    k_colnorm2<<<(unsigned)NV, 1024, 0, st>>>(w->Et.p, n, w->R, h->seg_row0.p, w->enorm2.p);
     for (int p = 0; p < w->tpanels; ++p)
         VF_TRY(tensor_to_panel(h, w->Et.p, n, nullptr, w->R, p * kTensorPanel, w->xpan[0].p + (size_t)p * bx, nullptr,
                                st));
@@ -1411,8 +1431,9 @@ static vf_status tensor_jacobi_loop(const vf_hmat* h, Workspace* w, int max_iter
             VF_TRY(tensor_multiply(h, 1, w->xpan[cur].p + (size_t)p * bx, nullptr, w->tpan.p, nullptr, ep,
                                    w->status.p, st));
         }
-        k_unconverged<<<(unsigned)w->R, 256, 0, st>>>(w->colpart.p, ntiles, w->R, w->enorm2.p, rtol * rtol,
-                                                      w->colres.p, w->tcount.p, w->tcount.p + 1);
+        k_unconverged<<<(unsigned)NV, 256, 0, st>>>(w->colpart.p, ntiles, w->R, h->nseg(), tensor_seg_parts(h, 1),
+                                                    w->enorm2.p, rtol * rtol, w->colres.p, w->tcount.p,
+                                                    w->tcount.p + 1);
         VF_TRY_CUDA(cudaGetLastError());
         *kernels += w->tpanels * tensor_kernels(h, 1) + 1;
         int hc = 0;
@@ -1463,8 +1484,9 @@ static vf_status tensor_residual(const vf_hmat* h, Workspace* w, const float* B,
         ep.ntiles = ntiles;
         VF_TRY(tensor_multiply(h, 2, xh, xl, w->tsplit[0].p, w->tsplit[1].p, ep, w->status.p, st));
     }
-    k_unconverged<<<(unsigned)w->R, 256, 0, st>>>(w->colpart.p, ntiles, w->R, w->enorm2.p, 0.0, w->colres.p,
-                                                  w->tcount.p, w->tcount.p + 1);
+    k_unconverged<<<(unsigned)(w->R * h->nseg()), 256, 0, st>>>(w->colpart.p, ntiles, w->R, h->nseg(),
+                                                                tensor_seg_parts(h, 2), w->enorm2.p, 0.0, w->colres.p,
+                                                                w->tcount.p, w->tcount.p + 1);
     VF_TRY_CUDA(cudaGetLastError());
     *kernels += w->tpanels * (1 + tensor_kernels(h, 2)) + 1;
     return VF_OK;
@@ -1517,8 +1539,8 @@ static vf_status ensure_graph(const vf_hmat* h, Workspace* w) {
     vf_status s =
         launch_multiply(h, w->prec, w, MODE_JACOBI, w->xsel.p, w->ysel.p, nullptr, nullptr, w->Et.p, w->rho_t.p, cs);
     const int64_t ntiles = (int64_t)h->h_tile_first.size();
-    k_sweep_reduce<<<1, 1024, 0, cs>>>(
-        w->colpart.p, ntiles, w->R, w->enorm2.p, w->colres.p, w->loop.p, w->bufs.p, w->xsel.p, w->ysel.p, w->handle, 1);
+    k_sweep_reduce<<<1, 1024, 0, cs>>>(w->colpart.p, ntiles, w->R, h->nseg(), h->seg_tile0.p, w->enorm2.p,
+                                       w->colres.p, w->loop.p, w->bufs.p, w->xsel.p, w->ysel.p, w->handle, 1);
     cudaError_t e1 = cudaGetLastError();
     cudaGraph_t outg;
     cudaError_t e2 = cudaStreamEndCapture(cs, &outg);
@@ -1545,18 +1567,19 @@ static vf_status jacobi_loop(const vf_hmat* h, Workspace* w, int max_iter, doubl
     const int64_t n = h->nf, nR = n * (int64_t)w->R;
     VF_TRY(ensure_graph(h, w));
     // B_0 = E
+    const int NV = w->R * h->nseg();
     VF_TRY_CUDA(cudaMemcpyAsync(w->Bt[0].p, w->Et.p, nR * 4, cudaMemcpyDeviceToDevice, st));
-    k_colnorm2<<<(unsigned)w->R, 1024, 0, st>>>(w->Et.p, n, w->enorm2.p);
+    k_colnorm2<<<(unsigned)NV, 1024, 0, st>>>(w->Et.p, n, w->R, h->seg_row0.p, w->enorm2.p);
     k_loop_init<<<1, 1, 0, st>>>(w->loop.p, max_iter, rtol * rtol, w->bufs.p, w->xsel.p, w->ysel.p);
     VF_TRY_CUDA(cudaGetLastError());
     if (max_iter > 0) VF_TRY_CUDA(cudaGraphLaunch(w->graph, st));
     if (hstate) {
         VF_TRY_CUDA(cudaMemcpyAsync(hstate, w->loop.p, sizeof(LoopState), cudaMemcpyDeviceToHost, st));
         if (colres) {
-            colres->resize(w->R);
-            en2->resize(w->R);
-            VF_TRY_CUDA(cudaMemcpyAsync(colres->data(), w->colres.p, w->R * 8, cudaMemcpyDeviceToHost, st));
-            VF_TRY_CUDA(cudaMemcpyAsync(en2->data(), w->enorm2.p, w->R * 8, cudaMemcpyDeviceToHost, st));
+            colres->resize(NV);
+            en2->resize(NV);
+            VF_TRY_CUDA(cudaMemcpyAsync(colres->data(), w->colres.p, NV * 8, cudaMemcpyDeviceToHost, st));
+            VF_TRY_CUDA(cudaMemcpyAsync(en2->data(), w->enorm2.p, NV * 8, cudaMemcpyDeviceToHost, st));
         }
         VF_TRY_CUDA(cudaStreamSynchronize(st));
     }
@@ -1566,9 +1589,14 @@ static vf_status jacobi_loop(const vf_hmat* h, Workspace* w, int max_iter, doubl
 }  // namespace vf
 
 // ============================================================ C ABI
+namespace vf {
+void drop_stacks_of(const vf_hmat* h);
+}
+
 extern "C" void vf_hmat_destroy(vf_hmat* h) {
     if (!h) return;
     device_guard g(h->device);
+    vf::drop_stacks_of(h);
     vf::drop_cache(h);
     delete h;
 }
@@ -1667,11 +1695,9 @@ extern "C" vf_status vf_apply_tree_static(const vf_hmat* h, vf_precision prec, c
     return VF_OK;
 }
 
-extern "C" vf_status vf_solve(const vf_hmat* h, const float* rho, const float* E, int64_t lde, float* B, int64_t ldb,
-                              int32_t R, const vf_solve_opts* opts_in, vf_solve_stats* stats, vf_stream stream) {
-    clear_error();
-    VF_CHECK(h && E && B, VF_E_INVAL, "vf_solve: null argument");
-    VF_CHECK(R >= 1 && lde >= h->nf && ldb >= h->nf, VF_E_INVAL, "vf_solve: need R >= 1 and ld >= N");
+namespace vf {
+
+static vf_solve_opts solve_defaults(const vf_solve_opts* in) {
     vf_solve_opts o{};
     o.rtol = 1e-6;
     o.max_iter = 100;
@@ -1681,122 +1707,126 @@ extern "C" vf_status vf_solve(const vf_hmat* h, const float* rho, const float* E
     o.inner_rtol = 1e-3;
     o.clamp = 0;
     o.rho = 0.f;
-    if (opts_in) o = *opts_in;
+    if (in) o = *in;
     if (o.max_iter <= 0) o.max_iter = 100;
     if (o.max_refine <= 0) o.max_refine = 8;
     if (!(o.inner_rtol > 0)) o.inner_rtol = 1e-3;
-    VF_CHECK(o.rtol > 0, VF_E_INVAL, "vf_solve: rtol must be positive");
-    VF_TRY(vf::check_prec(h, o.precision));
-    device_guard g(h->device);
-    cudaStream_t st = (cudaStream_t)stream;
-    const int64_t n = h->nf, nR = n * (int64_t)R;
-    vf::Workspace* w;
-    VF_TRY(vf::ws_get(h, R, o.precision, &w));
-    VF_TRY_CUDA(cudaStreamWaitEvent(st, w->done, 0));
-    vf::k_gather_cols<<<1024, 256, 0, st>>>(E, lde, h->perm.p, n, R, w->Et.p);
-    vf::k_gather_rho<<<(unsigned)vf::ceil_div(n, 256), 256, 0, st>>>(rho, o.rho, h->perm.p, n, w->rho_t.p);
-    VF_TRY_CUDA(cudaGetLastError());
-    vf_solve_stats S{};
-    vf::LoopState ls{};
-    std::vector<double> colres, en2;
-    const bool refine = o.refine && o.precision != VF_PREC_FP32;
+    return o;
+}
+
+// What the solve leaves: the result (tree order, column-major, ld nf) and,
+// per virtual column (segment, column), its final relative residual.
+struct SolveOut {
     float* result = nullptr;
-    vf_status status = VF_OK;
-    const int kps = vf::multiply_kernels(h) + 1;  // one sweep: the multiply and the column reduction
-    S.kernels = 3;                                // gather E, gather rho, scatter B
-    if (!refine) {
-        VF_TRY(vf::jacobi_loop(h, w, o.max_iter, o.rtol, st, &ls, &colres, &en2));
-        S.sweeps = ls.iter;
-        S.kernels += 2 + ls.iter * kps;           // column norms, loop init, the sweeps
-        result = w->Bt[ls.parity].p;
-        double mx = 0;
+    std::vector<double> rel;
+    std::vector<char> conv;
+};
+
+// The solve on tree-ordered data (w->Et = E, w->rho_t = rho set): Jacobi
+// in the requested precision, or mixed-precision iterative refinement
+// around low-precision Jacobi sweeps.  Adds sweeps, refinements and
+// kernel counts to S.
+static vf_status solve_core(const vf_hmat* h, const vf_solve_opts& o, int R, cudaStream_t st, Workspace* w,
+                            vf_solve_stats* S, SolveOut* out) {
+    const int64_t n = h->nf, nR = n * (int64_t)R;
+    const int nseg = h->nseg(), NV = R * nseg;
+    const bool refine = o.refine && o.precision != VF_PREC_FP32;
+    const int kps = multiply_kernels(h) + 1;  // one sweep: the multiply and the column reduction
+    out->rel.assign(NV, 0.0);
+    out->conv.assign(NV, 1);
+    auto judge = [&](const std::vector<double>& res2, const std::vector<double>& en2) {
         bool ok = true;
-        for (int c = 0; c < R; ++c) {
-            double rel = en2[c] > 0 ? std::sqrt(colres[c] / en2[c]) : 0.0;
-            mx = std::max(mx, rel);
-            ok = ok && colres[c] <= o.rtol * o.rtol * en2[c];
+        for (int v = 0; v < NV; ++v) {
+            out->rel[v] = en2[v] > 0 ? std::sqrt(res2[v] / en2[v]) : 0.0;
+            out->conv[v] = res2[v] <= o.rtol * o.rtol * en2[v];
+            ok = ok && out->conv[v];
         }
-        S.max_rel_residual = mx;
-        S.converged = ok;
-        if (!ok) status = VF_E_NOCONV;
-    } else {
-        // Mixed-precision iterative refinement.  Xt keeps E, Yt accumulates B.
-        vf::Workspace* w32;
-        VF_TRY(vf::ws_get(h, R, VF_PREC_FP32, &w32));
-        VF_TRY_CUDA(cudaMemcpyAsync(w->Xt.p, w->Et.p, nR * 4, cudaMemcpyDeviceToDevice, st));  // E (tree order)
-        VF_TRY_CUDA(cudaMemsetAsync(w->Yt.p, 0, nR * 4, st));                                 // B = 0
-        std::vector<double> en(R);
-        vf::k_colnorm2<<<(unsigned)R, 1024, 0, st>>>(w->Xt.p, n, w->enorm2.p);
-        S.kernels += 1;
-        VF_TRY_CUDA(cudaMemcpyAsync(en.data(), w->enorm2.p, R * 8, cudaMemcpyDeviceToHost, st));
-        VF_TRY_CUDA(cudaStreamSynchronize(st));
-        // residual workspace shares the FP32 factors; use w32's selection slots
-        VF_TRY_CUDA(cudaMemcpyAsync(w32->rho_t.p, w->rho_t.p, n * 4, cudaMemcpyDeviceToDevice, st));
-        double mx = 0;
-        bool ok = false;
-        const bool tensor = vf::use_tensor(h, o.precision, R);
-        for (int ref = 0; ref <= o.max_refine; ++ref) {
-            // r = E - B + rho F B  (FP32 factors, FP64 accumulation); the
-            // residual (written to Et) becomes the next inner right-hand side.
-            // With B = 0 (the first pass) r = E exactly, already in Et.
-            std::vector<double> rr(R, 0.0);
-            if (ref == 0) {
-                rr = en;
-            } else if (tensor) {
-                int kk = 0;
-                VF_TRY(vf::tensor_residual(h, w, w->Yt.p, w->Xt.p, w->Et.p, st, &kk));
-                S.kernels += kk;
-                VF_TRY_CUDA(cudaMemcpyAsync(rr.data(), w->colres.p, R * 8, cudaMemcpyDeviceToHost, st));
-                VF_TRY_CUDA(cudaStreamSynchronize(st));
-            } else {
-                VF_TRY(vf::launch_multiply(h, VF_PREC_FP32, w32, vf::MODE_RESID, nullptr, nullptr, w->Yt.p, w->Et.p,
-                                           w->Xt.p, w32->rho_t.p, st));
-                S.kernels += kps - 1;
-                const int64_t ntiles = (int64_t)h->h_tile_first.size();
-                std::vector<double> part((size_t)ntiles * R);
-                VF_TRY_CUDA(cudaMemcpyAsync(part.data(), w32->colpart.p, part.size() * 8, cudaMemcpyDeviceToHost, st));
-                VF_TRY_CUDA(cudaStreamSynchronize(st));
-                for (int c = 0; c < R; ++c)
-                    for (int64_t tt = 0; tt < ntiles; ++tt) rr[c] += part[(size_t)c * ntiles + tt];
-            }
-            mx = 0;
-            ok = true;
-            for (int c = 0; c < R; ++c) {
-                double rel = en[c] > 0 ? std::sqrt(rr[c] / en[c]) : 0.0;
-                mx = std::max(mx, rel);
-                ok = ok && rr[c] <= o.rtol * o.rtol * en[c];
-            }
-            if (ok || ref == o.max_refine) break;
-            S.refinements++;
-            // delta = (I - rho F_lowprec)^{-1} r, then B += delta
-            vf::LoopState l2{};
-            if (tensor) {
-                int kk = 0;
-                VF_TRY(vf::tensor_jacobi_loop(h, w, o.max_iter, o.inner_rtol, st, &l2.iter, &l2.parity, &kk));
-                S.kernels += kk + 1;  // the tensor sweeps, then the update
-            } else {
-                VF_TRY(vf::jacobi_loop(h, w, o.max_iter, o.inner_rtol, st, &ls, nullptr, nullptr));
-                VF_TRY_CUDA(cudaMemcpyAsync(&l2, w->loop.p, sizeof(l2), cudaMemcpyDeviceToHost, st));
-                VF_TRY_CUDA(cudaStreamSynchronize(st));
-                S.kernels += 2 + l2.iter * kps + 1;  // column norms, loop init, sweeps, the update
-            }
-            S.sweeps += l2.iter;
-            vf::k_axpy_inplace<<<1024, 256, 0, st>>>(w->Yt.p, w->Bt[l2.parity].p, nR);
-            VF_TRY_CUDA(cudaGetLastError());
-        }
-        S.max_rel_residual = mx;
-        S.converged = ok;
-        result = w->Yt.p;
-        if (!ok) status = VF_E_NOCONV;
+        return ok;
+    };
+    if (!refine) {
+        LoopState ls{};
+        std::vector<double> colres, en2;
+        VF_TRY(jacobi_loop(h, w, o.max_iter, o.rtol, st, &ls, &colres, &en2));
+        S->sweeps = ls.iter;
+        S->kernels += 2 + ls.iter * kps;  // column norms, loop init, the sweeps
+        out->result = w->Bt[ls.parity].p;
+        judge(colres, en2);
+        return VF_OK;
     }
-    vf::k_scatter_cols<<<1024, 256, 0, st>>>(result, h->perm.p, n, R, B, ldb, o.clamp);
-    VF_TRY_CUDA(cudaGetLastError());
-    // a bounded device-side wait that gave up left VF_E_TIMEOUT in a status word
+    // Mixed-precision iterative refinement.  Xt keeps E, Yt accumulates B.
+    Workspace* w32;
+    VF_TRY(ws_get(h, R, VF_PREC_FP32, &w32));
+    VF_TRY_CUDA(cudaMemcpyAsync(w->Xt.p, w->Et.p, nR * 4, cudaMemcpyDeviceToDevice, st));  // E (tree order)
+    VF_TRY_CUDA(cudaMemsetAsync(w->Yt.p, 0, nR * 4, st));                                 // B = 0
+    std::vector<double> en(NV);
+    k_colnorm2<<<(unsigned)NV, 1024, 0, st>>>(w->Xt.p, n, R, h->seg_row0.p, w->enorm2.p);
+    S->kernels += 1;
+    VF_TRY_CUDA(cudaMemcpyAsync(en.data(), w->enorm2.p, NV * 8, cudaMemcpyDeviceToHost, st));
+    VF_TRY_CUDA(cudaStreamSynchronize(st));
+    // residual workspace shares the FP32 factors; use w32's selection slots
+    VF_TRY_CUDA(cudaMemcpyAsync(w32->rho_t.p, w->rho_t.p, n * 4, cudaMemcpyDeviceToDevice, st));
+    const bool tensor = use_tensor(h, o.precision, R);
+    const int64_t ntiles = (int64_t)h->h_tile_first.size();
+    for (int ref = 0; ref <= o.max_refine; ++ref) {
+        // r = E - B + rho F B  (FP32 factors, FP64 accumulation); the
+        // residual (written to Et) becomes the next inner right-hand side.
+        // With B = 0 (the first pass) r = E exactly, already in Et.
+        std::vector<double> rr(NV, 0.0);
+        if (ref == 0) {
+            rr = en;
+        } else if (tensor) {
+            int kk = 0;
+            VF_TRY(tensor_residual(h, w, w->Yt.p, w->Xt.p, w->Et.p, st, &kk));
+            S->kernels += kk;
+            VF_TRY_CUDA(cudaMemcpyAsync(rr.data(), w->colres.p, NV * 8, cudaMemcpyDeviceToHost, st));
+            VF_TRY_CUDA(cudaStreamSynchronize(st));
+        } else {
+            VF_TRY(launch_multiply(h, VF_PREC_FP32, w32, MODE_RESID, nullptr, nullptr, w->Yt.p, w->Et.p, w->Xt.p,
+                                   w32->rho_t.p, st));
+            S->kernels += kps - 1;
+            std::vector<double> part((size_t)ntiles * R);
+            VF_TRY_CUDA(cudaMemcpyAsync(part.data(), w32->colpart.p, part.size() * 8, cudaMemcpyDeviceToHost, st));
+            VF_TRY_CUDA(cudaStreamSynchronize(st));
+            for (int v = 0; v < NV; ++v) {
+                const int c = v % R, sg = v / R;
+                for (int32_t tt = h->h_seg_tile0[sg]; tt < h->h_seg_tile0[sg + 1]; ++tt)
+                    rr[v] += part[(size_t)c * ntiles + tt];
+            }
+        }
+        const bool ok = judge(rr, en);
+        if (ok || ref == o.max_refine) break;
+        S->refinements++;
+        // delta = (I - rho F_lowprec)^{-1} r, then B += delta
+        LoopState l2{};
+        if (tensor) {
+            int kk = 0;
+            VF_TRY(tensor_jacobi_loop(h, w, o.max_iter, o.inner_rtol, st, &l2.iter, &l2.parity, &kk));
+            S->kernels += kk + 1;  // the tensor sweeps, then the update
+        } else {
+            LoopState ls{};
+            VF_TRY(jacobi_loop(h, w, o.max_iter, o.inner_rtol, st, &ls, nullptr, nullptr));
+            VF_TRY_CUDA(cudaMemcpyAsync(&l2, w->loop.p, sizeof(l2), cudaMemcpyDeviceToHost, st));
+            VF_TRY_CUDA(cudaStreamSynchronize(st));
+            S->kernels += 2 + l2.iter * kps + 1;  // column norms, loop init, sweeps, the update
+        }
+        S->sweeps += l2.iter;
+        k_axpy_inplace<<<1024, 256, 0, st>>>(w->Yt.p, w->Bt[l2.parity].p, nR);
+        VF_TRY_CUDA(cudaGetLastError());
+    }
+    out->result = w->Yt.p;
+    return VF_OK;
+}
+
+// A bounded device-side wait that gave up left VF_E_TIMEOUT in a status
+// word of the solve's workspaces: read (and clear) them once the stream has
+// drained.
+static vf_status solve_status(const vf_hmat* h, Workspace* w, int R, bool refine, cudaStream_t st,
+                              const char* who) {
     int ws[2] = {0, 0};
     VF_TRY_CUDA(cudaMemcpyAsync(&ws[0], w->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    vf::Workspace* wr = nullptr;
+    Workspace* wr = nullptr;
     if (refine) {
-        VF_TRY(vf::ws_get(h, R, VF_PREC_FP32, &wr));
+        VF_TRY(ws_get(h, R, VF_PREC_FP32, &wr));
         VF_TRY_CUDA(cudaMemcpyAsync(&ws[1], wr->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     }
     VF_TRY_CUDA(cudaEventRecord(w->done, st));
@@ -1805,12 +1835,158 @@ extern "C" vf_status vf_solve(const vf_hmat* h, const float* rho, const float* E
         cudaMemsetAsync(w->status.p, 0, sizeof(int), st);
         if (wr) cudaMemsetAsync(wr->status.p, 0, sizeof(int), st);
         cudaStreamSynchronize(st);
-        vf::set_error("vf_solve: a bounded device-side wait gave up");
+        set_error("%s: a bounded device-side wait gave up", who);
         return VF_E_TIMEOUT;
     }
+    return VF_OK;
+}
+
+// ---- many meshes: one stacked (block-diagonal) matrix, one launch per phase
+// Per mesh of a batched solve: where its facet-order E, B and rho live.
+struct SegIO {
+    const float* E;
+    float* B;
+    const float* rho;
+    int64_t lde, ldb;
+    int32_t R, pad;
+};
+
+// Et (tree order, N x R over all meshes) from each mesh's E; columns past a
+// mesh's own R are zero.  Facet f of mesh s is stacked row seg_row0[s] + f.
+__global__ void k_gather_seg(const SegIO* __restrict__ io, const int32_t* __restrict__ seg_row0, int nseg,
+                             const int32_t* __restrict__ perm, int64_t n, int R, float* __restrict__ dst) {
+    const int64_t tot = n * (int64_t)R;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / n, t = e - c * n;
+        const int32_t f = perm[t];
+        int lo = 0, hi = nseg - 1;  // the segment of stacked facet f
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (seg_row0[mid] <= f) lo = mid; else hi = mid - 1;
+        }
+        const SegIO s = io[lo];
+        dst[e] = c < s.R ? s.E[c * s.lde + (f - seg_row0[lo])] : 0.f;
+    }
+}
+
+__global__ void k_gather_rho_seg(const SegIO* __restrict__ io, const int32_t* __restrict__ seg_row0, int nseg,
+                                 float rho_u, const int32_t* __restrict__ perm, int64_t n, float* __restrict__ dst) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int32_t f = perm[t];
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (seg_row0[mid] <= f) lo = mid; else hi = mid - 1;
+    }
+    dst[t] = io[lo].rho ? io[lo].rho[f - seg_row0[lo]] : rho_u;
+}
+
+__global__ void k_scatter_seg(const float* __restrict__ src, const SegIO* __restrict__ io,
+                              const int32_t* __restrict__ seg_row0, int nseg, const int32_t* __restrict__ perm,
+                              int64_t n, int R, int clamp) {
+    const int64_t tot = n * (int64_t)R;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / n, t = e - c * n;
+        const int32_t f = perm[t];
+        int lo = 0, hi = nseg - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (seg_row0[mid] <= f) lo = mid; else hi = mid - 1;
+        }
+        const SegIO s = io[lo];
+        if (c >= s.R) continue;
+        float v = src[e];
+        if (clamp) v = fmaxf(v, 0.f);
+        s.B[c * s.ldb + (f - seg_row0[lo])] = v;
+    }
+}
+
+// Stacked matrices built by vf_solve_batched, keyed by the handles' ids
+// (dropped when any of them is destroyed).
+struct StackEntry {
+    std::vector<uint64_t> uids;
+    std::unique_ptr<vf_hmat, void (*)(vf_hmat*)> h{nullptr, vf_hmat_destroy};
+    dbuf<SegIO> io;
+};
+static std::mutex g_stack_mu;
+static std::vector<std::unique_ptr<StackEntry>> g_stacks;
+
+void drop_stacks_of(const vf_hmat* h) {
+    std::vector<std::unique_ptr<StackEntry>> gone;
+    {
+        std::lock_guard<std::mutex> lk(g_stack_mu);
+        for (auto it = g_stacks.begin(); it != g_stacks.end();) {
+            if (std::find((*it)->uids.begin(), (*it)->uids.end(), h->uid) != (*it)->uids.end()) {
+                gone.push_back(std::move(*it));
+                it = g_stacks.erase(it);
+            } else {
+                ++it;
+            }
+        }
+    }
+}
+
+static vf_status stack_for(const vf_hmat* const* F, int32_t k, StackEntry** out) {
+    std::vector<uint64_t> uids(k);
+    for (int32_t i = 0; i < k; ++i) uids[i] = F[i]->uid;
+    std::lock_guard<std::mutex> lk(g_stack_mu);
+    for (auto& e : g_stacks)
+        if (e->uids == uids) {
+            *out = e.get();
+            return VF_OK;
+        }
+    auto e = std::make_unique<StackEntry>();
+    e->uids = uids;
+    vf_hmat* s = nullptr;
+    VF_TRY(vf_hmat_stack(F, k, &s));
+    e->h.reset(s);
+    VF_TRY(e->io.alloc(k));
+    *out = e.get();
+    g_stacks.push_back(std::move(e));
+    return VF_OK;
+}
+
+}  // namespace vf
+
+extern "C" vf_status vf_solve(const vf_hmat* h, const float* rho, const float* E, int64_t lde, float* B, int64_t ldb,
+                              int32_t R, const vf_solve_opts* opts_in, vf_solve_stats* stats, vf_stream stream) {
+    clear_error();
+    VF_CHECK(h && E && B, VF_E_INVAL, "vf_solve: null argument");
+    VF_CHECK(R >= 1 && lde >= h->nf && ldb >= h->nf, VF_E_INVAL, "vf_solve: need R >= 1 and ld >= N");
+    const vf_solve_opts o = vf::solve_defaults(opts_in);
+    VF_CHECK(o.rtol > 0, VF_E_INVAL, "vf_solve: rtol must be positive");
+    VF_TRY(vf::check_prec(h, o.precision));
+    device_guard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = h->nf;
+    vf::Workspace* w;
+    VF_TRY(vf::ws_get(h, R, o.precision, &w));
+    VF_TRY_CUDA(cudaStreamWaitEvent(st, w->done, 0));
+    vf::k_gather_cols<<<1024, 256, 0, st>>>(E, lde, h->perm.p, n, R, w->Et.p);
+    vf::k_gather_rho<<<(unsigned)vf::ceil_div(n, 256), 256, 0, st>>>(rho, o.rho, h->perm.p, n, w->rho_t.p);
+    VF_TRY_CUDA(cudaGetLastError());
+    vf_solve_stats S{};
+    S.kernels = 3;  // gather E, gather rho, scatter B
+    vf::SolveOut so;
+    VF_TRY(vf::solve_core(h, o, R, st, w, &S, &so));
+    double mx = 0;
+    bool ok = true;
+    for (size_t v = 0; v < so.rel.size(); ++v) {
+        mx = std::max(mx, so.rel[v]);
+        ok = ok && so.conv[v];
+    }
+    S.max_rel_residual = mx;
+    S.converged = ok;
+    vf::k_scatter_cols<<<1024, 256, 0, st>>>(so.result, h->perm.p, n, R, B, ldb, o.clamp);
+    VF_TRY_CUDA(cudaGetLastError());
+    VF_TRY(vf::solve_status(h, w, R, o.refine && o.precision != VF_PREC_FP32, st, "vf_solve"));
     if (stats) *stats = S;
-    if (status == VF_E_NOCONV) vf::set_error("vf_solve: not converged (max rel residual %.3e)", S.max_rel_residual);
-    return status;
+    if (!ok) {
+        vf::set_error("vf_solve: not converged (max rel residual %.3e)", S.max_rel_residual);
+        return VF_E_NOCONV;
+    }
+    return VF_OK;
 }
 
 extern "C" vf_status vf_solve_host(const vf_hmat* h, const float* rho, const float* E, int64_t lde, float* B,
@@ -1852,16 +2028,66 @@ extern "C" vf_status vf_solve_host(const vf_hmat* h, const float* rho, const flo
 
 extern "C" vf_status vf_solve_batched(const vf_hmat* const* F, int32_t nmeshes, const float* const* rho,
                                       const float* const* E, const int64_t* lde, float* const* B, const int64_t* ldb,
-                                      const int32_t* R, const vf_solve_opts* opts, vf_solve_stats* stats,
+                                      const int32_t* R, const vf_solve_opts* opts_in, vf_solve_stats* stats,
                                       vf_stream stream) {
     clear_error();
     VF_CHECK(F && E && B && lde && ldb && R && nmeshes >= 1, VF_E_INVAL, "vf_solve_batched: null argument");
-    vf_status worst = VF_OK;
+    int32_t Rmax = 0;
     for (int32_t k = 0; k < nmeshes; ++k) {
-        vf_status s = vf_solve(F[k], rho ? rho[k] : nullptr, E[k], lde[k], B[k], ldb[k], R[k], opts,
-                               stats ? stats + k : nullptr, stream);
-        if (s != VF_OK && s != VF_E_NOCONV) return s;
-        if (s == VF_E_NOCONV) worst = s;
+        VF_CHECK(F[k] && E[k] && B[k], VF_E_INVAL, "vf_solve_batched: null argument for mesh %d", (int)k);
+        VF_CHECK(F[k]->device == F[0]->device, VF_E_INVAL, "vf_solve_batched: meshes on different devices");
+        VF_CHECK(R[k] >= 1 && lde[k] >= F[k]->nf && ldb[k] >= F[k]->nf, VF_E_INVAL,
+                 "vf_solve_batched: mesh %d needs R >= 1 and ld >= N", (int)k);
+        Rmax = std::max(Rmax, R[k]);
     }
-    return worst;
+    if (nmeshes == 1) return vf_solve(F[0], rho ? rho[0] : nullptr, E[0], lde[0], B[0], ldb[0], R[0], opts_in, stats,
+                                      stream);
+    const vf_solve_opts o = vf::solve_defaults(opts_in);
+    VF_CHECK(o.rtol > 0, VF_E_INVAL, "vf_solve_batched: rtol must be positive");
+    device_guard g(F[0]->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    vf::StackEntry* se;
+    VF_TRY(vf::stack_for(F, nmeshes, &se));
+    const vf_hmat* h = se->h.get();
+    VF_TRY(vf::check_prec(h, o.precision));
+    const int64_t n = h->nf;
+    vf::Workspace* w;
+    VF_TRY(vf::ws_get(h, Rmax, o.precision, &w));
+    VF_TRY_CUDA(cudaStreamWaitEvent(st, w->done, 0));
+    std::vector<vf::SegIO> io(nmeshes);
+    for (int32_t k = 0; k < nmeshes; ++k)
+        io[k] = vf::SegIO{E[k], B[k], rho ? rho[k] : nullptr, lde[k], ldb[k], R[k], 0};
+    VF_TRY_CUDA(cudaMemcpyAsync(se->io.p, io.data(), nmeshes * sizeof(vf::SegIO), cudaMemcpyHostToDevice, st));
+    vf::k_gather_seg<<<1024, 256, 0, st>>>(se->io.p, h->seg_row0.p, nmeshes, h->perm.p, n, Rmax, w->Et.p);
+    vf::k_gather_rho_seg<<<(unsigned)vf::ceil_div(n, 256), 256, 0, st>>>(se->io.p, h->seg_row0.p, nmeshes, o.rho,
+                                                                          h->perm.p, n, w->rho_t.p);
+    VF_TRY_CUDA(cudaGetLastError());
+    vf_solve_stats S{};
+    S.kernels = 3;
+    vf::SolveOut so;
+    VF_TRY(vf::solve_core(h, o, Rmax, st, w, &S, &so));
+    vf::k_scatter_seg<<<1024, 256, 0, st>>>(so.result, se->io.p, h->seg_row0.p, nmeshes, h->perm.p, n, Rmax, o.clamp);
+    VF_TRY_CUDA(cudaGetLastError());
+    VF_TRY(vf::solve_status(h, w, Rmax, o.refine && o.precision != VF_PREC_FP32, st, "vf_solve_batched"));
+    bool all = true;
+    double worst = 0;
+    for (int32_t k = 0; k < nmeshes; ++k) {
+        vf_solve_stats sk = S;
+        double mx = 0;
+        bool ok = true;
+        for (int32_t c = 0; c < R[k]; ++c) {
+            mx = std::max(mx, so.rel[(size_t)k * Rmax + c]);
+            ok = ok && so.conv[(size_t)k * Rmax + c];
+        }
+        sk.max_rel_residual = mx;
+        sk.converged = ok;
+        all = all && ok;
+        worst = std::max(worst, mx);
+        if (stats) stats[k] = sk;
+    }
+    if (!all) {
+        vf::set_error("vf_solve_batched: not converged (max rel residual %.3e)", worst);
+        return VF_E_NOCONV;
+    }
+    return VF_OK;
 }

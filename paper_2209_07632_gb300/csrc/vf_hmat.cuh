@@ -1,6 +1,8 @@
 // The compressed view-factor matrix as stored on the device (tree order).
 #pragma once
 
+#include <atomic>
+
 #include "vf_internal.cuh"
 
 namespace vf {
@@ -108,9 +110,15 @@ struct RecSrc {
 struct vf_tensor_plan;  // the tensor-core multiply's pages (vf_tensor.cu), built on first use
 namespace vf {
 void tensor_plan_free(vf_tensor_plan* p);
+// a process-unique id per matrix handle (keys of caches built from handles)
+inline uint64_t next_hmat_uid() {
+    static std::atomic<uint64_t> c{0};
+    return ++c;
+}
 }
 
 struct vf_hmat {
+    uint64_t uid = vf::next_hmat_uid();
     int device = 0;
     int64_t nf = 0;
     double tol = 0;
@@ -149,6 +157,12 @@ struct vf_hmat {
     vf::dbuf<int32_t> p1_warp_ptr;
     bool has_bf16 = false, has_fp8 = false;
     vf_tensor_plan* tplan = nullptr;
+    // Segments: the meshes of a stacked (block-diagonal) matrix, as row and
+    // row-tile ranges (nseg + 1 entries each); a plain matrix is one segment.
+    // The solve tracks convergence per segment and column.
+    std::vector<int32_t> h_seg_row0, h_seg_tile0;
+    vf::dbuf<int32_t> seg_row0, seg_tile0;
+    int32_t nseg() const { return h_seg_row0.empty() ? 1 : (int32_t)h_seg_row0.size() - 1; }
     ~vf_hmat() { vf::tensor_plan_free(tplan); }
     int64_t bytes_payload(int prec) const;        // bytes of the stored representation
     vf_status upload_all();

@@ -211,3 +211,119 @@ extern "C" vf_status vf_hmat_load(const char* path, int32_t device, vf_hmat** ou
     *out = H.release();
     return VF_OK;
 }
+
+// The block-diagonal composition diag(F_1, ..., F_k) of several matrices:
+// stacked facet (and tree) numbering mesh after mesh, every block shifted
+// to its mesh's rows and columns, the payload pools concatenated (column
+// and row indices in the pools shifted the same way), one segment per
+// mesh.  Multiplies and solves of the result run every mesh in the same
+// launches, over one work list of all meshes' row tiles.
+extern "C" vf_status vf_hmat_stack(const vf_hmat* const* F, int32_t nmeshes, vf_hmat** out) {
+    clear_error();
+    VF_CHECK(F && out && nmeshes >= 1, VF_E_INVAL, "vf_hmat_stack: null argument");
+    *out = nullptr;
+    for (int32_t k = 0; k < nmeshes; ++k) {
+        VF_CHECK(F[k], VF_E_INVAL, "vf_hmat_stack: null matrix %d", (int)k);
+        VF_CHECK(F[k]->device == F[0]->device, VF_E_INVAL, "vf_hmat_stack: matrices on different devices");
+    }
+    device_guard g(F[0]->device);
+    auto H = std::make_unique<vf_hmat>();
+    H->device = F[0]->device;
+    H->tree_kind = F[0]->tree_kind;
+    H->has_bf16 = H->has_fp8 = true;
+    int64_t nf = 0, nv = 0, na = 0, nT = 0;
+    std::vector<int32_t> aux_all;
+    std::vector<float> sc8;
+    H->h_seg_row0.push_back(0);
+    H->h_seg_tile0.push_back(0);
+    for (int32_t k = 0; k < nmeshes; ++k) {
+        const vf_hmat* f = F[k];
+        VF_CHECK(nf + f->nf < (1ll << 31), VF_E_INVAL, "vf_hmat_stack: more than 2^31 facets");
+        H->tol = std::max(H->tol, f->tol);
+        H->has_bf16 = H->has_bf16 && f->has_bf16;
+        H->has_fp8 = H->has_fp8 && f->has_fp8;
+        std::vector<int32_t> a;
+        if (f->n_aux > 0) VF_TRY(f->aux.download(a));
+        a.resize(f->n_aux);
+        for (const HBlock& b : f->h_blocks) {
+            HBlock c = b;
+            c.r0 += (int32_t)nf;
+            c.c0 += (int32_t)nf;
+            c.off_val += nv;
+            c.off_aux += na;
+            if (c.off_T >= 0) c.off_T += nT;
+            H->h_blocks.push_back(c);
+            // tree-order indices stored in the pool: CSR columns, SVD rows and columns
+            if (b.kind == VF_BLK_CSR)
+                for (int64_t z = b.off_aux + b.m + 1; z < b.off_aux + b.m + 1 + b.m1; ++z) a[z] += (int32_t)nf;
+            else if (b.kind == VF_BLK_SVD)
+                for (int64_t z = b.off_aux; z < b.off_aux + b.m1 + b.n1; ++z) a[z] += (int32_t)nf;
+        }
+        aux_all.insert(aux_all.end(), a.begin(), a.end());
+        for (int32_t p : f->h_perm) H->h_perm.push_back(p + (int32_t)nf);
+        for (size_t t = 0; t < f->h_tile_first.size(); ++t) {
+            H->h_tile_first.push_back(f->h_tile_first[t] + (int32_t)nf);
+            H->h_tile_count.push_back(f->h_tile_count[t]);
+        }
+        if (f->has_fp8) {
+            std::vector<float> s;
+            VF_TRY(f->scale8.download(s));
+            s.resize(f->h_blocks.size());
+            sc8.insert(sc8.end(), s.begin(), s.end());
+        }
+        H->max_q = std::max(H->max_q, f->max_q);
+        H->n_hier += f->n_hier;
+        vf_assemble_stats& S = H->stats;
+        for (int i = 0; i < 5; ++i) S.nblocks[i] += f->stats.nblocks[i], S.bytes[i] += f->stats.bytes[i];
+        S.nnz_visible += f->stats.nnz_visible;
+        S.probes += f->stats.probes;
+        S.probes_failed += f->stats.probes_failed;
+        S.probes_skipped += f->stats.probes_skipped;
+        S.probes_predicted_skip += f->stats.probes_predicted_skip;
+        S.verify_failed += f->stats.verify_failed;
+        S.max_rank = std::max(S.max_rank, f->stats.max_rank);
+        nf += f->nf;
+        nv += f->n_val;
+        na += f->n_aux;
+        nT += f->n_T;
+        H->h_seg_row0.push_back((int32_t)nf);
+        H->h_seg_tile0.push_back((int32_t)H->h_tile_first.size());
+    }
+    H->nf = nf;
+    H->n_val = nv;
+    H->n_aux = na;
+    H->n_T = nT;
+    // pools are padded by 16 elements: the multiply copies 16-byte aligned supersets
+    VF_TRY(H->val.alloc(nv + 16));
+    VF_TRY_CUDA(cudaMemset(H->val.p, 0, (nv + 16) * sizeof(float)));
+    if (H->has_bf16) {
+        VF_TRY(H->val16.alloc(nv + 16));
+        VF_TRY_CUDA(cudaMemset(H->val16.p, 0, (nv + 16) * sizeof(__nv_bfloat16)));
+    }
+    if (H->has_fp8) {
+        VF_TRY(H->val8.alloc(nv + 16));
+        VF_TRY_CUDA(cudaMemset(H->val8.p, 0, nv + 16));
+        VF_TRY(H->scale8.upload(sc8));
+    }
+    for (int64_t k = 0, o = 0; k < nmeshes; o += F[k]->n_val, ++k) {
+        const vf_hmat* f = F[k];
+        if (f->n_val == 0) continue;
+        VF_TRY_CUDA(cudaMemcpy(H->val.p + o, f->val.p, f->n_val * sizeof(float), cudaMemcpyDeviceToDevice));
+        if (H->has_bf16)
+            VF_TRY_CUDA(cudaMemcpy(H->val16.p + o, f->val16.p, f->n_val * sizeof(__nv_bfloat16),
+                                   cudaMemcpyDeviceToDevice));
+        if (H->has_fp8) VF_TRY_CUDA(cudaMemcpy(H->val8.p + o, f->val8.p, f->n_val, cudaMemcpyDeviceToDevice));
+    }
+    aux_all.resize(na + 16, 0);
+    VF_TRY(H->aux.upload(aux_all));
+    VF_TRY(H->perm.upload(H->h_perm));
+    std::vector<int32_t> ip(nf);
+    for (int64_t k = 0; k < nf; ++k) ip[H->h_perm[k]] = (int32_t)k;
+    VF_TRY(H->iperm.upload(ip));
+    VF_TRY(H->blocks.upload(H->h_blocks));
+    VF_TRY(H->upload_all());
+    *out = H.release();
+    return VF_OK;
+}
+
+extern "C" int32_t vf_hmat_nsegments(const vf_hmat* h) { return h ? h->nseg() : -1; }

@@ -135,6 +135,7 @@ struct vf_tensor_set {
     vf::dbuf<int32_t> cta_pages2, cta_pages1;  // ncta + 1 each
     vf::dbuf<int32_t> cta_tiles, cta_tile_ptr; // phase 2: each CTA's (super-)tiles in order
     vf::dbuf<int32_t> st_first, st_count;      // phase 2: rows of each (super-)tile
+    vf::dbuf<int32_t> seg_part0;               // phase 2: first (super-)tile of each segment (nseg + 1)
     int64_t nst = 0;                           // (super-)tiles
     vf::dbuf<int32_t> cta_units, cta_unit_ptr; // phase 1: each CTA's units (offT16, N16 pairs)
     int64_t bytes2 = 0, bytes1 = 0;
@@ -408,10 +409,13 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
     // share records (their rows side by side in B, one copy of the X rows per
     // K-chunk); SVD pieces (A = the block's own T rows) get their own records
     const int32_t r2 = cfg_r2(S);
-    std::vector<int32_t> stf, stc, st_of_row(n, -1), tile_of_row(n, -1);
-    for (int64_t k = 0; k < ntiles; ++k) {
+    std::vector<int32_t> stf, stc, st_of_row(n, -1), tile_of_row(n, -1), segp;
+    for (int64_t k = 0, sg = 0; k < ntiles; ++k) {
         const int32_t tf = H->h_tile_first[k], tc = H->h_tile_count[k];
-        if (stf.empty() || stc.back() + tc > r2) {
+        // (super-)tiles never cross a segment (one mesh of a stacked matrix)
+        const bool seg_start = sg < H->nseg() && k == H->h_seg_tile0[sg];
+        if (seg_start) segp.push_back((int32_t)stf.size()), ++sg;
+        if (stf.empty() || stc.back() + tc > r2 || seg_start) {
             stf.push_back(tf);
             stc.push_back(0);
         }
@@ -568,6 +572,9 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
         VF_TRY(check_records(heads, r2, P->n_rows_x, P->n_rows_t));
     }
     T->nst = nst;
+    segp.push_back((int32_t)nst);
+    VF_CHECK((int32_t)segp.size() == H->nseg() + 1, VF_E_INVAL, "tensor plan: empty segment");
+    VF_TRY(T->seg_part0.upload(segp));
     VF_TRY(T->st_first.upload(stf));
     VF_TRY(T->st_count.upload(stc));
     T->ncta2 = (int32_t)std::min<int64_t>((int64_t)nsm * cfg_ctas(S), nst);
@@ -1207,6 +1214,7 @@ vf_status tensor_multiply(const vf_hmat* H, int S, const unsigned char* Xhi, con
 }
 
 int64_t tensor_parts(const vf_hmat* H, int S) { return H->tplan->set[S - 1].nst; }
+const int32_t* tensor_seg_parts(const vf_hmat* H, int S) { return H->tplan->set[S - 1].seg_part0.p; }
 
 int tensor_kernels(const vf_hmat* H, int S) { return (H->tplan->set[S - 1].ncta1 > 0 ? 1 : 0) + 1; }
 

@@ -41,5 +41,7 @@ vf_status tensor_multiply(const vf_hmat* H, int S, const unsigned char* Xhi, con
 int tensor_kernels(const vf_hmat* H, int S);
 // per-column partial sums a phase-2 epilogue writes (one per row part)
 int64_t tensor_parts(const vf_hmat* H, int S);
+// first part of each segment (nseg + 1 entries, device)
+const int32_t* tensor_seg_parts(const vf_hmat* H, int S);
 
 }  // namespace vf

@@ -114,6 +114,8 @@ _SIGS = {
     "vf_solve": ([_P, _P, _P, _I64, _P, _I64, _I32, _P, _P, _P], ctypes.c_int),
     "vf_solve_host": ([_P, _P, _P, _I64, _P, _I64, _I32, _P, _P, _P], ctypes.c_int),
     "vf_solve_batched": ([_P, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "vf_hmat_stack": ([_P, _I32, _P], ctypes.c_int),
+    "vf_hmat_nsegments": ([_P], _I32),
     "vf_hmat_save": ([_P, ctypes.c_char_p], ctypes.c_int),
     "vf_hmat_load": ([ctypes.c_char_p, _I32, _P], ctypes.c_int),
 }
@@ -421,6 +423,19 @@ def vf_solve_batched(hs, Es, Bs, rho=0.12, rtol: float = 1e-6, max_iter: int = 1
     _check(load().vf_solve_batched(F, k, rho_arr, E, lde, B, lde, R, ctypes.byref(opts), st, _stream(stream)),
            allow=(VF_E_NOCONV,))
     return [s.as_dict() for s in st]
+
+
+def vf_hmat_stack(hs) -> HMat:
+    """The block-diagonal composition of the matrices hs (facets mesh after mesh)."""
+    k = len(hs)
+    P = ctypes.c_void_p * k
+    out = ctypes.c_void_p()
+    _check(load().vf_hmat_stack(P(*[h.ptr for h in hs]), k, ctypes.byref(out)))
+    return HMat(out)
+
+
+def vf_hmat_nsegments(h: HMat) -> int:
+    return int(load().vf_hmat_nsegments(h.ptr))
 
 
 def vf_hmat_save(h: HMat, path: str):
