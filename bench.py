@@ -51,13 +51,23 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--cpu-rows", type=int, default=128, help="rows of F in the CPU oracle sample")
     p.add_argument("--no-batched", action="store_true", help="skip the batched (tensor-core) section")
-    p.add_argument("--batch-rhs", type=int, default=128, help="RHS of the batched section")
+    p.add_argument("--batch-rhs", type=int, default=1440, help="RHS (sun positions) of the batched section")
+    p.add_argument("--multimesh", type=int, default=8, help="meshes of the multi-mesh section (0: skip)")
+    p.add_argument("--multimesh-max-side", type=int, default=100,
+                   help="largest DEM side of the multi-mesh section (50 -> 4,802 facets, 200 -> 79,202)")
+    p.add_argument("--multimesh-rhs", type=int, default=64, help="RHS per mesh in the multi-mesh section")
     return p.parse_args()
 
 
 def synth_dirs(R: int):
     import synth
     return synth.sun_directions(R, 10.0)
+
+
+def lunar_day_dirs(R: int):
+    """R sun directions over one lunar day: an azimuth sweep at 1.5 deg elevation."""
+    import synth
+    return synth.sun_directions(R, 1.5)
 
 
 def workload_inputs(R: int, side: int = 200):
@@ -300,33 +310,50 @@ def main():
     e2e = {"value": world * R / e2e_s, "unit": "RHS/s", "h2d_bytes_per_step": n * R * 4,
            "d2h_bytes_per_step": n * R * 4}
 
-    # ---- batched: many sun positions at once, BF16 sweeps on the tensor cores
-    # (tcgen05, FP32 accumulation) with split-BF16 residual refinement
+    # ---- batched: 1,440 sun positions over one lunar day (azimuth sweep at
+    # 1.5 deg elevation) on the same mesh, BF16 sweeps on the tensor cores
+    # (tcgen05, FP32 accumulation) with split-BF16 residual refinement; the
+    # autotuner picks the path and the RHS block, and RHS blocks of 64, 256
+    # and 1440 are timed as well
     batched = None
     if not a.no_batched and rank == 0:
         Rb = a.batch_rhs
         Eb = torch.empty((Rb, n), device="cuda", dtype=torch.float32)
-        vf.vf_mesh_insolation(prob.mesh, synth_dirs(Rb), 1365.0, Eb)
+        vf.vf_mesh_insolation(prob.mesh, lunar_day_dirs(Rb), 1365.0, Eb)
         Bb = torch.empty_like(Eb)
         Bref = torch.empty_like(Eb)
         vf.vf_solve(prob.hmat, Eb, Bref, rho=rho, rtol=rtol)  # FP32 CUDA-core solve: the accuracy reference
         bkw = dict(rho=rho, rtol=1e-4, precision="bf16", refine=True)
-        for _ in range(3):
-            sb = vf.vf_solve(prob.hmat, Eb, Bb, **bkw)
-        torch.cuda.synchronize()
-        bsteps = max(5, min(a.steps, 50))
-        b0 = torch.cuda.Event(enable_timing=True)
-        b1 = torch.cuda.Event(enable_timing=True)
-        b0.record(st)
-        for _ in range(bsteps):
-            sb = vf.vf_solve(prob.hmat, Eb, Bb, **bkw)
-        b1.record(st)
-        torch.cuda.synchronize()
-        bms = b0.elapsed_time(b1) / bsteps
+        t_tune = time.time()
+        tune = vf.vf_autotune(prob.hmat, "bf16", Rb)
+        t_tune = time.time() - t_tune
+
+        def time_solves(steps):
+            for _ in range(2):
+                sb = vf.vf_solve(prob.hmat, Eb, Bb, **bkw)
+            torch.cuda.synchronize()
+            b0 = torch.cuda.Event(enable_timing=True)
+            b1 = torch.cuda.Event(enable_timing=True)
+            b0.record(st)
+            for _ in range(steps):
+                sb = vf.vf_solve(prob.hmat, Eb, Bb, **bkw)
+            b1.record(st)
+            torch.cuda.synchronize()
+            return b0.elapsed_time(b1) / steps, sb
+
+        blocks = {}
+        for w in (64, 256, Rb):
+            if w > Rb:
+                continue
+            vf.vf_tune_set(prob.hmat, "bf16", Rb, rb=8, tensor=1, rhs_block=0 if w == Rb else w)
+            wms, _ = time_solves(3)
+            blocks[str(w)] = round(Rb / (wms / 1000.0), 1)
+        vf.vf_tune_set(prob.hmat, "bf16", Rb, rb=tune["rb"], tensor=tune["tensor"], rhs_block=tune["rhs_block"])
+        bms, sb = time_solves(max(3, min(a.steps, 20)))
         live = Bref.norm(dim=1) > 0
         brel = float(((Bb - Bref).norm(dim=1)[live] / Bref.norm(dim=1)[live]).max().item())
-        # the tensor-core multiply alone (one panel of 128, BF16), tree order
-        Xb = Eb.clone()
+        # the tensor-core multiply alone (panels of 128, BF16), tree order
+        Xb = Eb[:128].clone()
         Yb = torch.empty_like(Xb)
         for _ in range(3):
             vf.vf_apply_tree(prob.hmat, Xb, Yb, precision="bf16")
@@ -339,19 +366,83 @@ def main():
         m1.record(st)
         torch.cuda.synchronize()
         tms = m0.elapsed_time(m1) / 20
-        bf16_bytes = vf.vf_hmat_bytes(prob.hmat, "bf16") + n * Rb * (2 + 4)
+        bf16_bytes = vf.vf_hmat_bytes(prob.hmat, "bf16") + n * 128 * (2 + 4)
         single_apply = 1.0 / (mult_ms / 1000.0)  # FP32 single-RHS multiply, RHS/s
         batched = {"value": round(Rb / (bms / 1000.0), 1), "unit": "RHS/s", "rhs": Rb, "ms_per_solve": round(bms, 3),
+                   "suns": "lunar-day azimuth sweep at 1.5 deg elevation",
                    "precision": "bf16 factors and RHS on tcgen05 tensor cores, FP32 accumulation; "
                                 "split-BF16 residual refinement with FP64 update",
+                   "autotuned": dict(tune, seconds=round(t_tune, 2)), "rhs_per_s_by_rhs_block": blocks,
                    "rtol": 1e-4, "sweeps": sb["sweeps"], "refinements": sb["refinements"],
                    "max_rel_diff_vs_fp32_solve": brel,
                    "x_fp32_single_rhs_apply": round(Rb / (bms / 1000.0) / single_apply, 2),
                    "x_fp32_single_rhs_solve": round(Rb / (bms / 1000.0) / (value / world), 2),
-                   "tensor_multiply": {"ms": round(tms, 4), "rhs": Rb,
+                   "tensor_multiply": {"ms": round(tms, 4), "rhs": 128,
                                        "alg_bytes": bf16_bytes,
                                        "hbm_frac": round(bf16_bytes / (tms / 1000.0) / 1e9 / peak, 4)}}
         del Eb, Bb, Bref, Xb, Yb
+
+    # ---- many meshes in one launch per phase: K seeded fBm terrains (every
+    # other one with a crater) of growing size, each with its own suns, one
+    # vf_solve_batched on their block-diagonal stack against a loop of
+    # per-mesh vf_solve calls
+    multimesh = None
+    if a.multimesh > 0 and rank == 0:
+        import synth
+        K = a.multimesh
+        sides = [int(round(50 + (a.multimesh_max_side - 50) * k / max(K - 1, 1))) for k in range(K)]
+        mm0 = time.time()
+        ps = []
+        for k, side in enumerate(sides):
+            mv, mf = synth.fbm_dem_mesh(n=side, spacing=10.0, hurst=0.8, seed=100 + k, rms_slope_deg=15.0,
+                                        crater_diameter=min(1000.0, 4.0 * side) if k % 2 == 0 else None)
+            ps.append(vf.build_problem(mv, mf, kind="quad", leaf_size=64, tol=a.tol, device=dev,
+                                       precisions=("fp32", "bf16")))
+        t_mm_setup = time.time() - mm0
+        Rm = a.multimesh_rhs
+        Es = []
+        for k, p_ in enumerate(ps):
+            Ek = torch.empty((Rm, p_.mesh.n), device="cuda", dtype=torch.float32)
+            vf.vf_mesh_insolation(p_.mesh, synth.sun_directions(Rm, 5.0 + k % 10, 7.0 * k), 1365.0, Ek)
+            Es.append(Ek)
+        Bs = [torch.empty_like(e_) for e_ in Es]
+        Bl = [torch.empty_like(e_) for e_ in Es]
+        mkw = dict(rho=rho, rtol=1e-4, precision="bf16", refine=True)
+        hs = [p_.hmat for p_ in ps]
+        for _ in range(2):
+            vf.vf_solve_batched(hs, Es, Bs, **mkw)
+            for p_, e_, b_ in zip(ps, Es, Bl):
+                vf.vf_solve(p_.hmat, e_, b_, **mkw)
+        torch.cuda.synchronize()
+        steps_mm = 5
+        q0 = torch.cuda.Event(enable_timing=True)
+        q1 = torch.cuda.Event(enable_timing=True)
+        q0.record(st)
+        for _ in range(steps_mm):
+            sm = vf.vf_solve_batched(hs, Es, Bs, **mkw)
+        q1.record(st)
+        torch.cuda.synchronize()
+        bat_ms = q0.elapsed_time(q1) / steps_mm
+        q0.record(st)
+        for _ in range(steps_mm):
+            for p_, e_, b_ in zip(ps, Es, Bl):
+                vf.vf_solve(p_.hmat, e_, b_, **mkw)
+        q1.record(st)
+        torch.cuda.synchronize()
+        loop_ms = q0.elapsed_time(q1) / steps_mm
+        diff = 0.0
+        for b_, l_ in zip(Bs, Bl):
+            live = l_.norm(dim=1) > 0
+            diff = max(diff, float(((b_ - l_).norm(dim=1)[live] / l_.norm(dim=1)[live]).max().item()))
+        facets = [p_.mesh.n for p_ in ps]
+        multimesh = {"value": round(K * Rm / (bat_ms / 1000.0), 1), "unit": "RHS/s", "meshes": K,
+                     "facets_min_max_total": [min(facets), max(facets), sum(facets)], "rhs_per_mesh": Rm,
+                     "ms_per_batched_solve": round(bat_ms, 3), "ms_per_loop_of_solves": round(loop_ms, 3),
+                     "x_vs_loop": round(loop_ms / bat_ms, 2), "max_rel_diff_vs_loop": diff,
+                     "sweeps": sm[0]["sweeps"], "refinements": sm[0]["refinements"],
+                     "converged": all(x["converged"] for x in sm), "setup_s": round(t_mm_setup, 1),
+                     "precision": "bf16 tensor-core sweeps + split-BF16 refinement, rtol 1e-4"}
+        del ps, Es, Bs, Bl, hs
 
     # ---- the uncompressed dense FP32 F on the same GPU
     dense = None
@@ -390,7 +481,7 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "setup_s": round(t_setup, 2)},
             "roofline": roofline, "e2e": e2e, "gpu_launches": kernels, "clocks": clk,
-            "batched": batched, "dense_fp32": dense, "cpu_baseline": cpu,
+            "batched": batched, "multimesh": multimesh, "dense_fp32": dense, "cpu_baseline": cpu,
             "assembly": {k: prob.stats[k] for k in ("nblocks", "bytes", "probes", "max_rank", "t_visibility",
                                                     "t_probe", "t_total")}}
     if rank == 0:

@@ -344,6 +344,37 @@ vf_status vf_solve_batched(const vf_hmat* const* F, int32_t nmeshes, const float
                            const int32_t* R, const vf_solve_opts* opts, vf_solve_stats* stats,
                            vf_stream stream);
 
+/* ------------------------------------------------------------ autotuning
+ * What the multiply of one matrix runs with, per (precision, R): the
+ * CUDA-core path's right-hand sides per pass (its RHS tile), whether BF16
+ * multiplies of >= 16 columns use the tensor cores, and the RHS block: a
+ * call with more columns runs in column blocks of this width (0: all
+ * columns at once).  No counterpart in the paper (its multiply is one
+ * library call per block); the choice only changes speed and rounding
+ * order. */
+typedef struct {
+    int32_t rb;          /* 1, 2, 4 or 8 */
+    int32_t tensor;      /* 0 or 1 */
+    int32_t rhs_block;   /* 0 or a width < R */
+    float us_per_rhs;    /* measured multiply time per right-hand side (autotuner) */
+} vf_tune;
+
+/* Times the multiply of h on seeded synthetic columns (device memory the
+ * call allocates) for every candidate -- rb in {1, 2, 4, 8} (8 alone from
+ * 16 columns up), the tensor path (BF16, >= 16 columns), RHS blocks of R
+ * and of 64, 128, 256, ... < R
+ * -- and records the fastest per right-hand side for (prec, R) in the
+ * handle (and for (prec, rhs_block) when it splits); later vf_apply,
+ * vf_apply_tree and vf_solve calls with that precision and R use it.  out
+ * (host, may be NULL) receives the choice.  The handle's workspaces for the
+ * candidates stay cached until it is destroyed.  Errors: VF_E_INVAL,
+ * VF_E_NOMEM, VF_E_CUDA, VF_E_TIMEOUT. */
+vf_status vf_autotune(const vf_hmat* h, vf_precision prec, int32_t R, vf_tune* out, vf_stream stream);
+
+/* Record a choice for (prec, R) by hand (as vf_autotune would); rb must be
+ * 1, 2, 4 or 8, tensor 0 or 1, rhs_block 0 or in [1, R).  Errors: VF_E_INVAL. */
+vf_status vf_tune_set(const vf_hmat* h, vf_precision prec, int32_t R, const vf_tune* t);
+
 /* The block-diagonal composition of nmeshes matrices on one device (no
  * counterpart in the paper; it batches many meshes): facets numbered mesh
  * after mesh (facet f of mesh k is row off_k + f, off_k = the sizes of the

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <memory>
 #include <mutex>
 #include <queue>
@@ -1089,7 +1090,7 @@ struct Workspace {
 
 struct WsCache {
     std::mutex mu;
-    std::map<std::pair<int, int>, std::unique_ptr<Workspace>> m;
+    std::map<std::tuple<int, int, int>, std::unique_ptr<Workspace>> m;  // (R, precision, RB)
 };
 
 static std::mutex g_cache_mu;
@@ -1114,6 +1115,20 @@ static int pick_rb(int R) {
     return 8;
 }
 
+// The autotuner's record for (prec, R), if any.
+static bool tuned(const vf_hmat* h, int prec, int R, vf_tune* t) {
+    std::lock_guard<std::mutex> lk(h->tune_mu);
+    auto it = h->tunes.find({prec, R});
+    if (it == h->tunes.end()) return false;
+    *t = it->second;
+    return true;
+}
+
+static int pick_rb_for(const vf_hmat* h, int prec, int R) {
+    vf_tune t;
+    return tuned(h, prec, R, &t) ? t.rb : pick_rb(R);
+}
+
 static ApplyArgs make_args(const vf_hmat* h, int prec, int R) {
     (void)prec;
     ApplyArgs a{};
@@ -1130,10 +1145,10 @@ static ApplyArgs make_args(const vf_hmat* h, int prec, int R) {
 
 static vf_status phase2_attrs(int device);
 
-static vf_status ws_get(const vf_hmat* h, int R, int prec, Workspace** out) {
+static vf_status ws_get_rb(const vf_hmat* h, int R, int prec, int RB, Workspace** out) {
     WsCache& c = cache_for(h);
     std::lock_guard<std::mutex> lk(c.mu);
-    auto key = std::make_pair(R, prec);
+    auto key = std::make_tuple(R, prec, RB);
     auto it = c.m.find(key);
     if (it != c.m.end()) {
         *out = it->second.get();
@@ -1143,7 +1158,7 @@ static vf_status ws_get(const vf_hmat* h, int R, int prec, Workspace** out) {
     auto w = std::make_unique<Workspace>();
     w->R = R;
     w->prec = prec;
-    w->RB = pick_rb(R);
+    w->RB = RB;
     w->npanels = (int)ceil_div(R, w->RB);
     const int64_t n = h->nf, nR = n * (int64_t)R;
     const int64_t ntiles = (int64_t)h->h_tile_first.size();
@@ -1172,6 +1187,10 @@ static vf_status ws_get(const vf_hmat* h, int R, int prec, Workspace** out) {
     *out = w.get();
     c.m[key] = std::move(w);
     return VF_OK;
+}
+
+static vf_status ws_get(const vf_hmat* h, int R, int prec, Workspace** out) {
+    return ws_get_rb(h, R, prec, pick_rb_for(h, prec, R), out);
 }
 
 template <class T, int RB, int MODE>
@@ -1329,8 +1348,11 @@ static int multiply_kernels(const vf_hmat* h) {
     return (h->n_p1_pages > 0 ? 1 : 0) + (h->n_split > 0 ? 1 : 0) + 1;
 }
 
-// BF16 multiplies of at least kTensorMinR columns run on the tensor cores.
+// BF16 multiplies of at least kTensorMinR columns run on the tensor cores,
+// unless the autotuner found the CUDA-core path faster for this R.
 static bool use_tensor(const vf_hmat* h, int prec, int R) {
+    vf_tune t;
+    if (tuned(h, prec, R, &t) && !t.tensor) return false;
     return prec == VF_PREC_BF16 && h->has_bf16 && R >= kTensorMinR;
 }
 
@@ -1630,6 +1652,13 @@ extern "C" vf_status vf_apply(const vf_hmat* h, vf_precision prec, const float* 
     VF_CHECK(h && X && Y, VF_E_INVAL, "vf_apply: null argument");
     VF_CHECK(R >= 1 && ldx >= h->nf && ldy >= h->nf, VF_E_INVAL, "vf_apply: need R >= 1 and ld >= N");
     VF_TRY(vf::check_prec(h, prec));
+    vf_tune tc;
+    if (vf::tuned(h, prec, R, &tc) && tc.rhs_block > 0 && tc.rhs_block < R) {
+        for (int32_t c0 = 0; c0 < R; c0 += tc.rhs_block)
+            VF_TRY(vf_apply(h, prec, X + (int64_t)c0 * ldx, ldx, std::min(tc.rhs_block, R - c0),
+                            Y + (int64_t)c0 * ldy, ldy, stream));
+        return VF_OK;
+    }
     device_guard g(h->device);
     cudaStream_t st = (cudaStream_t)stream;
     vf::Workspace* w;
@@ -1654,6 +1683,13 @@ extern "C" vf_status vf_apply_tree(const vf_hmat* h, vf_precision prec, const fl
     VF_CHECK(h && Xt && Yt, VF_E_INVAL, "vf_apply_tree: null argument");
     VF_CHECK(R >= 1, VF_E_INVAL, "vf_apply_tree: need R >= 1");
     VF_TRY(vf::check_prec(h, prec));
+    vf_tune tc;
+    if (vf::tuned(h, prec, R, &tc) && tc.rhs_block > 0 && tc.rhs_block < R) {
+        for (int32_t c0 = 0; c0 < R; c0 += tc.rhs_block)
+            VF_TRY(vf_apply_tree(h, prec, Xt + (int64_t)c0 * h->nf, std::min(tc.rhs_block, R - c0),
+                                 Yt + (int64_t)c0 * h->nf, stream));
+        return VF_OK;
+    }
     device_guard g(h->device);
     cudaStream_t st = (cudaStream_t)stream;
     vf::Workspace* w;
@@ -1957,6 +1993,29 @@ extern "C" vf_status vf_solve(const vf_hmat* h, const float* rho, const float* E
     const vf_solve_opts o = vf::solve_defaults(opts_in);
     VF_CHECK(o.rtol > 0, VF_E_INVAL, "vf_solve: rtol must be positive");
     VF_TRY(vf::check_prec(h, o.precision));
+    vf_tune tc;
+    if (vf::tuned(h, o.precision, R, &tc) && tc.rhs_block > 0 && tc.rhs_block < R) {
+        // column blocks of the tuned width, one solve each
+        vf_solve_stats all{};
+        all.converged = 1;
+        vf_status worst = VF_OK;
+        for (int32_t c0 = 0; c0 < R; c0 += tc.rhs_block) {
+            vf_solve_stats sb{};
+            const vf_status sc = vf_solve(h, rho, E + (int64_t)c0 * lde, lde, B + (int64_t)c0 * ldb, ldb,
+                                          std::min(tc.rhs_block, R - c0), &o, &sb, stream);
+            if (sc != VF_OK && sc != VF_E_NOCONV) return sc;
+            if (sc == VF_E_NOCONV) worst = sc;
+            all.sweeps = std::max(all.sweeps, sb.sweeps);
+            all.refinements = std::max(all.refinements, sb.refinements);
+            all.kernels += sb.kernels;
+            all.max_rel_residual = std::max(all.max_rel_residual, sb.max_rel_residual);
+            all.converged = all.converged && sb.converged;
+        }
+        if (stats) *stats = all;
+        if (worst == VF_E_NOCONV)
+            vf::set_error("vf_solve: not converged (max rel residual %.3e)", all.max_rel_residual);
+        return worst;
+    }
     device_guard g(h->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = h->nf;
@@ -2089,5 +2148,116 @@ extern "C" vf_status vf_solve_batched(const vf_hmat* const* F, int32_t nmeshes, 
         vf::set_error("vf_solve_batched: not converged (max rel residual %.3e)", worst);
         return VF_E_NOCONV;
     }
+    return VF_OK;
+}
+
+// ============================================================ autotuner
+namespace vf {
+
+__global__ void k_fill_uniform(float* __restrict__ x, int64_t n, uint64_t seed) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t h = splitmix64(seed ^ ((uint64_t)i * 0x9E3779B97F4A7C15ull));
+        x[i] = (float)((double)(h >> 40) * (1.0 / 16777216.0));
+    }
+}
+
+static vf_status check_tune(const vf_tune& t, int R) {
+    VF_CHECK((t.rb == 1 || t.rb == 2 || t.rb == 4 || t.rb == 8) && (t.tensor == 0 || t.tensor == 1) &&
+                 t.rhs_block >= 0 && t.rhs_block < R,
+             VF_E_INVAL, "vf_tune: rb must be 1, 2, 4 or 8, tensor 0 or 1, rhs_block in [0, R)");
+    return VF_OK;
+}
+
+static void tune_store(const vf_hmat* h, int prec, int R, const vf_tune& t) {
+    std::lock_guard<std::mutex> lk(h->tune_mu);
+    h->tunes[{prec, R}] = t;
+    if (t.rhs_block > 0) {
+        vf_tune b = t;
+        b.rhs_block = 0;  // the blocks themselves run whole
+        h->tunes[{prec, t.rhs_block}] = b;
+    }
+}
+
+}  // namespace vf
+
+extern "C" vf_status vf_tune_set(const vf_hmat* h, vf_precision prec, int32_t R, const vf_tune* t) {
+    clear_error();
+    VF_CHECK(h && t && R >= 1, VF_E_INVAL, "vf_tune_set: null argument or R < 1");
+    VF_TRY(vf::check_prec(h, prec));
+    VF_TRY(vf::check_tune(*t, R));
+    VF_CHECK(!t->tensor || (prec == VF_PREC_BF16 && R >= vf::kTensorMinR &&
+                            (t->rhs_block == 0 || t->rhs_block >= vf::kTensorMinR)),
+             VF_E_INVAL, "vf_tune_set: the tensor path needs BF16 and >= %d columns", vf::kTensorMinR);
+    vf::tune_store(h, prec, R, *t);
+    return VF_OK;
+}
+
+extern "C" vf_status vf_autotune(const vf_hmat* h, vf_precision prec, int32_t R, vf_tune* out, vf_stream stream) {
+    clear_error();
+    VF_CHECK(h && R >= 1, VF_E_INVAL, "vf_autotune: null matrix or R < 1");
+    VF_TRY(vf::check_prec(h, prec));
+    device_guard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = h->nf;
+    std::vector<int32_t> widths{R};
+    for (int32_t w = 64; w < R; w *= 2) widths.push_back(w);
+    vf::dbuf<float> X, Y;
+    VF_TRY(X.alloc((size_t)n * R));
+    VF_TRY(Y.alloc((size_t)n * R));
+    vf::k_fill_uniform<<<1024, 256, 0, st>>>(X.p, n * (int64_t)R, 0x5EEDull);
+    VF_TRY_CUDA(cudaGetLastError());
+    cudaEvent_t e0, e1;
+    VF_TRY_CUDA(cudaEventCreate(&e0));
+    VF_TRY_CUDA(cudaEventCreate(&e1));
+    vf_tune best{};
+    best.us_per_rhs = -1.f;
+    vf_status s = VF_OK;
+    for (int32_t W : widths) {
+        std::vector<vf_tune> cands;
+        // RHS tiles up to the width (at 16 columns and more only the widest:
+        // a pass then always fills it)
+        for (int rb : {1, 2, 4, 8})
+            if ((rb == 1 || rb <= W) && (W < 16 || rb == 8)) cands.push_back(vf_tune{rb, 0, W < R ? W : 0, 0.f});
+        if (prec == VF_PREC_BF16 && h->has_bf16 && W >= vf::kTensorMinR)
+            cands.push_back(vf_tune{vf::pick_rb(W), 1, W < R ? W : 0, 0.f});
+        for (vf_tune& c : cands) {
+            vf::Workspace* w;
+            if ((s = vf::ws_get_rb(h, W, prec, c.rb, &w)) != VF_OK) break;
+            auto run = [&]() -> vf_status {
+                if (c.tensor) return vf::tensor_apply(h, w, X.p, n, nullptr, Y.p, st);
+                return vf::launch_multiply(h, prec, w, vf::MODE_APPLY, nullptr, nullptr, X.p, Y.p, nullptr, nullptr,
+                                           st);
+            };
+            constexpr int kReps = 3;
+            if ((s = run()) != VF_OK) break;  // warm-up (and, for the tensor path, its one-time plan)
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < kReps && s == VF_OK; ++r) s = run();
+            cudaEventRecord(e1, st);
+            if (s != VF_OK) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                s = VF_E_CUDA;
+                vf::set_error("vf_autotune: %s", cudaGetErrorString(cudaGetLastError()));
+                break;
+            }
+            int ws = 0;
+            cudaMemcpy(&ws, w->status.p, sizeof(int), cudaMemcpyDeviceToHost);
+            if (ws) {
+                cudaMemset(w->status.p, 0, sizeof(int));
+                s = VF_E_TIMEOUT;
+                vf::set_error("vf_autotune: a bounded device-side wait gave up");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            c.us_per_rhs = ms * 1000.f / kReps / (float)W;
+            if (best.us_per_rhs < 0.f || c.us_per_rhs < best.us_per_rhs) best = c;
+        }
+        if (s != VF_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    VF_TRY(s);
+    vf::tune_store(h, prec, R, best);
+    if (out) *out = best;
     return VF_OK;
 }

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <atomic>
+#include <map>
+#include <mutex>
 
 #include "vf_internal.cuh"
 
@@ -119,6 +121,9 @@ inline uint64_t next_hmat_uid() {
 
 struct vf_hmat {
     uint64_t uid = vf::next_hmat_uid();
+    // the autotuner's choices per (precision, R): vf_tune records
+    mutable std::mutex tune_mu;
+    mutable std::map<std::pair<int, int>, vf_tune> tunes;
     int device = 0;
     int64_t nf = 0;
     double tol = 0;

@@ -114,6 +114,8 @@ _SIGS = {
     "vf_solve": ([_P, _P, _P, _I64, _P, _I64, _I32, _P, _P, _P], ctypes.c_int),
     "vf_solve_host": ([_P, _P, _P, _I64, _P, _I64, _I32, _P, _P, _P], ctypes.c_int),
     "vf_solve_batched": ([_P, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "vf_autotune": ([_P, ctypes.c_int, _I32, _P, _P], ctypes.c_int),
+    "vf_tune_set": ([_P, ctypes.c_int, _I32, _P], ctypes.c_int),
     "vf_hmat_stack": ([_P, _I32, _P], ctypes.c_int),
     "vf_hmat_nsegments": ([_P], _I32),
     "vf_hmat_save": ([_P, ctypes.c_char_p], ctypes.c_int),
@@ -423,6 +425,26 @@ def vf_solve_batched(hs, Es, Bs, rho=0.12, rtol: float = 1e-6, max_iter: int = 1
     _check(load().vf_solve_batched(F, k, rho_arr, E, lde, B, lde, R, ctypes.byref(opts), st, _stream(stream)),
            allow=(VF_E_NOCONV,))
     return [s.as_dict() for s in st]
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [("rb", ctypes.c_int32), ("tensor", ctypes.c_int32), ("rhs_block", ctypes.c_int32),
+                ("us_per_rhs", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def vf_autotune(h: HMat, precision: str = "fp32", R: int = 1, stream=None) -> dict:
+    """Time the multiply's candidate configurations for (precision, R) and keep the fastest in h."""
+    t = Tune()
+    _check(load().vf_autotune(h.ptr, PREC[precision], R, ctypes.byref(t), _stream(stream)))
+    return t.as_dict()
+
+
+def vf_tune_set(h: HMat, precision: str, R: int, rb: int, tensor: int = 0, rhs_block: int = 0):
+    t = Tune(rb, tensor, rhs_block, 0.0)
+    _check(load().vf_tune_set(h.ptr, PREC[precision], R, ctypes.byref(t)))
 
 
 def vf_hmat_stack(hs) -> HMat:

@@ -127,3 +127,38 @@ def test_stack_cache_follows_handles(vf):
     vf.vf_solve_batched([p.hmat for p in ps], Es, Bs, rho=0.12, rtol=1e-6)
     for a, b in zip(first, Bs):
         assert _rel(b, a) <= 1e-6
+
+
+def test_autotune_records_a_valid_choice(vf, probs):
+    import torch
+    h, n = probs[2].hmat, probs[2].mesh.n
+    X = torch.rand((40, n), generator=torch.Generator().manual_seed(7)).cuda()
+    Y32 = torch.empty_like(X)
+    vf.vf_apply(h, X, Y32, precision="fp32")
+    t = vf.vf_autotune(h, "bf16", 40)
+    assert t["rb"] in (1, 2, 4, 8) and t["tensor"] in (0, 1) and t["rhs_block"] == 0 and t["us_per_rhs"] > 0
+    Y = torch.empty_like(X)
+    vf.vf_apply(h, X, Y, precision="bf16")
+    assert _rel(Y, Y32) <= 4e-3
+    t = vf.vf_autotune(h, "fp32", 5)
+    assert t["rb"] in (1, 2, 4) and t["tensor"] == 0
+    X5 = X[:5].contiguous()
+    Y5 = torch.empty_like(X5)
+    vf.vf_apply(h, X5, Y5, precision="fp32")
+    assert _rel(Y5, Y32[:5]) <= 1e-6
+
+
+def test_rhs_blocks_solve_like_one_block(vf):
+    import torch
+    p = vf.build_problem(*synth.fbm_dem_mesh(n=36, seed=9), tol=1e-3, precisions=("fp32",))
+    R = 200
+    E = torch.empty((R, p.mesh.n), device="cuda")
+    vf.vf_mesh_insolation(p.mesh, synth.sun_directions(R, 9.0), 1365.0, E)
+    B1, B2 = torch.empty_like(E), torch.empty_like(E)
+    vf.vf_solve(p.hmat, E, B1, rho=0.12, rtol=1e-8)
+    vf.vf_tune_set(p.hmat, "fp32", R, rb=8, rhs_block=64)
+    st = vf.vf_solve(p.hmat, E, B2, rho=0.12, rtol=1e-8)
+    assert st["converged"] == 1
+    assert _rel(B2, B1) <= 1e-6
+    with pytest.raises(vf.VFError):
+        vf.vf_tune_set(p.hmat, "fp32", R, rb=3)
