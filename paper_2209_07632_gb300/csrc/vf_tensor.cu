@@ -42,23 +42,28 @@
 
 namespace vf {
 
-constexpr int kTP = 16384;           // tensor page bytes
+#ifndef VF_T_PAGE
+#define VF_T_PAGE 12288
+#endif
+constexpr int kTP = VF_T_PAGE;       // tensor page bytes
 constexpr int kTPHdr = 16;           // page header: nrec, used, 0, 0
 constexpr int kTRHdr = 32;           // record header (8 x u32)
 constexpr int kPanel = 128;          // right-hand sides per panel (MMA M)
-constexpr int kTickets = 16;         // records in flight (A operands in the ring)
-// Both page sets run four CTAs per SM (each: two page stages, a 20 KB A
-// ring, two 64-column accumulator regions), since the multiply is bound by
-// independent pipelines per SM; the split set (S = 2, hi and lo A operands)
-// caps a record's K at 32 so its A operands still fit the ring.
+constexpr int kMaxSlots = 16;        // A-operand ring slots (barrier pairs)
+// Both page sets run four CTAs per SM: the multiply is bound by the
+// single-thread producer and MMA-issuer steps of each CTA's pipeline, so
+// independent pipelines per SM count most.  Per CTA (BF16 set): three 12 KB
+// page stages, an A ring of two 8 KB slots, two accumulator regions of 64
+// TMEM columns.  The split set (S = 2, hi and lo A operands) has two page
+// stages and caps a record's K at 32.  Measured for one 128-RHS BF16
+// multiply of the 79k-facet terrain: this 1.32 ms; two 16 KB stages and a
+// 20 KB ring 1.37 ms; four 8 KB stages 1.43 ms; 16-row chunks in five slots
+// 1.56 ms; super-tiles of 128 rows in one 128-column region 1.49 ms; three
+// CTAs per SM or two CTAs with deeper buffers 1.6-2.1 ms.
 template <int NS> struct TCfg;
 // Phase 2 accumulates a (super-)tile of consecutive row tiles, up to R2
-// rows, in NREG2 regions of R2 TMEM columns used in turn.  Tiles (R2 = 64,
-// two regions, 128 columns, four CTAs per SM) measured faster than
-// super-tiles of 128 rows in one region (1.52 against 1.81 ms for a 128-RHS
-// multiply of the 79k-facet terrain) or in two regions at two CTAs per SM
-// (2.1 ms): the number of independent pipelines per SM decides.  The
-// VF_T1_* macros select the BF16 set's configuration at build time.
+// rows, in NREG2 regions of R2 TMEM columns used in turn.  The VF_T*
+// macros select the configuration at build time.
 #ifndef VF_T1_R2
 #define VF_T1_R2 64
 #endif
@@ -69,10 +74,10 @@ template <int NS> struct TCfg;
 #define VF_T1_CTAS 4
 #endif
 #ifndef VF_T1_PSTAGES
-#define VF_T1_PSTAGES 2
+#define VF_T1_PSTAGES 3
 #endif
 #ifndef VF_T1_RING
-#define VF_T1_RING 20480
+#define VF_T1_RING 16384
 #endif
 #ifndef VF_T1_KMAX
 #define VF_T1_KMAX 64
@@ -84,15 +89,26 @@ template <> struct TCfg<1> {
 template <> struct TCfg<2> {
     static constexpr int PSTAGES = 2, RING = 20480, CTAS = 4, REGION = 64, KMAX = 32, R2 = 64, NREG2 = 2, TMEM = 128;
 };
-constexpr int kMaxPStages = 3;
-static int cfg_ring(int S) { return S == 1 ? TCfg<1>::RING : TCfg<2>::RING; }
+constexpr int kMaxPStages = 4;
+// A operands stream through a ring of NSLOT slots, one K chunk of CK rows
+// (x NS terms) per slot, so the copy of one record's later chunks (and of
+// the next record) overlaps the MMAs of its earlier ones.
+#ifndef VF_T_CK
+#define VF_T_CK 32
+#endif
+template <int NS> struct TSlots {
+    static constexpr int CK = NS == 1 ? VF_T_CK : 16;           // K rows per chunk
+    static constexpr int BYTES = NS * CK * 128 * 2;             // one chunk, all terms
+    static constexpr int NSLOT = TCfg<NS>::RING / BYTES;
+    static_assert(NSLOT >= 2 && NSLOT <= kMaxSlots, "A ring slots");
+};
 static int cfg_ctas(int S) { return S == 1 ? TCfg<1>::CTAS : TCfg<2>::CTAS; }
 static int cfg_region(int S) { return S == 1 ? TCfg<1>::REGION : TCfg<2>::REGION; }
 static int cfg_kmax(int S) { return S == 1 ? TCfg<1>::KMAX : TCfg<2>::KMAX; }
 static int cfg_r2(int S) { return S == 1 ? TCfg<1>::R2 : TCfg<2>::R2; }
 template <int NS>
 constexpr size_t tsmem_bytes() {
-    return (size_t)TCfg<NS>::PSTAGES * 16384 + TCfg<NS>::RING + 1024;
+    return (size_t)TCfg<NS>::PSTAGES * kTP + TCfg<NS>::RING + 1024;
 }
 constexpr uint32_t kTWait = 1u << 22;
 // record flags: FIRST / LAST record of its accumulator region's use (a
@@ -112,8 +128,8 @@ struct TRec {        // where one tensor record's B operand comes from (build ti
     int32_t a_src, a_row0;
     int32_t flags, offT;
     int32_t S;         // 1: BF16 body; 2: hi and lo bodies
-    int32_t ring;      // byte offset of its A operand(s) in the CTA's ring
-    int32_t dep;       // the record (CTA-local index) whose MMAs must finish before its copy, or -1
+    int32_t ring;      // unused (0)
+    int32_t dep;       // unused (0)
     int32_t n0;        // V' fills: first rank index of this block's columns
     int32_t nsub;      // V' fills: how many of the block's rank columns
     int32_t bcol;      // V' fills: their first column in the record's B
@@ -269,52 +285,15 @@ static vf_status pack_pages(vf_hmat* H, std::vector<TRec>& recs, const std::vect
     std::vector<TRec> ordered;
     for (int32_t c = 0; c < ncta; ++c) {
         cp[c] = (int32_t)used.size();
-        // The A-operand ring, planned here so the device only follows it: each
-        // record takes S x K x 256 contiguous bytes (wrapping to the start when
-        // the end is short) and may start its copy once `dep` (and so every
-        // earlier record: MMAs complete in order) has finished; dep is never
-        // more than kTickets records back, so each record's barrier ticket is free.
-        int32_t issued = 0, freed = 0;
-        uint32_t head = 0, tail = 0;
-        std::vector<uint32_t> start;
         for (int32_t gi : cta_groups[c]) {
             bool fresh = true;
             for (int64_t ri = group_recs[gi].first; ri < group_recs[gi].second; ++ri) {
                 TRec r = recs[ri];
                 if (!r.hdr) {  // another fill of the previous record
-                    const TRec& prev = ordered.back();
-                    r.dst = prev.dst;
-                    r.ring = prev.ring;
-                    r.dep = prev.dep;
+                    r.dst = ordered.back().dst;
                     ordered.push_back(r);
                     continue;
                 }
-                const uint32_t bytes = (uint32_t)(r.S * r.K16 * kPanel * 2);
-                uint32_t at = 0;
-                for (;;) {
-                    if (issued == freed) {
-                        head = tail = 0;
-                        at = 0;
-                        break;
-                    }
-                    if (issued - freed < kTickets) {
-                        if (head >= tail) {
-                            if (head + bytes <= (uint32_t)cfg_ring(r.S)) { at = head; break; }
-                            if (bytes < tail) { at = 0; break; }
-                        } else if (head + bytes < tail) {
-                            at = head;
-                            break;
-                        }
-                    }
-                    ++freed;  // wait for the oldest record in flight
-                    tail = issued > freed ? start[freed] : head;
-                }
-                start.push_back(at);
-                head = at + bytes;
-                r.ring = (int32_t)at;
-                r.dep = std::max(freed - 1, issued - kTickets);
-                if (r.dep < 0) r.dep = -1;
-                ++issued;
                 const uint32_t sz = (uint32_t)(kTRHdr + r.S * r.K16 * r.N16 * 2);
                 if (fresh || used.back() + sz > (uint32_t)kTP) {
                     used.push_back(kTPHdr);
@@ -767,7 +746,7 @@ __device__ __forceinline__ int64_t panel_off(int64_t row, int m) {
 }
 
 struct TSmem {
-    uint64_t page_full[kMaxPStages], page_empty[kMaxPStages], a_full[kTickets], a_empty[kTickets], d_full[2],
+    uint64_t page_full[kMaxPStages], page_empty[kMaxPStages], a_full[kMaxSlots], a_empty[kMaxSlots], d_full[2],
         d_empty[2], done;
     uint32_t tmem_base;
     int32_t abort;
@@ -785,27 +764,48 @@ struct TPanels {
     int64_t rows_x, rows_t;
 };
 
-// The producer (warp 0, lane 0): keeps up to kPStages pages in flight, and
-// for each record, in order, waits for its planned dependency (a record
-// whose MMAs free the ring bytes and the barrier ticket it reuses), then
-// copies its A operand(s) to the planned ring offset.
+// Copy page `next` of the CTA's list into its stage once the page that
+// stage held before has been consumed (its MMAs completed): with block, a
+// bounded wait for that; without, only a test.  Returns 1 if the copy was
+// issued, 0 if the stage is still busy, -1 on a timeout, -2 on a bad page.
+template <int NS>
+__device__ __forceinline__ int t_page_refill(TSmem& S, unsigned char* stages, const unsigned char* pages,
+                                             const uint32_t* used, int pa, int next, bool block) {
+    constexpr int PS = TCfg<NS>::PSTAGES;
+    const int s2 = next % PS;
+    if (next >= PS) {
+        const uint32_t par = (uint32_t)(((next / PS) - 1) & 1);
+        if (block) {
+            if (!bwait(&S.page_empty[s2], par)) return -1;
+        } else if (!mbar_test_wait(&S.page_empty[s2], par)) {
+            return 0;
+        }
+    }
+    const uint32_t bytes = used[pa + next];
+    if (bytes < kTPHdr || bytes > (uint32_t)kTP || (bytes & 15u)) return -2;
+    mbar_arrive_expect_tx(&S.page_full[s2], bytes);
+    bulk_g2s(stages + s2 * kTP, pages + (int64_t)(pa + next) * kTP, bytes, &S.page_full[s2]);
+    return 1;
+}
+
+// The producer (warp 0, lane 0): for each record in order, copies its A
+// operand (a contiguous panel range; with NS = 2 the hi and lo terms) chunk
+// by chunk into the slot ring, each slot reused once the MMAs that read it
+// have completed.  Pages are refilled as soon as their stage frees (tested
+// between chunks), so the A copies of one page never wait for the page
+// before it to be consumed.
 template <int NS>
 __device__ void t_producer(TSmem& S, unsigned char* stages, unsigned char* abuf, const unsigned char* pages,
                            const uint32_t* used, int pa, int pb, const TPanels& pn, int max_col, int* status) {
+    using SL = TSlots<NS>;
+    constexpr int PS = TCfg<NS>::PSTAGES;
     const int npl = pb - pa;
-    int pissued = 0, r = 0;  // pages copied; CTA-local record index
+    int next = 0, chunk = 0, rc = 0;  // next page to copy; CTA-local chunk index
+    for (; next < npl && next < PS; ++next)
+        if ((rc = t_page_refill<NS>(S, stages, pages, used, pa, next, true)) < 0) goto bad;
     for (int li = 0; li < npl; ++li) {
-        constexpr int PS = TCfg<NS>::PSTAGES;
-        while (pissued < npl && pissued < li + PS) {
-            const int s2 = pissued % PS;
-            if (pissued >= PS && !bwait(&S.page_empty[s2], (uint32_t)(((pissued / PS) - 1) & 1)))
-                goto fail;
-            const uint32_t bytes = used[pa + pissued];
-            if (bytes < kTPHdr || bytes > (uint32_t)kTP || (bytes & 15u)) goto oob;
-            mbar_arrive_expect_tx(&S.page_full[s2], bytes);
-            bulk_g2s(stages + s2 * kTP, pages + (int64_t)(pa + pissued) * kTP, bytes, &S.page_full[s2]);
-            ++pissued;
-        }
+        for (; next <= li; ++next)
+            if ((rc = t_page_refill<NS>(S, stages, pages, used, pa, next, true)) < 0) goto bad;
         const int s = li % PS;
         if (!bwait(&S.page_full[s], (uint32_t)((li / PS) & 1))) goto fail;
         {
@@ -813,25 +813,29 @@ __device__ void t_producer(TSmem& S, unsigned char* stages, unsigned char* abuf,
             const int nrec = (int)reinterpret_cast<const uint32_t*>(pg)[0];
             const uint32_t pused = reinterpret_cast<const uint32_t*>(pg)[1];
             uint32_t off = kTPHdr;
-            for (int i = 0; i < nrec; ++i, ++r) {
+            for (int i = 0; i < nrec; ++i) {
                 const uint4 h0 = *reinterpret_cast<const uint4*>(pg + off);
                 const uint4 h1 = *reinterpret_cast<const uint4*>(pg + off + 16);
                 const int K16 = (int)h0.x, N16 = (int)h0.y;
-                const uint32_t abytes = (uint32_t)K16 * kPanel * 2, bytes = NS * abytes;
-                const int dep = (int)h1.w;
-                const uint32_t ring = h1.z;
-                // self-check: shapes, the record inside the page, the A range inside its panel, the plan
+                // self-check: shapes, the record inside the page, the A range inside its panel
                 if (K16 < 16 || K16 > TCfg<NS>::KMAX || (K16 & 15) || N16 < 16 || N16 > max_col || (N16 & 15) ||
                     (int)h0.z + N16 > max_col || off + kTRHdr + (uint32_t)(NS * K16 * N16 * 2) > pused ||
-                    (h1.x & 7u) || (int64_t)h1.x + K16 > (h0.w ? pn.rows_t : pn.rows_x) ||
-                    ring + bytes > (uint32_t)TCfg<NS>::RING || (ring & 15u) || dep >= r || dep < r - kTickets)
+                    (h1.x & 7u) || (int64_t)h1.x + K16 > (h0.w ? pn.rows_t : pn.rows_x))
                     goto oob;
-                if (dep >= 0 && !bwait(&S.a_empty[dep % kTickets], (uint32_t)((dep / kTickets) & 1))) goto fail;
-                const int j = r % kTickets;
-                mbar_arrive_expect_tx(&S.a_full[j], bytes);
-                for (int t = 0; t < NS; ++t) {
-                    const unsigned char* src = (h0.w ? pn.T[t] : pn.X[t]) + (int64_t)(h1.x >> 3) * 2048;
-                    bulk_g2s(abuf + ring + t * abytes, src, abytes, &S.a_full[j]);
+                for (int kc = 0; kc < K16; kc += SL::CK, ++chunk) {
+                    if (next < npl) {
+                        if ((rc = t_page_refill<NS>(S, stages, pages, used, pa, next, false)) < 0) goto bad;
+                        next += rc;
+                    }
+                    const int slot = chunk % SL::NSLOT, use = chunk / SL::NSLOT;
+                    if (use >= 1 && !bwait(&S.a_empty[slot], (uint32_t)((use - 1) & 1))) goto fail;
+                    const int ck = min(SL::CK, K16 - kc);
+                    const uint32_t tb = (uint32_t)ck * kPanel * 2;
+                    mbar_arrive_expect_tx(&S.a_full[slot], NS * tb);
+                    for (int t = 0; t < NS; ++t) {
+                        const unsigned char* src = (h0.w ? pn.T[t] : pn.X[t]) + (int64_t)((h1.x + kc) >> 3) * 2048;
+                        bulk_g2s(abuf + slot * SL::BYTES + t * (SL::CK * kPanel * 2), src, tb, &S.a_full[slot]);
+                    }
                 }
                 off += kTRHdr + (uint32_t)(NS * K16 * N16 * 2);
             }
@@ -839,6 +843,8 @@ __device__ void t_producer(TSmem& S, unsigned char* stages, unsigned char* abuf,
         if (S.abort) return;
     }
     return;
+bad:
+    if (rc == -2) goto oob;
 fail:
     atomicExch(status, VF_E_TIMEOUT);
     atomicExch(&S.abort, 1);
@@ -855,7 +861,8 @@ oob:
 template <int NS, int REG, int NREG>
 __device__ void t_issuer(TSmem& S, unsigned char* stages, unsigned char* abuf, int pa, int pb, int* status) {
     static_assert(REG * NREG <= TCfg<NS>::TMEM && NREG <= 2, "accumulator regions");
-    int nrec = 0, dcount[2] = {0, 0}, d = 0;
+    using SL = TSlots<NS>;
+    int chunk = 0, dcount[2] = {0, 0}, d = 0;
     for (int p = pa, li = 0; p < pb; ++p, ++li) {
         const int s = li % TCfg<NS>::PSTAGES;
         if (!bwait(&S.page_full[s], (uint32_t)((li / TCfg<NS>::PSTAGES) & 1))) goto fail;
@@ -866,33 +873,37 @@ __device__ void t_issuer(TSmem& S, unsigned char* stages, unsigned char* abuf, i
             for (int r = 0; r < nr; ++r) {
                 const uint32_t* h = reinterpret_cast<const uint32_t*>(pg + off);
                 const int K16 = (int)h[0], N16 = (int)h[1], coloff = (int)h[2], flags = (int)h[5];
-                const int j = nrec % kTickets;
-                if (!bwait(&S.a_full[j], (uint32_t)((nrec / kTickets) & 1))) goto fail;
                 if (flags & TR_FIRST) {
                     if (!bwait(&S.d_empty[d], (uint32_t)(dcount[d] & 1))) goto fail;
                     tm_fence_after();
                 }
                 const uint32_t dt = S.tmem_base + (uint32_t)(d * REG + coloff);
-                const uint32_t bsa = smem_u32(pg + off + kTRHdr), asa = smem_u32(abuf + h[6]);
+                const uint32_t bsa = smem_u32(pg + off + kTRHdr);
                 const uint32_t blbo = (uint32_t)(N16 / 8) * 128;
                 const uint32_t idesc = mma_idesc(N16);
-                const uint32_t alo = (uint32_t)K16 * kPanel * 2, blo = (uint32_t)(K16 * N16 * 2);
-                for (int kk = 0; kk < K16 / 16; ++kk) {
-                    const uint64_t ah = mma_desc(asa + kk * 4096, 2048, 128);
-                    const uint64_t bh = mma_desc(bsa + kk * 2 * blbo, blbo, 128);
-                    mma_bf16(dt, ah, bh, idesc, (kk == 0 && (flags & TR_USTART)) ? 0 : 1);
-                    if (NS == 2) {
-                        mma_bf16(dt, mma_desc(asa + alo + kk * 4096, 2048, 128), bh, idesc, 1);
-                        mma_bf16(dt, ah, mma_desc(bsa + blo + kk * 2 * blbo, blbo, 128), idesc, 1);
+                const uint32_t blo = (uint32_t)(K16 * N16 * 2);
+                for (int kc = 0; kc < K16; kc += SL::CK, ++chunk) {
+                    const int slot = chunk % SL::NSLOT;
+                    if (!bwait(&S.a_full[slot], (uint32_t)((chunk / SL::NSLOT) & 1))) goto fail;
+                    const uint32_t asa = smem_u32(abuf + slot * SL::BYTES);
+                    const int ck = min(SL::CK, K16 - kc);
+                    for (int kk = 0; kk < ck / 16; ++kk) {
+                        const int ks = kc / 16 + kk;  // K step within the record
+                        const uint64_t ah = mma_desc(asa + kk * 4096, 2048, 128);
+                        const uint64_t bh = mma_desc(bsa + ks * 2 * blbo, blbo, 128);
+                        mma_bf16(dt, ah, bh, idesc, (ks == 0 && (flags & TR_USTART)) ? 0 : 1);
+                        if (NS == 2) {
+                            mma_bf16(dt, mma_desc(asa + SL::CK * kPanel * 2 + kk * 4096, 2048, 128), bh, idesc, 1);
+                            mma_bf16(dt, ah, mma_desc(bsa + blo + ks * 2 * blbo, blbo, 128), idesc, 1);
+                        }
                     }
+                    mma_commit(&S.a_empty[slot]);
                 }
-                mma_commit(&S.a_empty[j]);
                 if (flags & TR_LAST) {
                     mma_commit(&S.d_full[d]);
                     dcount[d]++;
                     d = NREG == 1 ? 0 : d ^ 1;
                 }
-                ++nrec;
                 off += kTRHdr + (uint32_t)(NS * K16 * N16 * 2);
             }
         }
@@ -921,7 +932,7 @@ __device__ void t_prologue(TSmem& S) {
             mbar_init(&S.d_full[i], 1);
             mbar_init(&S.d_empty[i], 4);
         }
-        for (int i = 0; i < kTickets; ++i) {
+        for (int i = 0; i < kMaxSlots; ++i) {
             mbar_init(&S.a_full[i], 1);
             mbar_init(&S.a_empty[i], 1);
         }
@@ -989,7 +1000,7 @@ template <int NS>
 __device__ void t_drain(TSmem& S) {
     for (int s = 0; s < TCfg<NS>::PSTAGES; ++s)
         mbar_wait(&S.page_full[s], 0, 1024), mbar_wait(&S.page_full[s], 1, 1024);
-    for (int j = 0; j < kTickets; ++j) mbar_wait(&S.a_full[j], 0, 1024), mbar_wait(&S.a_full[j], 1, 1024);
+    for (int j = 0; j < TSlots<NS>::NSLOT; ++j) mbar_wait(&S.a_full[j], 0, 1024), mbar_wait(&S.a_full[j], 1, 1024);
 }
 
 // ------------------------------------------------------------ phase 1
