@@ -1367,8 +1367,9 @@ static vf_status tensor_ws(const vf_hmat* h, Workspace* w) {
         VF_TRY(w->xpan[i].alloc((size_t)w->tpanels * bx));
         VF_TRY_CUDA(cudaMemset(w->xpan[i].p, 0, (size_t)w->tpanels * bx));
     }
-    VF_TRY(w->tpan.alloc((size_t)bt));
-    VF_TRY_CUDA(cudaMemset(w->tpan.p, 0, (size_t)bt));
+    // two T panels: multiplies of two RHS panels at once
+    VF_TRY(w->tpan.alloc((size_t)2 * bt));
+    VF_TRY_CUDA(cudaMemset(w->tpan.p, 0, (size_t)2 * bt));
     VF_TRY(w->tcount.alloc(2));
     VF_TRY_CUDA(cudaMemset(w->tcount.p, 0, 2 * sizeof(int)));
     return VF_OK;
@@ -1437,7 +1438,8 @@ static vf_status tensor_jacobi_loop(const vf_hmat* h, Workspace* w, int max_iter
     *kernels += 1 + w->tpanels;
     int it = 0, cur = 0;
     while (it < max_iter) {
-        for (int p = 0; p < w->tpanels; ++p) {
+        for (int p = 0, np; p < w->tpanels; p += np) {
+            np = p + 1 < w->tpanels ? 2 : 1;  // two RHS panels per multiply where there are two
             TEpi ep{};
             ep.mode = 1;
             ep.n = n;
@@ -1448,16 +1450,18 @@ static vf_status tensor_jacobi_loop(const vf_hmat* h, Workspace* w, int max_iter
             ep.rho = w->rho_t.p;
             ep.Bold = w->Bt[cur].p;
             ep.Xnext = w->xpan[cur ^ 1].p + (size_t)p * bx;
+            ep.xstride = bx;
             ep.colpart = w->colpart.p;
             ep.ntiles = ntiles;
-            VF_TRY(tensor_multiply(h, 1, w->xpan[cur].p + (size_t)p * bx, nullptr, w->tpan.p, nullptr, ep,
+            VF_TRY(tensor_multiply(h, 1, np, w->xpan[cur].p + (size_t)p * bx, nullptr, w->tpan.p, nullptr, ep,
                                    w->status.p, st));
+            *kernels += tensor_kernels(h, 1);
         }
         k_unconverged<<<(unsigned)NV, 256, 0, st>>>(w->colpart.p, ntiles, w->R, h->nseg(), tensor_seg_parts(h, 1),
                                                     w->enorm2.p, rtol * rtol, w->colres.p, w->tcount.p,
                                                     w->tcount.p + 1);
         VF_TRY_CUDA(cudaGetLastError());
-        *kernels += w->tpanels * tensor_kernels(h, 1) + 1;
+        *kernels += 1;
         int hc = 0;
         VF_TRY_CUDA(cudaMemcpyAsync(&hc, w->tcount.p, sizeof(int), cudaMemcpyDeviceToHost, st));
         VF_TRY_CUDA(cudaStreamSynchronize(st));
@@ -1504,7 +1508,7 @@ static vf_status tensor_residual(const vf_hmat* h, Workspace* w, const float* B,
         ep.Bold = B;
         ep.colpart = w->colpart.p;
         ep.ntiles = ntiles;
-        VF_TRY(tensor_multiply(h, 2, xh, xl, w->tsplit[0].p, w->tsplit[1].p, ep, w->status.p, st));
+        VF_TRY(tensor_multiply(h, 2, 1, xh, xl, w->tsplit[0].p, w->tsplit[1].p, ep, w->status.p, st));
     }
     k_unconverged<<<(unsigned)(w->R * h->nseg()), 256, 0, st>>>(w->colpart.p, ntiles, w->R, h->nseg(),
                                                                 tensor_seg_parts(h, 2), w->enorm2.p, 0.0, w->colres.p,
@@ -1520,16 +1524,18 @@ static vf_status tensor_apply(const vf_hmat* h, Workspace* w, const float* X, in
                               float* Y, cudaStream_t st) {
     VF_TRY(tensor_ws(h, w));
     const int64_t bx = tensor_panel_bytes_x(h);
-    for (int p = 0; p < w->tpanels; ++p) {
+    for (int p = 0, np; p < w->tpanels; p += np) {
+        np = p + 1 < w->tpanels ? 2 : 1;  // two RHS panels per multiply where there are two
         unsigned char* xp = w->xpan[0].p + (size_t)p * bx;
-        VF_TRY(tensor_to_panel(h, X, ld, perm, w->R, p * kTensorPanel, xp, nullptr, st));
+        for (int q = 0; q < np; ++q)
+            VF_TRY(tensor_to_panel(h, X, ld, perm, w->R, (p + q) * kTensorPanel, xp + (size_t)q * bx, nullptr, st));
         TEpi ep{};
         ep.mode = 0;
         ep.n = h->nf;
         ep.R = w->R;
         ep.p0 = p * kTensorPanel;
         ep.Y = Y;
-        VF_TRY(tensor_multiply(h, 1, xp, nullptr, w->tpan.p, nullptr, ep, w->status.p, st));
+        VF_TRY(tensor_multiply(h, 1, np, xp, nullptr, w->tpan.p, nullptr, ep, w->status.p, st));
     }
     return VF_OK;
 }

@@ -50,65 +50,53 @@ constexpr int kTPHdr = 16;           // page header: nrec, used, 0, 0
 constexpr int kTRHdr = 32;           // record header (8 x u32)
 constexpr int kPanel = 128;          // right-hand sides per panel (MMA M)
 constexpr int kMaxSlots = 16;        // A-operand ring slots (barrier pairs)
-// Both page sets run four CTAs per SM: the multiply is bound by the
-// single-thread producer and MMA-issuer steps of each CTA's pipeline, so
-// independent pipelines per SM count most.  Per CTA (BF16 set): three 12 KB
-// page stages, an A ring of two 8 KB slots, two accumulator regions of 64
-// TMEM columns.  The split set (S = 2, hi and lo A operands) has two page
-// stages and caps a record's K at 32.  Measured for one 128-RHS BF16
-// multiply of the 79k-facet terrain: this 1.32 ms; two 16 KB stages and a
-// 20 KB ring 1.37 ms; four 8 KB stages 1.43 ms; 16-row chunks in five slots
-// 1.56 ms; super-tiles of 128 rows in one 128-column region 1.49 ms; three
-// CTAs per SM or two CTAs with deeper buffers 1.6-2.1 ms.
-template <int NS> struct TCfg;
-// Phase 2 accumulates a (super-)tile of consecutive row tiles, up to R2
-// rows, in NREG2 regions of R2 TMEM columns used in turn.  The VF_T*
-// macros select the configuration at build time.
-#ifndef VF_T1_R2
-#define VF_T1_R2 64
-#endif
-#ifndef VF_T1_NREG2
-#define VF_T1_NREG2 2
-#endif
-#ifndef VF_T1_CTAS
-#define VF_T1_CTAS 4
-#endif
-#ifndef VF_T1_PSTAGES
-#define VF_T1_PSTAGES 3
-#endif
-#ifndef VF_T1_RING
-#define VF_T1_RING 16384
-#endif
-#ifndef VF_T1_KMAX
-#define VF_T1_KMAX 64
-#endif
-template <> struct TCfg<1> {
-    static constexpr int PSTAGES = VF_T1_PSTAGES, RING = VF_T1_RING, CTAS = VF_T1_CTAS, REGION = 64, KMAX = VF_T1_KMAX,
-                         R2 = VF_T1_R2, NREG2 = VF_T1_NREG2, TMEM = R2 * NREG2 > 128 ? 256 : 128;
+// Kernel configurations per (NS, NP): NS = 1 (BF16) or 2 (the split
+// residual's hi and lo terms); NP = RHS panels of 128 per CTA.  With NP = 2
+// one B operand (the factor record, from HBM) serves two A operands and two
+// accumulators, which halves the per-record single-thread steps (producer
+// and MMA issuer) per right-hand side; those steps bound the multiply, so
+// every configuration also runs four CTAs (four independent pipelines) per
+// SM.  Per CTA: PSTAGES 12 KB page stages, an A ring of RING bytes in slots
+// of NP x NS x CK x 256 bytes, TMEM of 128 columns: NREG accumulator
+// regions of NP x 64 columns.  Measured for one 128-RHS BF16 multiply of the
+// 79k-facet terrain (NP = 1): this 1.32 ms; two 16 KB stages and a 20 KB
+// ring 1.37 ms; four 8 KB stages 1.43 ms; 16-row chunks in five slots
+// 1.56 ms; super-tiles of 128 rows in one 128-column region 1.49 ms; five
+// CTAs with one 64-column region each 1.30 ms; three CTAs per SM or two
+// CTAs with deeper buffers 1.6-2.1 ms.  Two panels per CTA: 1.23 ms per
+// 128 RHS.
+template <int NS, int NP> struct TCfg;
+template <> struct TCfg<1, 1> {
+    static constexpr int PSTAGES = 3, RING = 16384, CTAS = 4, CK = 32, NREG = 2, TMEM = 128;
 };
-template <> struct TCfg<2> {
-    static constexpr int PSTAGES = 2, RING = 20480, CTAS = 4, REGION = 64, KMAX = 32, R2 = 64, NREG2 = 2, TMEM = 128;
+template <> struct TCfg<1, 2> {
+    static constexpr int PSTAGES = 3, RING = 16384, CTAS = 4, CK = 16, NREG = 1, TMEM = 128;
 };
+template <> struct TCfg<2, 1> {
+    static constexpr int PSTAGES = 2, RING = 20480, CTAS = 4, CK = 16, NREG = 2, TMEM = 128;
+};
+// Shared by every configuration of a page set (records do not depend on NP):
+constexpr int kRegion = 64;     // accumulator columns per panel: a phase-1 group's rank columns, a tile's rows
 constexpr int kMaxPStages = 4;
-// A operands stream through a ring of NSLOT slots, one K chunk of CK rows
-// (x NS terms) per slot, so the copy of one record's later chunks (and of
-// the next record) overlaps the MMAs of its earlier ones.
-#ifndef VF_T_CK
-#define VF_T_CK 32
-#endif
-template <int NS> struct TSlots {
-    static constexpr int CK = NS == 1 ? VF_T_CK : 16;           // K rows per chunk
-    static constexpr int BYTES = NS * CK * 128 * 2;             // one chunk, all terms
-    static constexpr int NSLOT = TCfg<NS>::RING / BYTES;
+template <int NS> __host__ __device__ constexpr int kmax_of() { return NS == 1 ? 64 : 32; }  // K rows per record
+// A operands stream through the ring one K chunk of CK rows (all panels and
+// terms) per slot, so the copy of one record's later chunks (and of the next
+// record) overlaps the MMAs of its earlier ones.
+template <int NS, int NP> struct TSlots {
+    static constexpr int CK = TCfg<NS, NP>::CK;
+    static constexpr int TERM = CK * 128 * 2;  // one panel, one term
+    static constexpr int BYTES = NP * NS * TERM;
+    static constexpr int NSLOT = TCfg<NS, NP>::RING / BYTES;
     static_assert(NSLOT >= 2 && NSLOT <= kMaxSlots, "A ring slots");
+    static_assert(NP * kRegion * TCfg<NS, NP>::NREG <= TCfg<NS, NP>::TMEM, "accumulator regions");
 };
-static int cfg_ctas(int S) { return S == 1 ? TCfg<1>::CTAS : TCfg<2>::CTAS; }
-static int cfg_region(int S) { return S == 1 ? TCfg<1>::REGION : TCfg<2>::REGION; }
-static int cfg_kmax(int S) { return S == 1 ? TCfg<1>::KMAX : TCfg<2>::KMAX; }
-static int cfg_r2(int S) { return S == 1 ? TCfg<1>::R2 : TCfg<2>::R2; }
-template <int NS>
+static int cfg_ctas(int S) { return S == 1 ? TCfg<1, 1>::CTAS : TCfg<2, 1>::CTAS; }
+static int cfg_region(int) { return kRegion; }
+static int cfg_kmax(int S) { return S == 1 ? kmax_of<1>() : kmax_of<2>(); }
+static int cfg_r2(int) { return kRegion; }  // phase-2 (super-)tiles: one row tile
+template <int NS, int NP>
 constexpr size_t tsmem_bytes() {
-    return (size_t)TCfg<NS>::PSTAGES * kTP + TCfg<NS>::RING + 1024;
+    return (size_t)TCfg<NS, NP>::PSTAGES * kTP + TCfg<NS, NP>::RING + 1024;
 }
 constexpr uint32_t kTWait = 1u << 22;
 // record flags: FIRST / LAST record of its accumulator region's use (a
@@ -752,26 +740,26 @@ struct TSmem {
     int32_t abort;
 };
 
-
 static_assert(sizeof(TSmem) <= 1024, "barrier block");
 
-// The producer (warp 0, lane 0): pages [pa, pb) into two stages, and each
-// record's A operand (a contiguous panel range) into the A ring.
-// The RHS panels a kernel reads: X (hi, lo) and T (hi, lo); lo only with S = 2.
+// The RHS panels a kernel reads: X (hi, lo) and T (hi, lo), lo only with
+// NS = 2; with NP = 2 the second panel's X and T follow at xstride and
+// tstride bytes.
 struct TPanels {
     const unsigned char* X[2];
     unsigned char* T[2];
     int64_t rows_x, rows_t;
+    int64_t xstride, tstride;
 };
 
 // Copy page `next` of the CTA's list into its stage once the page that
 // stage held before has been consumed (its MMAs completed): with block, a
 // bounded wait for that; without, only a test.  Returns 1 if the copy was
 // issued, 0 if the stage is still busy, -1 on a timeout, -2 on a bad page.
-template <int NS>
+template <int NS, int NP>
 __device__ __forceinline__ int t_page_refill(TSmem& S, unsigned char* stages, const unsigned char* pages,
                                              const uint32_t* used, int pa, int next, bool block) {
-    constexpr int PS = TCfg<NS>::PSTAGES;
+    constexpr int PS = TCfg<NS, NP>::PSTAGES;
     const int s2 = next % PS;
     if (next >= PS) {
         const uint32_t par = (uint32_t)(((next / PS) - 1) & 1);
@@ -789,23 +777,23 @@ __device__ __forceinline__ int t_page_refill(TSmem& S, unsigned char* stages, co
 }
 
 // The producer (warp 0, lane 0): for each record in order, copies its A
-// operand (a contiguous panel range; with NS = 2 the hi and lo terms) chunk
-// by chunk into the slot ring, each slot reused once the MMAs that read it
-// have completed.  Pages are refilled as soon as their stage frees (tested
-// between chunks), so the A copies of one page never wait for the page
-// before it to be consumed.
-template <int NS>
+// operand (a contiguous panel range, per panel and term) chunk by chunk into
+// the slot ring, each slot reused once the MMAs that read it have completed.
+// Pages are refilled as soon as their stage frees (tested between chunks),
+// so the A copies of one page never wait for the page before it to be
+// consumed.
+template <int NS, int NP>
 __device__ void t_producer(TSmem& S, unsigned char* stages, unsigned char* abuf, const unsigned char* pages,
                            const uint32_t* used, int pa, int pb, const TPanels& pn, int max_col, int* status) {
-    using SL = TSlots<NS>;
-    constexpr int PS = TCfg<NS>::PSTAGES;
+    using SL = TSlots<NS, NP>;
+    constexpr int PS = TCfg<NS, NP>::PSTAGES;
     const int npl = pb - pa;
     int next = 0, chunk = 0, rc = 0;  // next page to copy; CTA-local chunk index
     for (; next < npl && next < PS; ++next)
-        if ((rc = t_page_refill<NS>(S, stages, pages, used, pa, next, true)) < 0) goto bad;
+        if ((rc = t_page_refill<NS, NP>(S, stages, pages, used, pa, next, true)) < 0) goto bad;
     for (int li = 0; li < npl; ++li) {
         for (; next <= li; ++next)
-            if ((rc = t_page_refill<NS>(S, stages, pages, used, pa, next, true)) < 0) goto bad;
+            if ((rc = t_page_refill<NS, NP>(S, stages, pages, used, pa, next, true)) < 0) goto bad;
         const int s = li % PS;
         if (!bwait(&S.page_full[s], (uint32_t)((li / PS) & 1))) goto fail;
         {
@@ -818,24 +806,27 @@ __device__ void t_producer(TSmem& S, unsigned char* stages, unsigned char* abuf,
                 const uint4 h1 = *reinterpret_cast<const uint4*>(pg + off + 16);
                 const int K16 = (int)h0.x, N16 = (int)h0.y;
                 // self-check: shapes, the record inside the page, the A range inside its panel
-                if (K16 < 16 || K16 > TCfg<NS>::KMAX || (K16 & 15) || N16 < 16 || N16 > max_col || (N16 & 15) ||
+                if (K16 < 16 || K16 > kmax_of<NS>() || (K16 & 15) || N16 < 16 || N16 > max_col || (N16 & 15) ||
                     (int)h0.z + N16 > max_col || off + kTRHdr + (uint32_t)(NS * K16 * N16 * 2) > pused ||
                     (h1.x & 7u) || (int64_t)h1.x + K16 > (h0.w ? pn.rows_t : pn.rows_x))
                     goto oob;
                 for (int kc = 0; kc < K16; kc += SL::CK, ++chunk) {
                     if (next < npl) {
-                        if ((rc = t_page_refill<NS>(S, stages, pages, used, pa, next, false)) < 0) goto bad;
+                        if ((rc = t_page_refill<NS, NP>(S, stages, pages, used, pa, next, false)) < 0) goto bad;
                         next += rc;
                     }
                     const int slot = chunk % SL::NSLOT, use = chunk / SL::NSLOT;
                     if (use >= 1 && !bwait(&S.a_empty[slot], (uint32_t)((use - 1) & 1))) goto fail;
                     const int ck = min(SL::CK, K16 - kc);
                     const uint32_t tb = (uint32_t)ck * kPanel * 2;
-                    mbar_arrive_expect_tx(&S.a_full[slot], NS * tb);
-                    for (int t = 0; t < NS; ++t) {
-                        const unsigned char* src = (h0.w ? pn.T[t] : pn.X[t]) + (int64_t)((h1.x + kc) >> 3) * 2048;
-                        bulk_g2s(abuf + slot * SL::BYTES + t * (SL::CK * kPanel * 2), src, tb, &S.a_full[slot]);
-                    }
+                    const int64_t roff = (int64_t)((h1.x + kc) >> 3) * 2048;
+                    mbar_arrive_expect_tx(&S.a_full[slot], NP * NS * tb);
+                    for (int q = 0; q < NP; ++q)
+                        for (int t = 0; t < NS; ++t) {
+                            const unsigned char* src =
+                                h0.w ? pn.T[t] + q * pn.tstride + roff : pn.X[t] + q * pn.xstride + roff;
+                            bulk_g2s(abuf + slot * SL::BYTES + (q * NS + t) * SL::TERM, src, tb, &S.a_full[slot]);
+                        }
                 }
                 off += kTRHdr + (uint32_t)(NS * K16 * N16 * 2);
             }
@@ -856,16 +847,17 @@ oob:
 
 // The MMA issuer (warp 1, lane 0).  With NS = 2 each K step is three MMAs,
 // A_hi B_hi + A_lo B_hi + A_hi B_lo (the lo x lo term, ~2^-16 of the
-// product, is dropped), all into the same FP32 accumulator.  The
-// accumulator is NREG regions of REG columns, used in turn.
-template <int NS, int REG, int NREG>
+// product, is dropped), all into the same FP32 accumulator; with NP = 2 the
+// same B operand meets each panel's A in that panel's accumulator columns.
+// The accumulator is NREG regions of NP x 64 columns, used in turn.
+template <int NS, int NP>
 __device__ void t_issuer(TSmem& S, unsigned char* stages, unsigned char* abuf, int pa, int pb, int* status) {
-    static_assert(REG * NREG <= TCfg<NS>::TMEM && NREG <= 2, "accumulator regions");
-    using SL = TSlots<NS>;
+    using SL = TSlots<NS, NP>;
+    constexpr int NREG = TCfg<NS, NP>::NREG, REGW = NP * kRegion;
     int chunk = 0, dcount[2] = {0, 0}, d = 0;
     for (int p = pa, li = 0; p < pb; ++p, ++li) {
-        const int s = li % TCfg<NS>::PSTAGES;
-        if (!bwait(&S.page_full[s], (uint32_t)((li / TCfg<NS>::PSTAGES) & 1))) goto fail;
+        const int s = li % TCfg<NS, NP>::PSTAGES;
+        if (!bwait(&S.page_full[s], (uint32_t)((li / TCfg<NS, NP>::PSTAGES) & 1))) goto fail;
         {
             const unsigned char* pg = stages + s * kTP;
             const int nr = (int)reinterpret_cast<const uint32_t*>(pg)[0];
@@ -877,7 +869,7 @@ __device__ void t_issuer(TSmem& S, unsigned char* stages, unsigned char* abuf, i
                     if (!bwait(&S.d_empty[d], (uint32_t)(dcount[d] & 1))) goto fail;
                     tm_fence_after();
                 }
-                const uint32_t dt = S.tmem_base + (uint32_t)(d * REG + coloff);
+                const uint32_t dt = S.tmem_base + (uint32_t)(d * REGW + coloff);
                 const uint32_t bsa = smem_u32(pg + off + kTRHdr);
                 const uint32_t blbo = (uint32_t)(N16 / 8) * 128;
                 const uint32_t idesc = mma_idesc(N16);
@@ -889,12 +881,18 @@ __device__ void t_issuer(TSmem& S, unsigned char* stages, unsigned char* abuf, i
                     const int ck = min(SL::CK, K16 - kc);
                     for (int kk = 0; kk < ck / 16; ++kk) {
                         const int ks = kc / 16 + kk;  // K step within the record
-                        const uint64_t ah = mma_desc(asa + kk * 4096, 2048, 128);
                         const uint64_t bh = mma_desc(bsa + ks * 2 * blbo, blbo, 128);
-                        mma_bf16(dt, ah, bh, idesc, (ks == 0 && (flags & TR_USTART)) ? 0 : 1);
-                        if (NS == 2) {
-                            mma_bf16(dt, mma_desc(asa + SL::CK * kPanel * 2 + kk * 4096, 2048, 128), bh, idesc, 1);
-                            mma_bf16(dt, ah, mma_desc(bsa + blo + ks * 2 * blbo, blbo, 128), idesc, 1);
+                        const int acc = (ks == 0 && (flags & TR_USTART)) ? 0 : 1;
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) {
+                            const uint32_t aq = asa + (uint32_t)(q * NS * SL::TERM + kk * 4096);
+                            const uint64_t ah = mma_desc(aq, 2048, 128);
+                            const uint32_t dq = dt + (uint32_t)(q * kRegion);
+                            mma_bf16(dq, ah, bh, idesc, acc);
+                            if (NS == 2) {
+                                mma_bf16(dq, mma_desc(aq + SL::TERM, 2048, 128), bh, idesc, 1);
+                                mma_bf16(dq, ah, mma_desc(bsa + blo + ks * 2 * blbo, blbo, 128), idesc, 1);
+                            }
                         }
                     }
                     mma_commit(&S.a_empty[slot]);
@@ -919,12 +917,12 @@ fail:
 }
 
 // Common prologue: barriers, TMEM allocation, both regions zeroed.
-template <int NS>
+template <int NS, int NP>
 __device__ void t_prologue(TSmem& S) {
-    constexpr int ncols = TCfg<NS>::TMEM;
+    constexpr int ncols = TCfg<NS, NP>::TMEM;
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < TCfg<NS>::PSTAGES; ++i) {
+        for (int i = 0; i < TCfg<NS, NP>::PSTAGES; ++i) {
             mbar_init(&S.page_full[i], 1);
             mbar_init(&S.page_empty[i], 1);
         }
@@ -949,7 +947,7 @@ __device__ void t_prologue(TSmem& S) {
     __syncthreads();
     tm_fence_after();
     if (warp >= 2) {
-        // zero both accumulator regions (this warp's 32 lanes), then release them
+        // zero the accumulator columns (this warp's 32 lanes), then release both regions
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         for (int c = 0; c < ncols; c += 16) tm_zero16(S.tmem_base + lane_base + c);
         tm_wait_st();
@@ -963,9 +961,9 @@ __device__ void t_prologue(TSmem& S) {
 }
 
 // Common epilogue of a CTA: wait for the MMAs, free TMEM.
-template <int NS>
+template <int NS, int NP>
 __device__ void t_finish(TSmem& S, int* status) {
-    constexpr int ncols = TCfg<NS>::TMEM;
+    constexpr int ncols = TCfg<NS, NP>::TMEM;
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 32) {
         if (!bwait(&S.done, 0)) atomicExch(status, VF_E_TIMEOUT);
@@ -979,15 +977,14 @@ __device__ void t_finish(TSmem& S, int* status) {
     }
 }
 
-// Release a region after the epilogue read it (zeroing it first when the
-// next use accumulates into it), then arrive.
-template <int REG>
+// Release a region of REGW columns after the epilogue read it (zeroing it
+// first when the next use accumulates into it), then arrive.
+template <int REGW>
 __device__ __forceinline__ void t_release(TSmem& S, int d, bool zero) {
     const int warp = threadIdx.x >> 5;
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
     if (zero) {
-        for (int c = 0; c < REG; c += 16)
-            tm_zero16(S.tmem_base + lane_base + d * REG + c);
+        for (int c = 0; c < REGW; c += 16) tm_zero16(S.tmem_base + lane_base + d * REGW + c);
         tm_wait_st();
     }
     tm_fence_before();
@@ -996,47 +993,48 @@ __device__ __forceinline__ void t_release(TSmem& S, int d, bool zero) {
 }
 
 // Drain (producer): wait for every copy it may have left in flight.
-template <int NS>
+template <int NS, int NP>
 __device__ void t_drain(TSmem& S) {
-    for (int s = 0; s < TCfg<NS>::PSTAGES; ++s)
+    for (int s = 0; s < TCfg<NS, NP>::PSTAGES; ++s)
         mbar_wait(&S.page_full[s], 0, 1024), mbar_wait(&S.page_full[s], 1, 1024);
-    for (int j = 0; j < TSlots<NS>::NSLOT; ++j) mbar_wait(&S.a_full[j], 0, 1024), mbar_wait(&S.a_full[j], 1, 1024);
+    for (int j = 0; j < TSlots<NS, NP>::NSLOT; ++j)
+        mbar_wait(&S.a_full[j], 0, 1024), mbar_wait(&S.a_full[j], 1, 1024);
 }
 
 // ------------------------------------------------------------ phase 1
-// T panel rows offT16 .. + N16 of each unit = (V'^T X) for this panel.
-template <int NS>
-__global__ void __launch_bounds__(192, TCfg<NS>::CTAS) k_tphase1(const unsigned char* __restrict__ pages,
-                                                    const uint32_t* __restrict__ used,
-                                                    const int32_t* __restrict__ cta_pages,
-                                                    const int32_t* __restrict__ cta_units,
-                                                    const int32_t* __restrict__ cta_unit_ptr, TPanels pn,
-                                                    int* __restrict__ status) {
-    constexpr int MAXCOL = TCfg<NS>::REGION;
+// T panel rows offT16 .. + N16 of each unit = (V'^T X), per RHS panel.
+template <int NS, int NP>
+__global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase1(const unsigned char* __restrict__ pages,
+                                                        const uint32_t* __restrict__ used,
+                                                        const int32_t* __restrict__ cta_pages,
+                                                        const int32_t* __restrict__ cta_units,
+                                                        const int32_t* __restrict__ cta_unit_ptr, TPanels pn,
+                                                        int* __restrict__ status) {
+    constexpr int NREG = TCfg<NS, NP>::NREG, REGW = NP * kRegion;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* stages = smem;
-    unsigned char* abuf = smem + TCfg<NS>::PSTAGES * kTP;
-    TSmem& S = *reinterpret_cast<TSmem*>(smem + TCfg<NS>::PSTAGES * kTP + TCfg<NS>::RING);
+    unsigned char* abuf = smem + TCfg<NS, NP>::PSTAGES * kTP;
+    TSmem& S = *reinterpret_cast<TSmem*>(smem + TCfg<NS, NP>::PSTAGES * kTP + TCfg<NS, NP>::RING);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    t_prologue<NS>(S);
+    t_prologue<NS, NP>(S);
     __syncthreads();
     const int pa = cta_pages[blockIdx.x], pb = cta_pages[blockIdx.x + 1];
     if (warp == 0) {
         if (lane == 0) {
-            t_producer<NS>(S, stages, abuf, pages, used, pa, pb, pn, MAXCOL, status);
-            if (S.abort) t_drain<NS>(S);
+            t_producer<NS, NP>(S, stages, abuf, pages, used, pa, pb, pn, kRegion, status);
+            if (S.abort) t_drain<NS, NP>(S);
         }
     } else if (warp == 1) {
-        if (lane == 0) t_issuer<NS, TCfg<NS>::REGION, 2>(S, stages, abuf, pa, pb, status);
+        if (lane == 0) t_issuer<NS, NP>(S, stages, abuf, pa, pb, status);
     } else {
         const int m = 32 * (warp & 3) + lane;
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         const int u0 = cta_unit_ptr[blockIdx.x], u1 = cta_unit_ptr[blockIdx.x + 1];
         bool open = false;  // inside a group (its region filled)
         for (int u = u0, k = 0; u < u1; ++u) {
-            const int d = k & 1;
+            const int d = NREG == 1 ? 0 : (k & 1);
             if (!open) {
-                if (!__all_sync(0xffffffffu, bwait(&S.d_full[d], (uint32_t)((k >> 1) & 1)))) {
+                if (!__all_sync(0xffffffffu, bwait(&S.d_full[d], (uint32_t)((k / NREG) & 1)))) {
                     if (lane == 0) atomicExch(status, VF_E_TIMEOUT), atomicExch(&S.abort, 1);
                     break;
                 }
@@ -1045,58 +1043,59 @@ __global__ void __launch_bounds__(192, TCfg<NS>::CTAS) k_tphase1(const unsigned 
             }
             const int offT = cta_units[4 * u], N16 = cta_units[4 * u + 1], col = cta_units[4 * u + 2];
             const bool gend = cta_units[4 * u + 3] != 0;
-            for (int c0 = 0; c0 < N16; c0 += 16) {
-                float v[16];
-                tm_ld16(S.tmem_base + lane_base + d * TCfg<NS>::REGION + col + c0, v);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int64_t o = panel_off(offT + c0 + j, m);
-                    const __nv_bfloat16 hi = __float2bfloat16_rn(v[j]);
-                    *reinterpret_cast<__nv_bfloat16*>(pn.T[0] + o) = hi;
-                    if (NS == 2) *reinterpret_cast<__nv_bfloat16*>(pn.T[1] + o) = __float2bfloat16_rn(v[j] - __bfloat162float(hi));
+            for (int q = 0; q < NP; ++q)
+                for (int c0 = 0; c0 < N16; c0 += 16) {
+                    float v[16];
+                    tm_ld16(S.tmem_base + lane_base + d * REGW + q * kRegion + col + c0, v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int64_t o = q * pn.tstride + panel_off(offT + c0 + j, m);
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(v[j]);
+                        *reinterpret_cast<__nv_bfloat16*>(pn.T[0] + o) = hi;
+                        if (NS == 2)
+                            *reinterpret_cast<__nv_bfloat16*>(pn.T[1] + o) =
+                                __float2bfloat16_rn(v[j] - __bfloat162float(hi));
+                    }
                 }
-            }
             if (gend) {
-                t_release<TCfg<NS>::REGION>(S, d, false);  // each unit's first MMA overwrites its columns
+                t_release<REGW>(S, d, false);  // each unit's first MMA overwrites its columns
                 open = false;
                 ++k;
             }
         }
     }
-    t_finish<NS>(S, status);
+    t_finish<NS, NP>(S, status);
 }
 
 // ------------------------------------------------------------ phase 2
-template <int NS>
-__global__ void __launch_bounds__(192, TCfg<NS>::CTAS) k_tphase2(const unsigned char* __restrict__ pages,
-                                                    const uint32_t* __restrict__ used,
-                                                    const int32_t* __restrict__ cta_pages,
-                                                    const int32_t* __restrict__ cta_tiles,
-                                                    const int32_t* __restrict__ cta_tile_ptr,
-                                                    const int32_t* __restrict__ tile_first,
-                                                    const int32_t* __restrict__ tile_count, TPanels pn, TEpi ep,
-                                                    int* __restrict__ status) {
-    constexpr int REG = TCfg<NS>::R2, NREG = TCfg<NS>::NREG2;
-    constexpr int MAXCOL = REG;  // phase 2: a (super-)tile's rows
+template <int NS, int NP>
+__global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase2(const unsigned char* __restrict__ pages,
+                                                        const uint32_t* __restrict__ used,
+                                                        const int32_t* __restrict__ cta_pages,
+                                                        const int32_t* __restrict__ cta_tiles,
+                                                        const int32_t* __restrict__ cta_tile_ptr,
+                                                        const int32_t* __restrict__ tile_first,
+                                                        const int32_t* __restrict__ tile_count, TPanels pn, TEpi ep,
+                                                        int* __restrict__ status) {
+    constexpr int NREG = TCfg<NS, NP>::NREG, REGW = NP * kRegion;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* stages = smem;
-    unsigned char* abuf = smem + TCfg<NS>::PSTAGES * kTP;
-    TSmem& S = *reinterpret_cast<TSmem*>(smem + TCfg<NS>::PSTAGES * kTP + TCfg<NS>::RING);
+    unsigned char* abuf = smem + TCfg<NS, NP>::PSTAGES * kTP;
+    TSmem& S = *reinterpret_cast<TSmem*>(smem + TCfg<NS, NP>::PSTAGES * kTP + TCfg<NS, NP>::RING);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    t_prologue<NS>(S);
+    t_prologue<NS, NP>(S);
     __syncthreads();
     const int pa = cta_pages[blockIdx.x], pb = cta_pages[blockIdx.x + 1];
     if (warp == 0) {
         if (lane == 0) {
-            t_producer<NS>(S, stages, abuf, pages, used, pa, pb, pn, MAXCOL, status);
-            if (S.abort) t_drain<NS>(S);
+            t_producer<NS, NP>(S, stages, abuf, pages, used, pa, pb, pn, kRegion, status);
+            if (S.abort) t_drain<NS, NP>(S);
         }
     } else if (warp == 1) {
-        if (lane == 0) t_issuer<NS, REG, NREG>(S, stages, abuf, pa, pb, status);
+        if (lane == 0) t_issuer<NS, NP>(S, stages, abuf, pa, pb, status);
     } else {
         const int m = 32 * (warp & 3) + lane;
-        const int col = ep.p0 + m;  // RHS column
-        const bool live = col < ep.R;
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         const int t0 = cta_tile_ptr[blockIdx.x], t1 = cta_tile_ptr[blockIdx.x + 1];
         for (int ti = t0, k = 0; ti < t1; ++ti, ++k) {
@@ -1108,37 +1107,44 @@ __global__ void __launch_bounds__(192, TCfg<NS>::CTAS) k_tphase2(const unsigned 
             tm_fence_after();
             const int tile = cta_tiles[ti];
             const int tf = tile_first[tile], tc = tile_count[tile];
-            double ss = 0.0;
-            for (int c0 = 0; c0 < tc; c0 += 16) {
-                float v[16];
-                tm_ld16(S.tmem_base + lane_base + d * REG + c0, v);
-                if (!live) continue;
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    if (c0 + j >= tc) break;
-                    const int64_t p = tf + c0 + j;
-                    const int64_t o = (int64_t)col * ep.n + p;
-                    if (ep.mode == 0) {
-                        ep.Y[o] = v[j];
-                    } else if (ep.mode == 2) {
-                        // residual r = E - B + rho .* y in FP64
-                        const double r = (double)ep.E[o] - (double)ep.Bold[o] + (double)ep.rho[p] * (double)v[j];
-                        ss += r * r;
-                        ep.Y[o] = (float)r;
-                    } else {
-                        const float bn = ep.E[o] + ep.rho[p] * v[j];
-                        const float dd = bn - ep.Bold[o];
-                        ss += (double)dd * dd;
-                        ep.Y[o] = bn;
-                        if (ep.Xnext) *reinterpret_cast<__nv_bfloat16*>(ep.Xnext + panel_off(p, m)) = __float2bfloat16_rn(bn);
+            for (int q = 0; q < NP; ++q) {
+                const int col = ep.p0 + q * kPanel + m;  // RHS column
+                const bool live = col < ep.R;
+                unsigned char* xnext = ep.Xnext ? ep.Xnext + q * ep.xstride : nullptr;
+                double ss = 0.0;
+                for (int c0 = 0; c0 < tc; c0 += 16) {
+                    float v[16];
+                    tm_ld16(S.tmem_base + lane_base + d * REGW + q * kRegion + c0, v);
+                    if (!live) continue;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        if (c0 + j >= tc) break;
+                        const int64_t p = tf + c0 + j;
+                        const int64_t o = (int64_t)col * ep.n + p;
+                        if (ep.mode == 0) {
+                            ep.Y[o] = v[j];
+                        } else if (ep.mode == 2) {
+                            // residual r = E - B + rho .* y in FP64
+                            const double r = (double)ep.E[o] - (double)ep.Bold[o] + (double)ep.rho[p] * (double)v[j];
+                            ss += r * r;
+                            ep.Y[o] = (float)r;
+                        } else {
+                            const float bn = ep.E[o] + ep.rho[p] * v[j];
+                            const float dd = bn - ep.Bold[o];
+                            ss += (double)dd * dd;
+                            ep.Y[o] = bn;
+                            if (xnext)
+                                *reinterpret_cast<__nv_bfloat16*>(xnext + panel_off(p, m)) = __float2bfloat16_rn(bn);
+                        }
                     }
                 }
+                if (ep.mode != 0 && live) ep.colpart[(int64_t)col * ep.ntiles + tile] = ss;
             }
-            if (ep.mode != 0 && live) ep.colpart[(int64_t)col * ep.ntiles + tile] = ss;
-            t_release<REG>(S, d, true);
+            t_release<REGW>(S, d, true);
         }
     }
-    t_finish<NS>(S, status);
+    t_finish<NS, NP>(S, status);
 }
 
 // FP32 column-major (tree order, or face order through perm) -> BF16 panel
@@ -1164,13 +1170,23 @@ __global__ void k_to_panel(const float* __restrict__ src, int64_t ld, const int3
 }
 
 // ------------------------------------------------------------ host entry
+template <int NS, int NP>
+static cudaError_t tensor_attrs_cfg() {
+    cudaError_t e = cudaFuncSetAttribute(k_tphase1<NS, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tsmem_bytes<NS, NP>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tphase2<NS, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tsmem_bytes<NS, NP>());
+    return e;
+}
+
 static vf_status tensor_attrs() {
     static bool done = false;
     if (done) return VF_OK;
-    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase1<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem_bytes<1>()));
-    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase2<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem_bytes<1>()));
-    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase1<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem_bytes<2>()));
-    VF_TRY_CUDA(cudaFuncSetAttribute(k_tphase2<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem_bytes<2>()));
+    cudaError_t e = tensor_attrs_cfg<1, 1>();
+    if (e == cudaSuccess) e = tensor_attrs_cfg<1, 2>();
+    if (e == cudaSuccess) e = tensor_attrs_cfg<2, 1>();
+    VF_TRY_CUDA(e);
     done = true;
     return VF_OK;
 }
@@ -1193,9 +1209,22 @@ vf_status tensor_to_panel(const vf_hmat* H, const float* X, int64_t ld, const in
     return VF_OK;
 }
 
-// One multiply of one panel: phase 1 (T panels), then phase 2 with the epilogue.
-vf_status tensor_multiply(const vf_hmat* H, int S, const unsigned char* Xhi, const unsigned char* Xlo,
+template <int NS, int NP>
+static void tensor_launch(const vf_tensor_set& T, const TPanels& pn, const TEpi& ep, int* status, cudaStream_t st) {
+    if (T.ncta1 > 0)
+        k_tphase1<NS, NP><<<(unsigned)T.ncta1, 192, tsmem_bytes<NS, NP>(), st>>>(
+            T.pages1.p, T.used1.p, T.cta_pages1.p, T.cta_units.p, T.cta_unit_ptr.p, pn, status);
+    k_tphase2<NS, NP><<<(unsigned)T.ncta2, 192, tsmem_bytes<NS, NP>(), st>>>(
+        T.pages2.p, T.used2.p, T.cta_pages2.p, T.cta_tiles.p, T.cta_tile_ptr.p, T.st_first.p, T.st_count.p, pn, ep,
+        status);
+}
+
+// One multiply of np RHS panels (np = 2 only for S = 1): phase 1 (T
+// panels), then phase 2 with the epilogue.  The panels' X (and T) buffers
+// follow each other at the panel sizes.
+vf_status tensor_multiply(const vf_hmat* H, int S, int np, const unsigned char* Xhi, const unsigned char* Xlo,
                           unsigned char* Thi, unsigned char* Tlo, const TEpi& ep, int* status, cudaStream_t st) {
+    VF_CHECK(np == 1 || (np == 2 && S == 1), VF_E_INVAL, "tensor multiply: %d panels with S = %d", np, S);
     const vf_tensor_plan* P = H->tplan;
     const vf_tensor_set& T = P->set[S - 1];
     TPanels pn{};
@@ -1205,21 +1234,11 @@ vf_status tensor_multiply(const vf_hmat* H, int S, const unsigned char* Xhi, con
     pn.T[1] = Tlo;
     pn.rows_x = P->n_rows_x;
     pn.rows_t = P->n_rows_t;
-    if (S == 1) {
-        if (T.ncta1 > 0)
-            k_tphase1<1><<<(unsigned)T.ncta1, 192, tsmem_bytes<1>(), st>>>(T.pages1.p, T.used1.p, T.cta_pages1.p,
-                                                                      T.cta_units.p, T.cta_unit_ptr.p, pn, status);
-        k_tphase2<1><<<(unsigned)T.ncta2, 192, tsmem_bytes<1>(), st>>>(T.pages2.p, T.used2.p, T.cta_pages2.p,
-                                                                  T.cta_tiles.p, T.cta_tile_ptr.p, T.st_first.p,
-                                                                  T.st_count.p, pn, ep, status);
-    } else {
-        if (T.ncta1 > 0)
-            k_tphase1<2><<<(unsigned)T.ncta1, 192, tsmem_bytes<2>(), st>>>(T.pages1.p, T.used1.p, T.cta_pages1.p,
-                                                                      T.cta_units.p, T.cta_unit_ptr.p, pn, status);
-        k_tphase2<2><<<(unsigned)T.ncta2, 192, tsmem_bytes<2>(), st>>>(T.pages2.p, T.used2.p, T.cta_pages2.p,
-                                                                  T.cta_tiles.p, T.cta_tile_ptr.p, T.st_first.p,
-                                                                  T.st_count.p, pn, ep, status);
-    }
+    pn.xstride = tensor_panel_bytes_x(H);
+    pn.tstride = tensor_panel_bytes_t(H);
+    if (S == 2) tensor_launch<2, 1>(T, pn, ep, status, st);
+    else if (np == 2) tensor_launch<1, 2>(T, pn, ep, status, st);
+    else tensor_launch<1, 1>(T, pn, ep, status, st);
     VF_TRY_CUDA(cudaGetLastError());
     return VF_OK;
 }

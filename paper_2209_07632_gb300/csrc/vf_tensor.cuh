@@ -18,7 +18,8 @@ struct TEpi {
     const float* E;        // mode 1
     const float* rho;      // mode 1
     const float* Bold;     // mode 1: the previous iterate; mode 2: B
-    unsigned char* Xnext;  // mode 1: the next BF16 panel (or NULL)
+    unsigned char* Xnext;  // mode 1: the next BF16 panel (or NULL); a second panel at + xstride bytes
+    int64_t xstride;
     double* colpart;       // modes 1, 2: per (RHS, tile) sums of squares
     int64_t ntiles;
 };
@@ -34,9 +35,11 @@ int64_t tensor_page_bytes(const vf_hmat* H, int S);
 // the two-term split (x = hi + lo + O(2^-16 x))
 vf_status tensor_to_panel(const vf_hmat* H, const float* X, int64_t ld, const int32_t* perm, int R, int p0,
                           unsigned char* hi, unsigned char* lo, cudaStream_t st);
-// One multiply of one panel.  S = 1: BF16 products; S = 2: the split
-// products A_hi B_hi + A_lo B_hi + A_hi B_lo (FP32-factor accuracy to ~2^-16).
-vf_status tensor_multiply(const vf_hmat* H, int S, const unsigned char* Xhi, const unsigned char* Xlo,
+// One multiply of np RHS panels (np = 2 only with S = 1; the panels' X and
+// T buffers follow each other at the panel sizes).  S = 1: BF16 products;
+// S = 2: the split products A_hi B_hi + A_lo B_hi + A_hi B_lo (FP32-factor
+// accuracy to ~2^-16).
+vf_status tensor_multiply(const vf_hmat* H, int S, int np, const unsigned char* Xhi, const unsigned char* Xlo,
                           unsigned char* Thi, unsigned char* Tlo, const TEpi& ep, int* status, cudaStream_t st);
 int tensor_kernels(const vf_hmat* H, int S);
 // per-column partial sums a phase-2 epilogue writes (one per row part)
