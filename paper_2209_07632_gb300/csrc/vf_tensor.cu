@@ -141,13 +141,13 @@ struct vf_tensor_set {
     vf::dbuf<int32_t> st_first, st_count;      // phase 2: rows of each (super-)tile
     vf::dbuf<int32_t> seg_part0;               // phase 2: first (super-)tile of each segment (nseg + 1)
     int64_t nst = 0;                           // (super-)tiles
-    vf::dbuf<int32_t> cta_units, cta_unit_ptr; // phase 1: each CTA's units (offT16, N16 pairs)
+    vf::dbuf<int32_t> cta_units, cta_unit_ptr; // phase 1: each CTA's units (T row, columns, region column, group end)
     int64_t bytes2 = 0, bytes1 = 0;
 };
 
 struct vf_tensor_plan {
     int64_t n_rows_x = 0, n_rows_t = 0;  // panel rows (X, T), multiples of 16
-    std::vector<int32_t> h_offT16;       // per block: first T row (SVD), else -1
+    std::vector<int32_t> h_offT;         // per block: first T row (SVD), else -1
     vf_tensor_set set[2];                // [S - 1]
 };
 
@@ -339,8 +339,9 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
     if (!H->tplan) {
         auto P0 = std::make_unique<vf_tensor_plan>();
         P0->n_rows_x = r16(H->nf) + 32;
-        // T rows: q16 per SVD block, the blocks of one row cluster
-        // consecutive (phase 2 reads their T rows as one A operand)
+        // T rows: q per SVD block, packed; the blocks of one row cluster
+        // consecutive from an 8-row boundary (phase 2 reads their T rows
+        // as one A operand)
         const std::vector<HBlock>& hb = H->h_blocks;
         std::vector<int32_t> svd;
         for (size_t i = 0; i < hb.size(); ++i)
@@ -350,13 +351,15 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
             if (hb[x].m != hb[y].m) return hb[x].m < hb[y].m;
             return hb[x].c0 < hb[y].c0;
         });
-        P0->h_offT16.assign(hb.size(), -1);
+        P0->h_offT.assign(hb.size(), -1);
         int64_t nt = 0;
-        for (int32_t i : svd) {
-            P0->h_offT16[i] = (int32_t)nt;
-            nt += r16(hb[i].q);
+        for (size_t k = 0; k < svd.size(); ++k) {
+            const int32_t i = svd[k];
+            if (k == 0 || hb[i].r0 != hb[svd[k - 1]].r0 || hb[i].m != hb[svd[k - 1]].m) nt = (nt + 7) / 8 * 8;
+            P0->h_offT[i] = (int32_t)nt;
+            nt += hb[i].q;
         }
-        P0->n_rows_t = nt + 16;
+        P0->n_rows_t = r16(nt) + 32;
         H->tplan = P0.release();
     }
     vf_tensor_plan* P = H->tplan;
@@ -476,11 +479,11 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
         // its own K range (B row = T row - the chunk's first)
         std::vector<Piece>& sp = spieces[k];
         std::stable_sort(sp.begin(), sp.end(),
-                         [&](const Piece& x, const Piece& y) { return P->h_offT16[x.blk] < P->h_offT16[y.blk]; });
+                         [&](const Piece& x, const Piece& y) { return P->h_offT[x.blk] < P->h_offT[y.blk]; });
         for (size_t i = 0; i < sp.size();) {
             size_t j = i + 1;
             while (j < sp.size() && B[sp[j].blk].r0 == B[sp[i].blk].r0 && B[sp[j].blk].m == B[sp[i].blk].m &&
-                   P->h_offT16[sp[j].blk] == P->h_offT16[sp[j - 1].blk] + r16(B[sp[j - 1].blk].q))
+                   P->h_offT[sp[j].blk] == P->h_offT[sp[j - 1].blk] + B[sp[j - 1].blk].q)
                 ++j;
             TRec t{};
             t.kind = TREC_SVDU;
@@ -492,14 +495,16 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
             t.a_src = 1;
             t.S = S;
             const int32_t kmax = std::min<int32_t>(cfg_kmax(S), ((kTP - kTPHdr - kTRHdr) / (t.N16 * 2 * S)) / 16 * 16);
-            const int32_t base = P->h_offT16[sp[i].blk];
-            const int32_t ktot = P->h_offT16[sp[j - 1].blk] + r16(B[sp[j - 1].blk].q) - base;
+            // from the 8-row boundary at or before the run (rows of other
+            // blocks there meet zero B rows)
+            const int32_t base = P->h_offT[sp[i].blk] / 8 * 8;
+            const int32_t ktot = r16(P->h_offT[sp[j - 1].blk] + B[sp[j - 1].blk].q - base);
             for (int32_t kc = 0; kc < ktot; kc += kmax) {
                 const int32_t a0 = base + kc, kk = std::min(kmax, ktot - kc);
                 bool head = true;
                 for (size_t u = i; u < j; ++u) {
-                    const int32_t o = P->h_offT16[sp[u].blk], q16 = r16(B[sp[u].blk].q);
-                    if (o + q16 <= a0 || o >= a0 + kk) continue;
+                    const int32_t o = P->h_offT[sp[u].blk], q = B[sp[u].blk].q;
+                    if (o + q <= a0 || o >= a0 + kk) continue;
                     TRec f = t;
                     f.blk = sp[u].blk;
                     f.K16 = kk;
@@ -564,7 +569,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
     // blocks' V' side by side (one A copy serves the whole group).  A block
     // of rank above the region width becomes several parts.
     struct Part {
-        int32_t blk, n0, nsub;  // rank columns [n0, n0 + nsub) of block blk (nsub a multiple of 16)
+        int32_t blk, n0, nsub;  // rank columns [n0, n0 + nsub) of block blk
     };
     std::vector<std::vector<Part>> groups;
     {
@@ -581,9 +586,9 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
             std::vector<Part> cur;
             int32_t used_cols = 0;
             for (size_t t = i; t < j; ++t) {
-                const int32_t bi = order[t], q16 = r16(B[bi].q);
-                for (int32_t n0 = 0; n0 < q16; n0 += region) {
-                    const int32_t nsub = std::min(region, q16 - n0);
+                const int32_t bi = order[t], q = B[bi].q;
+                for (int32_t n0 = 0; n0 < q; n0 += region) {
+                    const int32_t nsub = std::min(region, q - n0);
                     if (used_cols + nsub > region) {
                         groups.push_back(cur);
                         cur.clear();
@@ -604,6 +609,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
         const HBlock& b0 = B[g[0].blk];
         int32_t n16 = 0;
         for (const Part& pt : g) n16 += pt.nsub;
+        n16 = r16(n16);  // the parts' columns side by side, padded once
         const int32_t kmax = std::min<int32_t>(cfg_kmax(S), ((kTP - kTPHdr - kTRHdr) / (n16 * 2 * S)) / 16 * 16);
         const int32_t c8 = (b0.c0 / 8) * 8;
         const int32_t ktot = r16(b0.c0 + b0.n - c8);
@@ -653,7 +659,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
                 int32_t col = 0;
                 for (size_t pi = 0; pi < groups[gi].size(); ++pi) {
                     const Part& pt = groups[gi][pi];
-                    units.push_back(P->h_offT16[pt.blk] + pt.n0);
+                    units.push_back(P->h_offT[pt.blk] + pt.n0);
                     units.push_back(pt.nsub);
                     units.push_back(col);
                     units.push_back(pi + 1 == groups[gi].size() ? 1 : 0);
@@ -1002,7 +1008,7 @@ __device__ void t_drain(TSmem& S) {
 }
 
 // ------------------------------------------------------------ phase 1
-// T panel rows offT16 .. + N16 of each unit = (V'^T X), per RHS panel.
+// T panel rows offT .. + nc of each unit = (V'^T X), per RHS panel.
 template <int NS, int NP>
 __global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase1(const unsigned char* __restrict__ pages,
                                                         const uint32_t* __restrict__ used,
@@ -1041,16 +1047,19 @@ __global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase1(const unsig
                 tm_fence_after();
                 open = true;
             }
-            const int offT = cta_units[4 * u], N16 = cta_units[4 * u + 1], col = cta_units[4 * u + 2];
+            const int offT = cta_units[4 * u], nc = cta_units[4 * u + 1], col = cta_units[4 * u + 2];
             const bool gend = cta_units[4 * u + 3] != 0;
 #pragma unroll
             for (int q = 0; q < NP; ++q)
-                for (int c0 = 0; c0 < N16; c0 += 16) {
+                // the unit's columns [col, col + nc) through 16-column loads
+                // aligned inside the panel's 64 columns
+                for (int b16 = col & ~15; b16 < col + nc; b16 += 16) {
                     float v[16];
-                    tm_ld16(S.tmem_base + lane_base + d * REGW + q * kRegion + col + c0, v);
+                    tm_ld16(S.tmem_base + lane_base + d * REGW + q * kRegion + b16, v);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const int64_t o = q * pn.tstride + panel_off(offT + c0 + j, m);
+                        if (b16 + j < col || b16 + j >= col + nc) continue;
+                        const int64_t o = q * pn.tstride + panel_off(offT + b16 + j - col, m);
                         const __nv_bfloat16 hi = __float2bfloat16_rn(v[j]);
                         *reinterpret_cast<__nv_bfloat16*>(pn.T[0] + o) = hi;
                         if (NS == 2)
