@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--multimesh-max-side", type=int, default=100,
                    help="largest DEM side of the multi-mesh section (50 -> 4,802 facets, 200 -> 79,202)")
     p.add_argument("--multimesh-rhs", type=int, default=64, help="RHS per mesh in the multi-mesh section")
+    p.add_argument("--profile-batched", action="store_true",
+                   help="only run --steps refined BF16 solves of --batch-rhs suns (for a profiler's launch list)")
     return p.parse_args()
 
 
@@ -213,6 +215,18 @@ def main():
     __graft_entry__.build()
     from paper_2209_07632_gb300 import vf
 
+    if a.profile_batched:
+        v, f, _ = workload_inputs(1, a.dem_size)
+        prob = vf.build_problem(v, f, kind="quad", leaf_size=64, tol=a.tol, device=dev, precisions=("fp32", "bf16"))
+        Eb = torch.empty((a.batch_rhs, prob.mesh.n), device="cuda", dtype=torch.float32)
+        vf.vf_mesh_insolation(prob.mesh, lunar_day_dirs(a.batch_rhs), 1365.0, Eb)
+        Bb = torch.empty_like(Eb)
+        for _ in range(a.warmup + a.steps):
+            vf.vf_solve(prob.hmat, Eb, Bb, rho=0.12, rtol=1e-4, precision="bf16", refine=True)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_batched": True, "facets": prob.mesh.n, "rhs": a.batch_rhs, "solves": a.steps}))
+        return
+
     R = a.rhs
     v, f, dirs = workload_inputs(R, a.dem_size)
     t0 = time.time()
@@ -367,6 +381,7 @@ def main():
         torch.cuda.synchronize()
         tms = m0.elapsed_time(m1) / 20
         bf16_bytes = vf.vf_hmat_bytes(prob.hmat, "bf16") + n * 128 * (2 + 4)
+        tpages = vf.vf_hmat_tensor_bytes(prob.hmat, 1)
         single_apply = 1.0 / (mult_ms / 1000.0)  # FP32 single-RHS multiply, RHS/s
         batched = {"value": round(Rb / (bms / 1000.0), 1), "unit": "RHS/s", "rhs": Rb, "ms_per_solve": round(bms, 3),
                    "suns": "lunar-day azimuth sweep at 1.5 deg elevation",
@@ -379,7 +394,10 @@ def main():
                    "x_fp32_single_rhs_solve": round(Rb / (bms / 1000.0) / (value / world), 2),
                    "tensor_multiply": {"ms": round(tms, 4), "rhs": 128,
                                        "alg_bytes": bf16_bytes,
-                                       "hbm_frac": round(bf16_bytes / (tms / 1000.0) / 1e9 / peak, 4)}}
+                                       "hbm_frac": round(bf16_bytes / (tms / 1000.0) / 1e9 / peak, 4),
+                                       "page_bytes": tpages,
+                                       "page_frac": round((tpages["total"] + n * 128 * 6) / (tms / 1000.0) / 1e9 / peak,
+                                                          4)}}
         del Eb, Bb, Bref, Xb, Yb
 
     # ---- many meshes in one launch per phase: K seeded fBm terrains (every

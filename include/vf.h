@@ -385,6 +385,14 @@ vf_status vf_tune_set(const vf_hmat* h, vf_precision prec, int32_t R, const vf_t
  * file loads back as one segment.  Errors: VF_E_INVAL, VF_E_NOMEM, VF_E_CUDA. */
 vf_status vf_hmat_stack(const vf_hmat* const* F, int32_t nmeshes, vf_hmat** out);
 
+/* Bytes of the tensor-core multiply's pages of h (the B operands: factors
+ * in BF16, terms = 1, or split in hi and lo, terms = 2; padded to the MMA
+ * shapes, CSR blocks dense), building them if not yet built; by_kind (5
+ * entries or NULL): dense, CSR, U', V' and empty-tile records.  No
+ * counterpart in the paper.  Errors: VF_E_INVAL (no BF16 copy), VF_E_NOMEM,
+ * VF_E_CUDA. */
+vf_status vf_hmat_tensor_bytes(const vf_hmat* h, int32_t terms, int64_t* total, int64_t* by_kind);
+
 /* Number of segments (stacked meshes) of a matrix; 1 for an assembled one, -1 for NULL. */
 int32_t vf_hmat_nsegments(const vf_hmat* h);
 

@@ -143,6 +143,7 @@ struct vf_tensor_set {
     int64_t nst = 0;                           // (super-)tiles
     vf::dbuf<int32_t> cta_units, cta_unit_ptr; // phase 1: each CTA's units (T row, columns, region column, group end)
     int64_t bytes2 = 0, bytes1 = 0;
+    int64_t kind_bytes[5] = {0, 0, 0, 0, 0};   // record bytes by the kind of their first fill
 };
 
 struct vf_tensor_plan {
@@ -265,7 +266,8 @@ static std::vector<std::vector<int32_t>> lpt(const std::vector<int64_t>& cost, i
 // Pack records (grouped: each group starts a new page) into pages per CTA.
 static vf_status pack_pages(vf_hmat* H, std::vector<TRec>& recs, const std::vector<std::vector<int32_t>>& cta_groups,
                             const std::vector<std::pair<int64_t, int64_t>>& group_recs, dbuf<unsigned char>& pool,
-                            dbuf<uint32_t>& used_d, dbuf<int32_t>& cta_pages, int64_t* bytes) {
+                            dbuf<uint32_t>& used_d, dbuf<int32_t>& cta_pages, int64_t* bytes,
+                            int64_t* kind_bytes) {
     const int32_t ncta = (int32_t)cta_groups.size();
     std::vector<int32_t> cp(ncta + 1, 0);
     std::vector<uint32_t> used;
@@ -283,6 +285,7 @@ static vf_status pack_pages(vf_hmat* H, std::vector<TRec>& recs, const std::vect
                     continue;
                 }
                 const uint32_t sz = (uint32_t)(kTRHdr + r.S * r.K16 * r.N16 * 2);
+                kind_bytes[r.kind] += sz;
                 if (fresh || used.back() + sz > (uint32_t)kTP) {
                     used.push_back(kTPHdr);
                     nrec.push_back(0);
@@ -561,7 +564,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
         VF_TRY(T->cta_tiles.upload(tiles));
         VF_TRY(T->cta_tile_ptr.upload(ptr));
     }
-    VF_TRY(pack_pages(H, recs2, lists2, tile_recs, T->pages2, T->used2, T->cta_pages2, &T->bytes2));
+    VF_TRY(pack_pages(H, recs2, lists2, tile_recs, T->pages2, T->used2, T->cta_pages2, &T->bytes2, T->kind_bytes));
 
     // ---- phase 1: SVD blocks with the same column cluster (the same X rows)
     // form groups whose ranks fit one accumulator region; a group's records
@@ -670,7 +673,8 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
         ptr[T->ncta1] = (int32_t)(units.size() / 4);
         VF_TRY(T->cta_units.upload(units));
         VF_TRY(T->cta_unit_ptr.upload(ptr));
-        VF_TRY(pack_pages(H, recs1, lists1, group_recs1, T->pages1, T->used1, T->cta_pages1, &T->bytes1));
+        VF_TRY(pack_pages(H, recs1, lists1, group_recs1, T->pages1, T->used1, T->cta_pages1, &T->bytes1,
+                          T->kind_bytes));
     }
     T->built = true;
     return VF_OK;
@@ -1258,3 +1262,17 @@ const int32_t* tensor_seg_parts(const vf_hmat* H, int S) { return H->tplan->set[
 int tensor_kernels(const vf_hmat* H, int S) { return (H->tplan->set[S - 1].ncta1 > 0 ? 1 : 0) + 1; }
 
 }  // namespace vf
+
+// The tensor pages of a matrix (built here if not yet): bytes per set and by record kind.
+extern "C" vf_status vf_hmat_tensor_bytes(const vf_hmat* h, int32_t terms, int64_t* total, int64_t* by_kind) {
+    vf::clear_error();
+    VF_CHECK(h && total && (terms == 1 || terms == 2), VF_E_INVAL, "vf_hmat_tensor_bytes: bad argument");
+    VF_CHECK(h->has_bf16, VF_E_INVAL, "vf_hmat_tensor_bytes: the matrix has no BF16 copy");
+    vf::device_guard g(h->device);
+    VF_TRY(vf::tensor_prepare(const_cast<vf_hmat*>(h), terms));
+    const vf_tensor_set& T = h->tplan->set[terms - 1];
+    *total = T.bytes1 + T.bytes2;
+    if (by_kind)
+        for (int k = 0; k < 5; ++k) by_kind[k] = T.kind_bytes[k];
+    return VF_OK;
+}

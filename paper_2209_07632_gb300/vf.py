@@ -118,6 +118,7 @@ _SIGS = {
     "vf_tune_set": ([_P, ctypes.c_int, _I32, _P], ctypes.c_int),
     "vf_hmat_stack": ([_P, _I32, _P], ctypes.c_int),
     "vf_hmat_nsegments": ([_P], _I32),
+    "vf_hmat_tensor_bytes": ([_P, _I32, _P, _P], ctypes.c_int),
     "vf_hmat_save": ([_P, ctypes.c_char_p], ctypes.c_int),
     "vf_hmat_load": ([ctypes.c_char_p, _I32, _P], ctypes.c_int),
 }
@@ -454,6 +455,15 @@ def vf_hmat_stack(hs) -> HMat:
     out = ctypes.c_void_p()
     _check(load().vf_hmat_stack(P(*[h.ptr for h in hs]), k, ctypes.byref(out)))
     return HMat(out)
+
+
+def vf_hmat_tensor_bytes(h: HMat, terms: int = 1) -> dict:
+    """Bytes of the tensor-core pages of h (terms 1: BF16, 2: hi/lo split), in all and by record kind."""
+    tot = ctypes.c_int64()
+    kinds = (ctypes.c_int64 * 5)()
+    _check(load().vf_hmat_tensor_bytes(h.ptr, terms, ctypes.byref(tot), kinds))
+    return {"total": tot.value, "dense": kinds[0], "csr": kinds[1], "svd_u": kinds[2], "svd_v": kinds[3],
+            "empty": kinds[4]}
 
 
 def vf_hmat_nsegments(h: HMat) -> int:
