@@ -336,6 +336,25 @@ static vf_status check_records(const std::vector<TRec>& recs, int max_col, int64
     return VF_OK;
 }
 
+// Runs of occupied 16-column chunks (occ[c] != 0), each at most kmax
+// columns: (first chunk, chunks).  K ranges with no nonzero in any of a
+// record's pieces are not copied or multiplied.
+static std::vector<std::pair<int32_t, int32_t>> chunk_runs(const std::vector<char>& occ, int32_t kmax) {
+    std::vector<std::pair<int32_t, int32_t>> out;
+    const int32_t n = (int32_t)occ.size(), lim = kmax / 16;
+    for (int32_t c = 0; c < n;) {
+        if (!occ[c]) {
+            ++c;
+            continue;
+        }
+        int32_t e = c;
+        while (e < n && occ[e] && e - c < lim) ++e;
+        out.push_back({c, e - c});
+        c = e;
+    }
+    return out;
+}
+
 // Build one set of tensor pages of a matrix (once, on first use).
 vf_status tensor_plan_build(vf_hmat* H, int S) {
     device_guard g(H->device);
@@ -455,7 +474,20 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
             const int32_t kmax = std::min<int32_t>(cfg_kmax(S), ((kTP - kTPHdr - kTRHdr) / (n16 * 2 * S)) / 16 * 16);
             const int32_t c8 = (b0.c0 / 8) * 8;
             const int32_t ktot = r16(b0.c0 + b0.n - c8);
-            for (int32_t kc = 0; kc < ktot; kc += kmax) {
+            // 16-column chunks holding a nonzero of some piece (dense pieces: all)
+            std::vector<char> occ(ktot / 16, 0);
+            for (size_t t = i; t < j; ++t) {
+                const HBlock& b = B[dp[t].blk];
+                if (b.kind == VF_BLK_DENSE) {
+                    for (int32_t c = (b.c0 - c8) / 16; c <= (b.c0 + b.n - 1 - c8) / 16; ++c) occ[c] = 1;
+                } else {
+                    const int32_t* rp = haux.data() + b.off_aux;
+                    const int32_t* ci = rp + b.m + 1;
+                    for (int32_t r = dp[t].rs; r < dp[t].re; ++r)
+                        for (int32_t z = rp[r - b.r0]; z < rp[r - b.r0 + 1]; ++z) occ[(ci[z] - c8) / 16] = 1;
+                }
+            }
+            for (const auto& run : chunk_runs(occ, kmax)) {
                 for (size_t t = i; t < j; ++t) {
                     TRec u{};
                     u.kind = B[dp[t].blk].kind == VF_BLK_DENSE ? TREC_DENSE : TREC_CSR;
@@ -465,8 +497,8 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
                     u.coloff = coloff;
                     u.row_base = row_base;
                     u.N16 = n16;
-                    u.k0 = c8 + kc;
-                    u.K16 = std::min(kmax, ktot - kc);
+                    u.k0 = c8 + 16 * run.first;
+                    u.K16 = 16 * run.second;
                     u.a_src = 0;
                     u.a_row0 = u.k0;
                     u.S = S;
@@ -618,14 +650,23 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
         const int32_t ktot = r16(b0.c0 + b0.n - c8);
         const int64_t first = (int64_t)recs1.size();
         int64_t cost = 0;
-        for (int32_t kc = 0; kc < ktot; kc += kmax) {
+        // 16-column chunks holding a compacted column of some block of the group
+        std::vector<char> occ(ktot / 16, 0);
+        for (const Part& pt : g) {
+            const HBlock& b = B[pt.blk];
+            const int32_t* cols = haux.data() + b.off_aux + b.m1;
+            for (int32_t z = 0; z < b.n1; ++z) occ[(cols[z] - c8) / 16] = 1;
+        }
+        const auto runs = chunk_runs(occ, kmax);
+        for (size_t ri = 0; ri < runs.size(); ++ri) {
+            const int32_t kc = 16 * runs[ri].first, kk = 16 * runs[ri].second;
             int32_t bcol = 0;
             for (size_t pi = 0; pi < g.size(); ++pi) {
                 TRec t{};
                 t.kind = TREC_VT;
                 t.blk = g[pi].blk;
                 t.k0 = c8 + kc;
-                t.K16 = std::min(kmax, ktot - kc);
+                t.K16 = kk;
                 t.N16 = n16;
                 t.n0 = g[pi].n0;
                 t.nsub = g[pi].nsub;
@@ -634,13 +675,12 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
                 t.a_row0 = t.k0;
                 t.S = S;
                 t.hdr = pi == 0;
-                t.flags = (kc == 0 && pi == 0) ? (TR_FIRST | TR_USTART) : 0;
-                if (kc + kmax >= ktot && pi == 0) t.flags |= TR_LAST;
+                t.flags = (ri == 0 && pi == 0) ? (TR_FIRST | TR_USTART) : 0;
+                if (ri + 1 == runs.size() && pi == 0) t.flags |= TR_LAST;
                 recs1.push_back(t);
                 bcol += g[pi].nsub;
             }
-            cost += S * ((int64_t)std::min(kmax, ktot - kc) * n16 * 2 + (int64_t)std::min(kmax, ktot - kc) * kPanel * 2) +
-                    rec_cost;
+            cost += S * ((int64_t)kk * n16 * 2 + (int64_t)kk * kPanel * 2) + rec_cost;
         }
         group_recs1.push_back({first, (int64_t)recs1.size()});
         group_cost.push_back(cost);
