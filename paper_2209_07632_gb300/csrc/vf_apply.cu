@@ -1489,14 +1489,17 @@ static vf_status tensor_residual(const vf_hmat* h, Workspace* w, const float* B,
         for (int i = 0; i < 2; ++i) {
             VF_TRY(w->xsplit[i].alloc((size_t)w->tpanels * bx));
             VF_TRY_CUDA(cudaMemset(w->xsplit[i].p, 0, (size_t)w->tpanels * bx));
-            VF_TRY(w->tsplit[i].alloc((size_t)bt));
-            VF_TRY_CUDA(cudaMemset(w->tsplit[i].p, 0, (size_t)bt));
+            VF_TRY(w->tsplit[i].alloc((size_t)2 * bt));  // two T panels: pairs of RHS panels
+            VF_TRY_CUDA(cudaMemset(w->tsplit[i].p, 0, (size_t)2 * bt));
         }
     }
-    for (int p = 0; p < w->tpanels; ++p) {
+    for (int p = 0, np; p < w->tpanels; p += np) {
+        np = p + 1 < w->tpanels ? 2 : 1;  // two RHS panels per multiply where there are two
         unsigned char* xh = w->xsplit[0].p + (size_t)p * bx;
         unsigned char* xl = w->xsplit[1].p + (size_t)p * bx;
-        VF_TRY(tensor_to_panel(h, B, n, nullptr, w->R, p * kTensorPanel, xh, xl, st));
+        for (int q = 0; q < np; ++q)
+            VF_TRY(tensor_to_panel(h, B, n, nullptr, w->R, (p + q) * kTensorPanel, xh + (size_t)q * bx,
+                                   xl + (size_t)q * bx, st));
         TEpi ep{};
         ep.mode = 2;
         ep.n = n;
@@ -1508,13 +1511,14 @@ static vf_status tensor_residual(const vf_hmat* h, Workspace* w, const float* B,
         ep.Bold = B;
         ep.colpart = w->colpart.p;
         ep.ntiles = ntiles;
-        VF_TRY(tensor_multiply(h, 2, 1, xh, xl, w->tsplit[0].p, w->tsplit[1].p, ep, w->status.p, st));
+        VF_TRY(tensor_multiply(h, 2, np, xh, xl, w->tsplit[0].p, w->tsplit[1].p, ep, w->status.p, st));
+        *kernels += np + tensor_kernels(h, 2);
     }
     k_unconverged<<<(unsigned)(w->R * h->nseg()), 256, 0, st>>>(w->colpart.p, ntiles, w->R, h->nseg(),
                                                                 tensor_seg_parts(h, 2), w->enorm2.p, 0.0, w->colres.p,
                                                                 w->tcount.p, w->tcount.p + 1);
     VF_TRY_CUDA(cudaGetLastError());
-    *kernels += w->tpanels * (1 + tensor_kernels(h, 2)) + 1;
+    *kernels += 1;
     return VF_OK;
 }
 

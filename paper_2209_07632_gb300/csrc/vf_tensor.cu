@@ -73,7 +73,11 @@ template <> struct TCfg<1, 2> {
     static constexpr int PSTAGES = 3, RING = 16384, CTAS = 4, CK = 16, NREG = 1, TMEM = 128;
 };
 template <> struct TCfg<2, 1> {
-    static constexpr int PSTAGES = 2, RING = 20480, CTAS = 4, CK = 16, NREG = 2, TMEM = 128;
+    static constexpr int PSTAGES = 2, RING = 20480, CTAS = 3, CK = 16, NREG = 2, TMEM = 128;
+};
+// two panels of the split set: 16 KB slots, so three CTAs per SM fit
+template <> struct TCfg<2, 2> {
+    static constexpr int PSTAGES = 2, RING = 32768, CTAS = 3, CK = 16, NREG = 1, TMEM = 128;
 };
 // Shared by every configuration of a page set (records do not depend on NP):
 constexpr int kRegion = 64;     // accumulator columns per panel: a phase-1 group's rank columns, a tile's rows
@@ -90,7 +94,8 @@ template <int NS, int NP> struct TSlots {
     static_assert(NSLOT >= 2 && NSLOT <= kMaxSlots, "A ring slots");
     static_assert(NP * kRegion * TCfg<NS, NP>::NREG <= TCfg<NS, NP>::TMEM, "accumulator regions");
 };
-static int cfg_ctas(int S) { return S == 1 ? TCfg<1, 1>::CTAS : TCfg<2, 1>::CTAS; }
+// CTAs of a page set's launches (every configuration of the set has room for them on each SM)
+static int cfg_ctas(int S) { return S == 1 ? TCfg<1, 1>::CTAS : TCfg<2, 2>::CTAS; }
 static int cfg_region(int) { return kRegion; }
 static int cfg_kmax(int S) { return S == 1 ? kmax_of<1>() : kmax_of<2>(); }
 static int cfg_r2(int) { return kRegion; }  // phase-2 (super-)tiles: one row tile
@@ -1239,6 +1244,7 @@ static vf_status tensor_attrs() {
     cudaError_t e = tensor_attrs_cfg<1, 1>();
     if (e == cudaSuccess) e = tensor_attrs_cfg<1, 2>();
     if (e == cudaSuccess) e = tensor_attrs_cfg<2, 1>();
+    if (e == cudaSuccess) e = tensor_attrs_cfg<2, 2>();
     VF_TRY_CUDA(e);
     done = true;
     return VF_OK;
@@ -1272,12 +1278,12 @@ static void tensor_launch(const vf_tensor_set& T, const TPanels& pn, const TEpi&
         status);
 }
 
-// One multiply of np RHS panels (np = 2 only for S = 1): phase 1 (T
-// panels), then phase 2 with the epilogue.  The panels' X (and T) buffers
-// follow each other at the panel sizes.
+// One multiply of np (1 or 2) RHS panels: phase 1 (T panels), then phase 2
+// with the epilogue.  The panels' X (and T) buffers follow each other at
+// the panel sizes.
 vf_status tensor_multiply(const vf_hmat* H, int S, int np, const unsigned char* Xhi, const unsigned char* Xlo,
                           unsigned char* Thi, unsigned char* Tlo, const TEpi& ep, int* status, cudaStream_t st) {
-    VF_CHECK(np == 1 || (np == 2 && S == 1), VF_E_INVAL, "tensor multiply: %d panels with S = %d", np, S);
+    VF_CHECK((np == 1 || np == 2) && (S == 1 || S == 2), VF_E_INVAL, "tensor multiply: %d panels, S = %d", np, S);
     const vf_tensor_plan* P = H->tplan;
     const vf_tensor_set& T = P->set[S - 1];
     TPanels pn{};
@@ -1289,7 +1295,8 @@ vf_status tensor_multiply(const vf_hmat* H, int S, int np, const unsigned char* 
     pn.rows_t = P->n_rows_t;
     pn.xstride = tensor_panel_bytes_x(H);
     pn.tstride = tensor_panel_bytes_t(H);
-    if (S == 2) tensor_launch<2, 1>(T, pn, ep, status, st);
+    if (S == 2 && np == 2) tensor_launch<2, 2>(T, pn, ep, status, st);
+    else if (S == 2) tensor_launch<2, 1>(T, pn, ep, status, st);
     else if (np == 2) tensor_launch<1, 2>(T, pn, ep, status, st);
     else tensor_launch<1, 1>(T, pn, ep, status, st);
     VF_TRY_CUDA(cudaGetLastError());

@@ -97,3 +97,22 @@ def test_tensor_apply_against_oracle(vf):
     live = np.linalg.norm(ref, axis=0) > 0
     err = np.linalg.norm(got - ref, axis=0)[live] / np.linalg.norm(ref, axis=0)[live]
     assert np.all(err <= 2e-3 + TOL_BF16), err.max()
+
+
+@pytest.mark.parametrize("R", [128, 300])
+def test_tensor_refined_solve_matches_fp32(vf, terrain, R):
+    # BF16 sweeps on the tensor cores, split-BF16 residual (pairs of 128-RHS
+    # panels where there are two): within 1e-5 of the FP32 CUDA-core solve
+    import torch
+
+    import synth
+    h, m = terrain.hmat, terrain.mesh
+    E = torch.empty((R, m.n), device="cuda")
+    vf.vf_mesh_insolation(m, synth.sun_directions(R, 6.0), 1365.0, E)
+    B32, Bt = torch.empty_like(E), torch.empty_like(E)
+    vf.vf_solve(h, E, B32, rho=0.12, rtol=1e-7)
+    st = vf.vf_solve(h, E, Bt, rho=0.12, rtol=1e-7, precision="bf16", refine=True)
+    assert st["converged"] == 1 and st["refinements"] >= 1
+    live = B32.norm(dim=1) > 0
+    err = ((Bt - B32).norm(dim=1)[live] / B32.norm(dim=1)[live]).max().item()
+    assert err <= 1e-5, err
