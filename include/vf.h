@@ -393,6 +393,14 @@ vf_status vf_hmat_stack(const vf_hmat* const* F, int32_t nmeshes, vf_hmat** out)
  * VF_E_CUDA. */
 vf_status vf_hmat_tensor_bytes(const vf_hmat* h, int32_t terms, int64_t* total, int64_t* by_kind);
 
+/* Release what multiplies and solves cached on h: its workspaces (per R
+ * and precision), its tensor-core pages and the stacked matrices that
+ * vf_solve_batched built from it; later calls rebuild them on demand.  For
+ * callers that hold many matrices.  Synchronises the device; no call on h
+ * may be in flight.  No counterpart in the paper.  Errors: VF_E_INVAL,
+ * VF_E_CUDA. */
+vf_status vf_hmat_trim(vf_hmat* h);
+
 /* Number of segments (stacked meshes) of a matrix; 1 for an assembled one, -1 for NULL. */
 int32_t vf_hmat_nsegments(const vf_hmat* h);
 

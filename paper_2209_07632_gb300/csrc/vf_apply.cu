@@ -1635,6 +1635,18 @@ extern "C" void vf_hmat_destroy(vf_hmat* h) {
 
 extern "C" int64_t vf_hmat_nfacets(const vf_hmat* h) { return h ? h->nf : -1; }
 
+extern "C" vf_status vf_hmat_trim(vf_hmat* h) {
+    clear_error();
+    VF_CHECK(h, VF_E_INVAL, "vf_hmat_trim: null argument");
+    device_guard g(h->device);
+    VF_TRY_CUDA(cudaDeviceSynchronize());  // nothing of the handle in flight
+    vf::drop_stacks_of(h);
+    vf::drop_cache(h);
+    vf::tensor_plan_free(h->tplan);
+    h->tplan = nullptr;
+    return VF_OK;
+}
+
 extern "C" vf_status vf_hmat_blocks(const vf_hmat* h, int64_t* nblocks, int32_t* desc) {
     clear_error();
     VF_CHECK(h && nblocks, VF_E_INVAL, "vf_hmat_blocks: null argument");

@@ -118,6 +118,7 @@ _SIGS = {
     "vf_tune_set": ([_P, ctypes.c_int, _I32, _P], ctypes.c_int),
     "vf_hmat_stack": ([_P, _I32, _P], ctypes.c_int),
     "vf_hmat_nsegments": ([_P], _I32),
+    "vf_hmat_trim": ([_P], ctypes.c_int),
     "vf_hmat_tensor_bytes": ([_P, _I32, _P, _P], ctypes.c_int),
     "vf_hmat_save": ([_P, ctypes.c_char_p], ctypes.c_int),
     "vf_hmat_load": ([ctypes.c_char_p, _I32, _P], ctypes.c_int),
@@ -464,6 +465,11 @@ def vf_hmat_tensor_bytes(h: HMat, terms: int = 1) -> dict:
     _check(load().vf_hmat_tensor_bytes(h.ptr, terms, ctypes.byref(tot), kinds))
     return {"total": tot.value, "dense": kinds[0], "csr": kinds[1], "svd_u": kinds[2], "svd_v": kinds[3],
             "empty": kinds[4]}
+
+
+def vf_hmat_trim(h: HMat):
+    """Free the workspaces, tensor pages and stacks cached on h (rebuilt on demand)."""
+    _check(load().vf_hmat_trim(h.ptr))
 
 
 def vf_hmat_nsegments(h: HMat) -> int:
