@@ -66,6 +66,21 @@ def synth_dirs(R: int):
     return synth.sun_directions(R, 10.0)
 
 
+def max_over_ranks(x: float, world: int, device: str) -> float:
+    """The largest of every rank's x (a time): the job is as slow as its slowest replica."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_all_ranks: int, seconds: float) -> float:
+    """Units processed by all replicas per second of the slowest one (weak scaling)."""
+    return units_all_ranks / seconds
+
+
 def lunar_day_dirs(R: int):
     """R sun directions over one lunar day: an azimuth sweep at 1.5 deg elevation."""
     import synth
@@ -263,12 +278,8 @@ def main():
     ev1.record(st)
     barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / a.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * R / (ms / 1000.0)
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / a.steps, world, "cuda")
+    value = whole_job_rate(world * R, ms / 1000.0)
 
     # ---- roofline of the multiply (phase 1 + phase 2), tree order, on `st`
     Xt = E.clone()
@@ -316,12 +327,8 @@ def main():
     for _ in range(a.steps):
         vf.vf_solve_host(prob.hmat, Eh, Bh, **solve_kw)
     barrier()
-    e2e_s = (time.perf_counter() - e0) / a.steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * R / e2e_s, "unit": "RHS/s", "h2d_bytes_per_step": n * R * 4,
+    e2e_s = max_over_ranks((time.perf_counter() - e0) / a.steps, world, "cuda")
+    e2e = {"value": whole_job_rate(world * R, e2e_s), "unit": "RHS/s", "h2d_bytes_per_step": n * R * 4,
            "d2h_bytes_per_step": n * R * 4}
 
     # ---- batched: 1,440 sun positions over one lunar day (azimuth sweep at
