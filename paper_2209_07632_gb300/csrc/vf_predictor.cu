@@ -2,7 +2,7 @@
 // predicts, from a candidate block's cluster geometry, the rank bin of its
 // truncated SVD or that the SVD cannot win (Algorithm 3's probe outcome).
 // Assembly uses the prediction as the probe's starting rank and to skip
-// probes predicted to lose; the probe and the byte test stay the judge.
+// probes predicted to lose; the probe and the byte test still decide.
 //
 // Network: x (VF_PRED_NFEAT) -> standardise -> W1 (64) ReLU -> W2 (64) ReLU
 // -> W3 (VF_PRED_NCLASS) -> softmax; loss = mean cross-entropy.  The forward
