@@ -388,7 +388,8 @@ vf_status vf_hmat_stack(const vf_hmat* const* F, int32_t nmeshes, vf_hmat** out)
 /* Bytes of the tensor-core multiply's pages of h (the B operands: factors
  * in BF16, terms = 1, or split in hi and lo, terms = 2; padded to the MMA
  * shapes, CSR blocks dense), building them if not yet built; by_kind (5
- * entries or NULL): dense, CSR, U', V' and empty-tile records.  No
+ * entries or NULL): the bytes of dense, CSR, U', V' and empty-tile records
+ * (headers and B operands); the total adds each page's 16-byte header.  No
  * counterpart in the paper.  Errors: VF_E_INVAL (no BF16 copy), VF_E_NOMEM,
  * VF_E_CUDA. */
 vf_status vf_hmat_tensor_bytes(const vf_hmat* h, int32_t terms, int64_t* total, int64_t* by_kind);

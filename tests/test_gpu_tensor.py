@@ -116,3 +116,23 @@ def test_tensor_refined_solve_matches_fp32(vf, terrain, R):
     live = B32.norm(dim=1) > 0
     err = ((Bt - B32).norm(dim=1)[live] / B32.norm(dim=1)[live]).max().item()
     assert err <= 1e-5, err
+
+
+def test_tensor_bytes_and_trim(vf, terrain):
+    # the tensor pages' bytes add up by record kind; trimming the handle's
+    # caches and rebuilding them gives the same product bit for bit
+    import torch
+    h, n = terrain.hmat, terrain.mesh.n
+    b1 = vf.vf_hmat_tensor_bytes(h, 1)
+    b2 = vf.vf_hmat_tensor_bytes(h, 2)
+    recs = sum(b1[k] for k in ("dense", "csr", "svd_u", "svd_v", "empty"))
+    # the total adds a 16-byte header per page (pages hold 12 KB)
+    assert 0 < recs <= b1["total"] <= recs + 16 * (b1["total"] // 1000 + 1)
+    assert b2["total"] > 1.5 * b1["total"]
+    X = torch.rand((128, n), generator=torch.Generator().manual_seed(4)).cuda()
+    Y0, Y1 = torch.empty_like(X), torch.empty_like(X)
+    vf.vf_apply(h, X, Y0, precision="bf16")
+    vf.vf_hmat_trim(h)
+    vf.vf_apply(h, X, Y1, precision="bf16")
+    assert torch.equal(Y0, Y1)
+    assert vf.vf_hmat_tensor_bytes(h, 1) == b1
