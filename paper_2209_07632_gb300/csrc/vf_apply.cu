@@ -1967,11 +1967,13 @@ struct StackEntry {
     std::unique_ptr<vf_hmat, void (*)(vf_hmat*)> h{nullptr, vf_hmat_destroy};
     dbuf<SegIO> io;
 };
-static std::mutex g_stack_mu;
-static std::vector<std::unique_ptr<StackEntry>> g_stacks;
+// Never destroyed: at process exit the entries are left to the driver, so
+// no handle is destroyed (and no cache walked) during static destruction.
+static std::mutex& g_stack_mu = *new std::mutex;
+static std::vector<std::unique_ptr<StackEntry>>& g_stacks = *new std::vector<std::unique_ptr<StackEntry>>;
 
 void drop_stacks_of(const vf_hmat* h) {
-    std::vector<std::unique_ptr<StackEntry>> gone;
+    std::vector<std::unique_ptr<StackEntry>> gone;  // destroyed after the lock is released
     {
         std::lock_guard<std::mutex> lk(g_stack_mu);
         for (auto it = g_stacks.begin(); it != g_stacks.end();) {
@@ -1996,10 +1998,10 @@ static vf_status stack_for(const vf_hmat* const* F, int32_t k, StackEntry** out)
         }
     auto e = std::make_unique<StackEntry>();
     e->uids = uids;
+    VF_TRY(e->io.alloc(k));  // before the stack: a failure here destroys no handle under the lock
     vf_hmat* s = nullptr;
     VF_TRY(vf_hmat_stack(F, k, &s));
     e->h.reset(s);
-    VF_TRY(e->io.alloc(k));
     *out = e.get();
     g_stacks.push_back(std::move(e));
     return VF_OK;
