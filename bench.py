@@ -30,6 +30,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -58,6 +60,13 @@ def parse():
     p.add_argument("--multimesh-rhs", type=int, default=64, help="RHS per mesh in the multi-mesh section")
     p.add_argument("--profile-batched", action="store_true",
                    help="only run --steps refined BF16 solves of --batch-rhs suns (for a profiler's launch list)")
+    p.add_argument("--no-config4", action="store_true", help="skip the 522,242-facet precision section")
+    p.add_argument("--config4-only", action="store_true",
+                   help="run only the 522,242-facet precision section (with its oracle check)")
+    p.add_argument("--config4-side", type=int, default=512, help="DEM side of the precision section (512 -> 522,242)")
+    p.add_argument("--config4-rows", type=int, default=4096, help="oracle-sampled rows of the precision section")
+    p.add_argument("--steady-s", type=float, default=2.0,
+                   help="seconds of back-to-back steps after the timed K (a steady-state cross-check)")
     return p.parse_args()
 
 
@@ -166,6 +175,27 @@ class CpuOracle:
         self.E = oracle.insolation(self.om, dirs[:R], 1365.0)
         self.R = R
 
+    def batched_check(self, v, f, host):
+        """The batched solve's error against the oracle on this sample's rows:
+        per column ||B_S - T(B)_S|| / ||T(B)_S|| with T(B)_S = E_S + rho F_S B,
+        one exact oracle Jacobi step from the GPU's B (within a factor
+        1 +- rho/(1 - rho) of the error against the oracle's exact B*); E_S
+        is the oracle's own insolation for the batch's suns."""
+        from oracle import sampled
+        t0 = time.time()
+        with sampled.SampledOracle(v, f, self.S) as so:
+            Eo = so.insolation_rows(host["dirs"], 1365.0)
+            workers = so.workers
+        Bg = host["B"]
+        TB = Eo + host["rho"] * (self.Fs @ Bg)
+        nr = np.linalg.norm(TB, axis=0)
+        live = nr > 0
+        err = np.linalg.norm(Bg[self.S] - TB, axis=0)[live] / nr[live]
+        return {"rows": int(self.rows), "seed": 7, "columns": int(live.sum()), "workers": workers,
+                "solve_rel_err_vs_oracle": float(err.max()), "median": float(np.median(err)),
+                "oracle_s": round(time.time() - t0, 1),
+                "reference": "oracle FP64 F rows and insolation on the sampled rows; E_S + rho F_S B"}
+
     def measure(self, sweeps: int, seconds: float):
         reps = 0
         t0 = time.perf_counter()
@@ -185,6 +215,163 @@ class CpuOracle:
                 "sample": f"dense FP64 F, {self.rows} of {self.om.n} rows (seeded), y = F_S E timed over "
                           f"{reps} repeats ({reps * t_rows:.1f} s), extrapolated x{self.om.n / self.rows:.0f} "
                           f"rows x {sweeps} sweeps"}
+
+
+# ------------------------------------------------------------- precision workload
+C4_RHO = 0.12
+
+
+def config4_inputs(side: int = 512):
+    """512 x 512 seeded fBm DEM (Hurst 0.8, 5 m spacing, RMS slope 15 deg,
+    seed 2, no crater): 522,242 triangles; 256 suns over one lunar day."""
+    import synth
+    v, f = synth.fbm_dem_mesh(n=side, spacing=5.0, hurst=0.8, seed=2, rms_slope_deg=15.0, crater_diameter=None)
+    return v, f, synth.sun_directions(256, 1.5)
+
+
+def c4_workload(n: int) -> str:
+    return f"fbm{int(round((n / 2) ** 0.5)) + 1}_5m_{n}tri_quadtree64_tol1e-3"
+
+
+def events_ms(fn, reps: int, st) -> float:
+    """Mean time of fn() over reps back-to-back calls, CUDA events on st."""
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        fn()
+    b.record(st)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_config4(a, dev, peak, st):
+    """The precision workload on the GPU: assembly, the FP32 single-RHS
+    multiply, the 256-RHS BF16 tensor-core solve with split-BF16 refinement
+    (and the FP8 solve), the tensor multiply's roofline.  Returns the
+    result object and what the oracle check needs (host copies)."""
+    import torch
+
+    from paper_2209_07632_gb300 import vf
+    v, f, dirs = config4_inputs(a.config4_side)
+    t0 = time.time()
+    prob = vf.build_problem(v, f, kind="quad", leaf_size=64, tol=1e-3, device=dev,
+                            precisions=("fp32", "bf16", "fp8"))
+    t_asm = time.time() - t0
+    n = prob.mesh.n
+    h = prob.hmat
+    R = dirs.shape[0]
+    E = torch.empty((R, n), device="cuda", dtype=torch.float32)
+    vf.vf_mesh_insolation(prob.mesh, dirs, 1365.0, E)
+    perm = torch.tensor(vf.vf_tree_perm(prob.tree).astype(np.int64), device="cuda")
+    # FP32 single-RHS multiply (the plain compressed apply): tree order, CUDA events
+    X1 = E[:1, perm].contiguous()
+    Y1 = torch.empty_like(X1)
+    for _ in range(3):
+        vf.vf_apply_tree(h, X1, Y1)
+    torch.cuda.synchronize()
+    ms1 = events_ms(lambda: vf.vf_apply_tree(h, X1, Y1), 20, st)
+    b32 = vf.vf_hmat_bytes(h, "fp32") + n * 8
+    single_rhs = 1000.0 / ms1
+    # the batched BF16 solve: tensor-core sweeps, split-BF16 residual refinement
+    B = torch.empty_like(E)
+    kw = dict(rho=C4_RHO, rtol=1e-4, precision="bf16", refine=True)
+    t1 = time.time()
+    sb = vf.vf_solve(h, E, B, **kw)
+    torch.cuda.synchronize()
+    t_first = time.time() - t1
+    sb = vf.vf_solve(h, E, B, **kw)
+    torch.cuda.synchronize()
+    bms = events_ms(lambda: vf.vf_solve(h, E, B, **kw), 5, st)
+    # the tensor multiply alone (128 and 256 RHS, BF16)
+    Xb = E[:, perm].contiguous()
+    Yb = torch.empty_like(Xb)
+    tm = {}
+    for r in (128, 256):
+        for _ in range(2):
+            vf.vf_apply_tree(h, Xb[:r], Yb[:r], precision="bf16")
+        torch.cuda.synchronize()
+        ms = events_ms(lambda: vf.vf_apply_tree(h, Xb[:r], Yb[:r], precision="bf16"), 10, st)
+        alg = vf.vf_hmat_bytes(h, "bf16") + n * r * 6
+        tm[str(r)] = {"ms": round(ms, 4), "alg_bytes": alg, "hbm_frac": round(alg / (ms / 1e3) / 1e9 / peak, 4)}
+    tpages = vf.vf_hmat_tensor_bytes(h, 1)
+    # FP8 (CUDA-core sweeps, per-block scales) with the same refinement
+    B8 = torch.empty_like(E)
+    kw8 = dict(rho=C4_RHO, rtol=1e-4, precision="fp8", refine=True)
+    s8 = vf.vf_solve(h, E, B8, **kw8)
+    torch.cuda.synchronize()
+    ms8 = events_ms(lambda: vf.vf_solve(h, E, B8, **kw8), 2, st)
+    # FP32 compressed multiply of all 256 suns (for the apply check)
+    Y32 = torch.empty_like(E)
+    vf.vf_apply(h, E, Y32, precision="fp32")
+    Ybf = torch.empty_like(E)
+    vf.vf_apply(h, E, Ybf, precision="bf16")
+    torch.cuda.synchronize()
+    res = {"workload": c4_workload(n), "facets": n, "rhs": R, "tol": 1e-3, "rho": C4_RHO,
+           "suns": "lunar-day azimuth sweep at 1.5 deg elevation",
+           "assembly_s": round(t_asm, 1),
+           "assembly": {k: prob.stats[k] for k in ("nblocks", "bytes", "probes", "max_rank", "t_visibility",
+                                                   "t_probe", "t_total")},
+           "bytes": {p: vf.vf_hmat_bytes(h, p) for p in ("fp32", "bf16", "fp8")},
+           "value": round(R / (bms / 1e3), 1), "unit": "RHS/s", "ms_per_solve": round(bms, 3),
+           "precision": "bf16 factors and RHS on tcgen05 tensor cores, FP32 accumulation; "
+                        "split-BF16 residual refinement with FP64 update, rtol 1e-4",
+           "sweeps": sb["sweeps"], "refinements": sb["refinements"], "converged": sb["converged"],
+           "first_solve_s": round(t_first, 2),
+           "fp32_single_rhs_multiply": {"ms": round(ms1, 4), "rhs_per_s": round(single_rhs, 1),
+                                        "hbm_frac": round(b32 / (ms1 / 1e3) / 1e9 / peak, 4)},
+           "x_fp32_single_rhs_apply": round((R / (bms / 1e3)) / single_rhs, 2),
+           "tensor_multiply": tm, "hbm_frac": tm["128"]["hbm_frac"], "tensor_page_bytes": tpages,
+           "fp8_solve": {"value": round(R / (ms8 / 1e3), 1), "unit": "RHS/s", "ms_per_solve": round(ms8, 3),
+                         "sweeps": s8["sweeps"], "refinements": s8["refinements"], "converged": s8["converged"],
+                         "precision": "fp8 e4m3 factors with per-block scales on CUDA cores, split-free FP64 "
+                                      "refinement"}}
+    host = {"v": v, "f": f, "dirs": dirs, "n": n,
+            "E": E.double().cpu().numpy().T, "B": B.double().cpu().numpy().T,
+            "B8": B8.double().cpu().numpy().T, "Y32": Y32.double().cpu().numpy().T,
+            "Ybf": Ybf.double().cpu().numpy().T}
+    del prob, h, E, B, B8, Xb, Yb, X1, Y1, Y32, Ybf, perm
+    return res, host
+
+
+def config4_oracle_check(host, nrows: int):
+    """The oracle on nrows rows sampled without replacement (seed 7): its F
+    rows (Eq. FF-def, its own visibility) and insolation; errors per
+    column over the sampled rows (max over columns).  The solve's reference
+    is one exact oracle Jacobi step from the GPU's B, T(B)_S = E_S + rho F_S B:
+    since T contracts by rho ||F|| <= rho, |B* - T(B)| <= rho/(1-rho) |B* - B|,
+    so this sampled error is within a factor 1 +- 0.14 of the error against
+    the oracle's exact solution B*."""
+    from oracle import sampled
+    n = host["n"]
+    rows = np.sort(np.random.default_rng(7).choice(n, nrows, replace=False))
+    t0 = time.time()
+    with sampled.SampledOracle(host["v"], host["f"], rows) as so:
+        ip, ix, dv = so.F_rows_sparse()
+        Eo = so.insolation_rows(host["dirs"], 1365.0)
+        workers = so.workers
+    t_or = time.time() - t0
+
+    def colerr(got, ref):
+        nr = np.linalg.norm(ref, axis=0)
+        live = nr > 0
+        return float((np.linalg.norm(got - ref, axis=0)[live] / nr[live]).max()), int(live.sum())
+
+    E = host["E"]
+    FE = sampled.csr_matmul(ip, ix, dv, E)
+    out = {"rows": nrows, "seed": 7, "workers": workers, "oracle_s": round(t_or, 1)}
+    out["insolation_max_abs_err_rel_to_max"] = float(np.abs(E[rows] - Eo).max() / max(Eo.max(), 1e-300))
+    out["apply_fp32_rel_err"], live = colerr(host["Y32"][rows], FE)
+    out["apply_bf16_rel_err"], _ = colerr(host["Ybf"][rows], FE)
+    out["columns"] = live
+    for key, name in (("B", "solve_bf16_refined_rel_err"), ("B8", "solve_fp8_refined_rel_err")):
+        Bg = host[key]
+        TB = Eo + C4_RHO * sampled.csr_matmul(ip, ix, dv, Bg)
+        out[name], _ = colerr(Bg[rows], TB)
+    out["reference"] = ("oracle FP64 F rows (own BVH visibility, Eq. FF-def) and insolation on the sampled rows; "
+                        "solve reference E_S + rho F_S B (one exact oracle Jacobi step from the GPU's B)")
+    return out
 
 
 # ------------------------------------------------------------- main
@@ -217,7 +404,6 @@ def main():
         print(json.dumps(line))
         return
 
-    import numpy as np
     import torch
     if world > 1:
         import torch.distributed as dist
@@ -229,6 +415,21 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2209_07632_gb300 import vf
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    st = torch.cuda.current_stream()
+
+    if a.config4_only:
+        c4, host = run_config4(a, dev, peak, st)
+        if not a.no_cpu:
+            c4["oracle_check"] = config4_oracle_check(host, a.config4_rows)
+        print(json.dumps({"config4": c4}))
+        return
 
     if a.profile_batched:
         v, f, _ = workload_inputs(1, a.dem_size)
@@ -252,7 +453,6 @@ def main():
     E = torch.empty((R, n), device="cuda", dtype=torch.float32)
     vf.vf_mesh_insolation(prob.mesh, dirs, 1365.0, E)
     B = torch.empty_like(E)
-    st = torch.cuda.current_stream()
     rho = 0.12
     rtol = 1e-6
 
@@ -277,8 +477,24 @@ def main():
         kernels += stats["kernels"]
     ev1.record(st)
     barrier()
-    clk = clocks.stop()
     ms = max_over_ranks(ev0.elapsed_time(ev1) / a.steps, world, "cuda")
+    # steady state: back-to-back steps for at least --steady-s seconds (not
+    # part of the K timed steps; a cross-check of ms_per_step with the clocks
+    # sampled over a longer window)
+    steady = None
+    if a.steady_s > 0:
+        nst = max(1, int(a.steady_s * 1000.0 / max(ms, 1e-3)))
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(st)
+        for _ in range(nst):
+            vf.vf_solve(prob.hmat, E, B, **solve_kw)
+        s1.record(st)
+        barrier()
+        sms = max_over_ranks(s0.elapsed_time(s1) / nst, world, "cuda")
+        steady = {"steps": nst, "seconds": round(sms * nst / 1000.0, 2), "ms_per_step": round(sms, 4),
+                  "value": round(whole_job_rate(world * R, sms / 1000.0), 3)}
+    clk = clocks.stop()
     value = whole_job_rate(world * R, ms / 1000.0)
 
     # ---- roofline of the multiply (phase 1 + phase 2), tree order, on `st`
@@ -297,12 +513,6 @@ def main():
     torch.cuda.synchronize()
     mult_ms = k0.elapsed_time(k1) / reps
     alg_bytes = vf.vf_hmat_bytes(prob.hmat, a.precision) + n * R * 8
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = alg_bytes / (mult_ms / 1000.0) / 1e9
     traffic = None
     try:
@@ -337,6 +547,7 @@ def main():
     # autotuner picks the path and the RHS block, and RHS blocks of 64, 256
     # and 1440 are timed as well
     batched = None
+    batched_host = None
     if not a.no_batched and rank == 0:
         Rb = a.batch_rhs
         Eb = torch.empty((Rb, n), device="cuda", dtype=torch.float32)
@@ -405,6 +616,7 @@ def main():
                                        "page_bytes": tpages,
                                        "page_frac": round((tpages["total"] + n * 128 * 6) / (tms / 1000.0) / 1e9 / peak,
                                                           4)}}
+        batched_host = {"B": Bb.double().cpu().numpy().T, "dirs": lunar_day_dirs(Rb), "rho": rho}
         del Eb, Bb, Bref, Xb, Yb
 
     # ---- many meshes in one launch per phase: K seeded fBm terrains (every
@@ -498,23 +710,49 @@ def main():
                  "compressed_vs_dense_rel_err": rel, "speedup_compressed": round(value / world / (R / (dms / 1e3)), 2)}
         del hd
 
+    # ---- the 522,242-facet precision workload (after the terrain's buffers are freed)
+    setup_info = {"workload": WORKLOAD if a.dem_size == 200 else f"fbm{a.dem_size}_crater_{n}tri", "facets": n,
+                  "l2": "inputs larger than L2 (compressed F %.0f MB)" % (vf.vf_hmat_bytes(prob.hmat, a.precision) / 1e6),
+                  "assembly": {k: prob.stats[k] for k in ("nblocks", "bytes", "probes", "max_rank", "t_visibility",
+                                                          "t_probe", "t_total")}}
+    config4 = None
+    c4_host = None
+    if not a.no_config4 and rank == 0 and world == 1:
+        import gc
+        del prob, E, B, Xt, Yt
+        gc.collect()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        config4, c4_host = run_config4(a, dev, peak, st)
+        gc.collect()
+        torch.cuda.empty_cache()
+
+    # ---- the CPU baseline leg: the oracle timed on a bounded sample of the
+    # terrain's rows; the same sampled oracle rows state the batched solve's
+    # error, and the precision workload's oracle rows its errors
     cpu = None
     if not a.no_cpu and rank == 0 and world == 1:
-        cpu = CpuOracle(v, f, dirs, a.cpu_rows, R).measure(sweeps, seconds=10.0)
+        co = CpuOracle(v, f, dirs, a.cpu_rows, R)
+        cpu = co.measure(sweeps, seconds=10.0)
+        if batched_host is not None:
+            batched["oracle_check"] = co.batched_check(v, f, batched_host)
+        if c4_host is not None:
+            config4["oracle_check"] = config4_oracle_check(c4_host, a.config4_rows)
+            chk = config4["oracle_check"]
+            config4["err_vs_oracle"] = chk["solve_bf16_refined_rel_err"]
+            config4["meets_1e-3"] = bool(chk["solve_bf16_refined_rel_err"] <= 1e-3)
 
     line = {"metric": METRIC, "value": round(value, 3), "unit": "RHS/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "fp8e4m3"}[a.precision],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if a.dem_size == 200 else f"fbm{a.dem_size}_crater_{n}tri", "facets": n, "rhs_per_gpu": R, "tol": a.tol, "rho": rho, "rtol": rtol,
-                       "sweeps": sweeps, "l2": "inputs larger than L2 (compressed F %.0f MB)" %
-                       (vf.vf_hmat_bytes(prob.hmat, a.precision) / 1e6),
+            "config": {"workload": setup_info["workload"], "facets": n, "rhs_per_gpu": R, "tol": a.tol, "rho": rho,
+                       "rtol": rtol, "sweeps": sweeps, "l2": setup_info["l2"],
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "setup_s": round(t_setup, 2)},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": kernels, "clocks": clk,
-            "batched": batched, "multimesh": multimesh, "dense_fp32": dense, "cpu_baseline": cpu,
-            "assembly": {k: prob.stats[k] for k in ("nblocks", "bytes", "probes", "max_rank", "t_visibility",
-                                                    "t_probe", "t_total")}}
+            "roofline": roofline, "e2e": e2e, "gpu_launches": kernels, "clocks": clk, "steady": steady,
+            "batched": batched, "multimesh": multimesh, "dense_fp32": dense, "config4": config4,
+            "cpu_baseline": cpu, "assembly": setup_info["assembly"]}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

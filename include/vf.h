@@ -50,7 +50,9 @@ typedef enum {
     VF_E_CUDA = 3,    /* a CUDA runtime call failed */
     VF_E_NOCONV = 4,  /* solve hit max_iter; outputs hold the last iterate */
     VF_E_TIMEOUT = 5, /* a bounded device-side wait gave up */
-    VF_E_OOB = 6,     /* a device-side bounds check fired */
+    VF_E_OOB = 6,     /* a device-side self-check fired: a tensor-core page record whose
+                         shape, page extent or operand range is out of bounds (the record
+                         is skipped, nothing is read or written through it) */
     VF_E_IO = 7,      /* file could not be opened, read or written */
     VF_E_CORRUPT = 8  /* file failed its magic/version/CRC checks */
 } vf_status;
@@ -62,6 +64,20 @@ typedef enum { VF_BLK_ZERO = 0, VF_BLK_DENSE = 1, VF_BLK_CSR = 2, VF_BLK_SVD = 3
 /* Thread-local message of the last failing call ("" if none). */
 const char* vf_last_error(void);
 const char* vf_version(void);
+
+/* Error-path testing (no counterpart in the paper).  vf_debug_fail_alloc:
+ * the nth device allocation the library makes from now on (counted over
+ * all threads) fails as if the device were out of memory, so the call
+ * making it returns VF_E_NOMEM and releases what it holds; 0 disarms.
+ * vf_set_wait_limit: the number of polls a bounded wait of the CUDA-core
+ * multiply (its page copies) makes on `device` before it gives up and the
+ * call reports VF_E_TIMEOUT (polls < 0 restores the default, 2^22; 0 makes
+ * every such wait give up at once).  A warp that gives up still waits, with
+ * the default bound, for the copies it has in flight before it stops, so
+ * the kernels exit normally.  The limit is read by each kernel when it
+ * starts (solve graphs included).  Errors: VF_E_INVAL, VF_E_CUDA. */
+vf_status vf_debug_fail_alloc(int64_t nth);
+vf_status vf_set_wait_limit(int32_t device, int64_t polls);
 
 /* ------------------------------------------------------------------ mesh
  * Section 3: A_i, x_i, n_i of each triangle (midpoint collocation).
@@ -258,16 +274,29 @@ vf_status vf_apply_tree(const vf_hmat* h, vf_precision p, const float* Xt, int32
  * allocator's latency or locks.  The paper has no counterpart: this is an
  * interface of this library, not a step of the method.
  *
+ * Path: always the CUDA-core multiply over all R columns at once.  It never
+ * takes the tensor-core path (BF16 with R >= 16) or a tuned RHS block, so
+ * where vf_apply_tree would take either, the two calls agree only to the
+ * rounding of the precision, not bit for bit; elsewhere they run the same
+ * kernels with the same RHS tile and agree exactly.
+ *
  * Scratch: the multiply's T vectors, the partial sums of cut blocks and a
- * status word live in fixed-size static device arrays of libvf, reserved
- * when its multiply module loads on a device (17 MiB):
+ * status word live in fixed-size static device arrays of libvf (17 MiB on
+ * each device that loads the library's multiply module, held until the
+ * process exits).  The memory is taken when that module is loaded on a
+ * device; with CUDA's lazy module loading (the default) that can be this
+ * call's first use, so a caller whose device memory is fully committed
+ * should make one call (or any other libvf multiply) while it still has
+ * 17 MiB free.
  *   T floats       npanels x RB x n_T   <= VF_STATIC_T_FLOATS    (4,194,304)
  *   partial floats npanels x RB x n_P   <= VF_STATIC_PART_FLOATS (262,144)
- * where RB = 1, 2, 4 or 8 (the smallest >= min(R, 8)), npanels =
+ * where RB = the RHS tile the autotuner recorded for (p, R) (vf_autotune,
+ * vf_tune_set), else 1, 2, 4 or 8 (the smallest >= min(R, 8)); npanels =
  * ceil(R / RB), n_T = the sum of the SVD blocks' ranks and n_P = the sum of
  * rank x pieces over the (few) SVD blocks whose V' rows are cut across
- * several pieces of the multiply's work plan.  A matrix and R that need more return VF_E_INVAL with the
- * sizes in the message, and nothing is launched.
+ * several pieces of the multiply's work plan.  A matrix and R that need
+ * more return VF_E_INVAL with the sizes in the message, and nothing is
+ * launched.
  * What must start at zero: only the status word; the call clears it itself
  * (cudaMemsetAsync) before the kernels run.  T and the partial slots are
  * written before they are read.

@@ -70,7 +70,12 @@ struct ApplyArgs {
 #define VF_STAGES 2
 #endif
 constexpr int kStages = VF_STAGES;
-constexpr uint32_t kWaitLimit = 1u << 22;  // polls before a wait reports a timeout
+constexpr uint32_t kWaitLimit = 1u << 22;  // polls before a wait reports a timeout (the default)
+// The page waits of the multiply kernels poll at most g_wait_polls times
+// (vf_set_wait_limit; read by each kernel at its start, so solve graphs see
+// changes too).  The drain before an early exit always uses kWaitLimit, so a
+// short limit never lets a warp leave with bulk copies in flight.
+__device__ uint32_t g_wait_polls = kWaitLimit;
 
 template <class T> __device__ __forceinline__ float lds(const T* p);
 template <> __device__ __forceinline__ float lds<float>(const float* p) { return *p; }
@@ -295,6 +300,7 @@ __global__ void __launch_bounds__(256) k_phase1(ApplyArgs a, PageArgs pg, const 
     const float* X = (xsel ? *xsel : xd) + (int64_t)p0 * a.n;
     const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
     const int pa = warp_ptr[gw], pb = warp_ptr[gw + 1];
+    const uint32_t lim = g_wait_polls;
     if (lane == 0) {
         pipe_init(wp);
         for (int s = 0; s < kStages && pa + s < pb; ++s) issue_page(pg, pa + s, wp, s);
@@ -304,9 +310,9 @@ __global__ void __launch_bounds__(256) k_phase1(ApplyArgs a, PageArgs pg, const 
     for (int p = pa; p < pb; ++p, ++n) {
         const int s = n % kStages;
         // warp-uniform decision: a lane that gave up makes the whole warp stop
-        if (!__all_sync(0xffffffffu, mbar_wait(&wp.bar[s], (uint32_t)((n / kStages) & 1), kWaitLimit))) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&wp.bar[s], (uint32_t)((n / kStages) & 1), lim))) {
             drain(wp, n, issued);  // no bulk copy may stay in flight into this warp's stages
-            if (lane == 0) atomicExch(status, VF_E_TIMEOUT);
+            if (lane == 0) atomicCAS(status, 0, (int)VF_E_TIMEOUT);
             return;
         }
         unsigned char* page = wp.buf[s];
@@ -441,6 +447,7 @@ __global__ void __launch_bounds__(256, RB == 1 ? 3 : 1) k_phase2(ApplyArgs a, Pa
     acc_t* slot = slots[warp];
     for (int i = lane; i < kTileRows * RB; i += 32) slot[i] = 0;
     const int pa = a.tile_page_ptr[tile * kWarps + warp], pb = a.tile_page_ptr[tile * kWarps + warp + 1];
+    const uint32_t lim = g_wait_polls;
     if (lane == 0) {
         pipe_init(wp);
         for (int s = 0; s < kStages && pa + s < pb; ++s) issue_page(pg, pa + s, wp, s);
@@ -450,7 +457,7 @@ __global__ void __launch_bounds__(256, RB == 1 ? 3 : 1) k_phase2(ApplyArgs a, Pa
     int consumed = 0, issued = min(kStages, pb - pa);
     for (int p = pa, n = 0; p < pb; ++p, ++n) {
         const int s = n % kStages;
-        if (!__all_sync(0xffffffffu, mbar_wait(&wp.bar[s], (uint32_t)((n / kStages) & 1), kWaitLimit))) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&wp.bar[s], (uint32_t)((n / kStages) & 1), lim))) {
             ok = false;  // warp-uniform: a lane that gave up makes the whole warp stop
             break;
         }
@@ -468,7 +475,7 @@ __global__ void __launch_bounds__(256, RB == 1 ? 3 : 1) k_phase2(ApplyArgs a, Pa
     }
     if (!ok) {
         drain(wp, consumed, issued);  // no bulk copy may stay in flight into this warp's stages
-        if (lane == 0) atomicExch(io.status, VF_E_TIMEOUT);
+        if (lane == 0) atomicCAS(io.status, 0, (int)VF_E_TIMEOUT);
     }
     __syncthreads();
     double mysum[RB];
@@ -1079,6 +1086,8 @@ struct Workspace {
     dbuf<unsigned char> xsplit[2], tsplit[2];  // hi / lo panels of the split residual
     dbuf<int> tcount;  // [0]: columns not converged after a tensor sweep; [1]: the reduction's ticket
     int tpanels = 0;
+    bool tready = false, sready = false;  // the tensor panels / the split panels are all allocated
+    bool cready = false;                  // the CUDA-core multiply's T and partial buffers are allocated
     cudaGraphExec_t graph = nullptr;
     cudaGraphConditionalHandle handle = 0;
     cudaEvent_t done = nullptr;
@@ -1169,9 +1178,6 @@ static vf_status ws_get_rb(const vf_hmat* h, int R, int prec, int RB, Workspace*
     VF_TRY(w->Bt[1].alloc(nR));
     VF_TRY(w->Rbuf.alloc(nR));
     VF_TRY(w->rho_t.alloc(n));
-    int64_t nT = std::max<int64_t>(h->n_T, 1);
-    VF_TRY(w->Tbuf.alloc((int64_t)w->npanels * w->RB * nT));
-    VF_TRY(w->part.alloc((int64_t)w->npanels * w->RB * std::max<int64_t>(h->n_part_slots, 1)));
     VF_TRY(w->colpart.alloc(std::max<int64_t>(ntiles * R, 1)));
     VF_TRY(w->enorm2.alloc((int64_t)R * h->nseg()));
     VF_TRY(w->colres.alloc((int64_t)R * h->nseg()));
@@ -1306,9 +1312,22 @@ static vf_status launch_multiply_sc(const vf_hmat* h, int prec, const Scratch* w
     return launch_multiply_rb<__nv_fp8_e4m3>(h, prec, a, w, mode, xsel, ysel, xd, yd, E, rho, st);
 }
 
+// The CUDA-core multiply's scratch of a workspace (T vectors of every RHS
+// panel, cut-block partials), allocated on its first use: workspaces whose
+// multiplies all run on the tensor cores never hold it.
+static vf_status ws_scratch(const vf_hmat* h, Workspace* w) {
+    if (w->cready) return VF_OK;
+    const int64_t nT = std::max<int64_t>(h->n_T, 1);
+    VF_TRY(w->Tbuf.alloc((int64_t)w->npanels * w->RB * nT));
+    VF_TRY(w->part.alloc((int64_t)w->npanels * w->RB * std::max<int64_t>(h->n_part_slots, 1)));
+    w->cready = true;
+    return VF_OK;
+}
+
 static vf_status launch_multiply(const vf_hmat* h, int prec, Workspace* w, int mode, const float* const* xsel,
                                  float* const* ysel, const float* xd, float* yd, const float* E, const float* rho,
                                  cudaStream_t st) {
+    VF_TRY(ws_scratch(h, w));  // a no-op inside graph capture: ensure_graph calls it first
     const Scratch sc{w->R, w->RB, w->npanels, w->Tbuf.p, w->part.p, w->status.p, w->colpart.p};
     return launch_multiply_sc(h, prec, &sc, mode, xsel, ysel, xd, yd, E, rho, st);
 }
@@ -1360,7 +1379,7 @@ static bool use_tensor(const vf_hmat* h, int prec, int R) {
 // and this workspace's panels.
 static vf_status tensor_ws(const vf_hmat* h, Workspace* w) {
     VF_TRY(tensor_prepare(const_cast<vf_hmat*>(h), 1));
-    if (w->xpan[0].p) return VF_OK;
+    if (w->tready) return VF_OK;  // set only once every buffer below exists
     w->tpanels = (int)ceil_div(w->R, kTensorPanel);
     const int64_t bx = tensor_panel_bytes_x(h), bt = tensor_panel_bytes_t(h);
     for (int i = 0; i < 2; ++i) {
@@ -1372,6 +1391,7 @@ static vf_status tensor_ws(const vf_hmat* h, Workspace* w) {
     VF_TRY_CUDA(cudaMemset(w->tpan.p, 0, (size_t)2 * bt));
     VF_TRY(w->tcount.alloc(2));
     VF_TRY_CUDA(cudaMemset(w->tcount.p, 0, 2 * sizeof(int)));
+    w->tready = true;
     return VF_OK;
 }
 
@@ -1485,13 +1505,14 @@ static vf_status tensor_residual(const vf_hmat* h, Workspace* w, const float* B,
     VF_TRY(tensor_prepare(const_cast<vf_hmat*>(h), 2));
     const int64_t n = h->nf, ntiles = tensor_parts(h, 2);
     const int64_t bx = tensor_panel_bytes_x(h), bt = tensor_panel_bytes_t(h);
-    if (!w->xsplit[0].p) {
+    if (!w->sready) {  // set only once every split buffer exists
         for (int i = 0; i < 2; ++i) {
             VF_TRY(w->xsplit[i].alloc((size_t)w->tpanels * bx));
             VF_TRY_CUDA(cudaMemset(w->xsplit[i].p, 0, (size_t)w->tpanels * bx));
             VF_TRY(w->tsplit[i].alloc((size_t)2 * bt));  // two T panels: pairs of RHS panels
             VF_TRY_CUDA(cudaMemset(w->tsplit[i].p, 0, (size_t)2 * bt));
         }
+        w->sready = true;
     }
     for (int p = 0, np; p < w->tpanels; p += np) {
         np = p + 1 < w->tpanels ? 2 : 1;  // two RHS panels per multiply where there are two
@@ -1554,6 +1575,7 @@ static vf_status check_prec(const vf_hmat* h, int prec) {
 // Jacobi sweep plus the column reduction that sets the loop condition.
 static vf_status ensure_graph(const vf_hmat* h, Workspace* w) {
     if (w->graph) return VF_OK;
+    VF_TRY(ws_scratch(h, w));  // no allocation may happen during the capture below
     cudaGraph_t g;
     VF_TRY_CUDA(cudaGraphCreate(&g, 0));
     VF_TRY_CUDA(cudaGraphConditionalHandleCreate(&w->handle, g, 1, cudaGraphCondAssignDefault));
@@ -1731,7 +1753,7 @@ extern "C" vf_status vf_apply_tree_static(const vf_hmat* h, vf_precision prec, c
     VF_CHECK(h && Xt && Yt, VF_E_INVAL, "vf_apply_tree_static: null argument");
     VF_CHECK(R >= 1, VF_E_INVAL, "vf_apply_tree_static: need R >= 1");
     VF_TRY(vf::check_prec(h, prec));
-    const int RB = vf::pick_rb(R), npanels = (int)vf::ceil_div(R, RB);
+    const int RB = vf::pick_rb_for(h, prec, R), npanels = (int)vf::ceil_div(R, RB);
     const int64_t nT = std::max<int64_t>(h->n_T, 1);
     const int64_t need_T = (int64_t)npanels * RB * nT;
     const int64_t need_part = (int64_t)npanels * RB * std::max<int64_t>(h->n_part_slots, 1);
@@ -1749,7 +1771,20 @@ extern "C" vf_status vf_apply_tree_static(const vf_hmat* h, vf_precision prec, c
     int hs = 0;
     VF_TRY_CUDA(cudaMemcpyAsync(&hs, ss.status, sizeof(int), cudaMemcpyDeviceToHost, st));
     VF_TRY_CUDA(cudaStreamSynchronize(st));
+    VF_CHECK(hs != VF_E_OOB, VF_E_OOB, "vf_apply_tree_static: a device-side bounds check fired");
     VF_CHECK(hs == 0, VF_E_TIMEOUT, "vf_apply_tree_static: a bounded device-side wait gave up");
+    return VF_OK;
+}
+
+extern "C" vf_status vf_set_wait_limit(int32_t device, int64_t polls) {
+    clear_error();
+    VF_CHECK(polls <= 0x7fffffffll, VF_E_INVAL, "vf_set_wait_limit: polls must be < 2^31");
+    int ndev = 0;
+    VF_TRY_CUDA(cudaGetDeviceCount(&ndev));
+    VF_CHECK(device >= 0 && device < ndev, VF_E_INVAL, "vf_set_wait_limit: no device %d", (int)device);
+    const uint32_t v = polls < 0 ? vf::kWaitLimit : (uint32_t)polls;
+    device_guard g(device);
+    VF_TRY_CUDA(cudaMemcpyToSymbol(vf::g_wait_polls, &v, sizeof(v)));
     return VF_OK;
 }
 
@@ -1893,6 +1928,10 @@ static vf_status solve_status(const vf_hmat* h, Workspace* w, int R, bool refine
         cudaMemsetAsync(w->status.p, 0, sizeof(int), st);
         if (wr) cudaMemsetAsync(wr->status.p, 0, sizeof(int), st);
         cudaStreamSynchronize(st);
+        if (ws[0] == VF_E_OOB || ws[1] == VF_E_OOB) {
+            set_error("%s: a device-side bounds check fired", who);
+            return VF_E_OOB;
+        }
         set_error("%s: a bounded device-side wait gave up", who);
         return VF_E_TIMEOUT;
     }
@@ -2082,16 +2121,28 @@ extern "C" vf_status vf_solve_host(const vf_hmat* h, const float* rho, const flo
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = h->nf;
     float *dE = nullptr, *dB = nullptr, *drho = nullptr;
-    VF_TRY_CUDA(cudaMallocAsync((void**)&dE, n * R * sizeof(float), st));
-    VF_TRY_CUDA(cudaMallocAsync((void**)&dB, n * R * sizeof(float), st));
-    if (rho) VF_TRY_CUDA(cudaMallocAsync((void**)&drho, n * sizeof(float), st));
     vf_status s = VF_OK;
-    cudaError_t e = cudaMemcpy2DAsync(dE, n * sizeof(float), E, lde * sizeof(float), n * sizeof(float), R,
-                                      cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && rho) e = cudaMemcpyAsync(drho, rho, n * sizeof(float), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) {
-        set_error("vf_solve_host: copy to device failed: %s", cudaGetErrorString(e));
-        s = VF_E_CUDA;
+    auto get = [&](float** p, size_t bytes) {
+        if (s != VF_OK) return;
+        cudaError_t ea = vf::inject_alloc_failure() ? cudaErrorMemoryAllocation : cudaMallocAsync((void**)p, bytes, st);
+        if (ea != cudaSuccess) {
+            *p = nullptr;
+            set_error("vf_solve_host: device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(ea));
+            s = ea == cudaErrorMemoryAllocation ? VF_E_NOMEM : VF_E_CUDA;
+        }
+    };
+    get(&dE, n * R * sizeof(float));
+    get(&dB, n * R * sizeof(float));
+    if (rho) get(&drho, n * sizeof(float));
+    cudaError_t e = cudaSuccess;
+    if (s == VF_OK) {
+        e = cudaMemcpy2DAsync(dE, n * sizeof(float), E, lde * sizeof(float), n * sizeof(float), R,
+                              cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && rho) e = cudaMemcpyAsync(drho, rho, n * sizeof(float), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) {
+            set_error("vf_solve_host: copy to device failed: %s", cudaGetErrorString(e));
+            s = VF_E_CUDA;
+        }
     }
     if (s == VF_OK) s = vf_solve(h, drho, dE, n, dB, n, R, opts, stats, stream);
     if (s == VF_OK || s == VF_E_NOCONV) {
@@ -2103,8 +2154,8 @@ extern "C" vf_status vf_solve_host(const vf_hmat* h, const float* rho, const flo
             s = VF_E_CUDA;
         }
     }
-    cudaFreeAsync(dE, st);
-    cudaFreeAsync(dB, st);
+    if (dE) cudaFreeAsync(dE, st);
+    if (dB) cudaFreeAsync(dB, st);
     if (drho) cudaFreeAsync(drho, st);
     return s;
 }

@@ -40,6 +40,10 @@ void clear_error();
         if (s_ != VF_OK) return s_;         \
     } while (0)
 
+// Allocation-failure injection (vf_debug_fail_alloc): true when the
+// library's next device allocation is the one armed to fail.
+bool inject_alloc_failure();
+
 // RAII device buffer
 template <class T>
 struct dbuf {
@@ -62,7 +66,7 @@ struct dbuf {
     vf_status alloc(size_t count) {
         release();
         if (count == 0) return VF_OK;
-        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        cudaError_t e = inject_alloc_failure() ? cudaErrorMemoryAllocation : cudaMalloc(&p, count * sizeof(T));
         if (e != cudaSuccess) {
             p = nullptr;
             set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));

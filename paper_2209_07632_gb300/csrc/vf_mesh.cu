@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 
 #include "vf_internal.cuh"
@@ -21,6 +22,17 @@
 namespace vf {
 
 static thread_local char g_err[1024] = "";
+
+// vf_debug_fail_alloc: allocations left before the armed one (0: disarmed)
+static std::atomic<int64_t> g_fail_alloc{0};
+
+bool inject_alloc_failure() {
+    int64_t c = g_fail_alloc.load(std::memory_order_relaxed);
+    while (c > 0) {
+        if (g_fail_alloc.compare_exchange_weak(c, c - 1, std::memory_order_relaxed)) return c == 1;
+    }
+    return false;
+}
 
 void set_error(const char* fmt, ...) {
     va_list ap;
@@ -416,7 +428,14 @@ using namespace vf;
 
 // ============================================================ C ABI
 extern "C" const char* vf_last_error(void) { return vf::g_err; }
-extern "C" const char* vf_version(void) { return "libvf 0.1 (sm_103a)"; }
+extern "C" const char* vf_version(void) { return "libvf 0.2 (sm_103a)"; }
+
+extern "C" vf_status vf_debug_fail_alloc(int64_t nth) {
+    clear_error();
+    VF_CHECK(nth >= 0, VF_E_INVAL, "vf_debug_fail_alloc: nth must be >= 0");
+    g_fail_alloc.store(nth, std::memory_order_relaxed);
+    return VF_OK;
+}
 
 extern "C" vf_status vf_mesh_create(const double* verts, int64_t nv, const int32_t* faces, int64_t nf,
                                     const vf_mesh_opts* opts, vf_mesh** out) {

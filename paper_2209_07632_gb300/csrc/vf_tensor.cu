@@ -892,11 +892,11 @@ __device__ void t_producer(TSmem& S, unsigned char* stages, unsigned char* abuf,
 bad:
     if (rc == -2) goto oob;
 fail:
-    atomicExch(status, VF_E_TIMEOUT);
+    atomicCAS(status, 0, (int)VF_E_TIMEOUT);
     atomicExch(&S.abort, 1);
     return;
 oob:
-    atomicExch(status, VF_E_OOB);
+    atomicCAS(status, 0, (int)VF_E_OOB);
     atomicExch(&S.abort, 1);
 }
 
@@ -966,7 +966,7 @@ __device__ void t_issuer(TSmem& S, unsigned char* stages, unsigned char* abuf, i
     mma_commit(&S.done);
     return;
 fail:
-    atomicExch(status, VF_E_TIMEOUT);
+    atomicCAS(status, 0, (int)VF_E_TIMEOUT);
     atomicExch(&S.abort, 1);
     mma_commit(&S.done);
 }
@@ -1021,7 +1021,7 @@ __device__ void t_finish(TSmem& S, int* status) {
     constexpr int ncols = TCfg<NS, NP>::TMEM;
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 32) {
-        if (!bwait(&S.done, 0)) atomicExch(status, VF_E_TIMEOUT);
+        if (!bwait(&S.done, 0)) atomicCAS(status, 0, (int)VF_E_TIMEOUT);
     }
     tm_fence_before();
     __syncthreads();
@@ -1090,7 +1090,7 @@ __global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase1(const unsig
             const int d = NREG == 1 ? 0 : (k & 1);
             if (!open) {
                 if (!__all_sync(0xffffffffu, bwait(&S.d_full[d], (uint32_t)((k / NREG) & 1)))) {
-                    if (lane == 0) atomicExch(status, VF_E_TIMEOUT), atomicExch(&S.abort, 1);
+                    if (lane == 0) atomicCAS(status, 0, (int)VF_E_TIMEOUT), atomicExch(&S.abort, 1);
                     break;
                 }
                 tm_fence_after();
@@ -1159,7 +1159,7 @@ __global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase2(const unsig
         for (int ti = t0, k = 0; ti < t1; ++ti, ++k) {
             const int d = NREG == 1 ? 0 : (k & 1);
             if (!__all_sync(0xffffffffu, bwait(&S.d_full[d], (uint32_t)((k / NREG) & 1)))) {
-                if (lane == 0) atomicExch(status, VF_E_TIMEOUT), atomicExch(&S.abort, 1);
+                if (lane == 0) atomicCAS(status, 0, (int)VF_E_TIMEOUT), atomicExch(&S.abort, 1);
                 break;
             }
             tm_fence_after();

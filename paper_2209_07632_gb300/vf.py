@@ -84,6 +84,8 @@ _I32 = ctypes.c_int32
 _SIGS = {
     "vf_last_error": ([], ctypes.c_char_p),
     "vf_version": ([], ctypes.c_char_p),
+    "vf_debug_fail_alloc": ([_I64], ctypes.c_int),
+    "vf_set_wait_limit": ([_I32, _I64], ctypes.c_int),
     "vf_mesh_create": ([_P, _I64, _P, _I64, _P, _P], ctypes.c_int),
     "vf_mesh_destroy": ([_P], None),
     "vf_mesh_nfacets": ([_P], _I64),
@@ -227,6 +229,16 @@ def vf_version() -> str:
     return load().vf_version().decode()
 
 
+def vf_debug_fail_alloc(nth: int):
+    """Make the library's nth device allocation from now on fail (0 disarms)."""
+    _check(load().vf_debug_fail_alloc(int(nth)))
+
+
+def vf_set_wait_limit(polls: int, device: int = 0):
+    """Polls of the CUDA-core multiply's bounded page waits (< 0: the default)."""
+    _check(load().vf_set_wait_limit(int(device), int(polls)))
+
+
 def vf_mesh_create(verts, faces, device: int = 0) -> Mesh:
     v = np.ascontiguousarray(verts, dtype=np.float64)
     f = np.ascontiguousarray(faces, dtype=np.int32)
@@ -338,8 +350,15 @@ def vf_apply(h: HMat, X, Y, precision: str = "fp32", stream=None):
     return Y
 
 
+def _same_shape(Xt, Yt, who: str):
+    """Yt receives R x N floats: its shape must be Xt's (checked before the library is called)."""
+    if tuple(Yt.shape) != tuple(Xt.shape):
+        raise VFError(VF_E_INVAL, f"{who}: Yt shape {tuple(Yt.shape)} != Xt shape {tuple(Xt.shape)}")
+
+
 def vf_apply_tree(h: HMat, Xt, Yt, precision: str = "fp32", stream=None):
     """The multiply alone on tree-ordered (R, N) tensors."""
+    _same_shape(Xt, Yt, "vf_apply_tree")
     n = h.n
     R = 1 if Xt.dim() == 1 else Xt.shape[0]
     _check(load().vf_apply_tree(h.ptr, PREC[precision], _dev_ptr(Xt, "Xt", n), R, _dev_ptr(Yt, "Yt", n),
@@ -350,6 +369,7 @@ def vf_apply_tree(h: HMat, Xt, Yt, precision: str = "fp32", stream=None):
 def vf_apply_tree_static(h: HMat, Xt, Yt, precision: str = "fp32", stream=None):
     """vf_apply_tree with the library's fixed static scratch: no device
     allocation; synchronous; calls must not overlap in time."""
+    _same_shape(Xt, Yt, "vf_apply_tree_static")
     n = h.n
     R = 1 if Xt.dim() == 1 else Xt.shape[0]
     _check(load().vf_apply_tree_static(h.ptr, PREC[precision], _dev_ptr(Xt, "Xt", n), R, _dev_ptr(Yt, "Yt", n),

@@ -69,3 +69,19 @@ def test_predictor_sizes_match_header():
         m = re.search(r"#define\s+" + name + r"\s+(\d+)", txt)
         assert m and int(m.group(1)) == getattr(vf, name)
     assert vf.VF_PRED_NPARAM == mlp.NPARAM and vf.VF_PRED_NFEAT == mlp.NF and vf.VF_PRED_NCLASS == mlp.NC
+
+
+@pytest.mark.parametrize("fn", ["vf_apply_tree", "vf_apply_tree_static"])
+def test_tree_multiply_rejects_a_mismatched_output(fn):
+    """Yt must have Xt's shape: the binding refuses before the library is called
+    (a smaller Yt would otherwise receive R x N floats)."""
+    import torch
+
+    from paper_2209_07632_gb300 import vf
+    h = vf.HMat(None)  # never reached: the shape check comes first
+    Xt = torch.zeros((8, 10))
+    for Yt in (torch.zeros(10), torch.zeros((2, 10)), torch.zeros((8, 11))):
+        with pytest.raises(vf.VFError) as ei:
+            getattr(vf, fn)(h, Xt, Yt)
+        assert ei.value.status == vf.VF_E_INVAL
+        assert "shape" in str(ei.value)
