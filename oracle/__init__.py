@@ -13,6 +13,10 @@ Each function cites the passage of the paper it follows:
 * ``assemble``: Algorithms 3 and 4 (Sections 4.2, 4.3) with exact FP64 SVDs
 * ``apply_blocks``: Algorithm 5 (Section 4.4)
 * ``jacobi``: the Jacobi iteration for Eq. radiosity-system (Sections 3, 5.1)
+* ``equilibrium_temperature``: the two time-independent systems of Section 5.1
+* ``flux_step``, ``flux_init``: the flux updates of Algorithm 6 (Section 5.2)
+* ``disk_sun_samples``, ``insolation_disk``: the finite solar disk as a sum
+  of point sources (Section 2)
 * ``bowl_*``: the analytic bowl-shaped crater solution (Section 6.1)
 
 Parity pins: see tests/test_oracle_*.py (closed forms, invariants, brute force).
@@ -465,3 +469,70 @@ def equilibrium_temperature(apply, Edirect: np.ndarray, albedo: float, emissivit
     absorbed = (1.0 - albedo) * Qvis + emissivity * Qir
     T = np.maximum(absorbed, 0.0) / (emissivity * SIGMA_SB)
     return T ** 0.25, Qvis, Qir
+
+
+# ------------------------------------------------------- Algorithm 6
+def flux_init(Edirect: np.ndarray, albedo, H=0.0):
+    """Algorithm 6, n = 0: Q_abs = (1 - albedo) Q_direct + H, Q_refl = 0,
+    Q_IR = 0, Q_rad = Q_abs.  Returns (Q_refl, Q_IR, Q_abs, Q_rad)."""
+    Ed = np.asarray(Edirect, dtype=np.float64)
+    Qabs = (1.0 - np.asarray(albedo, dtype=np.float64)) * Ed + H
+    return np.zeros_like(Ed), np.zeros_like(Ed), Qabs, Qabs.copy()
+
+
+def flux_step(apply, Edirect_next, Qrefl, Qir, Qrad, albedo, emissivity):
+    """Algorithm 6 (Section 5.2), one time step of the fluxes, one multiply
+    by F per flux:
+      Q_refl' = F diag(albedo) (Q_direct' + Q_refl)
+      Q_IR'   = F (Q_rad + (I - diag(emissivity)) Q_IR)
+      Q_abs'  = (I - diag(albedo)) (Q_direct' + Q_refl') + diag(emissivity) Q_IR'
+    albedo, emissivity: scalars or per-facet columns (N x 1).  Returns
+    (Q_refl', Q_IR', Q_abs')."""
+    a = np.asarray(albedo, dtype=np.float64)
+    e = np.asarray(emissivity, dtype=np.float64)
+    Ed = np.asarray(Edirect_next, dtype=np.float64)
+    Qrefl1 = apply(a * (Ed + Qrefl))
+    Qir1 = apply(Qrad + (1.0 - e) * Qir)
+    Qabs1 = (1.0 - a) * (Ed + Qrefl1) + e * Qir1
+    return Qrefl1, Qir1, Qabs1
+
+
+# ------------------------------------------------------- finite solar disk
+def disk_sun_samples(s, angular_radius: float, rings: int):
+    """Point sources standing for a uniformly bright solar disk of the given
+    angular radius (radians) around the unit direction s (Section 2: the
+    disk's flux is a sum over point sources).  The disk is cut into rings of
+    equal radial width; ring k (k = 0 is the central disk) is split into
+    max(1, 6k) equal sectors; each cell's point sits at its area-weighted
+    mean radius and mid angle, with weight = its share of the disk's area
+    (the weights sum to 1).  Returns (directions M x 3, weights M)."""
+    s = np.asarray(s, dtype=np.float64)
+    s = s / np.linalg.norm(s)
+    a = np.array([1.0, 0.0, 0.0]) if abs(s[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    u = np.cross(s, a)
+    u /= np.linalg.norm(u)
+    w = np.cross(s, u)
+    dirs, wts = [], []
+    for k in range(rings):
+        r0, r1 = k / rings, (k + 1) / rings
+        nsec = max(1, 6 * k)
+        area = (r1 * r1 - r0 * r0) / nsec  # share of the unit disk (pi cancels)
+        rc = 0.0 if k == 0 else (2.0 / 3.0) * (r1 ** 3 - r0 ** 3) / (r1 * r1 - r0 * r0)
+        for j in range(nsec):
+            phi = 2.0 * math.pi * (j + 0.5) / nsec
+            t = angular_radius * rc
+            d = math.cos(t) * s + math.sin(t) * (math.cos(phi) * u + math.sin(phi) * w)
+            dirs.append(d / np.linalg.norm(d))
+            wts.append(area)
+    return np.asarray(dirs), np.asarray(wts)
+
+
+def insolation_disk(m: Mesh, dirs, solar_flux: float, angular_radius: float, rings: int) -> np.ndarray:
+    """E (N x R) for a finite solar disk: the weighted sum over the disk's
+    point sources of the point-sun insolation (Section 2), per sun direction."""
+    dirs = np.atleast_2d(np.asarray(dirs, dtype=np.float64))
+    E = np.zeros((m.n, dirs.shape[0]))
+    for r, s in enumerate(dirs):
+        pts, wts = disk_sun_samples(s, angular_radius, rings)
+        E[:, r] = insolation(m, pts, solar_flux) @ wts
+    return E
