@@ -13,7 +13,9 @@ Each function cites the passage of the paper it follows:
 * ``assemble``: Algorithms 3 and 4 (Sections 4.2, 4.3) with exact FP64 SVDs
 * ``apply_blocks``: Algorithm 5 (Section 4.4)
 * ``jacobi``: the Jacobi iteration for Eq. radiosity-system (Sections 3, 5.1)
-* ``equilibrium_temperature``: the two time-independent systems of Section 5.1
+* ``equilibrium_temperature``, ``equilibrium_fluxes``: the two
+  time-independent systems of Section 5.1 (the second with per-facet albedo,
+  emissivity and heat flux, in the printed F diag(albedo) form)
 * ``flux_step``, ``flux_init``: the flux updates of Algorithm 6 (Section 5.2)
 * ``disk_sun_samples``, ``insolation_disk``: the finite solar disk as a sum
   of point sources (Section 2)
@@ -469,6 +471,40 @@ def equilibrium_temperature(apply, Edirect: np.ndarray, albedo: float, emissivit
     absorbed = (1.0 - albedo) * Qvis + emissivity * Qir
     T = np.maximum(absorbed, 0.0) / (emissivity * SIGMA_SB)
     return T ** 0.25, Qvis, Qir
+
+
+def _fixed_point(step, x0, scale, rtol, max_iter):
+    """x <- step(x) from x0 until ||x_{k+1} - x_k||_2 <= rtol ||scale||_2 per column."""
+    x = x0
+    ref = np.linalg.norm(scale, axis=0)
+    for _ in range(max_iter):
+        xn = step(x)
+        done = np.all(np.linalg.norm(xn - x, axis=0) <= rtol * np.maximum(ref, 1e-300))
+        x = xn
+        if done:
+            break
+    return x
+
+
+def equilibrium_fluxes(apply, Edirect: np.ndarray, albedo, emissivity, H=0.0, rtol: float = 1e-13,
+                       max_iter: int = 2000):
+    """Section 5.1 as printed, with per-facet albedo and emissivity (N x 1
+    columns or scalars) and interior heat flux H:
+      (I - F diag(albedo)) Q_refl = F diag(albedo) Q_direct      (Eq. time-indep-system-1)
+      (I - F) Q_IR = F (I - diag(albedo)) (Q_direct + Q_refl) + F H  (Eq. time-indep-system-2)
+      eps sigma T^4 = (1 - albedo)(Q_direct + Q_refl) + eps Q_IR   (Eq. 3d-equilbr)
+    each system by its fixed-point (Jacobi) iteration from 0.  Returns
+    (T, Q_refl, Q_IR)."""
+    a = np.asarray(albedo, dtype=np.float64)
+    e = np.asarray(emissivity, dtype=np.float64)
+    Ed = np.asarray(Edirect, dtype=np.float64)
+    b1 = apply(a * Ed)
+    Qrefl = _fixed_point(lambda x: b1 + apply(a * x), np.zeros_like(Ed), b1, rtol, max_iter)
+    b2 = apply((1.0 - a) * (Ed + Qrefl) + H)
+    Qir = _fixed_point(lambda x: b2 + apply(x), np.zeros_like(Ed), b2, rtol, max_iter)
+    absorbed = (1.0 - a) * (Ed + Qrefl) + e * Qir
+    T = (np.maximum(absorbed, 0.0) / (e * SIGMA_SB)) ** 0.25
+    return T, Qrefl, Qir
 
 
 # ------------------------------------------------------- Algorithm 6

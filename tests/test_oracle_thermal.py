@@ -96,3 +96,27 @@ def test_disk_insolation_lit_plane_and_point_limit(cap_small):
     # a vanishing disk is the point sun
     E0 = oracle.insolation_disk(m, dirs, 1365.0, 1e-9, 3)
     assert np.allclose(E0, Ep, rtol=1e-6, atol=1e-6)
+
+
+def test_equilibrium_fluxes_solve_the_printed_systems(cap_small):
+    """Per-facet albedo, emissivity and heat flux: the outputs satisfy
+    Eqs. time-indep-system-1/2 and 3d-equilbr to rounding; with uniform
+    values they equal equilibrium_temperature (B = Q_direct + Q_refl)."""
+    m = cap_small
+    F = oracle.F_dense(m, oracle.visibility_rows(m, np.arange(m.n)))
+    E = oracle.insolation(m, synth.sun_directions(2, 10.0), 1365.0)
+    rng = np.random.default_rng(5)
+    alb = rng.uniform(0.05, 0.3, size=(m.n, 1))
+    eps = rng.uniform(0.9, 1.0, size=(m.n, 1))
+    H = rng.uniform(0.0, 0.05, size=(m.n, 1))
+    T, Qr, Qi = oracle.equilibrium_fluxes(lambda X: F @ X, E, alb, eps, H)
+    sc = np.abs(F @ (alb * E)).max()
+    assert np.abs(Qr - F @ (alb * Qr) - F @ (alb * E)).max() <= 1e-11 * sc
+    r2 = Qi - F @ Qi - F @ ((1 - alb) * (E + Qr)) - F @ np.broadcast_to(H, E.shape)
+    assert np.abs(r2).max() <= 1e-11 * np.abs(Qi).max()
+    assert np.allclose(eps * oracle.SIGMA_SB * T ** 4, (1 - alb) * (E + Qr) + eps * Qi, rtol=1e-12)
+    T0, Qvis0, Qir0 = oracle.equilibrium_temperature(lambda X: F @ X, E, 0.12, 0.95)
+    T1, Qr1, Qi1 = oracle.equilibrium_fluxes(lambda X: F @ X, E, 0.12, 0.95)
+    assert np.allclose(Qr1, Qvis0 - E, rtol=1e-9, atol=1e-9 * E.max())
+    assert np.allclose(Qi1, Qir0, rtol=1e-9, atol=1e-9 * E.max())
+    assert np.allclose(T1, T0, rtol=1e-10)
