@@ -118,6 +118,21 @@ vf_status vf_mesh_visibility(const vf_mesh* m, const int64_t* rows, int64_t nrow
 vf_status vf_mesh_insolation(const vf_mesh* m, const double* sun_dirs, int32_t R, double solar_flux,
                              float* E, int64_t lde, vf_stream stream);
 
+/* Section 2: the Sun as a disk of finite extent, its flux a sum over point
+ * sources of the form of Eq. insolation-for-point-sun.  For each sun
+ * direction s_r (host, R x 3, unit), the disk of the given angular radius
+ * (radians, < 0.5; the Sun at 1 AU: 4.65e-3) around s_r is cut into
+ * `rings` rings of equal radial width, ring k (k = 0 the central disk) into
+ * max(1, 6k) equal sectors; each cell contributes one point source at its
+ * area-weighted mean radius and mid angle, weighted by its share of the
+ * disk's area (1 + 3 rings (rings - 1) sources, weights summing to 1):
+ * E[i + r*lde] = sum_k w_k solar_flux max(0, n_i . s_rk) V_sun(i, s_rk),
+ * each V_sun as in vf_mesh_insolation, the sum in FP64.  E: device FP32,
+ * column-major, face order.  Errors: VF_E_INVAL (rings outside [1, 64],
+ * radius outside [0, 0.5)), VF_E_NOMEM, VF_E_CUDA. */
+vf_status vf_mesh_insolation_disk(const vf_mesh* m, const double* sun_dirs, int32_t R, double solar_flux,
+                                  double angular_radius, int32_t rings, float* E, int64_t lde, vf_stream stream);
+
 /* ------------------------------------------------------------- partition
  * Algorithm 2 (quadtree on centroids, Section 4.1) and its octree analogue.
  * Each node splits at the midpoint of its own centroids' bounding box
@@ -373,6 +388,56 @@ vf_status vf_solve_batched(const vf_hmat* const* F, int32_t nmeshes, const float
                            const int32_t* R, const vf_solve_opts* opts, vf_solve_stats* stats,
                            vf_stream stream);
 
+/* ---------------------------------------------------------- thermal
+ * Section 5.1, equilibrium temperatures for R sun positions (columns of
+ * E = Q_direct): with W = diag(albedo) Q_vis,
+ *   W = diag(albedo) E + diag(albedo) F W      (Eq. time-indep-system-1, a
+ *   Q_vis = E + F W                             radiosity system, rho = albedo)
+ *   (I - F) Q_IR = F ((I - diag(albedo)) Q_vis + H)   (Eq. time-indep-system-2,
+ *                                                      rho = 1)
+ *   eps sigma T^4 = (1 - albedo) Q_vis + eps Q_IR      (Eq. 3d-equilbr, FP64,
+ *                                                      sigma = 5.670374419e-8)
+ * Q_vis = Q_direct + Q_refl.  Both solves are vf_solve calls (rtol,
+ * max_iter, precision, refine as there; the multiplies between them use the
+ * FP32 factors when refine = 1, else the sweeps' precision).  albedo,
+ * emissivity (device FP32 [N]) and H (interior heat flux, device [N]) may
+ * be NULL: the uniform opts values (H = 0) then apply.  E, Qvis, Qir, T:
+ * device FP32, column-major, face order (lde, ld); Qvis and Qir may be NULL
+ * (not returned).  stats: host, 2 entries (the Q_vis and Q_IR solves) or
+ * NULL.  Synchronous.  The IR system converges while F's spectral radius is
+ * below 1 (open surfaces).  Errors: VF_E_INVAL, VF_E_NOCONV (outputs still
+ * written), VF_E_NOMEM, VF_E_CUDA, VF_E_TIMEOUT. */
+typedef struct {
+    double rtol;       /* both solves, default 1e-6 */
+    int32_t max_iter;  /* per Jacobi loop, default 200 */
+    int32_t precision; /* vf_precision of the sweeps */
+    int32_t refine;    /* 1: mixed-precision refinement (BF16 / FP8 sweeps) */
+    float albedo;      /* uniform albedo (when albedo is NULL), in [0, 1) */
+    float emissivity;  /* uniform emissivity (when emissivity is NULL), in (0, 1] */
+} vf_equilibrium_opts;
+
+vf_status vf_equilibrium(const vf_hmat* h, const float* E, int64_t lde, int32_t R, const float* albedo,
+                         const float* emissivity, const float* H, const vf_equilibrium_opts* opts, float* Qvis,
+                         float* Qir, float* T, int64_t ld, vf_solve_stats* stats, vf_stream stream);
+
+/* Algorithm 6 (Section 5.2), one time step of the fluxes of R independent
+ * scenarios (columns):
+ *   Q_refl' = F diag(albedo) (Q_direct' + Q_refl)
+ *   Q_IR'   = F (Q_rad + (I - diag(emissivity)) Q_IR)
+ *   Q_abs'  = (I - diag(albedo)) (Q_direct' + Q_refl') + diag(emissivity) Q_IR'
+ * The two multiplies by F run as ONE multiply of 2R right-hand sides in
+ * precision p (vf_apply).  Edirect_next = Q_direct' and Qrad = eps sigma T^4
+ * of the current step are read; Qrefl and Qir are read (step n) and
+ * overwritten (step n + 1); Qabs is written.  The caller advances the
+ * subsurface model (or, with no heat storage, sets Q_rad' = Q_abs').
+ * albedo, emissivity: device FP32 [N] or NULL (then albedo_u,
+ * emissivity_u).  All blocks: device FP32, column-major, face order,
+ * leading dimension ld.  Asynchronous on `stream`.  Errors: VF_E_INVAL,
+ * VF_E_NOMEM, VF_E_CUDA. */
+vf_status vf_flux_step(const vf_hmat* h, vf_precision p, int32_t R, const float* albedo, const float* emissivity,
+                       float albedo_u, float emissivity_u, const float* Edirect_next, float* Qrefl, float* Qir,
+                       const float* Qrad, float* Qabs, int64_t ld, vf_stream stream);
+
 /* ------------------------------------------------------------ autotuning
  * What the multiply of one matrix runs with, per (precision, R): the
  * CUDA-core path's right-hand sides per pass (its RHS tile), whether BF16
@@ -415,10 +480,14 @@ vf_status vf_tune_set(const vf_hmat* h, vf_precision prec, int32_t R, const vf_t
 vf_status vf_hmat_stack(const vf_hmat* const* F, int32_t nmeshes, vf_hmat** out);
 
 /* Bytes of the tensor-core multiply's pages of h (the B operands: factors
- * in BF16, terms = 1, or split in hi and lo, terms = 2; padded to the MMA
- * shapes, CSR blocks dense), building them if not yet built; by_kind (5
- * entries or NULL): the bytes of dense, CSR, U', V' and empty-tile records
- * (headers and B operands); the total adds each page's 16-byte header.  No
+ * in BF16, terms = 1, or split in hi and lo, terms = 2), building them if
+ * not yet built.  A record's B operand is dense over the K rows it gathers
+ * (the nonzero columns of its dense and CSR pieces, the compacted columns
+ * of its V' blocks, the T slots of its U' blocks) and padded to the MMA
+ * shapes (K and the output rows to multiples of 16); each record also
+ * carries its K row list (4 bytes per row).  by_kind (5 entries or NULL):
+ * the bytes of dense, CSR, U', V' and empty-tile records (headers, row
+ * lists and B operands); the total adds each page's 16-byte header.  No
  * counterpart in the paper.  Errors: VF_E_INVAL (no BF16 copy), VF_E_NOMEM,
  * VF_E_CUDA. */
 vf_status vf_hmat_tensor_bytes(const vf_hmat* h, int32_t terms, int64_t* total, int64_t* by_kind);

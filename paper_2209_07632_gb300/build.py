@@ -12,7 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libvf.so")
-SOURCES = ["vf_mesh.cu", "vf_assemble.cu", "vf_apply.cu", "vf_io.cu", "vf_predictor.cu", "vf_tensor.cu"]
+SOURCES = ["vf_mesh.cu", "vf_assemble.cu", "vf_apply.cu", "vf_io.cu", "vf_predictor.cu", "vf_tensor.cu",
+           "vf_thermal.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

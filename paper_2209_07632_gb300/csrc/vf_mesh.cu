@@ -320,6 +320,64 @@ __global__ void k_insolation(const int32_t* __restrict__ c3, const long long* __
     E[i + (int64_t)r * lde] = e;
 }
 
+// Finite solar disk (Section 2: a sum over point sources): per (facet,
+// sun) the weighted sum of the point-sun insolation of the disk's M sample
+// directions dirs[r * M + k] with weights w[k], summed in FP64 in k order.
+__global__ void k_insolation_disk(const int32_t* __restrict__ c3, const long long* __restrict__ nint,
+                                  const double* __restrict__ nrm, const BvhNode* __restrict__ nodes,
+                                  const BvhTri* __restrict__ tris, int64_t nf, const double* __restrict__ dirs,
+                                  const long long* __restrict__ dq, const double* __restrict__ w, int M, int R,
+                                  double S, float* __restrict__ E, int64_t lde) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nf * (int64_t)R) return;
+    const int r = (int)(idx / nf);
+    const int i = (int)(idx - (int64_t)r * nf);
+    const P3 P{c3[3 * i], c3[3 * i + 1], c3[3 * i + 2]};
+    double e = 0.0;
+    for (int k = 0; k < M; ++k) {
+        const int64_t d = (int64_t)r * M + k;
+        const P3 D{dq[3 * d], dq[3 * d + 1], dq[3 * d + 2]};
+        const long long nd = nint[3 * i] * D.x + nint[3 * i + 1] * D.y + nint[3 * i + 2] * D.z;
+        if (nd <= 0 || bvh_blocked<1>(nodes, tris, P, D, i, -1)) continue;
+        const double c = nrm[3 * i] * dirs[3 * d] + nrm[3 * i + 1] * dirs[3 * d + 1] + nrm[3 * i + 2] * dirs[3 * d + 2];
+        e += w[k] * S * fmax(0.0, c);
+    }
+    E[i + (int64_t)r * lde] = (float)e;
+}
+
+// The disk's sample directions around the unit direction s: rings of equal
+// radial width (ring k split into max(1, 6k) equal sectors), each cell's
+// point at its area-weighted mean radius and mid angle, weight = its share
+// of the disk's area.
+static void disk_samples(const double* s_in, double radius, int rings, std::vector<double>& dirs,
+                         std::vector<double>& wts) {
+    double s[3] = {s_in[0], s_in[1], s_in[2]};
+    const double sn = std::sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+    for (double& x : s) x /= sn;
+    const double a[3] = {std::fabs(s[0]) < 0.9 ? 1.0 : 0.0, std::fabs(s[0]) < 0.9 ? 0.0 : 1.0, 0.0};
+    double u[3] = {s[1] * a[2] - s[2] * a[1], s[2] * a[0] - s[0] * a[2], s[0] * a[1] - s[1] * a[0]};
+    const double un = std::sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    for (double& x : u) x /= un;
+    const double v[3] = {s[1] * u[2] - s[2] * u[1], s[2] * u[0] - s[0] * u[2], s[0] * u[1] - s[1] * u[0]};
+    wts.clear();
+    for (int k = 0; k < rings; ++k) {
+        const double r0 = (double)k / rings, r1 = (double)(k + 1) / rings;
+        const int nsec = k == 0 ? 1 : 6 * k;
+        const double share = (r1 * r1 - r0 * r0) / nsec;
+        const double rc = k == 0 ? 0.0 : (2.0 / 3.0) * (r1 * r1 * r1 - r0 * r0 * r0) / (r1 * r1 - r0 * r0);
+        const double t = radius * rc;
+        for (int j = 0; j < nsec; ++j) {
+            const double phi = 2.0 * M_PI * (j + 0.5) / nsec;
+            double d[3];
+            for (int c = 0; c < 3; ++c)
+                d[c] = std::cos(t) * s[c] + std::sin(t) * (std::cos(phi) * u[c] + std::sin(phi) * v[c]);
+            const double dn = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            for (int c = 0; c < 3; ++c) dirs.push_back(d[c] / dn);
+            wts.push_back(share);
+        }
+    }
+}
+
 // ------------------------------------------------------------ BVH build
 // Median split on the longest axis of the centroid bounds, leaves <= 4
 // triangles; children allocated in adjacent slots.  Host code: integer
@@ -572,6 +630,35 @@ extern "C" vf_status vf_mesh_insolation(const vf_mesh* m, const double* sun_dirs
     VF_TRY_CUDA(cudaGetLastError());
     // the staging buffers are freed on return: order that after the kernel
     VF_TRY_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return VF_OK;
+}
+
+extern "C" vf_status vf_mesh_insolation_disk(const vf_mesh* m, const double* sun_dirs, int32_t R, double solar_flux,
+                                             double angular_radius, int32_t rings, float* E, int64_t lde,
+                                             vf_stream stream) {
+    clear_error();
+    VF_CHECK(m && sun_dirs && E, VF_E_INVAL, "vf_mesh_insolation_disk: null argument");
+    VF_CHECK(R >= 1 && lde >= m->nf, VF_E_INVAL, "vf_mesh_insolation_disk: need R >= 1 and lde >= nf");
+    VF_CHECK(rings >= 1 && rings <= 64 && angular_radius >= 0 && angular_radius < 0.5, VF_E_INVAL,
+             "vf_mesh_insolation_disk: need 1 <= rings <= 64 and 0 <= angular_radius < 0.5 rad");
+    device_guard g(m->device);
+    std::vector<double> dirs, w;
+    for (int32_t r = 0; r < R; ++r) disk_samples(sun_dirs + 3 * (size_t)r, angular_radius, rings, dirs, w);
+    const int M = (int)w.size();  // the same weights for every sun (disk_samples refills them per sun)
+    VF_CHECK((int64_t)dirs.size() == 3 * (int64_t)M * R, VF_E_INVAL, "vf_mesh_insolation_disk: sample count");
+    std::vector<long long> dq(dirs.size());
+    for (size_t k = 0; k < dirs.size(); ++k) dq[k] = std::llround(std::ldexp(dirs[k], 20));
+    dbuf<double> ddirs, dw;
+    dbuf<long long> ddq;
+    VF_TRY(ddirs.upload(dirs));
+    VF_TRY(ddq.upload(dq));
+    VF_TRY(dw.upload(w));
+    const int64_t tot = m->nf * (int64_t)R;
+    k_insolation_disk<<<(unsigned)ceil_div(tot, 128), 128, 0, (cudaStream_t)stream>>>(
+        m->c3.p, m->nint.p, m->nrm.p, m->bvh_nodes.p, m->bvh_tris.p, m->nf, ddirs.p, ddq.p, dw.p, M, R, solar_flux,
+        E, lde);
+    VF_TRY_CUDA(cudaGetLastError());
+    VF_TRY_CUDA(cudaStreamSynchronize((cudaStream_t)stream));  // the staging buffers are freed on return
     return VF_OK;
 }
 

@@ -93,6 +93,10 @@ _SIGS = {
     "vf_mesh_geometry": ([_P, _P, _P, _P], ctypes.c_int),
     "vf_mesh_visibility": ([_P, _P, _I64, _P], ctypes.c_int),
     "vf_mesh_insolation": ([_P, _P, _I32, ctypes.c_double, _P, _I64, _P], ctypes.c_int),
+    "vf_mesh_insolation_disk": ([_P, _P, _I32, ctypes.c_double, ctypes.c_double, _I32, _P, _I64, _P], ctypes.c_int),
+    "vf_equilibrium": ([_P, _P, _I64, _I32, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P], ctypes.c_int),
+    "vf_flux_step": ([_P, ctypes.c_int, _I32, _P, _P, ctypes.c_float, ctypes.c_float, _P, _P, _P, _P, _P, _I64, _P],
+                     ctypes.c_int),
     "vf_partition": ([_P, _P, _P], ctypes.c_int),
     "vf_tree_destroy": ([_P], None),
     "vf_tree_nnodes": ([_P], _I64),
@@ -288,6 +292,19 @@ def vf_mesh_insolation(m: Mesh, sun_dirs, solar_flux: float, E, stream=None):
     return E
 
 
+def vf_mesh_insolation_disk(m: Mesh, sun_dirs, solar_flux: float, angular_radius: float, rings: int, E,
+                            stream=None):
+    """E (R, N) for a finite solar disk of the given angular radius (radians) around each direction."""
+    d = np.ascontiguousarray(np.atleast_2d(sun_dirs), dtype=np.float64)
+    R = d.shape[0]
+    n = m.n
+    if E.shape != (R, n):
+        raise VFError(VF_E_INVAL, f"E must have shape (R, N) = {(R, n)}")
+    _check(load().vf_mesh_insolation_disk(m.ptr, _np_ptr(d), R, float(solar_flux), float(angular_radius),
+                                          int(rings), _dev_ptr(E, "E", n), n, _stream(stream)))
+    return E
+
+
 def vf_partition(m: Mesh, kind: str = "quad", leaf_size: int = 64, max_depth: int = 32) -> Tree:
     opts = PartitionOpts(0 if kind == "quad" else 1, leaf_size, max_depth)
     out = ctypes.c_void_p()
@@ -447,6 +464,55 @@ def vf_solve_batched(hs, Es, Bs, rho=0.12, rtol: float = 1e-6, max_iter: int = 1
     _check(load().vf_solve_batched(F, k, rho_arr, E, lde, B, lde, R, ctypes.byref(opts), st, _stream(stream)),
            allow=(VF_E_NOCONV,))
     return [s.as_dict() for s in st]
+
+
+class EquilibriumOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("refine", ctypes.c_int32), ("albedo", ctypes.c_float), ("emissivity", ctypes.c_float)]
+
+
+def _opt_vec(x, name, n):
+    """(device pointer or None, uniform value) for a scalar or an N-vector CUDA tensor."""
+    if isinstance(x, (int, float)):
+        return None, float(x)
+    return _dev_ptr(x, name, n), 0.0
+
+
+def vf_equilibrium(h: HMat, E, T, albedo=0.12, emissivity=0.95, H=None, Qvis=None, Qir=None, rtol: float = 1e-6,
+                   max_iter: int = 200, precision: str = "fp32", refine: bool = False, stream=None) -> list:
+    """Section 5.1 equilibrium temperatures T (R, N) for the direct fluxes E (R, N);
+    albedo / emissivity: floats or CUDA tensors of N values; H: None or N values.
+    Returns the statistics of the Q_vis and Q_IR solves."""
+    n = h.n
+    R = 1 if E.dim() == 1 else E.shape[0]
+    for nm, t in (("T", T), ("Qvis", Qvis), ("Qir", Qir)):
+        if t is not None and tuple(t.shape) != tuple(E.shape):
+            raise VFError(VF_E_INVAL, f"{nm} must have E's shape")
+    ap, au = _opt_vec(albedo, "albedo", n)
+    ep, eu = _opt_vec(emissivity, "emissivity", n)
+    hp = None if H is None else _dev_ptr(H, "H", n)
+    o = EquilibriumOpts(rtol, max_iter, PREC[precision], int(refine), au, eu)
+    st = (SolveStats * 2)()
+    _check(load().vf_equilibrium(h.ptr, _dev_ptr(E, "E", n), n, R, ap, ep, hp, ctypes.byref(o),
+                                 None if Qvis is None else _dev_ptr(Qvis, "Qvis", n),
+                                 None if Qir is None else _dev_ptr(Qir, "Qir", n), _dev_ptr(T, "T", n), n, st,
+                                 _stream(stream)), allow=(VF_E_NOCONV,))
+    return [x.as_dict() for x in st]
+
+
+def vf_flux_step(h: HMat, Edirect_next, Qrefl, Qir, Qrad, Qabs, albedo=0.12, emissivity=0.95,
+                 precision: str = "fp32", stream=None):
+    """Algorithm 6: one step of the fluxes (R, N) in place (Qrefl, Qir updated, Qabs written)."""
+    n = h.n
+    R = 1 if Edirect_next.dim() == 1 else Edirect_next.shape[0]
+    for nm, t in (("Qrefl", Qrefl), ("Qir", Qir), ("Qrad", Qrad), ("Qabs", Qabs)):
+        if tuple(t.shape) != tuple(Edirect_next.shape):
+            raise VFError(VF_E_INVAL, f"{nm} must have Edirect_next's shape")
+    ap, au = _opt_vec(albedo, "albedo", n)
+    ep, eu = _opt_vec(emissivity, "emissivity", n)
+    _check(load().vf_flux_step(h.ptr, PREC[precision], R, ap, ep, au, eu, _dev_ptr(Edirect_next, "Edirect_next", n),
+                               _dev_ptr(Qrefl, "Qrefl", n), _dev_ptr(Qir, "Qir", n), _dev_ptr(Qrad, "Qrad", n),
+                               _dev_ptr(Qabs, "Qabs", n), n, _stream(stream)))
 
 
 class Tune(ctypes.Structure):
