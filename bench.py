@@ -54,10 +54,11 @@ def parse():
     p.add_argument("--cpu-rows", type=int, default=128, help="rows of F in the CPU oracle sample")
     p.add_argument("--no-batched", action="store_true", help="skip the batched (tensor-core) section")
     p.add_argument("--batch-rhs", type=int, default=1440, help="RHS (sun positions) of the batched section")
-    p.add_argument("--multimesh", type=int, default=8, help="meshes of the multi-mesh section (0: skip)")
-    p.add_argument("--multimesh-max-side", type=int, default=100,
-                   help="largest DEM side of the multi-mesh section (50 -> 4,802 facets, 200 -> 79,202)")
-    p.add_argument("--multimesh-rhs", type=int, default=64, help="RHS per mesh in the multi-mesh section")
+    p.add_argument("--multimesh", type=int, default=32, help="meshes of the multi-mesh section (0: skip)")
+    p.add_argument("--multimesh-max-side", type=int, default=200,
+                   help="largest DEM side of the multi-mesh section (51 -> 5,000 facets, 200 -> 79,202)")
+    p.add_argument("--multimesh-rhs", type=int, default=256, help="RHS per mesh in the multi-mesh section")
+    p.add_argument("--no-tol-sweep", action="store_true", help="skip the terrain at tol 1e-2 and 1e-4")
     p.add_argument("--profile-batched", action="store_true",
                    help="only run --steps refined BF16 solves of --batch-rhs suns (for a profiler's launch list)")
     p.add_argument("--no-config4", action="store_true", help="skip the 522,242-facet precision section")
@@ -627,12 +628,16 @@ def main():
     if a.multimesh > 0 and rank == 0:
         import synth
         K = a.multimesh
-        sides = [int(round(50 + (a.multimesh_max_side - 50) * k / max(K - 1, 1))) for k in range(K)]
+        # the batching workload's meshes: sides 51 .. max side, seeds 100 + k,
+        # a crater of half the domain width on even seeds
+        specs = synth.batch_mesh_specs(count=K)
+        for sp_ in specs:
+            sp_["n"] = int(round(51 + (a.multimesh_max_side - 51) * (sp_["n"] - 51) / 149.0))
         mm0 = time.time()
         ps = []
-        for k, side in enumerate(sides):
-            mv, mf = synth.fbm_dem_mesh(n=side, spacing=10.0, hurst=0.8, seed=100 + k, rms_slope_deg=15.0,
-                                        crater_diameter=min(1000.0, 4.0 * side) if k % 2 == 0 else None)
+        for sp_ in specs:
+            mv, mf = synth.fbm_dem_mesh(n=sp_["n"], spacing=sp_["spacing"], hurst=sp_["hurst"], seed=sp_["seed"],
+                                        rms_slope_deg=15.0, crater_diameter=sp_["crater_diameter"])
             ps.append(vf.build_problem(mv, mf, kind="quad", leaf_size=64, tol=a.tol, device=dev,
                                        precisions=("fp32", "bf16")))
         t_mm_setup = time.time() - mm0
@@ -709,6 +714,34 @@ def main():
                  "bytes": vf.vf_hmat_bytes(hd, "fp32"), "sweeps": sd["sweeps"],
                  "compressed_vs_dense_rel_err": rel, "speedup_compressed": round(value / world / (R / (dms / 1e3)), 2)}
         del hd
+    # ---- the terrain at tol 1e-2 and 1e-4 (the headline is tol 1e-3): the
+    # same single-RHS FP32 solve, its multiply's roofline and its error
+    # against the uncompressed dense FP32 F's solve
+    tol_sweep = None
+    if not a.no_tol_sweep and rank == 0 and a.tol == 1e-3:
+        tol_sweep = {"1e-3": {"value": round(value / world, 3), "ms_per_step": round(ms, 4),
+                              "bytes_fp32": vf.vf_hmat_bytes(prob.hmat, "fp32"), "roofline_frac": roofline["frac"],
+                              "rel_err_vs_dense_fp32": dense["compressed_vs_dense_rel_err"] if dense else None}}
+        for tt in (1e-2, 1e-4):
+            t_a = time.time()
+            pt = vf.build_problem(v, f, kind="quad", leaf_size=64, tol=tt, device=dev, precisions=("fp32",))
+            t_a = time.time() - t_a
+            Bt_ = torch.empty_like(E)
+            for _ in range(3):
+                vf.vf_solve(pt.hmat, E, Bt_, rho=rho, rtol=rtol)
+            tms_ = events_ms(lambda: vf.vf_solve(pt.hmat, E, Bt_, rho=rho, rtol=rtol), max(20, a.steps), st)
+            Xt_ = E.clone()
+            Yt_ = torch.empty_like(Xt_)
+            for _ in range(3):
+                vf.vf_apply_tree(pt.hmat, Xt_, Yt_)
+            mms_ = events_ms(lambda: vf.vf_apply_tree(pt.hmat, Xt_, Yt_), 50, st)
+            ab_ = vf.vf_hmat_bytes(pt.hmat, "fp32") + n * R * 8
+            tol_sweep[f"{tt:.0e}"] = {
+                "value": round(R / (tms_ / 1e3), 3), "ms_per_step": round(tms_, 4), "assembly_s": round(t_a, 1),
+                "bytes_fp32": vf.vf_hmat_bytes(pt.hmat, "fp32"),
+                "roofline_frac": round(ab_ / (mms_ / 1e3) / 1e9 / peak, 4),
+                "rel_err_vs_dense_fp32": float(((Bt_ - Bd).norm() / Bd.norm()).item()) if dense else None}
+            del pt, Bt_, Xt_, Yt_
 
     # ---- the 522,242-facet precision workload (after the terrain's buffers are freed)
     setup_info = {"workload": WORKLOAD if a.dem_size == 200 else f"fbm{a.dem_size}_crater_{n}tri", "facets": n,
@@ -751,7 +784,8 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "setup_s": round(t_setup, 2)},
             "roofline": roofline, "e2e": e2e, "gpu_launches": kernels, "clocks": clk, "steady": steady,
-            "batched": batched, "multimesh": multimesh, "dense_fp32": dense, "config4": config4,
+            "batched": batched, "multimesh": multimesh, "dense_fp32": dense, "tol_sweep": tol_sweep,
+            "config4": config4,
             "cpu_baseline": cpu, "assembly": setup_info["assembly"]}
     if rank == 0:
         print(json.dumps(line))

@@ -173,8 +173,11 @@ vf_status vf_tree_nodes(const vf_tree* t, int32_t* first, int32_t* count, int32_
  * verify = 1 each accepted factorisation is checked against Algorithm 3's
  * criterion (Section 3): ||F_IJ - U'V'^T||_2 <= tol ||F_IJ||_2 (by
  * Eckart-Young the left side is sigma_{q+1}), both norms estimated by eight
- * FP64 power iterations on the GPU from one seeded start; a block that
- * fails goes back to the rank doubling (counted in verify_failed).
+ * FP64 power iterations on the GPU from one seeded start; since those
+ * estimates approach the norms from below, a factorisation passes only if
+ * the error's estimate is at most 0.9 tol times the norm's.  A block that
+ * fails goes back to the rank doubling (counted in verify_failed).  The
+ * check is on by default.
  * Errors: VF_E_INVAL, VF_E_NOMEM, VF_E_CUDA. */
 typedef struct {
     double tol;             /* compression tolerance, e.g. 1e-3 */
@@ -182,7 +185,8 @@ typedef struct {
     int32_t k0;             /* initial probe rank, default 8 */
     int32_t k_max;          /* largest probe rank, default 128 */
     int32_t power_iters;    /* subspace iterations of the probe, default 2 */
-    int32_t verify;         /* 1: FP64 truncation check on accepted SVD blocks (default 0) */
+    int32_t verify;         /* 1: FP64 truncation check on accepted SVD blocks (the default
+                               with opts = NULL and in the Python binding); 0: off */
     uint32_t precisions;    /* bit (1 << vf_precision): copies to build; FP32 always */
     const vf_rank_predictor* predictor; /* NULL: plain probe path */
     uint64_t seed;
@@ -200,6 +204,9 @@ typedef struct {
     int64_t probes_skipped; /* blocks where the byte bound ruled the SVD out */
     int64_t probes_predicted_skip; /* probes the predictor skipped */
     int64_t verify_failed;  /* SVD blocks whose check failed (rank raised) */
+    int64_t predictor_audits;      /* predicted skips probed anyway (one in 8) */
+    int64_t predictor_audit_wins;  /* audits whose probe stored an SVD */
+    int64_t predictor_fallbacks;   /* levels whose audits failed: their skips probed after all */
     int32_t max_rank;
     double t_visibility, t_stats, t_probe, t_pack, t_total; /* seconds */
 } vf_assemble_stats;
@@ -246,7 +253,11 @@ vf_status vf_hmat_probe_log(const vf_hmat* h, int64_t* n, float* feats, int32_t*
  * with probability >= 0.9 is not probed (counted in probes_predicted_skip);
  * any other prediction c sets its first probe rank to max(k0, 8 << c).  The
  * probe and the byte test still decide every block, so the matrix meets
- * the tolerance whatever the network predicts.
+ * the tolerance whatever the network predicts.  Skips are audited: one in
+ * eight predicted skips is probed anyway, and if at one level more than a
+ * quarter of the audits (and at least two) store an SVD -- the network is
+ * off the distribution it was trained on -- that level's skipped
+ * candidates are probed too (predictor_fallbacks).
  * Parameters (flat FP32, VF_PRED_NPARAM): W1 (64 x 10, row-major), b1 (64),
  * W2 (64 x 64), b2 (64), W3 (6 x 64), b3 (6); then the feature means and
  * scales (10 + 10) in vf_predictor_params.
@@ -481,15 +492,13 @@ vf_status vf_hmat_stack(const vf_hmat* const* F, int32_t nmeshes, vf_hmat** out)
 
 /* Bytes of the tensor-core multiply's pages of h (the B operands: factors
  * in BF16, terms = 1, or split in hi and lo, terms = 2), building them if
- * not yet built.  A record's B operand is dense over the K rows it gathers
- * (the nonzero columns of its dense and CSR pieces, the compacted columns
- * of its V' blocks, the T slots of its U' blocks) and padded to the MMA
- * shapes (K and the output rows to multiples of 16); each record also
- * carries its K row list (4 bytes per row).  by_kind (5 entries or NULL):
- * the bytes of dense, CSR, U', V' and empty-tile records (headers, row
- * lists and B operands); the total adds each page's 16-byte header.  No
- * counterpart in the paper.  Errors: VF_E_INVAL (no BF16 copy), VF_E_NOMEM,
- * VF_E_CUDA. */
+ * not yet built.  A record's B operand covers runs of 16-column chunks
+ * that hold a nonzero of one of its pieces (CSR pieces densified there)
+ * and is padded to the MMA shapes (K and the output rows to multiples of
+ * 16).  by_kind (5 entries or NULL): the bytes of dense, CSR, U', V' and
+ * empty-tile records (headers and B operands); the total adds each page's
+ * 16-byte header.  No counterpart in the paper.  Errors: VF_E_INVAL (no
+ * BF16 copy), VF_E_NOMEM, VF_E_CUDA. */
 vf_status vf_hmat_tensor_bytes(const vf_hmat* h, int32_t terms, int64_t* total, int64_t* by_kind);
 
 /* Release what multiplies and solves cached on h: its workspaces (per R

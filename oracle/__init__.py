@@ -275,6 +275,8 @@ class Block:
     rows_nz: np.ndarray | None = None
     cols_nz: np.ndarray | None = None
     sv: np.ndarray | None = None  # singular values of the block (probe)
+    nnz: int = 0                  # nonzero entries of the block
+    hier_bytes: int = -1          # bytes of the hierarchical candidate (non-leaf blocks), else -1
 
 
 def nbytes_dense(m: int, n: int) -> int:
@@ -341,7 +343,7 @@ def assemble(Ft: np.ndarray, tree: Tree, tol: float, leaf_threshold: int = 4096,
         leaf_block = (tree.is_leaf(I) and tree.is_leaf(J)) or m * n < leaf_threshold
         if leaf_block:
             b, kd = min(cand, key=lambda t: (t[0], t[1]))
-            return Block(I, J, kd, b)
+            return Block(I, J, kd, b, nnz=nnz)
         ch = [build(a, b) for a in kids(I) for b in kids(J)]
         hb = sum(c.nbytes for c in ch)
         Ac = A[np.ix_(rows_nz, cols_nz)]
@@ -358,17 +360,17 @@ def assemble(Ft: np.ndarray, tree: Tree, tol: float, leaf_threshold: int = 4096,
         if kd == HIER:
             nzk = [c.kind for c in ch if c.kind != ZERO]
             if nzk and all(k == CSR for k in nzk):
-                return Block(I, J, CSR, nbytes_csr(m, nnz))
+                return Block(I, J, CSR, nbytes_csr(m, nnz), sv=sv, nnz=nnz, hier_bytes=hb)
             if nzk and all(k == DENSE for k in nzk):
-                return Block(I, J, DENSE, nbytes_dense(m, n))
-            return Block(I, J, HIER, hb, children=ch, sv=sv)
+                return Block(I, J, DENSE, nbytes_dense(m, n), sv=sv, nnz=nnz, hier_bytes=hb)
+            return Block(I, J, HIER, hb, children=ch, sv=sv, nnz=nnz, hier_bytes=hb)
         if kd == SVD:
-            blk = Block(I, J, SVD, b, q=q, rows_nz=rows_nz, cols_nz=cols_nz, sv=sv)
+            blk = Block(I, J, SVD, b, q=q, rows_nz=rows_nz, cols_nz=cols_nz, sv=sv, nnz=nnz, hier_bytes=hb)
             if keep_factors:
                 blk.U = Uf[:, :q] * sv[:q]
                 blk.V = Vt[:q, :].T.copy()
             return blk
-        return Block(I, J, kd, b, sv=sv)
+        return Block(I, J, kd, b, sv=sv, nnz=nnz, hier_bytes=hb)
 
     root = 0
     if tree.is_leaf(root):

@@ -1090,9 +1090,12 @@ struct Workspace {
     bool cready = false;                  // the CUDA-core multiply's T and partial buffers are allocated
     cudaGraphExec_t graph = nullptr;
     cudaGraphConditionalHandle handle = 0;
+    cudaGraphExec_t tgraph = nullptr;  // the tensor-core Jacobi loop
+    cudaGraphConditionalHandle thandle = 0;
     cudaEvent_t done = nullptr;
     ~Workspace() {
         if (graph) cudaGraphExecDestroy(graph);
+        if (tgraph) cudaGraphExecDestroy(tgraph);
         if (done) cudaEventDestroy(done);
     }
 };
@@ -1442,12 +1445,85 @@ __global__ void __launch_bounds__(256) k_unconverged(const double* __restrict__ 
 
 // Jacobi on the tensor cores: B_0 = Et, B_{k+1} = Et + rho .* (F_bf16 B_k)
 // until every column's update is <= rtol ||Et|| or max_iter sweeps; the
-// result is in Bt[*par].  One host check per sweep.
+// result is in Bt[*par].  The sweep loop is one CUDA graph per workspace
+// (built on first use): a conditional while node whose body is one sweep
+// (the multiplies of every RHS panel, each writing B_{k+1} and the next
+// BF16 panel from its epilogue) and the column reduction that decides the
+// loop.  The ping-pong direction comes from the loop state's parity, which
+// the kernels read when they start, so one captured sweep serves both
+// directions.  The host synchronises once, after the loop.
+static vf_status ensure_tensor_graph(const vf_hmat* h, Workspace* w) {
+    if (w->tgraph) return VF_OK;
+    const int64_t n = h->nf;
+    const int64_t ntiles = tensor_parts(h, 1);
+    const int64_t bx = tensor_panel_bytes_x(h);
+    cudaGraph_t g;
+    VF_TRY_CUDA(cudaGraphCreate(&g, 0));
+    VF_TRY_CUDA(cudaGraphConditionalHandleCreate(&w->thandle, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = w->thandle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    VF_TRY_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t cs;
+    VF_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    VF_TRY_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    vf_status s = VF_OK;
+    const int* par = &w->loop.p->parity;
+    for (int p = 0, np; p < w->tpanels && s == VF_OK; p += np) {
+        np = p + 1 < w->tpanels ? 2 : 1;  // two RHS panels per multiply where there are two
+        TEpi ep{};
+        ep.mode = 1;
+        ep.n = n;
+        ep.R = w->R;
+        ep.p0 = p * kTensorPanel;
+        ep.E = w->Et.p;
+        ep.rho = w->rho_t.p;
+        ep.xstride = bx;
+        ep.colpart = w->colpart.p;
+        ep.ntiles = ntiles;
+        // parity 0: B_k in Bt[0] and xpan[0]; parity 1: in Bt[1] and xpan[1]
+        ep.Y = w->Bt[1].p;
+        ep.Bold = w->Bt[0].p;
+        ep.Xnext = w->xpan[1].p + (size_t)p * bx;
+        ep.par = par;
+        ep.Xalt = w->xpan[1].p + (size_t)p * bx;
+        ep.Yalt = w->Bt[0].p;
+        ep.Boldalt = w->Bt[1].p;
+        ep.Xnextalt = w->xpan[0].p + (size_t)p * bx;
+        s = tensor_multiply(h, 1, np, w->xpan[0].p + (size_t)p * bx, nullptr, w->tpan.p, nullptr, ep, w->status.p,
+                            cs);
+    }
+    k_sweep_reduce<<<1, 1024, 0, cs>>>(w->colpart.p, ntiles, w->R, h->nseg(), tensor_seg_parts(h, 1), w->enorm2.p,
+                                       w->colres.p, w->loop.p, w->bufs.p, w->xsel.p, w->ysel.p, w->thandle, 1);
+    cudaError_t e1 = cudaGetLastError();
+    cudaGraph_t outg;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &outg);
+    cudaStreamDestroy(cs);
+    if (s != VF_OK) { cudaGraphDestroy(g); return s; }
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        cudaGraphDestroy(g);
+        set_error("tensor graph capture failed: %s / %s", cudaGetErrorString(e1), cudaGetErrorString(e2));
+        return VF_E_CUDA;
+    }
+    cudaError_t e3 = cudaGraphInstantiate(&w->tgraph, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) {
+        set_error("tensor graph instantiate failed: %s", cudaGetErrorString(e3));
+        w->tgraph = nullptr;
+        return VF_E_CUDA;
+    }
+    return VF_OK;
+}
+
 static vf_status tensor_jacobi_loop(const vf_hmat* h, Workspace* w, int max_iter, double rtol, cudaStream_t st,
                                     int* iters, int* par, int* kernels) {
     VF_TRY(tensor_ws(h, w));
+    VF_TRY(ensure_tensor_graph(h, w));
     const int64_t n = h->nf, nR = n * (int64_t)w->R;
-    const int64_t ntiles = tensor_parts(h, 1);
     const int64_t bx = tensor_panel_bytes_x(h);
     const int NV = w->R * h->nseg();
     VF_TRY_CUDA(cudaMemcpyAsync(w->Bt[0].p, w->Et.p, nR * 4, cudaMemcpyDeviceToDevice, st));
@@ -1455,42 +1531,21 @@ static vf_status tensor_jacobi_loop(const vf_hmat* h, Workspace* w, int max_iter
     for (int p = 0; p < w->tpanels; ++p)
         VF_TRY(tensor_to_panel(h, w->Et.p, n, nullptr, w->R, p * kTensorPanel, w->xpan[0].p + (size_t)p * bx, nullptr,
                                st));
-    *kernels += 1 + w->tpanels;
-    int it = 0, cur = 0;
-    while (it < max_iter) {
-        for (int p = 0, np; p < w->tpanels; p += np) {
-            np = p + 1 < w->tpanels ? 2 : 1;  // two RHS panels per multiply where there are two
-            TEpi ep{};
-            ep.mode = 1;
-            ep.n = n;
-            ep.R = w->R;
-            ep.p0 = p * kTensorPanel;
-            ep.Y = w->Bt[cur ^ 1].p;
-            ep.E = w->Et.p;
-            ep.rho = w->rho_t.p;
-            ep.Bold = w->Bt[cur].p;
-            ep.Xnext = w->xpan[cur ^ 1].p + (size_t)p * bx;
-            ep.xstride = bx;
-            ep.colpart = w->colpart.p;
-            ep.ntiles = ntiles;
-            VF_TRY(tensor_multiply(h, 1, np, w->xpan[cur].p + (size_t)p * bx, nullptr, w->tpan.p, nullptr, ep,
-                                   w->status.p, st));
-            *kernels += tensor_kernels(h, 1);
-        }
-        k_unconverged<<<(unsigned)NV, 256, 0, st>>>(w->colpart.p, ntiles, w->R, h->nseg(), tensor_seg_parts(h, 1),
-                                                    w->enorm2.p, rtol * rtol, w->colres.p, w->tcount.p,
-                                                    w->tcount.p + 1);
-        VF_TRY_CUDA(cudaGetLastError());
-        *kernels += 1;
-        int hc = 0;
-        VF_TRY_CUDA(cudaMemcpyAsync(&hc, w->tcount.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-        VF_TRY_CUDA(cudaStreamSynchronize(st));
-        cur ^= 1;
-        ++it;
-        if (hc == 0) break;
+    k_loop_init<<<1, 1, 0, st>>>(w->loop.p, max_iter, rtol * rtol, w->bufs.p, w->xsel.p, w->ysel.p);
+    VF_TRY_CUDA(cudaGetLastError());
+    *kernels += 2 + w->tpanels;
+    if (max_iter > 0) VF_TRY_CUDA(cudaGraphLaunch(w->tgraph, st));
+    LoopState ls{};
+    VF_TRY_CUDA(cudaMemcpyAsync(&ls, w->loop.p, sizeof(ls), cudaMemcpyDeviceToHost, st));
+    VF_TRY_CUDA(cudaStreamSynchronize(st));
+    int per_sweep = 1;  // the column reduction
+    for (int p = 0, np; p < w->tpanels; p += np) {
+        np = p + 1 < w->tpanels ? 2 : 1;
+        per_sweep += tensor_kernels(h, 1);
     }
-    *iters = it;
-    *par = cur;
+    *kernels += ls.iter * per_sweep;
+    *iters = ls.iter;
+    *par = ls.parity;
     return VF_OK;
 }
 

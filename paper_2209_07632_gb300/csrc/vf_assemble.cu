@@ -18,6 +18,11 @@ namespace vf {
 
 constexpr float kPi = 3.14159265358979323846f;
 constexpr int kMaxEll = 160;   // largest probe subspace (shared-memory Jacobi)
+// Rank-predictor audits: one in kAuditEvery predicted skips is probed
+// anyway; if more than one in kAuditMaxWinInv of a level's audits (and at
+// least two) would have stored an SVD, that level's skips are probed too.
+constexpr int64_t kAuditEvery = 8;
+constexpr int64_t kAuditMaxWinInv = 4;
 
 // ------------------------------------------------------------ geometry
 struct Geo {
@@ -380,6 +385,11 @@ __global__ void k_form_factors(const ProbeDesc* __restrict__ pd, const FactorDes
 // evaluates them), and accepts iff the first <= tol x the second.  A
 // failed check sends the block back to Algorithm 3's rank doubling.
 constexpr int kVerifyIters = 8;
+// Power iteration approaches both norms from below; the error's estimate
+// must clear tol x ||A|| by this factor, which covers its shortfall.
+constexpr double kVerifyMargin = 0.9;
+// ranks a candidate may add, one at a time, after a failed check
+constexpr int kVerifyRaise = 4;
 
 struct VerDesc {
     int32_t probe, q;
@@ -930,7 +940,7 @@ static vf_status verify_factors(const Geo& g, const ProbeBatch& B, const std::ve
     for (size_t f = 0; f < nv; ++f) {
         est[2 * f] = std::sqrt(est[2 * f]);  // sigma_max(E), sigma_max(A)
         est[2 * f + 1] = std::sqrt(est[2 * f + 1]);
-        ok[f] = est[2 * f] <= tol * est[2 * f + 1] ? 1 : 0;
+        ok[f] = est[2 * f] <= kVerifyMargin * tol * est[2 * f + 1] ? 1 : 0;
     }
     return VF_OK;
 }
@@ -952,7 +962,7 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
     o.k0 = 8;
     o.k_max = 128;
     o.power_iters = 2;
-    o.verify = 0;
+    o.verify = 1;
     o.precisions = (1u << VF_PREC_FP32) | (1u << VF_PREC_BF16);
     o.seed = 12345;
     o.storage = 0;
@@ -1189,6 +1199,8 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
             // the candidates' features; the predictor (if any) picks each
             // first probe rank or skips the probe
             const size_t log0 = log_ids.size();
+            std::vector<int32_t> audit, skipped;
+            std::vector<float> skipped_feat;
             {
                 std::vector<float> fl(pending.size() * VF_PRED_NFEAT);
                 for (size_t i = 0; i < pending.size(); ++i) features(N[pending[i]], &fl[i * VF_PRED_NFEAT]);
@@ -1198,11 +1210,20 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
                     std::vector<float> prob;
                     VF_TRY(predictor_classify(o.predictor, fl, (int64_t)pending.size(), cls, prob));
                     std::vector<float> fk;
+                    int64_t nskip = 0;
                     for (size_t i = 0; i < pending.size(); ++i) {
                         DNode& d = N[pending[i]];
                         if (cls[i] == VF_PRED_NCLASS - 1 && prob[i * VF_PRED_NCLASS + cls[i]] >= 0.9f) {
-                            S.probes_predicted_skip++;
-                            continue;
+                            // every kAuditEvery-th predicted skip is probed anyway (an audit)
+                            if (nskip++ % kAuditEvery == 0) {
+                                audit.push_back(pending[i]);
+                            } else {
+                                S.probes_predicted_skip++;
+                                skipped.push_back(pending[i]);
+                                skipped_feat.insert(skipped_feat.end(), fl.begin() + i * VF_PRED_NFEAT,
+                                                    fl.begin() + (i + 1) * VF_PRED_NFEAT);
+                                continue;
+                            }
                         }
                         if (cls[i] < VF_PRED_NCLASS - 1) d.k = std::min(std::max(o.k0, 8 << cls[i]), o.k_max);
                         keep.push_back(pending[i]);
@@ -1215,6 +1236,7 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
                 H->h_probe_feat.insert(H->h_probe_feat.end(), fl.begin(), fl.end());
             }
             // probe rounds (k doubling, Algorithm 3)
+            auto probe_rounds = [&](std::vector<int32_t>& pending) -> vf_status {
             while (!pending.empty()) {
                 ProbeBatch B;
                 std::vector<int32_t> who;
@@ -1248,12 +1270,14 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
                 std::vector<FactorDesc> fds;
                 std::vector<int32_t> sel;
                 std::vector<int32_t> fd_owner;
+                std::vector<std::vector<int32_t>> orders(who.size());  // per probe: columns by singular value
                 int64_t fstage = 0;
                 for (size_t pi = 0; pi < who.size(); ++pi) {
                     DNode& d = N[who[pi]];
                     const ProbeDesc& p = B.pd[pi];
                     const float* sig = hsmall.data() + p.s_off + 2 * (int64_t)p.ell * p.ell;
-                    std::vector<int32_t> order(p.ell);
+                    std::vector<int32_t>& order = orders[pi];
+                    order.resize(p.ell);
                     std::iota(order.begin(), order.end(), 0);
                     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sig[a] > sig[b]; });
                     float s1 = sig[order[0]];
@@ -1291,7 +1315,14 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
                     fds.push_back(f);
                     fd_owner.push_back(who[pi]);
                 }
-                if (!fds.empty()) {
+                // Form the accepted factorisations and check them.  A check can
+                // fail when sigma_{q+1} sits just below tol sigma_1: the
+                // randomized factors carry a little more than the optimal
+                // truncation error.  Such a candidate retries with one more
+                // rank from the same probe (up to kVerifyRaise times, while
+                // the SVD still wins on bytes) before it goes back to the rank
+                // doubling.
+                for (int attempt = 0; !fds.empty(); ++attempt) {
                     auto buf = std::make_unique<dbuf<float>>();
                     VF_TRY(buf->alloc(fstage));
                     dbuf<FactorDesc> dfd;
@@ -1304,16 +1335,35 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
                     std::vector<uint8_t> ver_ok(fds.size(), 1);
                     if (o.verify) {
                         std::vector<double> ver_est;
-                        VF_TRY(verify_factors(g, B, fds, buf->p, o.tol, o.seed ^ (uint64_t)h, ver_ok, ver_est, st));
+                        VF_TRY(verify_factors(g, B, fds, buf->p, o.tol, o.seed ^ (uint64_t)h ^ ((uint64_t)attempt << 32),
+                                              ver_ok, ver_est, st));
                     }
                     int32_t bi = (int32_t)stage_bufs.size();
+                    std::vector<FactorDesc> fds2;
+                    std::vector<int32_t> sel2, owner2;
+                    int64_t fstage2 = 0;
                     for (size_t f = 0; f < fds.size(); ++f) {
                         int32_t id = fd_owner[f];
                         if (!ver_ok[f]) {
-                            // the check failed: back to the rank doubling
                             DNode& d = N[id];
                             const ProbeDesc& p = B.pd[fds[f].probe];
                             S.verify_failed++;
+                            const int32_t q1 = fds[f].q + 1;
+                            if (attempt < kVerifyRaise && q1 <= p.ell && q1 <= o.k_max &&
+                                svd_bytes(q1, d.st.m1, d.st.n1) < d.best_alt) {
+                                // one more rank from the same probe
+                                FactorDesc g2 = fds[f];
+                                g2.q = q1;
+                                g2.sel_off = (int64_t)sel2.size();
+                                for (int32_t k = 0; k < q1; ++k) sel2.push_back(orders[fds[f].probe][k]);
+                                g2.u_off = fstage2;
+                                fstage2 += (int64_t)(p.m1 + p.n1) * q1;
+                                fds2.push_back(g2);
+                                owner2.push_back(id);
+                                d.q = q1;
+                                continue;
+                            }
+                            // back to the rank doubling
                             d.q = 0;
                             const bool full = p.ell == std::min(p.m1, p.n1);
                             if (!full && 2 * d.k <= o.k_max && svd_bytes(d.k, d.st.m1, d.st.n1) < d.best_alt) {
@@ -1334,8 +1384,32 @@ extern "C" vf_status vf_assemble(const vf_mesh* m, const vf_tree* t, const vf_as
                                           B.lists.begin() + p.cols_off + p.n1);
                     }
                     stage_bufs.push_back(std::move(buf));
+                    fds.swap(fds2);
+                    sel.swap(sel2);
+                    fd_owner.swap(owner2);
+                    fstage = fstage2;
                 }
                 pending.swap(next);
+            }
+            return VF_OK;
+            };
+            VF_TRY(probe_rounds(pending));
+            // The audits: if the probes of audited skips won too often, the
+            // predictor is off its training distribution at this level, and
+            // the skipped candidates are probed after all.
+            if (!audit.empty()) {
+                int64_t wins = 0;
+                for (int32_t id : audit) wins += (N[id].q > 0 && stage_ref[id].buf >= 0) ? 1 : 0;
+                S.predictor_audits += (int64_t)audit.size();
+                S.predictor_audit_wins += wins;
+                if (wins >= 2 && wins * kAuditMaxWinInv > (int64_t)audit.size() && !skipped.empty()) {
+                    S.predictor_fallbacks++;
+                    S.probes_predicted_skip -= (int64_t)skipped.size();
+                    for (int32_t id : skipped) N[id].k = std::min(o.k0, o.k_max);
+                    log_ids.insert(log_ids.end(), skipped.begin(), skipped.end());
+                    H->h_probe_feat.insert(H->h_probe_feat.end(), skipped_feat.begin(), skipped_feat.end());
+                    VF_TRY(probe_rounds(skipped));
+                }
             }
             // the probe log's labels: the rank bin of an accepted SVD, else "no SVD"
             for (size_t i = log0; i < log_ids.size(); ++i) {

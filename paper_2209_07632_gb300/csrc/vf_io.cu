@@ -47,7 +47,7 @@ struct FileHeader {
     vf_assemble_stats stats;
 };
 
-static const uint32_t kVersion = 1;
+static const uint32_t kVersion = 2;  // 2: assembly statistics with the predictor audits
 
 static bool write_section(FILE* f, const void* p, uint64_t bytes) {
     uint32_t c = crc32(p, bytes);
@@ -280,6 +280,9 @@ extern "C" vf_status vf_hmat_stack(const vf_hmat* const* F, int32_t nmeshes, vf_
         S.probes_failed += f->stats.probes_failed;
         S.probes_skipped += f->stats.probes_skipped;
         S.probes_predicted_skip += f->stats.probes_predicted_skip;
+        S.predictor_audits += f->stats.predictor_audits;
+        S.predictor_audit_wins += f->stats.predictor_audit_wins;
+        S.predictor_fallbacks += f->stats.predictor_fallbacks;
         S.verify_failed += f->stats.verify_failed;
         S.max_rank = std::max(S.max_rank, f->stats.max_rank);
         nf += f->nf;

@@ -805,7 +805,21 @@ struct TPanels {
     unsigned char* T[2];
     int64_t rows_x, rows_t;
     int64_t xstride, tstride;
+    const int* par;            // ping-pong selection (see TEpi): X[0] = Xalt when *par == 1
+    const unsigned char* Xalt;
 };
+
+// Apply the ping-pong selection of a graph-captured sweep (every thread, at kernel start).
+__device__ __forceinline__ void t_select(TPanels& pn) {
+    if (pn.par && *pn.par) pn.X[0] = pn.Xalt;
+}
+__device__ __forceinline__ void t_select(TEpi& ep) {
+    if (ep.par && *ep.par) {
+        ep.Y = ep.Yalt;
+        ep.Bold = ep.Boldalt;
+        ep.Xnext = ep.Xnextalt;
+    }
+}
 
 // Copy page `next` of the CTA's list into its stage once the page that
 // stage held before has been consumed (its MMAs completed): with block, a
@@ -1066,6 +1080,7 @@ __global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase1(const unsig
                                                         const int32_t* __restrict__ cta_unit_ptr, TPanels pn,
                                                         int* __restrict__ status) {
     constexpr int NREG = TCfg<NS, NP>::NREG, REGW = NP * kRegion;
+    t_select(pn);
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* stages = smem;
     unsigned char* abuf = smem + TCfg<NS, NP>::PSTAGES * kTP;
@@ -1137,6 +1152,8 @@ __global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase2(const unsig
                                                         const int32_t* __restrict__ tile_count, TPanels pn, TEpi ep,
                                                         int* __restrict__ status) {
     constexpr int NREG = TCfg<NS, NP>::NREG, REGW = NP * kRegion;
+    t_select(pn);
+    t_select(ep);
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* stages = smem;
     unsigned char* abuf = smem + TCfg<NS, NP>::PSTAGES * kTP;
@@ -1295,6 +1312,8 @@ vf_status tensor_multiply(const vf_hmat* H, int S, int np, const unsigned char* 
     pn.rows_t = P->n_rows_t;
     pn.xstride = tensor_panel_bytes_x(H);
     pn.tstride = tensor_panel_bytes_t(H);
+    pn.par = ep.par;
+    pn.Xalt = ep.Xalt;
     if (S == 2 && np == 2) tensor_launch<2, 2>(T, pn, ep, status, st);
     else if (S == 2) tensor_launch<2, 1>(T, pn, ep, status, st);
     else if (np == 2) tensor_launch<1, 2>(T, pn, ep, status, st);

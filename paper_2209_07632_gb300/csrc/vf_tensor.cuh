@@ -22,6 +22,15 @@ struct TEpi {
     int64_t xstride;
     double* colpart;       // modes 1, 2: per (RHS, tile) sums of squares
     int64_t ntiles;
+    // Ping-pong selection for a sweep captured once in a CUDA graph: when
+    // par is not NULL and *par (read when the kernel starts) is 1, the
+    // kernels use Xalt (the input panel), Yalt, Boldalt and Xnextalt
+    // instead of the input panel, Y, Bold and Xnext.
+    const int* par;
+    const unsigned char* Xalt;
+    float* Yalt;
+    const float* Boldalt;
+    unsigned char* Xnextalt;
 };
 
 // Build one page set of the matrix once (S = 1: BF16 factors; S = 2: each

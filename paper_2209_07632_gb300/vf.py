@@ -51,6 +51,8 @@ class AssembleStats(ctypes.Structure):
     _fields_ = [("nblocks", ctypes.c_int64 * 5), ("bytes", ctypes.c_int64 * 5), ("nnz_visible", ctypes.c_int64),
                 ("probes", ctypes.c_int64), ("probes_failed", ctypes.c_int64), ("probes_skipped", ctypes.c_int64),
                 ("probes_predicted_skip", ctypes.c_int64), ("verify_failed", ctypes.c_int64),
+                ("predictor_audits", ctypes.c_int64), ("predictor_audit_wins", ctypes.c_int64),
+                ("predictor_fallbacks", ctypes.c_int64),
                 ("max_rank", ctypes.c_int32), ("t_visibility", ctypes.c_double), ("t_stats", ctypes.c_double),
                 ("t_probe", ctypes.c_double), ("t_pack", ctypes.c_double), ("t_total", ctypes.c_double)]
 
@@ -331,7 +333,7 @@ STORAGE = {"compressed": 0, "dense": 1, "csr": 2}
 
 
 def vf_assemble(m: Mesh, t: Tree, tol: float = 1e-3, leaf_threshold: int = 4096, k0: int = 8, k_max: int = 128,
-                power_iters: int = 2, verify: bool = False, precisions=("fp32", "bf16"), predictor=None,
+                power_iters: int = 2, verify: bool = True, precisions=("fp32", "bf16"), predictor=None,
                 seed: int = 12345, storage: str = "compressed"):
     bits = 0
     for p in precisions:

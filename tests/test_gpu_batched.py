@@ -20,12 +20,60 @@ def vf():
     return _vf
 
 
+MESHES = [(lambda: synth.cap_bowl_mesh(), "quad"),
+          (lambda: synth.fbm_dem_mesh(n=30, seed=3, crater_diameter=120.0), "quad"),
+          (lambda: synth.fbm_dem_mesh(n=44, seed=5), "quad"),
+          (lambda: synth.gaussian_sphere_mesh(level=3, sigma=0.3, seed=4), "oct")]
+
+
 @pytest.fixture(scope="module")
-def probs(vf):
-    meshes = [synth.cap_bowl_mesh(), synth.fbm_dem_mesh(n=30, seed=3, crater_diameter=120.0),
-              synth.fbm_dem_mesh(n=44, seed=5), synth.gaussian_sphere_mesh(level=3, sigma=0.3, seed=4)]
-    kinds = ["quad", "quad", "quad", "oct"]
-    return [vf.build_problem(v, f, kind=k, tol=1e-3, precisions=("fp32", "bf16")) for (v, f), k in zip(meshes, kinds)]
+def meshes():
+    return [(mk(), kind) for mk, kind in MESHES]
+
+
+@pytest.fixture(scope="module")
+def probs(vf, meshes):
+    return [vf.build_problem(v, f, kind=k, tol=1e-3, precisions=("fp32", "bf16")) for (v, f), k in meshes]
+
+
+@pytest.fixture(scope="module")
+def oracle_F(meshes):
+    """Each mesh's dense FP64 F (Eq. FF-def, the oracle's own visibility)."""
+    import oracle
+    out = []
+    for (v, f), _ in meshes:
+        om = oracle.mesh(v, f)
+        out.append((om, oracle.F_rows(om, np.arange(om.n))))
+    return out
+
+
+@pytest.mark.parametrize("prec,R", [("fp32", 3), ("bf16", 128)])
+def test_batched_solve_against_the_oracle(vf, probs, oracle_F, prec, R):
+    """One vf_solve_batched over the stack of all meshes against the oracle's
+    per-mesh FP64 Jacobi solution of the uncompressed system: within the
+    compression error (2 tol) for every mesh and column."""
+    import oracle
+    import torch
+    Es, Bs, dirs = [], [], []
+    for k, p in enumerate(probs):
+        d = synth.sun_directions(R, 9.0 + 3 * k)
+        E = torch.empty((R, p.mesh.n), device="cuda")
+        vf.vf_mesh_insolation(p.mesh, d, 1365.0, E)
+        Es.append(E)
+        Bs.append(torch.empty_like(E))
+        dirs.append(d)
+    kw = dict(rho=0.12, rtol=1e-7)
+    if prec != "fp32":
+        kw.update(precision=prec, refine=True)
+    stats = vf.vf_solve_batched([p.hmat for p in probs], Es, Bs, **kw)
+    for (om, F), B, d, st in zip(oracle_F, Bs, dirs, stats):
+        assert st["converged"] == 1
+        Bo, _, _ = oracle.jacobi(lambda X: F @ X, oracle.insolation(om, d, 1365.0), 0.12, rtol=1e-12)
+        nb = np.linalg.norm(Bo, axis=0)
+        live = nb > 0
+        assert live.sum() >= R // 2
+        err = np.linalg.norm(B.double().cpu().numpy().T - Bo, axis=0)[live] / nb[live]
+        assert np.all(err <= 2e-3), (om.n, err.max())
 
 
 def _rel(a, b):

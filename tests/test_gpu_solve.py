@@ -7,8 +7,8 @@ Tolerances:
   fraction is bounded and every GPU block meets its own invariant;
 * dense / CSR entries: the same sparsity pattern, values to FP32 evaluation
   error (1e-6 of A_j / (pi r^2) plus 2e-6 relative);
-* SVD blocks: ||F_hat_IJ - F_IJ||_2 <= tol sigma_1(F_IJ) (5% slack for
-  FP32 entries and the probe);
+* SVD blocks: ||F_hat_IJ - F_IJ||_2 <= tol sigma_1(F_IJ) (the default
+  assembly checks each factorisation in FP64);
 * multiply and solve in FP32: relative error per column <= 2 tol;
 * BF16/FP8 sweeps with FP64-residual refinement: within 1e-5 of the FP32
   solve on the same compressed F, hence within 2 tol of the oracle.
@@ -65,16 +65,98 @@ def case(request, vf):
     return dict(name=request.param, v=v, f=f, om=om, F=F, tree=tree, Ft=Ft, top=top, prob=prob, Fh=Fh, tol=tol)
 
 
+def _gpu_decision(gpu, anc, I, J):
+    """What the GPU stored for the oracle node (I, J): ('stored', kind, q),
+    'above' (a stored GPU block covers a strictly larger pair), 'HIER' (GPU
+    blocks strictly inside) or 'ZERO' (nothing stored there)."""
+    if (I, J) in gpu:
+        return ("stored",) + gpu[(I, J)]
+    for a in anc[I]:
+        for b in anc[J]:
+            if (a, b) != (I, J) and (a, b) in gpu:
+                return "above"
+    return "INSIDE"
+
+
+def _near_tie(b, g, Ft, tree, tol, k_max=128, band=1.5, slack=0.02):
+    """A divergence at oracle node b is a near-tie when the GPU's choice is
+    one of the choices Algorithms 3-4 make under a perturbed rank rule
+    (tol / band .. tol * band, the GPU probe's FP32 randomized spectrum
+    against exact FP64 singular values; an SVD may carry up to 4 more ranks,
+    added by the FP64 check of assembly) and byte costs within `slack`."""
+    if b.sv is None or b.hier_bytes < 0:
+        return False, "leaf block: dense / CSR costs are exact integers"
+    r0, m = tree.first[b.I], tree.count[b.I]
+    c0, n = tree.first[b.J], tree.count[b.J]
+    A = Ft[r0:r0 + m, c0:c0 + n] != 0
+    m1, n1 = int(A.any(1).sum()), int(A.any(0).sum())
+    qs = sorted({oracle.numerical_rank(b.sv, tol * f) for f in (1 / band, 1.0, band)})
+    cost = {oracle.DENSE: oracle.nbytes_dense(m, n), oracle.CSR: oracle.nbytes_csr(m, b.nnz),
+            oracle.HIER: b.hier_bytes}
+    svd = [oracle.nbytes_svd(q, m1, n1) for q in qs if q <= k_max]
+    best = min(list(cost.values()) + svd)
+    if g[0] == "stored":
+        kind, q = g[1], g[2]
+        if kind == oracle.SVD:
+            # the FP64 check may add up to 4 ranks to a factorisation that
+            # sits at the threshold; the SVD must still beat the other kinds
+            other = min(cost.values())
+            ok = qs[0] <= q <= qs[-1] + 4 and oracle.nbytes_svd(q, m1, n1) <= (1 + slack) * other
+            return ok, f"GPU SVD q={q}, oracle ranks {qs} in the band, kind {b.kind} q={b.q}"
+        ok = cost[kind] <= (1 + slack) * best
+        return ok, f"GPU kind {kind} ({cost[kind]} B) vs best {best} B in the band (oracle kind {b.kind} q={b.q})"
+    ok = cost[oracle.HIER] <= (1 + slack) * best
+    return ok, f"GPU hierarchical ({cost[oracle.HIER]} B) vs best {best} B (oracle kind {b.kind} q={b.q})"
+
+
 def test_block_structure_matches_oracle(vf, case):
+    """The stored blocks equal the oracle's Algorithm 4 except where the two
+    diverge at a near-tie of the rank rule or the byte comparison (reading
+    R11: the GPU probe's randomized FP32 spectrum against exact FP64 SVDs);
+    every divergence is listed and checked to be such a near-tie."""
+    tree = case["tree"]
     desc = vf.vf_hmat_blocks(case["prob"].hmat)
     gpu = {(int(d[0]), int(d[1])): (int(d[2]), int(d[3])) for d in desc}
-    ora = {(b.I, b.J): (b.kind, b.q) for b in oracle.leaf_blocks(case["top"]) if b.kind != oracle.ZERO}
-    same = sum(1 for k, v in ora.items() if gpu.get(k) == v)
-    frac = same / max(len(ora), 1)
-    # near-ties of the rank rule can flip a block's representation
-    assert frac >= 0.9, f"{case['name']}: only {frac:.3f} of blocks identical"
+    anc = []
+    for k in range(len(tree.count)):
+        a, x = [], k
+        while x >= 0:
+            a.append(x)
+            x = int(tree.parent[x])
+        anc.append(a)
+    div = []
+
+    def walk(b):
+        g = _gpu_decision(gpu, anc, b.I, b.J)
+        if g == "above":
+            return
+        if g == "INSIDE":
+            if b.kind == oracle.HIER:
+                for c in b.children:
+                    walk(c)
+                return
+            if b.kind == oracle.ZERO:
+                return
+            g = ("hier",)
+        elif (b.kind, b.q if b.kind == oracle.SVD else 0) == (g[1], g[2] if g[1] == oracle.SVD else 0):
+            return
+        div.append((b, g))
+
+    for b in case["top"]:
+        walk(b)
+    nstored = sum(1 for b in oracle.leaf_blocks(case["top"]) if b.kind != oracle.ZERO)
+    report = []
+    for b, g in div:
+        ok, why = _near_tie(b, g, case["Ft"], tree, case["tol"])
+        report.append((ok, (b.I, b.J), why))
+    print(f"{case['name']}: {len(div)} divergences from the oracle's {nstored} stored blocks")
+    for ok, ij, why in report:
+        print(f"  {'near-tie' if ok else 'NOT A TIE'} at {ij}: {why}")
+    assert all(ok for ok, _, _ in report), [r for r in report if not r[0]]
+    # the check's extra rank at the threshold is the usual divergence; the
+    # rest of the structure is identical
+    assert len(div) <= 0.5 * nstored
     # the stored blocks tile the matrix exactly once
-    tree = case["tree"]
     cover = np.zeros((case["om"].n, case["om"].n), dtype=np.int32)
     for d in desc:
         r0, m = tree.first[d[0]], tree.count[d[0]]
@@ -109,7 +191,8 @@ def test_blocks_meet_their_invariants(vf, case):
         else:
             s1 = np.linalg.norm(A, 2)
             err = np.linalg.norm(Ah - A, 2)
-            assert err <= 1.05 * tol * s1, f"block {tuple(d[:2])}: {err / s1:.3e} > tol"
+            # the default assembly checks every factorisation in FP64 (verify on)
+            assert err <= tol * s1, f"block {tuple(d[:2])}: {err / s1:.3e} > tol"
 
 
 def test_apply_fp32_within_two_tol(vf, case):
@@ -176,6 +259,39 @@ def test_solve_refined_low_precision(vf, case, prec):
     a, b = B32.double().cpu().numpy(), Blp.double().cpu().numpy()
     err = np.linalg.norm(a - b, axis=1) / np.linalg.norm(a, axis=1)
     assert np.all(err < 1e-5), err
+
+
+@pytest.mark.parametrize("prec,bound", [("bf16", 1.2e-2), ("fp8", 1.5e-1)])
+def test_apply_low_precision_against_oracle(vf, case, prec, bound):
+    """BF16 / FP8 E4M3 (per-block scale) multiplies against the oracle's
+    FP64 F: compression (2 tol, reading R8) plus the factors' rounding."""
+    import torch
+    om, F, tol = case["om"], case["F"], case["tol"]
+    X = synth.uniform_columns(om.n, 4, seed=6)
+    Xt = torch.tensor(X.T.copy(), device="cuda", dtype=torch.float32)
+    Y = torch.empty_like(Xt)
+    vf.vf_apply(case["prob"].hmat, Xt, Y, precision=prec)
+    Yo = F @ X
+    err = np.linalg.norm(Y.double().cpu().numpy().T - Yo, axis=0) / np.linalg.norm(Yo, axis=0)
+    assert np.all(err <= 2 * tol + bound), err
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_solve_refined_low_precision_against_oracle(vf, case, prec):
+    """BF16 / FP8 sweeps with FP64-residual refinement reach the oracle's
+    FP64 solution of the uncompressed system to the compression error
+    (2 tol), like the FP32 solve."""
+    import torch
+    om, F, tol = case["om"], case["F"], case["tol"]
+    dirs = synth.sun_directions(3, 25.0)
+    E = torch.empty((3, om.n), device="cuda")
+    vf.vf_mesh_insolation(case["prob"].mesh, dirs, 1365.0, E)
+    B = torch.empty_like(E)
+    st = vf.vf_solve(case["prob"].hmat, E, B, rho=0.5, rtol=1e-7, precision=prec, refine=True)
+    assert st["converged"] == 1
+    Bo, _, _ = oracle.jacobi(lambda X: F @ X, oracle.insolation(om, dirs, 1365.0), 0.5, rtol=1e-12)
+    err = np.linalg.norm(B.double().cpu().numpy().T - Bo, axis=0) / np.linalg.norm(Bo, axis=0)
+    assert np.all(err <= 2 * tol), err
 
 
 def test_solve_edge_cases(vf, case):

@@ -61,8 +61,9 @@ def test_verified_svd_blocks_meet_the_criterion(vf, name):
         c0, nn = nodes["first"][d[1]], nodes["count"][d[1]]
         A = Ft[r0:r0 + mm, c0:c0 + nn]
         err = np.linalg.norm(Fh[r0:r0 + mm, c0:c0 + nn] - A, 2)
-        # the check's norms are power-iteration estimates (from below): 10% slack
-        assert err <= 1.10 * tol * np.linalg.norm(A, 2), (tuple(d[:2]), err / np.linalg.norm(A, 2))
+        # the check accepts only below 0.9 tol of its power-iteration
+        # estimates (which approach the norms from below): no slack here
+        assert err <= tol * np.linalg.norm(A, 2), (tuple(d[:2]), err / np.linalg.norm(A, 2))
     assert nsvd > 0
 
 
@@ -71,7 +72,7 @@ def test_check_keeps_passing_blocks(vf):
     v, f = synth.fbm_dem_mesh(n=40, seed=8)
     m = vf.vf_mesh_create(v, f)
     t = vf.vf_partition(m, "quad", 64)
-    h0, s0 = vf.vf_assemble(m, t, tol=1e-3, precisions=("fp32",))
+    h0, s0 = vf.vf_assemble(m, t, tol=1e-3, verify=False, precisions=("fp32",))
     h1, s1 = vf.vf_assemble(m, t, tol=1e-3, verify=True, precisions=("fp32",))
     assert s0["verify_failed"] == 0
     X = torch.rand((4, m.n), generator=torch.Generator().manual_seed(1)).cuda()
