@@ -619,6 +619,10 @@ def main():
                                                           4)}}
         batched_host = {"B": Bb.double().cpu().numpy().T, "dirs": lunar_day_dirs(Rb), "rho": rho}
         del Eb, Bb, Bref, Xb, Yb
+        # the autotuner's candidate workspaces and the tensor pages of this
+        # section are released before the many-mesh section needs the memory
+        vf.vf_hmat_trim(prob.hmat)
+        torch.cuda.empty_cache()
 
     # ---- many meshes in one launch per phase: K seeded fBm terrains (every
     # other one with a crater) of growing size, each with its own suns, one
@@ -691,6 +695,9 @@ def main():
                      "converged": all(x["converged"] for x in sm), "setup_s": round(t_mm_setup, 1),
                      "precision": "bf16 tensor-core sweeps + split-BF16 refinement, rtol 1e-4"}
         del ps, Es, Bs, Bl, hs
+        import gc
+        gc.collect()
+        torch.cuda.empty_cache()
 
     # ---- the uncompressed dense FP32 F on the same GPU
     dense = None

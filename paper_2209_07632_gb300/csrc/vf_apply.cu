@@ -636,11 +636,19 @@ __global__ void __launch_bounds__(1024) k_colnorm2(const float* __restrict__ E, 
     __shared__ double ws[32];
     const int v = blockIdx.x, c = v % R, sg = v / R, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float* e = E + (int64_t)c * n;
-    const int64_t r1 = seg_row0[sg + 1];
+    const int64_t r0 = seg_row0[sg], r1 = seg_row0[sg + 1];
     double s = 0;
-    for (int64_t t = seg_row0[sg] + threadIdx.x; t < r1; t += 1024) {
-        const double v = e[t];
-        s += v * v;
+    // eight independent loads in flight per thread and step (one column is
+    // read by one CTA, so latency, not bandwidth, bounds a plain loop)
+    for (int64_t t0 = r0; t0 < r1; t0 += 8 * 1024) {
+        float x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int64_t t = t0 + k * 1024 + threadIdx.x;
+            x[k] = t < r1 ? __ldg(e + t) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s += (double)x[k] * (double)x[k];
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) ws[warp] = s;

@@ -81,6 +81,9 @@ def main():
             res[label] = {"assembly_s": round(wall, 3), "t_probe_s": round(st["t_probe"], 3),
                           "probes": st["probes"], "probes_failed": st["probes_failed"],
                           "probes_predicted_skip": st["probes_predicted_skip"],
+                          "predictor_audits": st["predictor_audits"],
+                          "predictor_audit_wins": st["predictor_audit_wins"],
+                          "predictor_fallbacks": st["predictor_fallbacks"],
                           "bytes_fp32": vf.vf_hmat_bytes(h, "fp32"), "blocks": st["nblocks"]}
             dirs = synth.sun_directions(8, 10.0)
             E = torch.empty((8, m.n), device="cuda")
