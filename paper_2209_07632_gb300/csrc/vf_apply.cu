@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(256, RB == 1 ? 3 : 1) k_phase2(ApplyArgs a, Pa
 template <class T>
 __global__ void k_pack_pages(const RecSrc* __restrict__ recs, int64_t nrec, const T* __restrict__ val,
                              const int32_t* __restrict__ aux, const float* __restrict__ scales,
-                             unsigned char* __restrict__ pool) {
+                             const int32_t* __restrict__ xtra, unsigned char* __restrict__ pool) {
     const int64_t ri = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (ri >= nrec) return;
@@ -554,6 +554,24 @@ __global__ void k_pack_pages(const RecSrc* __restrict__ recs, int64_t nrec, cons
         T* o = reinterpret_cast<T*>(dst + kRecHdr);
         for (int e = lane; e < r.cnt * r.w; e += 32) o[e] = val[r.val + e];
         for (int k = lane; k < r.w; k += 32) xl[k] = r.x + k;
+    } else if (r.kind == REC_SVD && r.csr) {
+        // a CSR piece as a dense slab over its nonempty rows and used columns
+        // (both sorted, from xtra); the pool was cleared, so absent entries are 0
+        const int32_t* rl = xtra + r.idx;
+        const int32_t* cl = rl + r.cnt;
+        unsigned char* rows = dst + kRecHdr;
+        T* o = reinterpret_cast<T*>(dst + kRecHdr + pad4((uint32_t)r.cnt));
+        for (int u = lane; u < r.cnt; u += 32) {
+            rows[u] = (unsigned char)(rl[u] - r.tile_first);
+            const int lr = rl[u] - r.first;  // block-local row
+            int k = 0;
+            for (int z = aux[r.nz0 + lr]; z < aux[r.nz0 + lr + 1]; ++z) {
+                const int col = aux[r.idx2 + z];
+                while (k < r.w && cl[k] < col) ++k;  // the row's columns are a sorted subset of cl
+                if (k < r.w) o[k * r.cnt + u] = val[r.val + z];
+            }
+        }
+        for (int k = lane; k < r.w; k += 32) xl[k] = cl[k];
     } else if (r.kind == REC_SVD) {
         unsigned char* rows = dst + kRecHdr;
         for (int u = lane; u < r.cnt; u += 32) rows[u] = (unsigned char)(aux[r.idx + u] - r.tile_first);
@@ -740,7 +758,7 @@ struct PagePlan {
 }  // namespace
 
 static vf_status build_pages(vf_hmat* H, std::vector<vf::RecSrc>& recs, const std::vector<int64_t>& page_of,
-                             int64_t npages, bool phase1) {
+                             int64_t npages, bool phase1, const std::vector<int32_t>& xtra) {
     // per element size: offsets inside pages, page headers, pack kernel
     const int es_of[3] = {4, 2, 1};
     for (int prec = 0; prec < 3; ++prec) {
@@ -775,15 +793,18 @@ static vf_status build_pages(vf_hmat* H, std::vector<vf::RecSrc>& recs, const st
         VF_TRY(dx.upload(nx));
         vf::dbuf<vf::RecSrc> dr;
         VF_TRY(dr.upload(recs));
+        vf::dbuf<int32_t> dxt;
+        if (!xtra.empty()) VF_TRY(dxt.upload(xtra));
         const int64_t nr = (int64_t)recs.size();
         const unsigned grid = (unsigned)vf::ceil_div(nr * 32, 256);
         if (nr) {
             if (prec == VF_PREC_FP32)
-                vf::k_pack_pages<float><<<grid, 256>>>(dr.p, nr, H->val.p, H->aux.p, nullptr, pool.p);
+                vf::k_pack_pages<float><<<grid, 256>>>(dr.p, nr, H->val.p, H->aux.p, nullptr, dxt.p, pool.p);
             else if (prec == VF_PREC_BF16)
-                vf::k_pack_pages<__nv_bfloat16><<<grid, 256>>>(dr.p, nr, H->val16.p, H->aux.p, nullptr, pool.p);
+                vf::k_pack_pages<__nv_bfloat16><<<grid, 256>>>(dr.p, nr, H->val16.p, H->aux.p, nullptr, dxt.p, pool.p);
             else
-                vf::k_pack_pages<__nv_fp8_e4m3><<<grid, 256>>>(dr.p, nr, H->val8.p, H->aux.p, H->scale8.p, pool.p);
+                vf::k_pack_pages<__nv_fp8_e4m3><<<grid, 256>>>(dr.p, nr, H->val8.p, H->aux.p, H->scale8.p, dxt.p,
+                                                                  pool.p);
             VF_TRY_CUDA(cudaGetLastError());
         }
         vf::k_page_headers<<<(unsigned)vf::ceil_div(npages, 256), 256>>>(dn.p, u.p, dx.p, npages, pool.p);
@@ -830,6 +851,11 @@ vf_status vf_hmat::upload_all() {
     };
     std::vector<std::vector<vf::RecSrc>> per(ntiles);
     std::vector<int64_t> cost(ntiles, 0);
+    std::vector<int32_t> xtra;  // rows and columns of CSR pieces laid out as dense slabs
+    std::vector<int32_t> mark;  // per column of the current CSR block: the stamp of the slab that uses it
+    int32_t stamp = 1;
+    for (const vf::HBlock& b : B)
+        if (b.kind == VF_BLK_CSR) mark.resize(std::max<size_t>(mark.size(), (size_t)b.n), 0);
     for (size_t bi = 0; bi < B.size(); ++bi) {
         const vf::HBlock& b = B[bi];
         for (int32_t r = b.r0; r < b.r0 + b.m;) {
@@ -855,8 +881,58 @@ vf_status vf_hmat::upload_all() {
                 }
             } else if (b.kind == VF_BLK_CSR) {
                 const int32_t* rp = haux.data() + b.off_aux;
+                const int32_t* ci = rp + b.m + 1;
                 src.idx2 = (int32_t)(b.off_aux + b.m + 1);
                 src.val = b.off_val;
+                // The piece as dense slabs over its nonempty rows and the columns
+                // they use (greedy in row order, each slab within a page), if
+                // that takes no more bytes than its CSR records.
+                std::vector<vf::RecSrc> dense_recs;
+                std::vector<int32_t> dense_xtra;
+                int64_t dense_bytes = 0;
+                bool dense_ok = true;
+                {
+                    std::vector<int32_t> rows, cols;
+                    auto close = [&]() {
+                        if (rows.empty()) return;
+                        std::sort(cols.begin(), cols.end());
+                        vf::RecSrc d = src;
+                        d.kind = vf::REC_SVD;
+                        d.csr = 1;
+                        d.cnt = (int32_t)rows.size();
+                        d.w = (int32_t)cols.size();
+                        d.idx = (int32_t)(xtra.size() + dense_xtra.size());
+                        d.nz0 = (int32_t)b.off_aux;
+                        d.first = b.r0;
+                        dense_xtra.insert(dense_xtra.end(), rows.begin(), rows.end());
+                        dense_xtra.insert(dense_xtra.end(), cols.begin(), cols.end());
+                        dense_bytes += tot(vf::REC_SVD, d.cnt, d.w);
+                        dense_recs.push_back(d);
+                        rows.clear();
+                        cols.clear();
+                        ++stamp;
+                    };
+                    for (int32_t i = 0; i < cnt && dense_ok; ++i) {
+                        const int32_t lr = br + i;
+                        if (rp[lr + 1] == rp[lr]) continue;
+                        int32_t fresh = 0;
+                        for (int32_t z = rp[lr]; z < rp[lr + 1]; ++z) fresh += mark[ci[z] - b.c0] != stamp;
+                        if (!rows.empty() &&
+                            tot(vf::REC_SVD, (int)rows.size() + 1, (int)(cols.size() + fresh)) > cap)
+                            close();
+                        for (int32_t z = rp[lr]; z < rp[lr + 1]; ++z)
+                            if (mark[ci[z] - b.c0] != stamp) {
+                                mark[ci[z] - b.c0] = stamp;
+                                cols.push_back(ci[z]);
+                            }
+                        rows.push_back(rs + i);
+                        if (tot(vf::REC_SVD, (int)rows.size(), (int)cols.size()) > cap) dense_ok = false;
+                    }
+                    if (dense_ok) close();
+                    ++stamp;
+                }
+                int64_t csr_bytes = 0;
+                const size_t first_csr = per[k].size();
                 int32_t i = 0;
                 while (i < cnt) {
                     const int32_t row = br + i;
@@ -888,6 +964,13 @@ vf_status vf_hmat::upload_all() {
                     cr.w = rp[br + j] - rp[br + i];
                     if (cr.w > 0) per[k].push_back(cr);
                     i = j;
+                }
+                for (size_t t = first_csr; t < per[k].size(); ++t)
+                    csr_bytes += tot(per[k][t].kind, per[k][t].cnt, per[k][t].w);
+                if (dense_ok && dense_bytes <= csr_bytes) {
+                    per[k].resize(first_csr);
+                    per[k].insert(per[k].end(), dense_recs.begin(), dense_recs.end());
+                    xtra.insert(xtra.end(), dense_xtra.begin(), dense_xtra.end());
                 }
             } else {
                 const int32_t* rows = haux.data() + b.off_aux;
@@ -947,7 +1030,7 @@ vf_status vf_hmat::upload_all() {
     }
     h_tile_page_ptr[ntiles * kWarps] = (int32_t)npages;
     n_pages = npages;
-    VF_TRY(build_pages(this, recs, page_of, npages, false));
+    VF_TRY(build_pages(this, recs, page_of, npages, false, xtra));
     h_tile_order.resize(ntiles);
     for (int64_t k = 0; k < ntiles; ++k) h_tile_order[k] = (int32_t)k;
     std::stable_sort(h_tile_order.begin(), h_tile_order.end(),
@@ -1064,7 +1147,7 @@ vf_status vf_hmat::upload_all() {
         h_p1_warp_ptr[n_p1_warps] = (int32_t)np;
         n_p1_pages = np;
     }
-    VF_TRY(build_pages(this, p1, p1_page, n_p1_pages, true));
+    VF_TRY(build_pages(this, p1, p1_page, n_p1_pages, true, {}));
     VF_TRY(p1_warp_ptr.upload(h_p1_warp_ptr));
     n_split = (int64_t)split.size() / 5;
     if (n_split > 0) VF_TRY(p1_split.upload(split));

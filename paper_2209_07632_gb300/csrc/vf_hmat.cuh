@@ -44,7 +44,11 @@ struct HBlock {
 //   CSR    (2): tile rows roff..roff+cnt-1, w = nnz; row pointers (cnt + 1,
 //               from 0), values (nnz); x entries: the nonzeros' columns
 //   SVD    (3): w = q; tile-local rows (cnt bytes), U' (cnt x q) as a
-//               column-major slab; x entries: its q T slots
+//               column-major slab; x entries: its q T slots.  The same
+//               layout carries a CSR block's piece where that is smaller:
+//               its nonempty rows x the columns they use, zeros stored,
+//               x entries: those columns (one gather per column instead
+//               of one per nonzero)
 //   long CSR row (5): tile row roff, w = nnz; values; x entries: columns
 //   phase-1 (6): header + i32 chunk (within its unit), chunks in the unit,
 //               partial offset (-1: the unit is the whole block), T slot;
@@ -104,7 +108,8 @@ struct RecSrc {
     int64_t dst;         // byte offset of the record in the page pool (per element size)
     int64_t xdst;        // byte offset of its first x-list entry in the page pool
     int32_t xbase;       // its first x-list entry within the page
-    int32_t pad;
+    int32_t csr;         // REC_SVD layout filled from a CSR block: its nonempty rows x its columns, dense
+                         // (rows, then columns, at xtra[idx]; rp at aux[nz0], cols at aux[idx2]; block row first)
 };
 
 }  // namespace vf

@@ -793,6 +793,10 @@ struct TSmem {
         d_empty[2], done;
     uint32_t tmem_base;
     int32_t abort;
+    // the producer's window of page sizes (pages used_base .. + 63 of its list),
+    // refilled by 64 independent loads, so no page copy waits on a global load
+    int32_t used_base;
+    uint32_t used_win[64];
 };
 
 static_assert(sizeof(TSmem) <= 1024, "barrier block");
@@ -827,7 +831,7 @@ __device__ __forceinline__ void t_select(TEpi& ep) {
 // issued, 0 if the stage is still busy, -1 on a timeout, -2 on a bad page.
 template <int NS, int NP>
 __device__ __forceinline__ int t_page_refill(TSmem& S, unsigned char* stages, const unsigned char* pages,
-                                             const uint32_t* used, int pa, int next, bool block) {
+                                             const uint32_t* used, int pa, int npl, int next, bool block) {
     constexpr int PS = TCfg<NS, NP>::PSTAGES;
     const int s2 = next % PS;
     if (next >= PS) {
@@ -838,7 +842,13 @@ __device__ __forceinline__ int t_page_refill(TSmem& S, unsigned char* stages, co
             return 0;
         }
     }
-    const uint32_t bytes = used[pa + next];
+    const int base = next & ~63;
+    if (S.used_base != base) {
+#pragma unroll 16
+        for (int i = 0; i < 64; ++i) S.used_win[i] = used[pa + min(base + i, npl - 1)];
+        S.used_base = base;
+    }
+    const uint32_t bytes = S.used_win[next & 63];
     if (bytes < kTPHdr || bytes > (uint32_t)kTP || (bytes & 15u)) return -2;
     mbar_arrive_expect_tx(&S.page_full[s2], bytes);
     bulk_g2s(stages + s2 * kTP, pages + (int64_t)(pa + next) * kTP, bytes, &S.page_full[s2]);
@@ -859,10 +869,10 @@ __device__ void t_producer(TSmem& S, unsigned char* stages, unsigned char* abuf,
     const int npl = pb - pa;
     int next = 0, chunk = 0, rc = 0;  // next page to copy; CTA-local chunk index
     for (; next < npl && next < PS; ++next)
-        if ((rc = t_page_refill<NS, NP>(S, stages, pages, used, pa, next, true)) < 0) goto bad;
+        if ((rc = t_page_refill<NS, NP>(S, stages, pages, used, pa, npl, next, true)) < 0) goto bad;
     for (int li = 0; li < npl; ++li) {
         for (; next <= li; ++next)
-            if ((rc = t_page_refill<NS, NP>(S, stages, pages, used, pa, next, true)) < 0) goto bad;
+            if ((rc = t_page_refill<NS, NP>(S, stages, pages, used, pa, npl, next, true)) < 0) goto bad;
         const int s = li % PS;
         if (!bwait(&S.page_full[s], (uint32_t)((li / PS) & 1))) goto fail;
         {
@@ -881,7 +891,7 @@ __device__ void t_producer(TSmem& S, unsigned char* stages, unsigned char* abuf,
                     goto oob;
                 for (int kc = 0; kc < K16; kc += SL::CK, ++chunk) {
                     if (next < npl) {
-                        if ((rc = t_page_refill<NS, NP>(S, stages, pages, used, pa, next, false)) < 0) goto bad;
+                        if ((rc = t_page_refill<NS, NP>(S, stages, pages, used, pa, npl, next, false)) < 0) goto bad;
                         next += rc;
                     }
                     const int slot = chunk % SL::NSLOT, use = chunk / SL::NSLOT;
@@ -1005,6 +1015,7 @@ __device__ void t_prologue(TSmem& S) {
         }
         mbar_init(&S.done, 1);
         S.abort = 0;
+        S.used_base = -64;
         mbar_init_fence();
     }
     if (warp == 1) {
@@ -1101,7 +1112,14 @@ __global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase1(const unsig
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         const int u0 = cta_unit_ptr[blockIdx.x], u1 = cta_unit_ptr[blockIdx.x + 1];
         bool open = false;  // inside a group (its region filled)
+        // unit descriptors, 32 at a time: lane i holds unit ub + i
+        int4 ud = make_int4(0, 0, 0, 0);
+        int ub = u0 - 32;
         for (int u = u0, k = 0; u < u1; ++u) {
+            if (u - ub >= 32) {
+                ub = u;
+                if (u + lane < u1) ud = reinterpret_cast<const int4*>(cta_units)[u + lane];
+            }
             const int d = NREG == 1 ? 0 : (k & 1);
             if (!open) {
                 if (!__all_sync(0xffffffffu, bwait(&S.d_full[d], (uint32_t)((k / NREG) & 1)))) {
@@ -1111,8 +1129,9 @@ __global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase1(const unsig
                 tm_fence_after();
                 open = true;
             }
-            const int offT = cta_units[4 * u], nc = cta_units[4 * u + 1], col = cta_units[4 * u + 2];
-            const bool gend = cta_units[4 * u + 3] != 0;
+            const int offT = __shfl_sync(0xffffffffu, ud.x, u - ub), nc = __shfl_sync(0xffffffffu, ud.y, u - ub);
+            const int col = __shfl_sync(0xffffffffu, ud.z, u - ub);
+            const bool gend = __shfl_sync(0xffffffffu, ud.w, u - ub) != 0;
 #pragma unroll
             for (int q = 0; q < NP; ++q)
                 // the unit's columns [col, col + nc) through 16-column loads
@@ -1173,15 +1192,25 @@ __global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase2(const unsig
         const int m = 32 * (warp & 3) + lane;
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         const int t0 = cta_tile_ptr[blockIdx.x], t1 = cta_tile_ptr[blockIdx.x + 1];
+        // (super-)tile descriptors, 32 at a time: lane i holds tile tb + i
+        int my_tile = 0, my_tf = 0, my_tc = 0, tb = t0 - 32;
         for (int ti = t0, k = 0; ti < t1; ++ti, ++k) {
+            if (ti - tb >= 32) {
+                tb = ti;
+                if (ti + lane < t1) {
+                    my_tile = cta_tiles[ti + lane];
+                    my_tf = tile_first[my_tile];
+                    my_tc = tile_count[my_tile];
+                }
+            }
             const int d = NREG == 1 ? 0 : (k & 1);
             if (!__all_sync(0xffffffffu, bwait(&S.d_full[d], (uint32_t)((k / NREG) & 1)))) {
                 if (lane == 0) atomicCAS(status, 0, (int)VF_E_TIMEOUT), atomicExch(&S.abort, 1);
                 break;
             }
             tm_fence_after();
-            const int tile = cta_tiles[ti];
-            const int tf = tile_first[tile], tc = tile_count[tile];
+            const int tile = __shfl_sync(0xffffffffu, my_tile, ti - tb);
+            const int tf = __shfl_sync(0xffffffffu, my_tf, ti - tb), tc = __shfl_sync(0xffffffffu, my_tc, ti - tb);
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
                 const int col = ep.p0 + q * kPanel + m;  // RHS column
