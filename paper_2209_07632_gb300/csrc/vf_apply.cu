@@ -1175,6 +1175,7 @@ struct Workspace {
     // tensor-core path (BF16, R >= kTensorMinR): BF16 panels of 128 RHS, ping-pong, and the T panel
     dbuf<unsigned char> xpan[2], tpan;
     dbuf<unsigned char> xsplit[2], tsplit[2];  // hi / lo panels of the split residual
+    dbuf<float> sx8, isx8;                     // FP8 panels: per RHS column scale and its inverse
     dbuf<int> tcount;  // [0]: columns not converged after a tensor sweep; [1]: the reduction's ticket
     int tpanels = 0;
     bool tready = false, sready = false;  // the tensor panels / the split panels are all allocated
@@ -1466,16 +1467,36 @@ static int multiply_kernels(const vf_hmat* h) {
 static bool use_tensor(const vf_hmat* h, int prec, int R) {
     vf_tune t;
     if (tuned(h, prec, R, &t) && !t.tensor) return false;
-    return prec == VF_PREC_BF16 && h->has_bf16 && R >= kTensorMinR;
+    return ((prec == VF_PREC_BF16 && h->has_bf16) || (prec == VF_PREC_FP8 && h->has_fp8)) && R >= kTensorMinR;
+}
+
+// The tensor page set of a workspace's precision (1: BF16, 3: FP8) and its
+// panels' bytes.
+static int tset(const Workspace* w) { return w->prec == VF_PREC_FP8 ? 3 : 1; }
+static int64_t tpbx(const vf_hmat* h, int S) { return S == 3 ? tensor_panel_bytes_x8(h) : tensor_panel_bytes_x(h); }
+static int64_t tpbt(const vf_hmat* h, int S) { return S == 3 ? tensor_panel_bytes_t8(h) : tensor_panel_bytes_t(h); }
+
+// Scales of the FP8 panels of X (columns [0, R), ld, rows through perm):
+// headroom 1 for a single multiply, 1/4 for Jacobi iterates (which may grow
+// by up to 1 / (1 - rho) over the right-hand side; beyond that the FP8
+// values saturate and the refinement's residual corrects them).
+static vf_status fp8_scales(const vf_hmat* h, Workspace* w, const float* X, int64_t ld, const int32_t* perm,
+                            float headroom, cudaStream_t st) {
+    return tensor_fp8_colscale(h, X, ld, perm, w->R, headroom, w->sx8.p, w->isx8.p, st);
 }
 
 // The tensor pages (built once per matrix; the handle's lazily built part)
 // and this workspace's panels.
 static vf_status tensor_ws(const vf_hmat* h, Workspace* w) {
-    VF_TRY(tensor_prepare(const_cast<vf_hmat*>(h), 1));
+    const int S = tset(w);
+    VF_TRY(tensor_prepare(const_cast<vf_hmat*>(h), S));
     if (w->tready) return VF_OK;  // set only once every buffer below exists
     w->tpanels = (int)ceil_div(w->R, kTensorPanel);
-    const int64_t bx = tensor_panel_bytes_x(h), bt = tensor_panel_bytes_t(h);
+    const int64_t bx = tpbx(h, S), bt = tpbt(h, S);
+    if (S == 3) {
+        VF_TRY(w->sx8.alloc(w->R));
+        VF_TRY(w->isx8.alloc(w->R));
+    }
     for (int i = 0; i < 2; ++i) {
         VF_TRY(w->xpan[i].alloc((size_t)w->tpanels * bx));
         VF_TRY_CUDA(cudaMemset(w->xpan[i].p, 0, (size_t)w->tpanels * bx));
@@ -1545,9 +1566,10 @@ __global__ void __launch_bounds__(256) k_unconverged(const double* __restrict__ 
 // directions.  The host synchronises once, after the loop.
 static vf_status ensure_tensor_graph(const vf_hmat* h, Workspace* w) {
     if (w->tgraph) return VF_OK;
+    const int S = tset(w);
     const int64_t n = h->nf;
-    const int64_t ntiles = tensor_parts(h, 1);
-    const int64_t bx = tensor_panel_bytes_x(h);
+    const int64_t ntiles = tensor_parts(h, S);
+    const int64_t bx = tpbx(h, S);
     cudaGraph_t g;
     VF_TRY_CUDA(cudaGraphCreate(&g, 0));
     VF_TRY_CUDA(cudaGraphConditionalHandleCreate(&w->thandle, g, 1, cudaGraphCondAssignDefault));
@@ -1585,10 +1607,15 @@ static vf_status ensure_tensor_graph(const vf_hmat* h, Workspace* w) {
         ep.Yalt = w->Bt[0].p;
         ep.Boldalt = w->Bt[1].p;
         ep.Xnextalt = w->xpan[0].p + (size_t)p * bx;
-        s = tensor_multiply(h, 1, np, w->xpan[0].p + (size_t)p * bx, nullptr, w->tpan.p, nullptr, ep, w->status.p,
+        if (S == 3) {
+            ep.sx = w->sx8.p;
+            ep.isx = w->isx8.p;
+            ep.irs = tensor_fp8_irs(h);
+        }
+        s = tensor_multiply(h, S, np, w->xpan[0].p + (size_t)p * bx, nullptr, w->tpan.p, nullptr, ep, w->status.p,
                             cs);
     }
-    k_sweep_reduce<<<1, 1024, 0, cs>>>(w->colpart.p, ntiles, w->R, h->nseg(), tensor_seg_parts(h, 1), w->enorm2.p,
+    k_sweep_reduce<<<1, 1024, 0, cs>>>(w->colpart.p, ntiles, w->R, h->nseg(), tensor_seg_parts(h, S), w->enorm2.p,
                                        w->colres.p, w->loop.p, w->bufs.p, w->xsel.p, w->ysel.p, w->thandle, 1);
     cudaError_t e1 = cudaGetLastError();
     cudaGraph_t outg;
@@ -1614,17 +1641,24 @@ static vf_status tensor_jacobi_loop(const vf_hmat* h, Workspace* w, int max_iter
                                     int* iters, int* par, int* kernels) {
     VF_TRY(tensor_ws(h, w));
     VF_TRY(ensure_tensor_graph(h, w));
+    const int S = tset(w);
     const int64_t n = h->nf, nR = n * (int64_t)w->R;
-    const int64_t bx = tensor_panel_bytes_x(h);
+    const int64_t bx = tpbx(h, S);
     const int NV = w->R * h->nseg();
     VF_TRY_CUDA(cudaMemcpyAsync(w->Bt[0].p, w->Et.p, nR * 4, cudaMemcpyDeviceToDevice, st));
     k_colnorm2<<<(unsigned)NV, 1024, 0, st>>>(w->Et.p, n, w->R, h->seg_row0.p, w->enorm2.p);
-    for (int p = 0; p < w->tpanels; ++p)
-        VF_TRY(tensor_to_panel(h, w->Et.p, n, nullptr, w->R, p * kTensorPanel, w->xpan[0].p + (size_t)p * bx, nullptr,
-                               st));
+    if (S == 3) VF_TRY(fp8_scales(h, w, w->Et.p, n, nullptr, 0.25f, st));
+    for (int p = 0; p < w->tpanels; ++p) {
+        if (S == 3)
+            VF_TRY(tensor_to_panel8(h, w->Et.p, n, nullptr, w->R, p * kTensorPanel, w->sx8.p,
+                                    w->xpan[0].p + (size_t)p * bx, st));
+        else
+            VF_TRY(tensor_to_panel(h, w->Et.p, n, nullptr, w->R, p * kTensorPanel, w->xpan[0].p + (size_t)p * bx,
+                                   nullptr, st));
+    }
     k_loop_init<<<1, 1, 0, st>>>(w->loop.p, max_iter, rtol * rtol, w->bufs.p, w->xsel.p, w->ysel.p);
     VF_TRY_CUDA(cudaGetLastError());
-    *kernels += 2 + w->tpanels;
+    *kernels += 2 + w->tpanels + (S == 3 ? 1 : 0);
     if (max_iter > 0) VF_TRY_CUDA(cudaGraphLaunch(w->tgraph, st));
     LoopState ls{};
     VF_TRY_CUDA(cudaMemcpyAsync(&ls, w->loop.p, sizeof(ls), cudaMemcpyDeviceToHost, st));
@@ -1632,7 +1666,7 @@ static vf_status tensor_jacobi_loop(const vf_hmat* h, Workspace* w, int max_iter
     int per_sweep = 1;  // the column reduction
     for (int p = 0, np; p < w->tpanels; p += np) {
         np = p + 1 < w->tpanels ? 2 : 1;
-        per_sweep += tensor_kernels(h, 1);
+        per_sweep += tensor_kernels(h, S);
     }
     *kernels += ls.iter * per_sweep;
     *iters = ls.iter;
@@ -1694,19 +1728,32 @@ static vf_status tensor_residual(const vf_hmat* h, Workspace* w, const float* B,
 static vf_status tensor_apply(const vf_hmat* h, Workspace* w, const float* X, int64_t ld, const int32_t* perm,
                               float* Y, cudaStream_t st) {
     VF_TRY(tensor_ws(h, w));
-    const int64_t bx = tensor_panel_bytes_x(h);
+    const int S = tset(w);
+    const int64_t bx = tpbx(h, S);
+    if (S == 3) VF_TRY(fp8_scales(h, w, X, ld, perm, 1.f, st));
     for (int p = 0, np; p < w->tpanels; p += np) {
         np = p + 1 < w->tpanels ? 2 : 1;  // two RHS panels per multiply where there are two
         unsigned char* xp = w->xpan[0].p + (size_t)p * bx;
-        for (int q = 0; q < np; ++q)
-            VF_TRY(tensor_to_panel(h, X, ld, perm, w->R, (p + q) * kTensorPanel, xp + (size_t)q * bx, nullptr, st));
+        for (int q = 0; q < np; ++q) {
+            if (S == 3)
+                VF_TRY(tensor_to_panel8(h, X, ld, perm, w->R, (p + q) * kTensorPanel, w->sx8.p, xp + (size_t)q * bx,
+                                        st));
+            else
+                VF_TRY(tensor_to_panel(h, X, ld, perm, w->R, (p + q) * kTensorPanel, xp + (size_t)q * bx, nullptr,
+                                       st));
+        }
         TEpi ep{};
         ep.mode = 0;
         ep.n = h->nf;
         ep.R = w->R;
         ep.p0 = p * kTensorPanel;
         ep.Y = Y;
-        VF_TRY(tensor_multiply(h, 1, np, xp, nullptr, w->tpan.p, nullptr, ep, w->status.p, st));
+        if (S == 3) {
+            ep.sx = w->sx8.p;
+            ep.isx = w->isx8.p;
+            ep.irs = tensor_fp8_irs(h);
+        }
+        VF_TRY(tensor_multiply(h, S, np, xp, nullptr, w->tpan.p, nullptr, ep, w->status.p, st));
     }
     return VF_OK;
 }
@@ -2406,9 +2453,9 @@ extern "C" vf_status vf_tune_set(const vf_hmat* h, vf_precision prec, int32_t R,
     VF_CHECK(h && t && R >= 1, VF_E_INVAL, "vf_tune_set: null argument or R < 1");
     VF_TRY(vf::check_prec(h, prec));
     VF_TRY(vf::check_tune(*t, R));
-    VF_CHECK(!t->tensor || (prec == VF_PREC_BF16 && R >= vf::kTensorMinR &&
+    VF_CHECK(!t->tensor || ((prec == VF_PREC_BF16 || prec == VF_PREC_FP8) && R >= vf::kTensorMinR &&
                             (t->rhs_block == 0 || t->rhs_block >= vf::kTensorMinR)),
-             VF_E_INVAL, "vf_tune_set: the tensor path needs BF16 and >= %d columns", vf::kTensorMinR);
+             VF_E_INVAL, "vf_tune_set: the tensor path needs BF16 or FP8 and >= %d columns", vf::kTensorMinR);
     vf::tune_store(h, prec, R, *t);
     return VF_OK;
 }
@@ -2439,7 +2486,7 @@ extern "C" vf_status vf_autotune(const vf_hmat* h, vf_precision prec, int32_t R,
         // a pass then always fills it)
         for (int rb : {1, 2, 4, 8})
             if ((rb == 1 || rb <= W) && (W < 16 || rb == 8)) cands.push_back(vf_tune{rb, 0, W < R ? W : 0, 0.f});
-        if (prec == VF_PREC_BF16 && h->has_bf16 && W >= vf::kTensorMinR)
+        if (((prec == VF_PREC_BF16 && h->has_bf16) || (prec == VF_PREC_FP8 && h->has_fp8)) && W >= vf::kTensorMinR)
             cands.push_back(vf_tune{vf::pick_rb(W), 1, W < R ? W : 0, 0.f});
         for (vf_tune& c : cands) {
             vf::Workspace* w;

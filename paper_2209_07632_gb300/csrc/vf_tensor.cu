@@ -79,25 +79,43 @@ template <> struct TCfg<2, 1> {
 template <> struct TCfg<2, 2> {
     static constexpr int PSTAGES = 2, RING = 32768, CTAS = 3, CK = 16, NREG = 1, TMEM = 128;
 };
+// FP8 E4M3 (kind::f8f6f4, K-major operands): the same bytes per slot as BF16
+template <> struct TCfg<3, 1> {
+    static constexpr int PSTAGES = 3, RING = 16384, CTAS = 4, CK = 64, NREG = 2, TMEM = 128;
+};
+template <> struct TCfg<3, 2> {
+    static constexpr int PSTAGES = 3, RING = 16384, CTAS = 4, CK = 32, NREG = 1, TMEM = 128;
+};
+// A page set's element kind: S = 1 BF16; S = 2 each FP32 value as two BF16
+// terms (hi, lo); S = 3 FP8 E4M3.  terms per element, bytes per term, the K
+// of one MMA (records' K granularity) and the alignment of an A operand's
+// first panel row (one core-matrix group: 8 rows MN-major BF16; FP8 records
+// start on a whole MMA step of 32 rows).
+__host__ __device__ constexpr int set_terms(int S) { return S == 2 ? 2 : 1; }
+__host__ __device__ constexpr int set_es(int S) { return S == 3 ? 1 : 2; }
+__host__ __device__ constexpr int set_kg(int S) { return S == 3 ? 32 : 16; }
+__host__ __device__ constexpr int set_al(int S) { return S == 3 ? 32 : 8; }
+// record body bytes
+__host__ __device__ constexpr int set_body(int S, int K, int N) { return set_terms(S) * set_es(S) * K * N; }
 // Shared by every configuration of a page set (records do not depend on NP):
 constexpr int kRegion = 64;     // accumulator columns per panel: a phase-1 group's rank columns, a tile's rows
 constexpr int kMaxPStages = 4;
-template <int NS> __host__ __device__ constexpr int kmax_of() { return NS == 1 ? 64 : 32; }  // K rows per record
+template <int NS> __host__ __device__ constexpr int kmax_of() { return NS == 1 ? 64 : NS == 2 ? 32 : 128; }  // K rows per record
 // A operands stream through the ring one K chunk of CK rows (all panels and
 // terms) per slot, so the copy of one record's later chunks (and of the next
 // record) overlaps the MMAs of its earlier ones.
 template <int NS, int NP> struct TSlots {
     static constexpr int CK = TCfg<NS, NP>::CK;
-    static constexpr int TERM = CK * 128 * 2;  // one panel, one term
-    static constexpr int BYTES = NP * NS * TERM;
+    static constexpr int TERM = CK * 128 * set_es(NS);  // one panel, one term
+    static constexpr int BYTES = NP * set_terms(NS) * TERM;
     static constexpr int NSLOT = TCfg<NS, NP>::RING / BYTES;
     static_assert(NSLOT >= 2 && NSLOT <= kMaxSlots, "A ring slots");
     static_assert(NP * kRegion * TCfg<NS, NP>::NREG <= TCfg<NS, NP>::TMEM, "accumulator regions");
 };
 // CTAs of a page set's launches (every configuration of the set has room for them on each SM)
-static int cfg_ctas(int S) { return S == 1 ? TCfg<1, 1>::CTAS : TCfg<2, 2>::CTAS; }
+static int cfg_ctas(int S) { return S == 1 ? TCfg<1, 1>::CTAS : S == 2 ? TCfg<2, 2>::CTAS : TCfg<3, 1>::CTAS; }
 static int cfg_region(int) { return kRegion; }
-static int cfg_kmax(int S) { return S == 1 ? kmax_of<1>() : kmax_of<2>(); }
+static int cfg_kmax(int S) { return S == 1 ? kmax_of<1>() : S == 2 ? kmax_of<2>() : kmax_of<3>(); }
 static int cfg_r2(int) { return kRegion; }  // phase-2 (super-)tiles: one row tile
 template <int NS, int NP>
 constexpr size_t tsmem_bytes() {
@@ -154,7 +172,16 @@ struct vf_tensor_set {
 struct vf_tensor_plan {
     int64_t n_rows_x = 0, n_rows_t = 0;  // panel rows (X, T), multiples of 16
     std::vector<int32_t> h_offT;         // per block: first T row (SVD), else -1
-    vf_tensor_set set[2];                // [S - 1]
+    // FP8 (S = 3): T rows with each row cluster's run starting on 32 rows,
+    // and the static scales (powers of two) that keep every FP8 operand in
+    // range: per T row, V' column scale cv and T store scale ct (g = cv ct);
+    // per tree row, rs for the phase-2 factors of that row (and 1 / rs)
+    int64_t n_rows_t8 = 0;
+    std::vector<int32_t> h_offT8;
+    vf::dbuf<int32_t> offT8;
+    vf::dbuf<float> cv8, ct8, g8, rs8, irs8;
+    bool scales8 = false;
+    vf_tensor_set set[3];                // [S - 1]
 };
 
 namespace vf {
@@ -169,9 +196,24 @@ __device__ __forceinline__ void st_bf16(unsigned char* base, int64_t k, int mn, 
     if (lo_off) *reinterpret_cast<__nv_bfloat16*>(base + lo_off + o) = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
+// The FP8 set's static scales (all NULL for the BF16 sets).
+struct F8Scales {
+    const float* rs;       // per tree row: phase-2 factors of the row
+    const float* g;        // per FP8 T row: cv ct (divides U' columns)
+    const float* cv;       // per FP8 T row: V' column scale
+    const int32_t* offT8;  // per block: first FP8 T row (SVD), else -1
+};
+
+// B element (k, mn) of an FP8 record: K-major core matrices of 8 MN rows x
+// 16 K bytes, 16-K groups (N16 / 8) x 128 bytes apart
+__device__ __forceinline__ void st_fp8(unsigned char* base, int64_t k, int mn, int n16, float v) {
+    const int64_t o = (k >> 4) * (n16 * 16) + (mn >> 3) * 128 + (mn & 7) * 16 + (k & 15);
+    base[o] = (unsigned char)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
+
 // One CTA per record: header, zero-filled B body, then the values.
 __global__ void k_tpack(const TRec* __restrict__ recs, const HBlock* __restrict__ blocks,
-                        const float* __restrict__ val, const int32_t* __restrict__ aux,
+                        const float* __restrict__ val, const int32_t* __restrict__ aux, F8Scales f8,
                         unsigned char* __restrict__ pool) {
     const TRec r = recs[blockIdx.x];
     unsigned char* dst = pool + r.dst;
@@ -201,7 +243,9 @@ __global__ void k_tpack(const TRec* __restrict__ recs, const HBlock* __restrict_
         for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
             const int j = e / nr, i = e - j * nr;
             const int row = r.rs + i, col = c_lo + j;
-            st_bf16(B, col - r.k0, row - r.row_base, lbo, slab[(int64_t)(col - b.c0) * nr + i], lo);
+            const float v = slab[(int64_t)(col - b.c0) * nr + i];
+            if (r.S == 3) st_fp8(B, col - r.k0, row - r.row_base, r.N16, v * f8.rs[row]);
+            else st_bf16(B, col - r.k0, row - r.row_base, lbo, v, lo);
         }
     } else if (r.kind == TREC_CSR) {
         const int32_t* rp = aux + b.off_aux;
@@ -210,8 +254,10 @@ __global__ void k_tpack(const TRec* __restrict__ recs, const HBlock* __restrict_
             const int lr = row - b.r0;
             for (int z = rp[lr] + (threadIdx.x & 31); z < rp[lr + 1]; z += 32) {
                 const int col = ci[z];
-                if (col >= r.k0 && col < r.k0 + r.K16)
-                    st_bf16(B, col - r.k0, row - r.row_base, lbo, val[b.off_val + z], lo);
+                if (col >= r.k0 && col < r.k0 + r.K16) {
+                    if (r.S == 3) st_fp8(B, col - r.k0, row - r.row_base, r.N16, val[b.off_val + z] * f8.rs[row]);
+                    else st_bf16(B, col - r.k0, row - r.row_base, lbo, val[b.off_val + z], lo);
+                }
             }
         }
     } else if (r.kind == TREC_SVDU) {
@@ -222,8 +268,11 @@ __global__ void k_tpack(const TRec* __restrict__ recs, const HBlock* __restrict_
         for (int e = threadIdx.x; e < b.m1 * b.q; e += blockDim.x) {
             const int u = e / b.q, k = e - u * b.q;
             const int row = rows[u];
-            if (row >= r.rs && row < r.re && k >= r.k0 && k < r.k0 + r.K16)
-                st_bf16(B, k - r.k0, row - r.row_base, lbo, val[b.off_val + (int64_t)u * b.q + k], lo);
+            if (row >= r.rs && row < r.re && k >= r.k0 && k < r.k0 + r.K16) {
+                const float v = val[b.off_val + (int64_t)u * b.q + k];
+                if (r.S == 3) st_fp8(B, k - r.k0, row - r.row_base, r.N16, v * f8.rs[row] / f8.g[f8.offT8[r.blk] + k]);
+                else st_bf16(B, k - r.k0, row - r.row_base, lbo, v, lo);
+            }
         }
     } else {
         // V' rows (compacted columns) inside [k0, k0 + K16); N = the rank
@@ -232,8 +281,11 @@ __global__ void k_tpack(const TRec* __restrict__ recs, const HBlock* __restrict_
         for (int e = threadIdx.x; e < b.n1 * b.q; e += blockDim.x) {
             const int j = e / b.q, k = e - j * b.q;
             const int col = cols[j];
-            if (col >= r.k0 && col < r.k0 + r.K16 && k >= r.n0 && k < r.n0 + r.nsub)
-                st_bf16(B, col - r.k0, r.bcol + k - r.n0, lbo, Vp[(int64_t)j * b.q + k], lo);
+            if (col >= r.k0 && col < r.k0 + r.K16 && k >= r.n0 && k < r.n0 + r.nsub) {
+                const float v = Vp[(int64_t)j * b.q + k];
+                if (r.S == 3) st_fp8(B, col - r.k0, r.bcol + k - r.n0, r.N16, v * f8.cv[f8.offT8[r.blk] + k]);
+                else st_bf16(B, col - r.k0, r.bcol + k - r.n0, lbo, v, lo);
+            }
         }
     }
 }
@@ -247,6 +299,156 @@ __global__ void k_tpage_headers(const int32_t* __restrict__ nrec, const uint32_t
     h[1] = used[p];
     h[2] = 0u;
     h[3] = 0u;
+}
+
+// ---- FP8 scales (powers of two, so scaling is exact)
+__device__ __forceinline__ float pow2_below(float lim, float v) {  // largest 2^e with v 2^e <= lim (v > 0)
+    float s = exp2f(floorf(log2f(lim / v)));
+    while (v * s > lim) s *= 0.5f;
+    return s;
+}
+
+// Per SVD block (one warp), per rank column t of V': cv scales the column
+// to at most 448; ct scales T = (sx X) V' cv back into FP8 range whatever X
+// (|T| <= 448 cv ||V'_t||_1 when |sx X| <= 448); g = cv ct.
+__global__ void k_f8_vscale(const int32_t* __restrict__ svd, int64_t nsvd, const HBlock* __restrict__ blocks,
+                            const float* __restrict__ val, const int32_t* __restrict__ offT8, float* __restrict__ cv,
+                            float* __restrict__ ct, float* __restrict__ g) {
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= nsvd) return;
+    const int32_t bi = svd[i];
+    const HBlock b = blocks[bi];
+    const float* Vp = val + b.off_val + (int64_t)b.m1 * b.q;
+    for (int t = lane; t < b.q; t += 32) {
+        float vmax = 0.f, l1 = 0.f;
+        for (int j = 0; j < b.n1; ++j) {
+            const float a = fabsf(Vp[(int64_t)j * b.q + t]);
+            vmax = fmaxf(vmax, a);
+            l1 += a;
+        }
+        const float c = vmax > 0.f ? pow2_below(448.f, vmax) : 1.f;
+        const float d = l1 > 0.f ? pow2_below(1.f, c * l1) : 1.f;
+        const int64_t o = offT8[bi] + t;
+        cv[o] = c;
+        ct[o] = d;
+        g[o] = c * d;
+    }
+}
+
+// Per tree row, the largest phase-2 FP8 operand entry before the row
+// scale: dense and CSR entries, U' entries / g.  items: (block, first row,
+// end row) -- a dense block once per row tile (its values sit in one
+// column-major slab per tile), CSR and SVD blocks once.
+__global__ void k_f8_rowmax(const int3* __restrict__ items, int64_t nitems, const HBlock* __restrict__ blocks,
+                            const float* __restrict__ val, const int32_t* __restrict__ aux,
+                            const float* __restrict__ g8, const int32_t* __restrict__ offT8,
+                            unsigned* __restrict__ rowmax) {
+    const int64_t it = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (it >= nitems) return;
+    const int3 e = items[it];
+    const HBlock b = blocks[e.x];
+    if (b.kind == VF_BLK_DENSE) {
+        const int nr = e.z - e.y;
+        const float* slab = val + b.off_val + (int64_t)(e.y - b.r0) * b.n;
+        for (int i = lane; i < nr; i += 32) {
+            float mx = 0.f;
+            for (int j = 0; j < b.n; ++j) mx = fmaxf(mx, fabsf(slab[(int64_t)j * nr + i]));
+            atomicMax(rowmax + e.y + i, __float_as_uint(mx));
+        }
+    } else if (b.kind == VF_BLK_CSR) {
+        const int32_t* rp = aux + b.off_aux;
+        for (int lr = lane; lr < b.m; lr += 32) {
+            float mx = 0.f;
+            for (int z = rp[lr]; z < rp[lr + 1]; ++z) mx = fmaxf(mx, fabsf(val[b.off_val + z]));
+            atomicMax(rowmax + b.r0 + lr, __float_as_uint(mx));
+        }
+    } else if (b.kind == VF_BLK_SVD) {
+        const int32_t* rows = aux + b.off_aux;
+        const int64_t o = offT8[e.x];
+        for (int u = lane; u < b.m1; u += 32) {
+            float mx = 0.f;
+            for (int t = 0; t < b.q; ++t) mx = fmaxf(mx, fabsf(val[b.off_val + (int64_t)u * b.q + t]) / g8[o + t]);
+            atomicMax(rowmax + rows[u], __float_as_uint(mx));
+        }
+    }
+}
+
+__global__ void k_f8_rs(const unsigned* __restrict__ rowmax, int64_t n, float* __restrict__ rs,
+                        float* __restrict__ irs) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float mx = __uint_as_float(rowmax[i]);
+    const float s = mx > 0.f ? pow2_below(448.f, mx) : 1.f;
+    rs[i] = s;
+    irs[i] = 1.f / s;
+}
+
+__global__ void k_fill1(float* __restrict__ a, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) a[i] = 1.f;
+}
+
+static vf_status tensor_fp8_scales(vf_hmat* H) {
+    vf_tensor_plan* P = H->tplan;
+    if (P->scales8) return VF_OK;
+    const std::vector<HBlock>& B = H->h_blocks;
+    const int64_t nt8 = P->n_rows_t8, n = H->nf;
+    VF_TRY(P->offT8.upload(P->h_offT8));
+    VF_TRY(P->cv8.alloc(nt8));
+    VF_TRY(P->ct8.alloc(nt8));
+    VF_TRY(P->g8.alloc(nt8));
+    VF_TRY(P->rs8.alloc(std::max<int64_t>(n, 1)));
+    VF_TRY(P->irs8.alloc(std::max<int64_t>(n, 1)));
+    for (float* a : {P->cv8.p, P->ct8.p, P->g8.p}) k_fill1<<<(unsigned)ceil_div(nt8, 256), 256>>>(a, nt8);
+    VF_TRY_CUDA(cudaGetLastError());
+    std::vector<int32_t> svd;
+    std::vector<int3> items;
+    std::vector<int32_t> tile_of_row(n, 0);
+    for (size_t k = 0; k < H->h_tile_first.size(); ++k)
+        for (int32_t r = H->h_tile_first[k]; r < H->h_tile_first[k] + H->h_tile_count[k]; ++r)
+            tile_of_row[r] = (int32_t)k;
+    for (size_t bi = 0; bi < B.size(); ++bi) {
+        const HBlock& b = B[bi];
+        if (b.kind == VF_BLK_SVD) {
+            svd.push_back((int32_t)bi);
+            items.push_back(make_int3((int)bi, b.r0, b.r0 + b.m));
+        } else if (b.kind == VF_BLK_CSR) {
+            items.push_back(make_int3((int)bi, b.r0, b.r0 + b.m));
+        } else if (b.kind == VF_BLK_DENSE) {
+            for (int32_t r = b.r0; r < b.r0 + b.m;) {
+                const int32_t k = tile_of_row[r];
+                const int32_t re = std::min(b.r0 + b.m, H->h_tile_first[k] + H->h_tile_count[k]);
+                items.push_back(make_int3((int)bi, r, re));
+                r = re;
+            }
+        }
+    }
+    dbuf<int32_t> dsvd;
+    dbuf<int3> ditems;
+    dbuf<unsigned> rowmax;
+    VF_TRY(rowmax.alloc(std::max<int64_t>(n, 1)));
+    VF_TRY_CUDA(cudaMemset(rowmax.p, 0, std::max<int64_t>(n, 1) * sizeof(unsigned)));
+    if (!svd.empty()) {
+        VF_TRY(dsvd.upload(svd));
+        k_f8_vscale<<<(unsigned)ceil_div((int64_t)svd.size() * 32, 256), 256>>>(
+            dsvd.p, (int64_t)svd.size(), H->blocks.p, H->val.p, P->offT8.p, P->cv8.p, P->ct8.p, P->g8.p);
+        VF_TRY_CUDA(cudaGetLastError());
+    }
+    if (!items.empty()) {
+        VF_TRY(ditems.upload(items));
+        k_f8_rowmax<<<(unsigned)ceil_div((int64_t)items.size() * 32, 256), 256>>>(
+            ditems.p, (int64_t)items.size(), H->blocks.p, H->val.p, H->aux.p, P->g8.p, P->offT8.p, rowmax.p);
+        VF_TRY_CUDA(cudaGetLastError());
+    }
+    if (n > 0) {
+        k_f8_rs<<<(unsigned)ceil_div(n, 256), 256>>>(rowmax.p, n, P->rs8.p, P->irs8.p);
+        VF_TRY_CUDA(cudaGetLastError());
+    }
+    VF_TRY_CUDA(cudaDeviceSynchronize());
+    P->scales8 = true;
+    return VF_OK;
 }
 
 // Longest-processing-time assignment of items (costs) to ncta lists.
@@ -272,7 +474,7 @@ static std::vector<std::vector<int32_t>> lpt(const std::vector<int64_t>& cost, i
 static vf_status pack_pages(vf_hmat* H, std::vector<TRec>& recs, const std::vector<std::vector<int32_t>>& cta_groups,
                             const std::vector<std::pair<int64_t, int64_t>>& group_recs, dbuf<unsigned char>& pool,
                             dbuf<uint32_t>& used_d, dbuf<int32_t>& cta_pages, int64_t* bytes,
-                            int64_t* kind_bytes) {
+                            int64_t* kind_bytes, const F8Scales& f8) {
     const int32_t ncta = (int32_t)cta_groups.size();
     std::vector<int32_t> cp(ncta + 1, 0);
     std::vector<uint32_t> used;
@@ -289,7 +491,7 @@ static vf_status pack_pages(vf_hmat* H, std::vector<TRec>& recs, const std::vect
                     ordered.push_back(r);
                     continue;
                 }
-                const uint32_t sz = (uint32_t)(kTRHdr + r.S * r.K16 * r.N16 * 2);
+                const uint32_t sz = (uint32_t)(kTRHdr + set_body(r.S, r.K16, r.N16));
                 kind_bytes[r.kind] += sz;
                 if (fresh || used.back() + sz > (uint32_t)kTP) {
                     used.push_back(kTPHdr);
@@ -316,7 +518,7 @@ static vf_status pack_pages(vf_hmat* H, std::vector<TRec>& recs, const std::vect
     VF_TRY(dr.upload(ordered));
     dbuf<int32_t> dn;
     VF_TRY(dn.upload(nrec));
-    k_tpack<<<(unsigned)ordered.size(), 256>>>(dr.p, H->blocks.p, H->val.p, H->aux.p, pool.p);
+    k_tpack<<<(unsigned)ordered.size(), 256>>>(dr.p, H->blocks.p, H->val.p, H->aux.p, f8, pool.p);
     VF_TRY_CUDA(cudaGetLastError());
     k_tpage_headers<<<(unsigned)ceil_div(np, 256), 256>>>(dn.p, used_d.p, np, pool.p);
     VF_TRY_CUDA(cudaGetLastError());
@@ -329,11 +531,11 @@ static inline int32_t r16(int64_t x) { return (int32_t)((x + 15) / 16 * 16); }
 // The invariants every record must meet (checked on the host before upload).
 static vf_status check_records(const std::vector<TRec>& recs, int max_col, int64_t rows_x, int64_t rows_t) {
     for (const TRec& r : recs) {
-        const bool ok = r.K16 >= 16 && r.K16 <= cfg_kmax(r.S) && r.K16 % 16 == 0 && r.N16 >= 16 && r.N16 <= max_col &&
-                        r.N16 % 16 == 0 && r.coloff >= 0 && r.coloff % 16 == 0 && r.coloff + r.N16 <= max_col &&
-                        r.a_row0 >= 0 && r.a_row0 % 8 == 0 &&
-                        (int64_t)r.a_row0 + r.K16 <= (r.a_src ? rows_t : rows_x) &&
-                        (r.S == 1 || r.S == 2) && kTPHdr + kTRHdr + r.S * r.K16 * r.N16 * 2 <= kTP;
+        const bool ok = (r.S == 1 || r.S == 2 || r.S == 3) && r.K16 >= set_kg(r.S) && r.K16 <= cfg_kmax(r.S) &&
+                        r.K16 % set_kg(r.S) == 0 && r.N16 >= 16 && r.N16 <= max_col && r.N16 % 16 == 0 &&
+                        r.coloff >= 0 && r.coloff % 16 == 0 && r.coloff + r.N16 <= max_col && r.a_row0 >= 0 &&
+                        r.a_row0 % set_al(r.S) == 0 && (int64_t)r.a_row0 + r.K16 <= (r.a_src ? rows_t : rows_x) &&
+                        kTPHdr + kTRHdr + set_body(r.S, r.K16, r.N16) <= kTP;
         VF_CHECK(ok, VF_E_INVAL,
                  "tensor plan: bad record (kind %d, K %d, N %d, col %d, src %d, row %d)", r.kind, r.K16, r.N16,
                  r.coloff, r.a_src, r.a_row0);
@@ -341,12 +543,12 @@ static vf_status check_records(const std::vector<TRec>& recs, int max_col, int64
     return VF_OK;
 }
 
-// Runs of occupied 16-column chunks (occ[c] != 0), each at most kmax
+// Runs of occupied kg-column chunks (occ[c] != 0), each at most kmax
 // columns: (first chunk, chunks).  K ranges with no nonzero in any of a
 // record's pieces are not copied or multiplied.
-static std::vector<std::pair<int32_t, int32_t>> chunk_runs(const std::vector<char>& occ, int32_t kmax) {
+static std::vector<std::pair<int32_t, int32_t>> chunk_runs(const std::vector<char>& occ, int32_t kmax, int32_t kg) {
     std::vector<std::pair<int32_t, int32_t>> out;
-    const int32_t n = (int32_t)occ.size(), lim = kmax / 16;
+    const int32_t n = (int32_t)occ.size(), lim = kmax / kg;
     for (int32_t c = 0; c < n;) {
         if (!occ[c]) {
             ++c;
@@ -387,11 +589,24 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
             nt += hb[i].q;
         }
         P0->n_rows_t = r16(nt) + 32;
+        P0->h_offT8.assign(hb.size(), -1);
+        nt = 0;
+        for (size_t k = 0; k < svd.size(); ++k) {
+            const int32_t i = svd[k];
+            if (k == 0 || hb[i].r0 != hb[svd[k - 1]].r0 || hb[i].m != hb[svd[k - 1]].m) nt = (nt + 31) / 32 * 32;
+            P0->h_offT8[i] = (int32_t)nt;
+            nt += hb[i].q;
+        }
+        P0->n_rows_t8 = (nt + 31) / 32 * 32 + 128;
         H->tplan = P0.release();
     }
     vf_tensor_plan* P = H->tplan;
     vf_tensor_set* T = &P->set[S - 1];
     if (T->built) return VF_OK;
+    const int32_t KG = set_kg(S), AL = set_al(S), TB = set_terms(S) * set_es(S);
+    auto rkg = [&](int64_t x) { return (int32_t)((x + KG - 1) / KG * KG); };
+    const std::vector<int32_t>& offT = S == 3 ? P->h_offT8 : P->h_offT;
+    if (S == 3) VF_TRY(tensor_fp8_scales(H));
     const std::vector<HBlock>& B = H->h_blocks;
     std::vector<int32_t> haux;
     if (H->n_aux > 0) VF_TRY(H->aux.download(haux));
@@ -456,7 +671,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
         tile_recs[k].first = (int64_t)recs2.size();
         const int64_t first = (int64_t)recs2.size();
         auto add_cost = [&](const TRec& t) {
-            tile_cost[k] += S * ((int64_t)t.K16 * t.N16 * 2 + (int64_t)t.K16 * kPanel * 2) + rec_cost;
+            tile_cost[k] += (int64_t)TB * ((int64_t)t.K16 * t.N16 + (int64_t)t.K16 * kPanel) + rec_cost;
         };
         // dense / CSR pieces grouped by column cluster
         std::vector<Piece>& dp = dpieces[k];
@@ -476,23 +691,23 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
             const int32_t coloff = ((lo - stf[k]) / 16) * 16;
             const int32_t row_base = stf[k] + coloff;
             const int32_t n16 = r16(hi - row_base);
-            const int32_t kmax = std::min<int32_t>(cfg_kmax(S), ((kTP - kTPHdr - kTRHdr) / (n16 * 2 * S)) / 16 * 16);
-            const int32_t c8 = (b0.c0 / 8) * 8;
-            const int32_t ktot = r16(b0.c0 + b0.n - c8);
-            // 16-column chunks holding a nonzero of some piece (dense pieces: all)
-            std::vector<char> occ(ktot / 16, 0);
+            const int32_t kmax = std::min<int32_t>(cfg_kmax(S), ((kTP - kTPHdr - kTRHdr) / (n16 * TB)) / KG * KG);
+            const int32_t c8 = (b0.c0 / AL) * AL;
+            const int32_t ktot = rkg(b0.c0 + b0.n - c8);
+            // KG-column chunks holding a nonzero of some piece (dense pieces: all)
+            std::vector<char> occ(ktot / KG, 0);
             for (size_t t = i; t < j; ++t) {
                 const HBlock& b = B[dp[t].blk];
                 if (b.kind == VF_BLK_DENSE) {
-                    for (int32_t c = (b.c0 - c8) / 16; c <= (b.c0 + b.n - 1 - c8) / 16; ++c) occ[c] = 1;
+                    for (int32_t c = (b.c0 - c8) / KG; c <= (b.c0 + b.n - 1 - c8) / KG; ++c) occ[c] = 1;
                 } else {
                     const int32_t* rp = haux.data() + b.off_aux;
                     const int32_t* ci = rp + b.m + 1;
                     for (int32_t r = dp[t].rs; r < dp[t].re; ++r)
-                        for (int32_t z = rp[r - b.r0]; z < rp[r - b.r0 + 1]; ++z) occ[(ci[z] - c8) / 16] = 1;
+                        for (int32_t z = rp[r - b.r0]; z < rp[r - b.r0 + 1]; ++z) occ[(ci[z] - c8) / KG] = 1;
                 }
             }
-            for (const auto& run : chunk_runs(occ, kmax)) {
+            for (const auto& run : chunk_runs(occ, kmax, KG)) {
                 for (size_t t = i; t < j; ++t) {
                     TRec u{};
                     u.kind = B[dp[t].blk].kind == VF_BLK_DENSE ? TREC_DENSE : TREC_CSR;
@@ -502,8 +717,8 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
                     u.coloff = coloff;
                     u.row_base = row_base;
                     u.N16 = n16;
-                    u.k0 = c8 + 16 * run.first;
-                    u.K16 = 16 * run.second;
+                    u.k0 = c8 + KG * run.first;
+                    u.K16 = KG * run.second;
                     u.a_src = 0;
                     u.a_row0 = u.k0;
                     u.S = S;
@@ -519,11 +734,11 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
         // its own K range (B row = T row - the chunk's first)
         std::vector<Piece>& sp = spieces[k];
         std::stable_sort(sp.begin(), sp.end(),
-                         [&](const Piece& x, const Piece& y) { return P->h_offT[x.blk] < P->h_offT[y.blk]; });
+                         [&](const Piece& x, const Piece& y) { return offT[x.blk] < offT[y.blk]; });
         for (size_t i = 0; i < sp.size();) {
             size_t j = i + 1;
             while (j < sp.size() && B[sp[j].blk].r0 == B[sp[i].blk].r0 && B[sp[j].blk].m == B[sp[i].blk].m &&
-                   P->h_offT[sp[j].blk] == P->h_offT[sp[j - 1].blk] + B[sp[j - 1].blk].q)
+                   offT[sp[j].blk] == offT[sp[j - 1].blk] + B[sp[j - 1].blk].q)
                 ++j;
             TRec t{};
             t.kind = TREC_SVDU;
@@ -534,16 +749,16 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
             t.N16 = r16(t.re - t.row_base);
             t.a_src = 1;
             t.S = S;
-            const int32_t kmax = std::min<int32_t>(cfg_kmax(S), ((kTP - kTPHdr - kTRHdr) / (t.N16 * 2 * S)) / 16 * 16);
-            // from the 8-row boundary at or before the run (rows of other
+            const int32_t kmax = std::min<int32_t>(cfg_kmax(S), ((kTP - kTPHdr - kTRHdr) / (t.N16 * TB)) / KG * KG);
+            // from the AL-row boundary at or before the run (rows of other
             // blocks there meet zero B rows)
-            const int32_t base = P->h_offT[sp[i].blk] / 8 * 8;
-            const int32_t ktot = r16(P->h_offT[sp[j - 1].blk] + B[sp[j - 1].blk].q - base);
+            const int32_t base = offT[sp[i].blk] / AL * AL;
+            const int32_t ktot = rkg(offT[sp[j - 1].blk] + B[sp[j - 1].blk].q - base);
             for (int32_t kc = 0; kc < ktot; kc += kmax) {
                 const int32_t a0 = base + kc, kk = std::min(kmax, ktot - kc);
                 bool head = true;
                 for (size_t u = i; u < j; ++u) {
-                    const int32_t o = P->h_offT[sp[u].blk], q = B[sp[u].blk].q;
+                    const int32_t o = offT[sp[u].blk], q = B[sp[u].blk].q;
                     if (o + q <= a0 || o >= a0 + kk) continue;
                     TRec f = t;
                     f.blk = sp[u].blk;
@@ -562,7 +777,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
             // a (super-)tile with no blocks still needs its epilogue: one empty record
             TRec t{};
             t.kind = TREC_EMPTY;
-            t.K16 = 16;
+            t.K16 = KG;
             t.N16 = 16;
             t.rs = t.re = stf[k];
             t.row_base = t.rs;
@@ -581,7 +796,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
         std::vector<TRec> heads;
         for (const TRec& t : recs2)
             if (t.hdr) heads.push_back(t);
-        VF_TRY(check_records(heads, r2, P->n_rows_x, P->n_rows_t));
+        VF_TRY(check_records(heads, r2, P->n_rows_x, S == 3 ? P->n_rows_t8 : P->n_rows_t));
     }
     T->nst = nst;
     segp.push_back((int32_t)nst);
@@ -601,7 +816,9 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
         VF_TRY(T->cta_tiles.upload(tiles));
         VF_TRY(T->cta_tile_ptr.upload(ptr));
     }
-    VF_TRY(pack_pages(H, recs2, lists2, tile_recs, T->pages2, T->used2, T->cta_pages2, &T->bytes2, T->kind_bytes));
+    const F8Scales f8s = S == 3 ? F8Scales{P->rs8.p, P->g8.p, P->cv8.p, P->offT8.p} : F8Scales{};
+    VF_TRY(pack_pages(H, recs2, lists2, tile_recs, T->pages2, T->used2, T->cta_pages2, &T->bytes2, T->kind_bytes,
+                      f8s));
 
     // ---- phase 1: SVD blocks with the same column cluster (the same X rows)
     // form groups whose ranks fit one accumulator region; a group's records
@@ -650,21 +867,21 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
         int32_t n16 = 0;
         for (const Part& pt : g) n16 += pt.nsub;
         n16 = r16(n16);  // the parts' columns side by side, padded once
-        const int32_t kmax = std::min<int32_t>(cfg_kmax(S), ((kTP - kTPHdr - kTRHdr) / (n16 * 2 * S)) / 16 * 16);
-        const int32_t c8 = (b0.c0 / 8) * 8;
-        const int32_t ktot = r16(b0.c0 + b0.n - c8);
+        const int32_t kmax = std::min<int32_t>(cfg_kmax(S), ((kTP - kTPHdr - kTRHdr) / (n16 * TB)) / KG * KG);
+        const int32_t c8 = (b0.c0 / AL) * AL;
+        const int32_t ktot = rkg(b0.c0 + b0.n - c8);
         const int64_t first = (int64_t)recs1.size();
         int64_t cost = 0;
-        // 16-column chunks holding a compacted column of some block of the group
-        std::vector<char> occ(ktot / 16, 0);
+        // KG-column chunks holding a compacted column of some block of the group
+        std::vector<char> occ(ktot / KG, 0);
         for (const Part& pt : g) {
             const HBlock& b = B[pt.blk];
             const int32_t* cols = haux.data() + b.off_aux + b.m1;
-            for (int32_t z = 0; z < b.n1; ++z) occ[(cols[z] - c8) / 16] = 1;
+            for (int32_t z = 0; z < b.n1; ++z) occ[(cols[z] - c8) / KG] = 1;
         }
-        const auto runs = chunk_runs(occ, kmax);
+        const auto runs = chunk_runs(occ, kmax, KG);
         for (size_t ri = 0; ri < runs.size(); ++ri) {
-            const int32_t kc = 16 * runs[ri].first, kk = 16 * runs[ri].second;
+            const int32_t kc = KG * runs[ri].first, kk = KG * runs[ri].second;
             int32_t bcol = 0;
             for (size_t pi = 0; pi < g.size(); ++pi) {
                 TRec t{};
@@ -685,7 +902,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
                 recs1.push_back(t);
                 bcol += g[pi].nsub;
             }
-            cost += S * ((int64_t)kk * n16 * 2 + (int64_t)kk * kPanel * 2) + rec_cost;
+            cost += (int64_t)TB * ((int64_t)kk * n16 + (int64_t)kk * kPanel) + rec_cost;
         }
         group_recs1.push_back({first, (int64_t)recs1.size()});
         group_cost.push_back(cost);
@@ -694,7 +911,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
         std::vector<TRec> heads;
         for (const TRec& t : recs1)
             if (t.hdr) heads.push_back(t);
-        VF_TRY(check_records(heads, cfg_region(S), P->n_rows_x, P->n_rows_t));
+        VF_TRY(check_records(heads, cfg_region(S), P->n_rows_x, S == 3 ? P->n_rows_t8 : P->n_rows_t));
     }
     T->ncta1 = (int32_t)std::min<int64_t>((int64_t)nsm * cfg_ctas(S), (int64_t)group_cost.size());
     if (T->ncta1 > 0) {
@@ -707,7 +924,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
                 int32_t col = 0;
                 for (size_t pi = 0; pi < groups[gi].size(); ++pi) {
                     const Part& pt = groups[gi][pi];
-                    units.push_back(P->h_offT[pt.blk] + pt.n0);
+                    units.push_back(offT[pt.blk] + pt.n0);
                     units.push_back(pt.nsub);
                     units.push_back(col);
                     units.push_back(pi + 1 == groups[gi].size() ? 1 : 0);
@@ -719,7 +936,7 @@ vf_status tensor_plan_build(vf_hmat* H, int S) {
         VF_TRY(T->cta_units.upload(units));
         VF_TRY(T->cta_unit_ptr.upload(ptr));
         VF_TRY(pack_pages(H, recs1, lists1, group_recs1, T->pages1, T->used1, T->cta_pages1, &T->bytes1,
-                          T->kind_bytes));
+                          T->kind_bytes, f8s));
     }
     T->built = true;
     return VF_OK;
@@ -741,6 +958,18 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// kind::f8f6f4 instruction descriptor: D F32, A and B E4M3, both K-major, M = 128
+__device__ __forceinline__ uint32_t mma_idesc_f8(int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kPanel >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
@@ -787,6 +1016,13 @@ __device__ __forceinline__ bool bwait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ int64_t panel_off(int64_t row, int m) {
     return (row >> 3) * 2048 + (m >> 3) * 128 + (row & 7) * 16 + (m & 7) * 2;
 }
+// FP8 panel element (row, m): K-major, 16 consecutive rows of one RHS in 16 bytes
+__device__ __forceinline__ int64_t panel_off8(int64_t row, int m) {
+    return (row >> 4) * 2048 + (m >> 3) * 128 + (m & 7) * 16 + (row & 15);
+}
+__device__ __forceinline__ unsigned char to_e4m3(float v) {
+    return (unsigned char)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+}
 
 struct TSmem {
     uint64_t page_full[kMaxPStages], page_empty[kMaxPStages], a_full[kMaxSlots], a_empty[kMaxSlots], d_full[2],
@@ -807,6 +1043,7 @@ static_assert(sizeof(TSmem) <= 1024, "barrier block");
 struct TPanels {
     const unsigned char* X[2];
     unsigned char* T[2];
+    const float* ct8;          // FP8: per T row, the scale of its stored values
     int64_t rows_x, rows_t;
     int64_t xstride, tstride;
     const int* par;            // ping-pong selection (see TEpi): X[0] = Xalt when *par == 1
@@ -885,9 +1122,9 @@ __device__ void t_producer(TSmem& S, unsigned char* stages, unsigned char* abuf,
                 const uint4 h1 = *reinterpret_cast<const uint4*>(pg + off + 16);
                 const int K16 = (int)h0.x, N16 = (int)h0.y;
                 // self-check: shapes, the record inside the page, the A range inside its panel
-                if (K16 < 16 || K16 > kmax_of<NS>() || (K16 & 15) || N16 < 16 || N16 > max_col || (N16 & 15) ||
-                    (int)h0.z + N16 > max_col || off + kTRHdr + (uint32_t)(NS * K16 * N16 * 2) > pused ||
-                    (h1.x & 7u) || (int64_t)h1.x + K16 > (h0.w ? pn.rows_t : pn.rows_x))
+                if (K16 < set_kg(NS) || K16 > kmax_of<NS>() || (K16 % set_kg(NS)) || N16 < 16 || N16 > max_col ||
+                    (N16 & 15) || (int)h0.z + N16 > max_col || off + kTRHdr + (uint32_t)set_body(NS, K16, N16) > pused ||
+                    (h1.x % set_al(NS)) || (int64_t)h1.x + K16 > (h0.w ? pn.rows_t : pn.rows_x))
                     goto oob;
                 for (int kc = 0; kc < K16; kc += SL::CK, ++chunk) {
                     if (next < npl) {
@@ -897,17 +1134,19 @@ __device__ void t_producer(TSmem& S, unsigned char* stages, unsigned char* abuf,
                     const int slot = chunk % SL::NSLOT, use = chunk / SL::NSLOT;
                     if (use >= 1 && !bwait(&S.a_empty[slot], (uint32_t)((use - 1) & 1))) goto fail;
                     const int ck = min(SL::CK, K16 - kc);
-                    const uint32_t tb = (uint32_t)ck * kPanel * 2;
-                    const int64_t roff = (int64_t)((h1.x + kc) >> 3) * 2048;
-                    mbar_arrive_expect_tx(&S.a_full[slot], NP * NS * tb);
+                    // panel rows are aligned to whole core-matrix groups: row r starts at r x 128 x es bytes
+                    const uint32_t tb = (uint32_t)ck * kPanel * set_es(NS);
+                    const int64_t roff = (int64_t)(h1.x + kc) * kPanel * set_es(NS);
+                    mbar_arrive_expect_tx(&S.a_full[slot], NP * set_terms(NS) * tb);
                     for (int q = 0; q < NP; ++q)
-                        for (int t = 0; t < NS; ++t) {
+                        for (int t = 0; t < set_terms(NS); ++t) {
                             const unsigned char* src =
                                 h0.w ? pn.T[t] + q * pn.tstride + roff : pn.X[t] + q * pn.xstride + roff;
-                            bulk_g2s(abuf + slot * SL::BYTES + (q * NS + t) * SL::TERM, src, tb, &S.a_full[slot]);
+                            bulk_g2s(abuf + slot * SL::BYTES + (q * set_terms(NS) + t) * SL::TERM, src, tb,
+                                     &S.a_full[slot]);
                         }
                 }
-                off += kTRHdr + (uint32_t)(NS * K16 * N16 * 2);
+                off += kTRHdr + (uint32_t)set_body(NS, K16, N16);
             }
         }
         if (S.abort) return;
@@ -950,24 +1189,29 @@ __device__ void t_issuer(TSmem& S, unsigned char* stages, unsigned char* abuf, i
                 }
                 const uint32_t dt = S.tmem_base + (uint32_t)(d * REGW + coloff);
                 const uint32_t bsa = smem_u32(pg + off + kTRHdr);
-                const uint32_t blbo = (uint32_t)(N16 / 8) * 128;
-                const uint32_t idesc = mma_idesc(N16);
+                // B: BF16 MN-major (8-row K groups of N16 x 16 bytes) or FP8 K-major
+                // (16-column K groups of N16 x 16 bytes); one MMA step spans two groups
+                const uint32_t blbo = NS == 3 ? (uint32_t)N16 * 16 : (uint32_t)(N16 / 8) * 128;
+                const uint32_t idesc = NS == 3 ? mma_idesc_f8(N16) : mma_idesc(N16);
                 const uint32_t blo = (uint32_t)(K16 * N16 * 2);
+                constexpr int KG = set_kg(NS);
                 for (int kc = 0; kc < K16; kc += SL::CK, ++chunk) {
                     const int slot = chunk % SL::NSLOT;
                     if (!bwait(&S.a_full[slot], (uint32_t)((chunk / SL::NSLOT) & 1))) goto fail;
                     const uint32_t asa = smem_u32(abuf + slot * SL::BYTES);
                     const int ck = min(SL::CK, K16 - kc);
-                    for (int kk = 0; kk < ck / 16; ++kk) {
-                        const int ks = kc / 16 + kk;  // K step within the record
+                    for (int kk = 0; kk < ck / KG; ++kk) {
+                        const int ks = kc / KG + kk;  // K step within the record
                         const uint64_t bh = mma_desc(bsa + ks * 2 * blbo, blbo, 128);
                         const int acc = (ks == 0 && (flags & TR_USTART)) ? 0 : 1;
 #pragma unroll
                         for (int q = 0; q < NP; ++q) {
-                            const uint32_t aq = asa + (uint32_t)(q * NS * SL::TERM + kk * 4096);
+                            // one step of A: 16 BF16 rows x 256 bytes, or 32 FP8 rows x 128 bytes
+                            const uint32_t aq = asa + (uint32_t)(q * set_terms(NS) * SL::TERM + kk * 4096);
                             const uint64_t ah = mma_desc(aq, 2048, 128);
                             const uint32_t dq = dt + (uint32_t)(q * kRegion);
-                            mma_bf16(dq, ah, bh, idesc, acc);
+                            if (NS == 3) mma_f8(dq, ah, bh, idesc, acc);
+                            else mma_bf16(dq, ah, bh, idesc, acc);
                             if (NS == 2) {
                                 mma_bf16(dq, mma_desc(aq + SL::TERM, 2048, 128), bh, idesc, 1);
                                 mma_bf16(dq, ah, mma_desc(bsa + blo + ks * 2 * blbo, blbo, 128), idesc, 1);
@@ -981,7 +1225,7 @@ __device__ void t_issuer(TSmem& S, unsigned char* stages, unsigned char* abuf, i
                     dcount[d]++;
                     d = NREG == 1 ? 0 : d ^ 1;
                 }
-                off += kTRHdr + (uint32_t)(NS * K16 * N16 * 2);
+                off += kTRHdr + (uint32_t)set_body(NS, K16, N16);
             }
         }
         mma_commit(&S.page_empty[s]);
@@ -1142,7 +1386,12 @@ __global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase1(const unsig
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         if (b16 + j < col || b16 + j >= col + nc) continue;
-                        const int64_t o = q * pn.tstride + panel_off(offT + b16 + j - col, m);
+                        const int64_t row = offT + b16 + j - col;
+                        if (NS == 3) {
+                            pn.T[0][q * pn.tstride + panel_off8(row, m)] = to_e4m3(v[j] * pn.ct8[row]);
+                            continue;
+                        }
+                        const int64_t o = q * pn.tstride + panel_off(row, m);
                         const __nv_bfloat16 hi = __float2bfloat16_rn(v[j]);
                         *reinterpret_cast<__nv_bfloat16*>(pn.T[0] + o) = hi;
                         if (NS == 2)
@@ -1216,6 +1465,9 @@ __global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase2(const unsig
                 const int col = ep.p0 + q * kPanel + m;  // RHS column
                 const bool live = col < ep.R;
                 unsigned char* xnext = ep.Xnext ? ep.Xnext + q * ep.xstride : nullptr;
+                // FP8: D = sx(column) rs(row) (F X); undo both
+                const float isx = (NS == 3 && live) ? ep.isx[col] : 1.f;
+                const float sxn = (NS == 3 && live) ? ep.sx[col] : 1.f;
                 double ss = 0.0;
                 for (int c0 = 0; c0 < tc; c0 += 16) {
                     float v[16];
@@ -1226,6 +1478,7 @@ __global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase2(const unsig
                         if (c0 + j >= tc) break;
                         const int64_t p = tf + c0 + j;
                         const int64_t o = (int64_t)col * ep.n + p;
+                        if (NS == 3) v[j] *= isx * ep.irs[p];
                         if (ep.mode == 0) {
                             ep.Y[o] = v[j];
                         } else if (ep.mode == 2) {
@@ -1238,7 +1491,8 @@ __global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase2(const unsig
                             const float dd = bn - ep.Bold[o];
                             ss += (double)dd * dd;
                             ep.Y[o] = bn;
-                            if (xnext)
+                            if (xnext && NS == 3) xnext[panel_off8(p, m)] = to_e4m3(bn * sxn);
+                            else if (xnext)
                                 *reinterpret_cast<__nv_bfloat16*>(xnext + panel_off(p, m)) = __float2bfloat16_rn(bn);
                         }
                     }
@@ -1273,6 +1527,48 @@ __global__ void k_to_panel(const float* __restrict__ src, int64_t ld, const int3
     if (lo) *reinterpret_cast<uint4*>(lo + o) = *reinterpret_cast<const uint4*>(vl);
 }
 
+// FP32 column-major (tree order, or face order through perm) -> FP8 panel,
+// x sx[column]: one thread per (16-row group, RHS), one 16-byte store.
+__global__ void k_to_panel8(const float* __restrict__ src, int64_t ld, const int32_t* __restrict__ perm, int64_t n,
+                            int R, int p0, int64_t rows, const float* __restrict__ sx, unsigned char* __restrict__ out) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // (16-row group, column)
+    if (e >= (rows >> 4) * kPanel) return;
+    const int64_t g = e >> 7;
+    const int m = (int)(e & 127), c = p0 + m;
+    __align__(16) unsigned char v[16];
+    const float s = c < R ? sx[c] : 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int64_t row = g * 16 + i;
+        float x = 0.f;
+        if (row < n && c < R) x = src[(int64_t)c * ld + (perm ? perm[row] : row)];
+        v[i] = to_e4m3(x * s);
+    }
+    *reinterpret_cast<uint4*>(out + g * 2048 + (m >> 3) * 128 + (m & 7) * 16) = *reinterpret_cast<const uint4*>(v);
+}
+
+// Per column c < R of an FP32 column-major array: sx = the largest power of
+// two with sx max|x| <= 448 h (h: headroom for growth, e.g. Jacobi iterates
+// of a right-hand side), and 1 / sx.  One CTA per column.
+__global__ void __launch_bounds__(256) k_fp8_colscale(const float* __restrict__ src, int64_t ld,
+                                                      const int32_t* __restrict__ perm, int64_t n, float h,
+                                                      float* __restrict__ sx, float* __restrict__ isx) {
+    const int c = blockIdx.x;
+    float mx = 0.f;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+        mx = fmaxf(mx, fabsf(src[(int64_t)c * ld + (perm ? perm[i] : i)]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __shared__ float wm[8];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) mx = fmaxf(mx, wm[w]);
+        const float s = mx > 0.f ? pow2_below(448.f * h, mx) : 1.f;
+        sx[c] = s;
+        isx[c] = 1.f / s;
+    }
+}
+
 // ------------------------------------------------------------ host entry
 template <int NS, int NP>
 static cudaError_t tensor_attrs_cfg() {
@@ -1291,6 +1587,8 @@ static vf_status tensor_attrs() {
     if (e == cudaSuccess) e = tensor_attrs_cfg<1, 2>();
     if (e == cudaSuccess) e = tensor_attrs_cfg<2, 1>();
     if (e == cudaSuccess) e = tensor_attrs_cfg<2, 2>();
+    if (e == cudaSuccess) e = tensor_attrs_cfg<3, 1>();
+    if (e == cudaSuccess) e = tensor_attrs_cfg<3, 2>();
     VF_TRY_CUDA(e);
     done = true;
     return VF_OK;
@@ -1304,6 +1602,27 @@ vf_status tensor_prepare(vf_hmat* H, int S) {
 
 int64_t tensor_panel_bytes_x(const vf_hmat* H) { return H->tplan->n_rows_x * kPanel * 2; }
 int64_t tensor_panel_bytes_t(const vf_hmat* H) { return H->tplan->n_rows_t * kPanel * 2; }
+int64_t tensor_panel_bytes_x8(const vf_hmat* H) { return H->tplan->n_rows_x * kPanel; }
+int64_t tensor_panel_bytes_t8(const vf_hmat* H) { return H->tplan->n_rows_t8 * kPanel; }
+
+vf_status tensor_to_panel8(const vf_hmat* H, const float* X, int64_t ld, const int32_t* perm, int R, int p0,
+                           const float* sx, unsigned char* out, cudaStream_t st) {
+    const int64_t rows = H->tplan->n_rows_x;
+    k_to_panel8<<<(unsigned)ceil_div((rows >> 4) * kPanel, 256), 256, 0, st>>>(X, ld, perm, H->nf, R, p0, rows, sx,
+                                                                                out);
+    VF_TRY_CUDA(cudaGetLastError());
+    return VF_OK;
+}
+
+vf_status tensor_fp8_colscale(const vf_hmat* H, const float* X, int64_t ld, const int32_t* perm, int R, float headroom,
+                              float* sx, float* isx, cudaStream_t st) {
+    if (R <= 0) return VF_OK;
+    k_fp8_colscale<<<(unsigned)R, 256, 0, st>>>(X, ld, perm, H->nf, headroom, sx, isx);
+    VF_TRY_CUDA(cudaGetLastError());
+    return VF_OK;
+}
+
+const float* tensor_fp8_irs(const vf_hmat* H) { return H->tplan->irs8.p; }
 int64_t tensor_page_bytes(const vf_hmat* H, int S) { return H->tplan->set[S - 1].bytes1 + H->tplan->set[S - 1].bytes2; }
 
 vf_status tensor_to_panel(const vf_hmat* H, const float* X, int64_t ld, const int32_t* perm, int R, int p0,
@@ -1329,7 +1648,8 @@ static void tensor_launch(const vf_tensor_set& T, const TPanels& pn, const TEpi&
 // the panel sizes.
 vf_status tensor_multiply(const vf_hmat* H, int S, int np, const unsigned char* Xhi, const unsigned char* Xlo,
                           unsigned char* Thi, unsigned char* Tlo, const TEpi& ep, int* status, cudaStream_t st) {
-    VF_CHECK((np == 1 || np == 2) && (S == 1 || S == 2), VF_E_INVAL, "tensor multiply: %d panels, S = %d", np, S);
+    VF_CHECK((np == 1 || np == 2) && (S == 1 || S == 2 || S == 3), VF_E_INVAL, "tensor multiply: %d panels, S = %d",
+             np, S);
     const vf_tensor_plan* P = H->tplan;
     const vf_tensor_set& T = P->set[S - 1];
     TPanels pn{};
@@ -1338,12 +1658,15 @@ vf_status tensor_multiply(const vf_hmat* H, int S, int np, const unsigned char* 
     pn.T[0] = Thi;
     pn.T[1] = Tlo;
     pn.rows_x = P->n_rows_x;
-    pn.rows_t = P->n_rows_t;
-    pn.xstride = tensor_panel_bytes_x(H);
-    pn.tstride = tensor_panel_bytes_t(H);
+    pn.rows_t = S == 3 ? P->n_rows_t8 : P->n_rows_t;
+    pn.xstride = S == 3 ? tensor_panel_bytes_x8(H) : tensor_panel_bytes_x(H);
+    pn.tstride = S == 3 ? tensor_panel_bytes_t8(H) : tensor_panel_bytes_t(H);
+    pn.ct8 = S == 3 ? P->ct8.p : nullptr;
     pn.par = ep.par;
     pn.Xalt = ep.Xalt;
-    if (S == 2 && np == 2) tensor_launch<2, 2>(T, pn, ep, status, st);
+    if (S == 3 && np == 2) tensor_launch<3, 2>(T, pn, ep, status, st);
+    else if (S == 3) tensor_launch<3, 1>(T, pn, ep, status, st);
+    else if (S == 2 && np == 2) tensor_launch<2, 2>(T, pn, ep, status, st);
     else if (S == 2) tensor_launch<2, 1>(T, pn, ep, status, st);
     else if (np == 2) tensor_launch<1, 2>(T, pn, ep, status, st);
     else tensor_launch<1, 1>(T, pn, ep, status, st);
@@ -1361,8 +1684,9 @@ int tensor_kernels(const vf_hmat* H, int S) { return (H->tplan->set[S - 1].ncta1
 // The tensor pages of a matrix (built here if not yet): bytes per set and by record kind.
 extern "C" vf_status vf_hmat_tensor_bytes(const vf_hmat* h, int32_t terms, int64_t* total, int64_t* by_kind) {
     vf::clear_error();
-    VF_CHECK(h && total && (terms == 1 || terms == 2), VF_E_INVAL, "vf_hmat_tensor_bytes: bad argument");
-    VF_CHECK(h->has_bf16, VF_E_INVAL, "vf_hmat_tensor_bytes: the matrix has no BF16 copy");
+    VF_CHECK(h && total && (terms == 1 || terms == 2 || terms == 3), VF_E_INVAL, "vf_hmat_tensor_bytes: bad argument");
+    VF_CHECK(terms == 3 ? h->has_fp8 : h->has_bf16, VF_E_INVAL, "vf_hmat_tensor_bytes: the matrix has no %s copy",
+             terms == 3 ? "FP8" : "BF16");
     vf::device_guard g(h->device);
     VF_TRY(vf::tensor_prepare(const_cast<vf_hmat*>(h), terms));
     const vf_tensor_set& T = h->tplan->set[terms - 1];

@@ -18,10 +18,16 @@ struct TEpi {
     const float* E;        // mode 1
     const float* rho;      // mode 1
     const float* Bold;     // mode 1: the previous iterate; mode 2: B
-    unsigned char* Xnext;  // mode 1: the next BF16 panel (or NULL); a second panel at + xstride bytes
+    unsigned char* Xnext;  // mode 1: the next BF16 (FP8) panel (or NULL); a second panel at + xstride bytes
     int64_t xstride;
     double* colpart;       // modes 1, 2: per (RHS, tile) sums of squares
     int64_t ntiles;
+    // FP8 (S = 3): the product is sx(column) rs(row) F X; sx and 1 / sx per
+    // RHS column (global index), 1 / rs per tree row.  Xnext is written as
+    // FP8 of sx B'.
+    const float* sx;
+    const float* isx;
+    const float* irs;
     // Ping-pong selection for a sweep captured once in a CUDA graph: when
     // par is not NULL and *par (read when the kernel starts) is 1, the
     // kernels use Xalt (the input panel), Yalt, Boldalt and Xnextalt
@@ -34,7 +40,9 @@ struct TEpi {
 };
 
 // Build one page set of the matrix once (S = 1: BF16 factors; S = 2: each
-// FP32 factor as two BF16 terms hi + lo) and set the kernels' attributes.
+// FP32 factor as two BF16 terms hi + lo; S = 3: FP8 E4M3 factors with
+// power-of-two scales per row and per SVD rank column) and set the
+// kernels' attributes.
 vf_status tensor_prepare(vf_hmat* H, int S);
 int64_t tensor_panel_bytes_x(const vf_hmat* H);
 int64_t tensor_panel_bytes_t(const vf_hmat* H);
@@ -51,6 +59,17 @@ vf_status tensor_to_panel(const vf_hmat* H, const float* X, int64_t ld, const in
 vf_status tensor_multiply(const vf_hmat* H, int S, int np, const unsigned char* Xhi, const unsigned char* Xlo,
                           unsigned char* Thi, unsigned char* Tlo, const TEpi& ep, int* status, cudaStream_t st);
 int tensor_kernels(const vf_hmat* H, int S);
+// FP8 (S = 3) panels: 128 bytes per panel row, K-major
+int64_t tensor_panel_bytes_x8(const vf_hmat* H);
+int64_t tensor_panel_bytes_t8(const vf_hmat* H);
+// per column c < R: sx[c] = the largest power of two with sx max|x| <= 448 headroom, isx = 1 / sx
+vf_status tensor_fp8_colscale(const vf_hmat* H, const float* X, int64_t ld, const int32_t* perm, int R, float headroom,
+                              float* sx, float* isx, cudaStream_t st);
+// FP32 column-major X -> the FP8 panel of columns [p0, p0 + 128), scaled by sx per column
+vf_status tensor_to_panel8(const vf_hmat* H, const float* X, int64_t ld, const int32_t* perm, int R, int p0,
+                           const float* sx, unsigned char* out, cudaStream_t st);
+// 1 / rs per tree row (the FP8 set's row scales; after tensor_prepare(H, 3))
+const float* tensor_fp8_irs(const vf_hmat* H);
 // per-column partial sums a phase-2 epilogue writes (one per row part)
 int64_t tensor_parts(const vf_hmat* H, int S);
 // first part of each segment (nseg + 1 entries, device)
