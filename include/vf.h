@@ -283,9 +283,15 @@ vf_status vf_predictor_predict(const vf_rank_predictor* p, const float* feats, i
 /* ---------------------------------------------------------------- apply
  * Algorithm 5 (Section 4.4): Y = F_hat X for R columns.  X, Y: device FP32,
  * column-major, face order (the tree permutation is applied inside).
- * p selects the factor copy (FP32 master, BF16, or FP8 E4M3 with a scale
- * per block); accumulation is FP32.  Errors: VF_E_INVAL (R < 1, ld < N,
- * precision not built), VF_E_CUDA. */
+ * p selects the factor copy (FP32 master, BF16, or FP8 E4M3); accumulation
+ * is FP32.  Below 16 columns (or as tuned) the CUDA cores stream the FP32 /
+ * BF16 / FP8 copy (FP8: one scale per block).  From 16 columns BF16 and FP8
+ * run on the tensor cores in panels of 128 columns: BF16 as kind::f16 MMAs;
+ * FP8 as kind::f8f6f4 E4M3 MMAs whose right-hand sides are FP8 too, with
+ * power-of-two scales per RHS column, per matrix row and per SVD rank
+ * column (exact, undone in the epilogue; values beyond E4M3's range
+ * saturate).  Errors: VF_E_INVAL (R < 1, ld < N, precision not built),
+ * VF_E_CUDA, VF_E_TIMEOUT, VF_E_OOB. */
 vf_status vf_apply(const vf_hmat* h, vf_precision p, const float* X, int64_t ldx, int32_t R, float* Y,
                    int64_t ldy, vf_stream stream);
 
@@ -301,7 +307,7 @@ vf_status vf_apply_tree(const vf_hmat* h, vf_precision p, const float* Xt, int32
  * interface of this library, not a step of the method.
  *
  * Path: always the CUDA-core multiply over all R columns at once.  It never
- * takes the tensor-core path (BF16 with R >= 16) or a tuned RHS block, so
+ * takes the tensor-core path (BF16 or FP8 with R >= 16) or a tuned RHS block, so
  * where vf_apply_tree would take either, the two calls agree only to the
  * rounding of the precision, not bit for bit; elsewhere they run the same
  * kernels with the same RHS tile and agree exactly.
@@ -351,7 +357,10 @@ vf_status vf_apply_tree_static(const vf_hmat* h, vf_precision p, const float* Xt
  * bounded by max_iter).  With precision BF16/FP8 and refine = 1 the inner
  * sweeps use the low-precision factors and an outer loop corrects with the
  * residual r = E - B + rho .* F B computed from the FP32 factors with FP64
- * accumulation.  clamp = 1 sets negative outputs to 0 (Section 4.2).
+ * accumulation (from 16 columns, where the BF16 / FP8 sweeps run on the
+ * tensor cores: the FP32 factors and B split in BF16 hi + lo terms, FP32
+ * accumulation, about 2^-16 relative).  clamp = 1 sets negative outputs to
+ * 0 (Section 4.2).
  * rho: device FP32 [nf] in face order, or NULL for opts.rho.  E, B: device
  * FP32 column-major, face order.  VF_E_NOCONV: B holds the last iterate. */
 typedef struct {
@@ -452,7 +461,7 @@ vf_status vf_flux_step(const vf_hmat* h, vf_precision p, int32_t R, const float*
 /* ------------------------------------------------------------ autotuning
  * What the multiply of one matrix runs with, per (precision, R): the
  * CUDA-core path's right-hand sides per pass (its RHS tile), whether BF16
- * multiplies of >= 16 columns use the tensor cores, and the RHS block: a
+ * or FP8 multiplies of >= 16 columns use the tensor cores, and the RHS block: a
  * call with more columns runs in column blocks of this width (0: all
  * columns at once).  No counterpart in the paper (its multiply is one
  * library call per block); the choice only changes speed and rounding
@@ -466,7 +475,7 @@ typedef struct {
 
 /* Times the multiply of h on seeded synthetic columns (device memory the
  * call allocates) for every candidate -- rb in {1, 2, 4, 8} (8 alone from
- * 16 columns up), the tensor path (BF16, >= 16 columns), RHS blocks of R
+ * 16 columns up), the tensor path (BF16 or FP8, >= 16 columns), RHS blocks of R
  * and of 64, 128, 256, ... < R
  * -- and records the fastest per right-hand side for (prec, R) in the
  * handle (and for (prec, rhs_block) when it splits); later vf_apply,
@@ -491,14 +500,15 @@ vf_status vf_tune_set(const vf_hmat* h, vf_precision prec, int32_t R, const vf_t
 vf_status vf_hmat_stack(const vf_hmat* const* F, int32_t nmeshes, vf_hmat** out);
 
 /* Bytes of the tensor-core multiply's pages of h (the B operands: factors
- * in BF16, terms = 1, or split in hi and lo, terms = 2), building them if
- * not yet built.  A record's B operand covers runs of 16-column chunks
- * that hold a nonzero of one of its pieces (CSR pieces densified there)
- * and is padded to the MMA shapes (K and the output rows to multiples of
- * 16).  by_kind (5 entries or NULL): the bytes of dense, CSR, U', V' and
- * empty-tile records (headers and B operands); the total adds each page's
- * 16-byte header.  No counterpart in the paper.  Errors: VF_E_INVAL (no
- * BF16 copy), VF_E_NOMEM, VF_E_CUDA. */
+ * in BF16, terms = 1, split in hi and lo, terms = 2, or FP8 E4M3, terms =
+ * 3), building them if not yet built.  A record's B operand covers runs of
+ * K-chunks (16 columns; 32 for FP8, one MMA's K) that hold a nonzero of one
+ * of its pieces (CSR pieces densified there) and is padded to the MMA
+ * shapes (the output rows to multiples of 16).  by_kind (5 entries or
+ * NULL): the bytes of dense, CSR, U', V' and empty-tile records (headers
+ * and B operands); the total adds each page's 16-byte header.  No
+ * counterpart in the paper.  Errors: VF_E_INVAL (no BF16 / FP8 copy),
+ * VF_E_NOMEM, VF_E_CUDA. */
 vf_status vf_hmat_tensor_bytes(const vf_hmat* h, int32_t terms, int64_t* total, int64_t* by_kind);
 
 /* Release what multiplies and solves cached on h: its workspaces (per R

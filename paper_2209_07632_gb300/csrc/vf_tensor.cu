@@ -305,6 +305,7 @@ __global__ void k_tpage_headers(const int32_t* __restrict__ nrec, const uint32_t
 __device__ __forceinline__ float pow2_below(float lim, float v) {  // largest 2^e with v 2^e <= lim (v > 0)
     float s = exp2f(floorf(log2f(lim / v)));
     while (v * s > lim) s *= 0.5f;
+    while (v * (2.f * s) <= lim) s *= 2.f;
     return s;
 }
 

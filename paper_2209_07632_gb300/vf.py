@@ -547,7 +547,7 @@ def vf_hmat_stack(hs) -> HMat:
 
 
 def vf_hmat_tensor_bytes(h: HMat, terms: int = 1) -> dict:
-    """Bytes of the tensor-core pages of h (terms 1: BF16, 2: hi/lo split), in all and by record kind."""
+    """Bytes of the tensor-core pages of h (terms 1: BF16, 2: hi/lo split, 3: FP8), in all and by record kind."""
     tot = ctypes.c_int64()
     kinds = (ctypes.c_int64 * 5)()
     _check(load().vf_hmat_tensor_bytes(h.ptr, terms, ctypes.byref(tot), kinds))
