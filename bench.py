@@ -297,7 +297,17 @@ def run_config4(a, dev, peak, st):
         alg = vf.vf_hmat_bytes(h, "bf16") + n * r * 6
         tm[str(r)] = {"ms": round(ms, 4), "alg_bytes": alg, "hbm_frac": round(alg / (ms / 1e3) / 1e9 / peak, 4)}
     tpages = vf.vf_hmat_tensor_bytes(h, 1)
-    # FP8 (CUDA-core sweeps, per-block scales) with the same refinement
+    # the FP8 tensor multiply (kind::f8f6f4; FP8 panels: 1 byte read per RHS entry, FP32 result)
+    tm8 = {}
+    for r in (128, 256):
+        for _ in range(2):
+            vf.vf_apply_tree(h, Xb[:r], Yb[:r], precision="fp8")
+        torch.cuda.synchronize()
+        ms = events_ms(lambda: vf.vf_apply_tree(h, Xb[:r], Yb[:r], precision="fp8"), 10, st)
+        alg = vf.vf_hmat_bytes(h, "fp8") + n * r * 5
+        tm8[str(r)] = {"ms": round(ms, 4), "alg_bytes": alg, "hbm_frac": round(alg / (ms / 1e3) / 1e9 / peak, 4)}
+    tpages8 = vf.vf_hmat_tensor_bytes(h, 3)
+    # FP8 sweeps on the tensor cores with the same refinement
     B8 = torch.empty_like(E)
     kw8 = dict(rho=C4_RHO, rtol=1e-4, precision="fp8", refine=True)
     s8 = vf.vf_solve(h, E, B8, **kw8)
@@ -308,6 +318,8 @@ def run_config4(a, dev, peak, st):
     vf.vf_apply(h, E, Y32, precision="fp32")
     Ybf = torch.empty_like(E)
     vf.vf_apply(h, E, Ybf, precision="bf16")
+    Yf8 = torch.empty_like(E)
+    vf.vf_apply(h, E, Yf8, precision="fp8")
     torch.cuda.synchronize()
     res = {"workload": c4_workload(n), "facets": n, "rhs": R, "tol": 1e-3, "rho": C4_RHO,
            "suns": "lunar-day azimuth sweep at 1.5 deg elevation",
@@ -326,13 +338,16 @@ def run_config4(a, dev, peak, st):
            "tensor_multiply": tm, "hbm_frac": tm["128"]["hbm_frac"], "tensor_page_bytes": tpages,
            "fp8_solve": {"value": round(R / (ms8 / 1e3), 1), "unit": "RHS/s", "ms_per_solve": round(ms8, 3),
                          "sweeps": s8["sweeps"], "refinements": s8["refinements"], "converged": s8["converged"],
-                         "precision": "fp8 e4m3 factors with per-block scales on CUDA cores, split-free FP64 "
-                                      "refinement"}}
+                         "precision": "fp8 e4m3 factors and RHS on tcgen05 tensor cores (kind::f8f6f4), "
+                                      "power-of-two scales per RHS column, row and SVD rank column, FP32 "
+                                      "accumulation; split-BF16 residual refinement with FP64 update, rtol 1e-4",
+                         "tensor_multiply": tm8, "hbm_frac": tm8["128"]["hbm_frac"],
+                         "tensor_page_bytes": tpages8}}
     host = {"v": v, "f": f, "dirs": dirs, "n": n,
             "E": E.double().cpu().numpy().T, "B": B.double().cpu().numpy().T,
             "B8": B8.double().cpu().numpy().T, "Y32": Y32.double().cpu().numpy().T,
-            "Ybf": Ybf.double().cpu().numpy().T}
-    del prob, h, E, B, B8, Xb, Yb, X1, Y1, Y32, Ybf, perm
+            "Ybf": Ybf.double().cpu().numpy().T, "Yf8": Yf8.double().cpu().numpy().T}
+    del prob, h, E, B, B8, Xb, Yb, X1, Y1, Y32, Ybf, Yf8, perm
     return res, host
 
 
@@ -365,6 +380,7 @@ def config4_oracle_check(host, nrows: int):
     out["insolation_max_abs_err_rel_to_max"] = float(np.abs(E[rows] - Eo).max() / max(Eo.max(), 1e-300))
     out["apply_fp32_rel_err"], live = colerr(host["Y32"][rows], FE)
     out["apply_bf16_rel_err"], _ = colerr(host["Ybf"][rows], FE)
+    out["apply_fp8_rel_err"], _ = colerr(host["Yf8"][rows], FE)
     out["columns"] = live
     for key, name in (("B", "solve_bf16_refined_rel_err"), ("B8", "solve_fp8_refined_rel_err")):
         Bg = host[key]
@@ -617,8 +633,33 @@ def main():
                                        "page_bytes": tpages,
                                        "page_frac": round((tpages["total"] + n * 128 * 6) / (tms / 1000.0) / 1e9 / peak,
                                                           4)}}
-        batched_host = {"B": Bb.double().cpu().numpy().T, "dirs": lunar_day_dirs(Rb), "rho": rho}
-        del Eb, Bb, Bref, Xb, Yb
+        # the same solve with FP8 sweeps on the tensor cores (kind::f8f6f4)
+        # and the same split-BF16 refinement; the FP8 multiply of 128 RHS
+        B8 = torch.empty_like(Eb)
+        kw8 = dict(rho=rho, rtol=1e-4, precision="fp8", refine=True)
+        for _ in range(2):
+            s8 = vf.vf_solve(prob.hmat, Eb, B8, **kw8)
+        torch.cuda.synchronize()
+        ms8 = events_ms(lambda: vf.vf_solve(prob.hmat, Eb, B8, **kw8), 3, st)
+        rel8 = float(((B8 - Bref).norm(dim=1)[live] / Bref.norm(dim=1)[live]).max().item())
+        for _ in range(3):
+            vf.vf_apply_tree(prob.hmat, Xb, Yb, precision="fp8")
+        torch.cuda.synchronize()
+        tms8 = events_ms(lambda: vf.vf_apply_tree(prob.hmat, Xb, Yb, precision="fp8"), 20, st)
+        fp8_bytes = vf.vf_hmat_bytes(prob.hmat, "fp8") + n * 128 * (1 + 4)
+        tpages8 = vf.vf_hmat_tensor_bytes(prob.hmat, 3)
+        batched["fp8"] = {"value": round(Rb / (ms8 / 1000.0), 1), "unit": "RHS/s", "ms_per_solve": round(ms8, 3),
+                          "precision": "fp8 e4m3 factors and RHS on tcgen05 tensor cores (kind::f8f6f4), "
+                                       "power-of-two scales per RHS column, row and SVD rank column; "
+                                       "split-BF16 residual refinement with FP64 update",
+                          "rtol": 1e-4, "sweeps": s8["sweeps"], "refinements": s8["refinements"],
+                          "converged": s8["converged"], "max_rel_diff_vs_fp32_solve": rel8,
+                          "tensor_multiply": {"ms": round(tms8, 4), "rhs": 128, "alg_bytes": fp8_bytes,
+                                              "hbm_frac": round(fp8_bytes / (tms8 / 1000.0) / 1e9 / peak, 4),
+                                              "page_bytes": tpages8}}
+        batched_host = {"B": Bb.double().cpu().numpy().T, "B8": B8.double().cpu().numpy().T,
+                        "dirs": lunar_day_dirs(Rb), "rho": rho}
+        del Eb, Bb, Bref, Xb, Yb, B8
         # the autotuner's candidate workspaces and the tensor pages of this
         # section are released before the many-mesh section needs the memory
         vf.vf_hmat_trim(prob.hmat)
@@ -776,6 +817,7 @@ def main():
         cpu = co.measure(sweeps, seconds=10.0)
         if batched_host is not None:
             batched["oracle_check"] = co.batched_check(v, f, batched_host)
+            batched["fp8"]["oracle_check"] = co.batched_check(v, f, dict(batched_host, B=batched_host["B8"]))
         if c4_host is not None:
             config4["oracle_check"] = config4_oracle_check(c4_host, a.config4_rows)
             chk = config4["oracle_check"]
