@@ -313,14 +313,17 @@ def run_config4(a, dev, peak, st):
     s8 = vf.vf_solve(h, E, B8, **kw8)
     torch.cuda.synchronize()
     ms8 = events_ms(lambda: vf.vf_solve(h, E, B8, **kw8), 2, st)
-    # FP32 compressed multiply of all 256 suns (for the apply check)
-    Y32 = torch.empty_like(E)
-    vf.vf_apply(h, E, Y32, precision="fp32")
-    Ybf = torch.empty_like(E)
-    vf.vf_apply(h, E, Ybf, precision="bf16")
-    Yf8 = torch.empty_like(E)
-    vf.vf_apply(h, E, Yf8, precision="fp8")
+    # the three multiplies of all 256 suns (for the apply check), each after
+    # the handle's cached pages and workspaces are released (the 256-column
+    # FP32 multiply alone holds ~20 GB of T scratch at this size)
+    Y32, Ybf, Yf8 = torch.empty_like(E), torch.empty_like(E), torch.empty_like(E)
+    for prec, Y in (("fp32", Y32), ("bf16", Ybf), ("fp8", Yf8)):
+        torch.cuda.synchronize()
+        vf.vf_hmat_trim(h)
+        torch.cuda.empty_cache()
+        vf.vf_apply(h, E, Y, precision=prec)
     torch.cuda.synchronize()
+    vf.vf_hmat_trim(h)
     res = {"workload": c4_workload(n), "facets": n, "rhs": R, "tol": 1e-3, "rho": C4_RHO,
            "suns": "lunar-day azimuth sweep at 1.5 deg elevation",
            "assembly_s": round(t_asm, 1),
