@@ -60,7 +60,11 @@ def parse():
     p.add_argument("--multimesh-rhs", type=int, default=256, help="RHS per mesh in the multi-mesh section")
     p.add_argument("--no-tol-sweep", action="store_true", help="skip the terrain at tol 1e-2 and 1e-4")
     p.add_argument("--profile-batched", action="store_true",
-                   help="only run --steps refined BF16 solves of --batch-rhs suns (for a profiler's launch list)")
+                   help="only run --steps refined solves of --batch-rhs suns, BF16 (or --precision fp8) "
+                        "sweeps on the tensor cores (for a profiler's launch list)")
+    p.add_argument("--profile-apply", action="store_true",
+                   help="only run --warmup + --steps tensor-core multiplies of --batch-rhs seeded columns in "
+                        "--precision (bf16 or fp8; outside any CUDA graph, for a profiler)")
     p.add_argument("--no-config4", action="store_true", help="skip the 522,242-facet precision section")
     p.add_argument("--config4-only", action="store_true",
                    help="run only the 522,242-facet precision section (with its oracle check)")
@@ -451,14 +455,31 @@ def main():
         print(json.dumps({"config4": c4}))
         return
 
-    if a.profile_batched:
+    if a.profile_apply:
+        prec = a.precision if a.precision != "fp32" else "bf16"
         v, f, _ = workload_inputs(1, a.dem_size)
-        prob = vf.build_problem(v, f, kind="quad", leaf_size=64, tol=a.tol, device=dev, precisions=("fp32", "bf16"))
+        prob = vf.build_problem(v, f, kind="quad", leaf_size=64, tol=a.tol, device=dev,
+                                precisions=("fp32", "bf16", "fp8"))
+        gen = torch.Generator(device="cpu").manual_seed(5)
+        X = torch.rand((a.batch_rhs, prob.mesh.n), generator=gen).cuda()
+        Y = torch.empty_like(X)
+        for _ in range(a.warmup + a.steps):
+            vf.vf_apply_tree(prob.hmat, X, Y, precision=prec)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_apply": True, "precision": prec, "facets": prob.mesh.n, "rhs": a.batch_rhs,
+                          "multiplies": a.warmup + a.steps}))
+        return
+
+    if a.profile_batched:
+        prec = a.precision if a.precision != "fp32" else "bf16"  # the sweeps' precision (tensor cores)
+        v, f, _ = workload_inputs(1, a.dem_size)
+        prob = vf.build_problem(v, f, kind="quad", leaf_size=64, tol=a.tol, device=dev,
+                                precisions=("fp32", "bf16", "fp8"))
         Eb = torch.empty((a.batch_rhs, prob.mesh.n), device="cuda", dtype=torch.float32)
         vf.vf_mesh_insolation(prob.mesh, lunar_day_dirs(a.batch_rhs), 1365.0, Eb)
         Bb = torch.empty_like(Eb)
         for _ in range(a.warmup + a.steps):
-            vf.vf_solve(prob.hmat, Eb, Bb, rho=0.12, rtol=1e-4, precision="bf16", refine=True)
+            vf.vf_solve(prob.hmat, Eb, Bb, rho=0.12, rtol=1e-4, precision=prec, refine=True)
         torch.cuda.synchronize()
         print(json.dumps({"profile_batched": True, "facets": prob.mesh.n, "rhs": a.batch_rhs, "solves": a.steps}))
         return
