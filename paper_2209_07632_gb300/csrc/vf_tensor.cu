@@ -1384,12 +1384,19 @@ __global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase1(const unsig
                 for (int b16 = col & ~15; b16 < col + nc; b16 += 16) {
                     float v[16];
                     tm_ld16(S.tmem_base + lane_base + d * REGW + q * kRegion + b16, v);
+                    // FP8: the block's 16 T-row scales, one load per lane, shared by shuffles
+                    float ctl = 0.f;
+                    if (NS == 3) {
+                        const int jj = lane & 15;
+                        if (b16 + jj >= col && b16 + jj < col + nc) ctl = pn.ct8[offT + b16 + jj - col];
+                    }
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         if (b16 + j < col || b16 + j >= col + nc) continue;
                         const int64_t row = offT + b16 + j - col;
                         if (NS == 3) {
-                            pn.T[0][q * pn.tstride + panel_off8(row, m)] = to_e4m3(v[j] * pn.ct8[row]);
+                            const float c = __shfl_sync(0xffffffffu, ctl, j);
+                            pn.T[0][q * pn.tstride + panel_off8(row, m)] = to_e4m3(v[j] * c);
                             continue;
                         }
                         const int64_t o = q * pn.tstride + panel_off(row, m);
@@ -1473,13 +1480,18 @@ __global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase2(const unsig
                 for (int c0 = 0; c0 < tc; c0 += 16) {
                     float v[16];
                     tm_ld16(S.tmem_base + lane_base + d * REGW + q * kRegion + c0, v);
+                    if (NS == 3) {
+                        // the 16 rows' 1 / rs: one load per lane, shared by shuffles (whole warp)
+                        const float irl = c0 + (lane & 15) < tc ? ep.irs[tf + c0 + (lane & 15)] : 0.f;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) v[j] *= isx * __shfl_sync(0xffffffffu, irl, j);
+                    }
                     if (!live) continue;
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         if (c0 + j >= tc) break;
                         const int64_t p = tf + c0 + j;
                         const int64_t o = (int64_t)col * ep.n + p;
-                        if (NS == 3) v[j] *= isx * ep.irs[p];
                         if (ep.mode == 0) {
                             ep.Y[o] = v[j];
                         } else if (ep.mode == 2) {
