@@ -302,10 +302,17 @@ __global__ void k_tpage_headers(const int32_t* __restrict__ nrec, const uint32_t
 }
 
 // ---- FP8 scales (powers of two, so scaling is exact)
-__device__ __forceinline__ float pow2_below(float lim, float v) {  // largest 2^e with v 2^e <= lim (v > 0)
-    float s = exp2f(floorf(log2f(lim / v)));
-    while (v * s > lim) s *= 0.5f;
-    while (v * (2.f * s) <= lim) s *= 2.f;
+// The largest 2^e (|e| <= 126) with v 2^e <= lim, for v > 0 (1 for v not
+// finite).  The first guess from log2 is off by at most one either way;
+// the two corrections are bounded loops.
+__device__ __forceinline__ float pow2_below(float lim, float v) {
+    if (!(v > 0.f) || !(v <= 3.0e38f)) return 1.f;
+    const float r = lim / v;
+    int e = r <= 3.0e38f ? (int)floorf(log2f(r)) : 126;
+    e = max(-126, min(e, 126));
+    float s = ldexpf(1.f, e);
+    for (int i = 0; i < 4 && v * s > lim && s > 1e-37f; ++i) s *= 0.5f;
+    for (int i = 0; i < 4 && v * (2.f * s) <= lim && s < 1e37f; ++i) s *= 2.f;
     return s;
 }
 
