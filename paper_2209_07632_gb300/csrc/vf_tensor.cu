@@ -1,5 +1,5 @@
 // The multiply on the 5th-generation tensor cores for panels of 128
-// right-hand sides (BF16 factors and BF16 right-hand sides, FP32
+// right-hand sides (BF16 or FP8 E4M3 factors and right-hand sides, FP32
 // accumulation in tensor memory): Algorithm 5 with the block products as
 // tcgen05 MMAs.
 //
@@ -18,12 +18,19 @@
 // of 8 = 2 KB), so the A operand of any block is one contiguous byte range:
 // its column range (or T slots) rounded to 8 rows, fetched by one bulk copy.
 // B operands (the matrix) are packed once into "tensor pages" in the same
-// layout.
+// layout.  FP8 (kind::f8f6f4) uses K-major operands instead: core matrices
+// of 8 MN rows x 16 K bytes, element (mn, k) at (k / 16) * LBO + (mn / 8) *
+// 128 + (mn % 8) * 16 + k % 16, LBO = (MN / 8) * 128 along K, SBO = 128 along
+// MN, and an MMA step of K = 32; FP8 panels are 128 bytes per row, records
+// come in 32-column chunks and every value carries a power-of-two scale
+// (per RHS column, per output row, per SVD rank column) that the epilogues
+// undo.
 //
-// Each kernel is persistent (two CTAs per SM) with warp roles: warp 0 lane 0
-// copies pages and A operands (cp.async.bulk, mbarrier completion), warp 1
-// lane 0 issues the MMAs and commits them to mbarriers, warps 2-5 read the
-// finished accumulators (tcgen05.ld) and run the epilogue.  Two accumulator
+// Each kernel is persistent (four CTAs per SM, three for the split set)
+// with warp roles: warp 0 lane 0 copies pages and A operands
+// (cp.async.bulk, mbarrier completion), warp 1 lane 0 issues the MMAs and
+// commits them to mbarriers, warps 2-5 read the finished accumulators
+// (tcgen05.ld) and run the epilogue.  Two accumulator
 // regions alternate between tiles (units), so the epilogue of one overlaps
 // the MMAs of the next.  Every wait is bounded; a role that gives up records
 // VF_E_TIMEOUT and stops issuing, and the kernel waits (bounded) for work in
