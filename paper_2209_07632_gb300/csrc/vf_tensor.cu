@@ -1038,6 +1038,27 @@ __device__ __forceinline__ int64_t panel_off8(int64_t row, int m) {
 __device__ __forceinline__ unsigned char to_e4m3(float v) {
     return (unsigned char)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
 }
+// FP8 panel rows base + j, j in [jlo, jhi), of RHS m: e[j].  A K-major FP8
+// panel keeps 16 consecutive rows of one RHS in 16 bytes, so every 4-row
+// word wholly inside the range is one 32-bit store; the rest are bytes
+// (rows outside the range belong to other blocks or tiles and stay as they are).
+__device__ __forceinline__ void st_fp8_rows(unsigned char* P, int64_t base, int m, int jlo, int jhi,
+                                            const unsigned char (&e)[16]) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        if (j < jlo || j >= jhi) continue;
+        const int64_t row = base + j;
+        const int j0 = j - (int)(row & 3);  // the first j of row's 4-row word
+        if (j0 >= jlo && j0 + 4 <= jhi) {
+            if (j == j0)
+                *reinterpret_cast<uint32_t*>(P + panel_off8(row, m)) =
+                    (uint32_t)e[j] | ((uint32_t)e[j + 1 < 16 ? j + 1 : 15] << 8) |
+                    ((uint32_t)e[j + 2 < 16 ? j + 2 : 15] << 16) | ((uint32_t)e[j + 3 < 16 ? j + 3 : 15] << 24);
+            continue;
+        }
+        P[panel_off8(row, m)] = e[j];
+    }
+}
 
 struct TSmem {
     uint64_t page_full[kMaxPStages], page_empty[kMaxPStages], a_full[kMaxSlots], a_empty[kMaxSlots], d_full[2],
@@ -1403,16 +1424,20 @@ __global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase1(const unsig
                     if (NS == 3) {
                         const int jj = lane & 15;
                         if (b16 + jj >= col && b16 + jj < col + nc) ctl = pn.ct8[offT + b16 + jj - col];
+                        unsigned char e[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) e[j] = to_e4m3(v[j] * __shfl_sync(0xffffffffu, ctl, j));
+                        // column b16 + j holds T row base + j; 4-row words wholly
+                        // inside this unit's rows are one 32-bit store, the rest bytes
+                        const int jlo = max(0, col - b16), jhi = min(16, col + nc - b16);
+                        const int64_t base = (int64_t)offT + b16 - col;
+                        st_fp8_rows(pn.T[0] + q * pn.tstride, base, m, jlo, jhi, e);
+                        continue;
                     }
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         if (b16 + j < col || b16 + j >= col + nc) continue;
                         const int64_t row = offT + b16 + j - col;
-                        if (NS == 3) {
-                            const float c = __shfl_sync(0xffffffffu, ctl, j);
-                            pn.T[0][q * pn.tstride + panel_off8(row, m)] = to_e4m3(v[j] * c);
-                            continue;
-                        }
                         const int64_t o = q * pn.tstride + panel_off(row, m);
                         const __nv_bfloat16 hi = __float2bfloat16_rn(v[j]);
                         *reinterpret_cast<__nv_bfloat16*>(pn.T[0] + o) = hi;
@@ -1501,6 +1526,7 @@ __global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase2(const unsig
                         for (int j = 0; j < 16; ++j) v[j] *= isx * __shfl_sync(0xffffffffu, irl, j);
                     }
                     if (!live) continue;
+                    unsigned char e8[16] = {};  // FP8 Jacobi: the next panel's bytes of these rows
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         if (c0 + j >= tc) break;
@@ -1518,11 +1544,13 @@ __global__ void __launch_bounds__(192, TCfg<NS, NP>::CTAS) k_tphase2(const unsig
                             const float dd = bn - ep.Bold[o];
                             ss += (double)dd * dd;
                             ep.Y[o] = bn;
-                            if (xnext && NS == 3) xnext[panel_off8(p, m)] = to_e4m3(bn * sxn);
+                            if (NS == 3) e8[j] = to_e4m3(bn * sxn);
                             else if (xnext)
                                 *reinterpret_cast<__nv_bfloat16*>(xnext + panel_off(p, m)) = __float2bfloat16_rn(bn);
                         }
                     }
+                    // the tile's rows only (a 4-row word across a tile boundary is written bytewise)
+                    if (NS == 3 && ep.mode == 1 && xnext) st_fp8_rows(xnext, (int64_t)tf + c0, m, 0, min(16, tc - c0), e8);
                 }
                 if (ep.mode != 0 && live) ep.colpart[(int64_t)col * ep.ntiles + tile] = ss;
             }
